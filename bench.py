@@ -1,0 +1,366 @@
+#!/usr/bin/env python3
+"""Benchmark of the gg -> (n-2) gluon event generator on GB300.
+
+A step = one tess_generate call over the whole workload: counter RNG ->
+Rambo -> luminosity, alpha_s, cuts, observables -> polarisations ->
+Berends-Giele amplitude -> weight -> cross-section/histogram accumulation,
+writing per-event weight, |A|^2 estimator and pass flag.
+
+Default workload "gg4g": gg -> 4 gluons (6-point), 2^24 events per GPU,
+sampled helicity and colour ordering, FP32 currents (FP64 plain form
+measured alongside).  Multi-GPU: each rank generates its own disjoint event
+range (weak scaling); the only exchange is the sum of the accumulators.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (n, events per GPU, pt_min, helicity mode, precision, hist (obs, bins, lo, hi))
+    "gg4g": dict(n=6, n_events=1 << 24, pt_min=20.0, hel="sample", precision="fp32", hist=None),
+    "gg2g": dict(n=4, n_events=1 << 20, pt_min=20.0, hel="sum", precision="fp64", hist=(0, 50, 20.0, 1020.0)),
+    "gg8g": dict(n=10, n_events=1 << 26, pt_min=30.0, hel="sample", precision="fp32", hist=(1, 40, 200.0, 3000.0)),
+}
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5, from unit counts and clock
+FP64_PEAK_TFLOPS = 1.25                                                     # GB300 FP64 (vendor figure)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tess", choices=["tess", "reference"])
+    ap.add_argument("--workload", default="gg4g", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison measurement")
+    ap.add_argument("--no-per-n", action="store_true", help="skip the per-multiplicity sweep")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in self.rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ tess arm
+def make_proc(tess, wl, precision=None):
+    prec = precision or wl["precision"]
+    kw = dict(precision=tess.TESS_FP32_CURRENTS if prec == "fp32" else tess.TESS_FP64,
+              helicity_mode=tess.TESS_HEL_SUM if wl["hel"] == "sum" else tess.TESS_HEL_SAMPLE, pt_min=wl["pt_min"])
+    if wl["hist"]:
+        obs, nb, lo, hi = wl["hist"]
+        kw.update(hist_observable=obs, hist_bins=nb, hist_lo=lo, hist_hi=hi)
+    return tess.process(wl["n"], **kw)
+
+
+def time_steps(torch, run, seed, first, steps, warmup, flush):
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        run.reset()
+        run.generate(seed, first)
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(steps):
+        flush.fill_(1.0)  # evict L2 (buffer larger than the 129 MB L2); not timed
+        run.reset()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        run.generate(seed, first)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def run_tess(args):
+    import torch
+    import paper_1002_3446_gb300 as tess
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wl = WORKLOADS[args.workload]
+    n, N = wl["n"], wl["n_events"]
+    ctx = tess.tess_init(local)
+    proc = make_proc(tess, wl)
+    run = tess.Run(ctx, proc, N, per_event=("weight", "me2", "pass"))
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    first = rank * N
+    seed = 1
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    try:
+        gpu_id = torch.cuda.get_device_properties(local).uuid
+        gpu_id = "GPU-" + str(gpu_id) if not str(gpu_id).startswith("GPU-") else str(gpu_id)
+    except Exception:
+        gpu_id = str(local)
+
+    # ---- headline: device time of K steps
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_id) as clk:
+        step_ms = time_steps(torch, run, seed, first, args.steps, args.warmup, flush)
+    torch.cuda.synchronize()
+    barrier()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * N / (ms_per_step * 1e-3)
+    sigma = run.result()
+    acc = run.acc.clone()
+    if dist:
+        dist.all_reduce(acc, op=dist.ReduceOp.SUM)
+
+    # ---- end to end: public API with host buffers (D2H of weights, flags, sigma)
+    hw = torch.empty(N, dtype=torch.float64).pin_memory()
+    hp = torch.empty(N, dtype=torch.uint8).pin_memory()
+    for _ in range(2):
+        run.reset()
+        run.generate(seed, first)
+        tess.tess_weights(ctx, run.outputs, N, hw, hp)
+        run.result()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run.reset()
+        run.generate(seed, first)
+        tess.tess_weights(ctx, run.outputs, N, hw, hp)
+        run.result()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    barrier()
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # ---- FP64 plain form of the same workload, and the per-n sweep
+    extra = {}
+    if not args.no_fp64 and wl["precision"] == "fp32" and rank == 0:
+        p64 = make_proc(tess, wl, "fp64")
+        n64 = N >> 3
+        r64 = tess.Run(ctx, p64, n64, per_event=("weight", "me2", "pass"))
+        ms = time_steps(torch, r64, seed, first, max(1, args.steps // 2), 1, flush)
+        extra["fp64"] = {"value": n64 / (statistics.mean(ms) * 1e-3), "events": n64,
+                         "ms_per_step": statistics.mean(ms),
+                         "achieved_tflops": tess.bg_flops(n) * n64 / (statistics.mean(ms) * 1e-3) / 1e12,
+                         "peak_tflops": FP64_PEAK_TFLOPS}
+        del r64
+    if not args.no_per_n and rank == 0:
+        sweep = {}
+        for nn in range(4, 13):
+            row = {}
+            for prec in ("fp32", "fp64"):
+                w2 = dict(wl, n=nn, pt_min=30.0 if nn >= 10 else 20.0, hel="sample", hist=None)
+                pp = make_proc(tess, w2, prec)
+                ne = (1 << 20) if prec == "fp32" else (1 << 16)
+                rr = tess.Run(ctx, pp, ne, per_event=("weight",))
+                ms = time_steps(torch, rr, seed, 0, 2, 1, flush)
+                ev = ne / (min(ms) * 1e-3)
+                row[prec] = {"events_per_s": ev, "tflops": tess.bg_flops(nn) * ev / 1e12}
+                del rr
+            sweep[str(nn)] = row
+        extra["per_n"] = sweep
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, budget_s=12.0)
+
+    if rank == 0:
+        achieved = tess.bg_flops(n) * N / (ms_per_step * 1e-3) / 1e12
+        traffic = read_traffic(args.workload)
+        line = {
+            "metric": f"events/s (gg->{n - 2}g, {n}-point, FP32 currents)",
+            "value": value,
+            "unit": "events/s",
+            "n_gpus": ws,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_per_step,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32 currents, f64 kinematics and accumulation",
+            "data": "synthetic (counter-based Philox draws, toy gluon PDF)",
+            "config": {"workload": f"{args.workload}: gg->{n - 2} gluons, {N} events per GPU, seed 1, sqrt(S)=14 TeV, "
+                                   f"pT>{wl['pt_min']:g} |eta|<2.5 dR>0.4, helicity+ordering sampled",
+                       "events_per_gpu": N, "n_gluons": n, "l2": "flushed between timed steps (256 MB write)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts and clock)",
+                         "flops_per_event": tess.bg_flops(n),
+                         "timed": "tess_generate (fused event kernel + 1-block finalize), CUDA events"},
+            "e2e": {"value": ws * N / e2e_s, "unit": "events/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": N * 9 + 64},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk.summary(),
+            "sigma_pb": float((acc[0] + acc[4]).item() / (ws * N)),
+            "cpu_baseline": cpu,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    tess.tess_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+
+
+def read_traffic(workload):
+    """DRAM bytes per launch of the event kernel from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
+    try:
+        with open(path) as f:
+            return json.load(f).get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------ oracle (CPU) arm
+def cpu_baseline(wl, budget_s=12.0, events=None):
+    import oracle
+    threads = os.cpu_count() or 1
+    prec_hel = 0 if wl["hel"] == "sum" else 1
+    kw = dict(hel_mode=prec_hel, pt_min=wl["pt_min"])
+    if wl["hist"]:
+        obs, nb, lo, hi = wl["hist"]
+        kw.update(hist_obs=obs, hist_bins=nb, hist_lo=lo, hist_hi=hi)
+    op = oracle.process(wl["n"], **kw)
+    if events is None:
+        probe = 1 << 12
+        t0 = time.perf_counter()
+        oracle.generate(op, 1, 0, probe, threads=threads, per_event=False, hist=False)
+        rate = probe / max(time.perf_counter() - t0, 1e-6)
+        events = int(min(wl["n_events"], max(probe, rate * budget_s)))
+    t0 = time.perf_counter()
+    oracle.generate(op, 1, 0, events, threads=threads, per_event=True)
+    dt = time.perf_counter() - t0
+    return {"value": events / dt, "unit": "events/s", "cores": threads, "kind": "oracle",
+            "sample": f"events 0..{events - 1} of seed 1 of the same workload ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    n = wl["n"]
+    for _ in range(args.warmup):
+        cpu_baseline(wl, events=1 << 12)
+    vals = []
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(wl, budget_s=8.0))
+    v = statistics.mean(x["value"] for x in vals)
+    line = {
+        "impl": "reference",
+        "metric": f"events/s (gg->{n - 2}g, {n}-point, FP32 currents)",
+        "value": v,
+        "unit": "events/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": statistics.mean(1e3 * int(x["sample"].split("..")[1].split()[0]) / x["value"] for x in vals),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (counter-based Philox draws, toy gluon PDF)",
+        "config": {"workload": args.workload, "events_per_gpu": wl["n_events"], "n_gluons": n},
+        "cpu_baseline": {"value": v, "unit": "events/s", "cores": vals[0]["cores"], "kind": "oracle",
+                         "sample": vals[0]["sample"]},
+        "e2e": {"value": v, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_tess(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * tess.h -- C ABI of the GB300 (sm_103a) leading-order, leading-colour
+ * multi-gluon event generator ("TESS": Giele, Stavenga, Winter,
+ * "Thread-Scalable Evaluation of Multi-Jet Observables", arXiv:1002.3446).
+ *
+ * Every step of an event runs in this library's CUDA kernels: counter-based
+ * random numbers -> Rambo phase space -> parton luminosity, alpha_s, jet cuts
+ * and observables -> helicity polarisation vectors -> Berends-Giele
+ * colour-ordered amplitude -> event weight -> cross-section and histogram
+ * accumulation (Sec. 3 of the paper, Fig. 1 stages).
+ *
+ * Conventions for every entry point
+ *   - Return value: TESS_OK (0) on success, a negative TESS_E_* code on
+ *     failure; tess_last_error() then returns a message (thread-local).
+ *   - Memory: the library allocates no device memory in tess_generate,
+ *     tess_me2 or tess_generate_batched.  The caller owns every buffer; device
+ *     pointers are plain CUDA device addresses (e.g. from cudaMalloc or a
+ *     torch tensor) on the context's device.  Host pointers are marked "host".
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  Generating calls are asynchronous on that stream;
+ *     calls that return host data synchronise it.
+ *   - Inputs are never retained after a call returns.
+ *   - n is the TOTAL number of gluons (the paper's n): gg -> (n-2) g.
+ */
+#ifndef TESS_H
+#define TESS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TESS_OK 0
+#define TESS_E_INVALID (-1)     /* bad argument (size, pointer, value)          */
+#define TESS_E_UNSUPPORTED (-2) /* n or mode combination not built              */
+#define TESS_E_CUDA (-3)        /* a CUDA runtime call or launch failed         */
+#define TESS_E_WORKSPACE (-4)   /* workspace missing or too small               */
+#define TESS_E_NUMERICAL (-5)   /* non-finite weights were produced             */
+
+#define TESS_MIN_N 4
+#define TESS_MAX_N 12
+#define TESS_MAX_BINS 1024
+#define TESS_ACC_LEN 8
+
+/* precision */
+#define TESS_FP64 0          /* every step in FP64                                 */
+#define TESS_FP32_CURRENTS 1 /* Berends-Giele currents and vertex contractions in
+                                FP32 on momenta in units of sqrt(s_hat); momenta,
+                                polarisation vectors and accumulation in FP64     */
+/* helicity_mode */
+#define TESS_HEL_SUM 0    /* exact sum over 2^n helicities and (n-1)! orderings (n <= 5) */
+#define TESS_HEL_SAMPLE 1 /* one helicity configuration and colour ordering per event,
+                             sampled uniformly; estimator 2^n (n-1)! |A|^2          */
+/* hist_observable */
+#define TESS_OBS_PTLEAD 0
+#define TESS_OBS_HT 1
+#define TESS_OBS_RMIN 2
+
+/* Process and run parameters (Sec. 4 workload: sqrt(S) = 14 TeV, jet cuts
+ * pT > pt_min, |eta| < eta_max, Delta R > dr_min).  Units: GeV. */
+typedef struct tess_process {
+  int32_t n_gluons;        /* total gluons, TESS_MIN_N..TESS_MAX_N            */
+  int32_t precision;       /* TESS_FP64 or TESS_FP32_CURRENTS                 */
+  int32_t helicity_mode;   /* TESS_HEL_SUM or TESS_HEL_SAMPLE                 */
+  int32_t hist_observable; /* TESS_OBS_*                                      */
+  int32_t hist_bins;       /* 0 = no histogram, else 1..TESS_MAX_BINS         */
+  int32_t nf;              /* flavours in the one-loop running of alpha_s     */
+  double sqrt_s;           /* hadronic centre-of-mass energy (> 0)            */
+  double pt_min;           /* > 0                                             */
+  double eta_max;          /* > 0                                             */
+  double dr_min;           /* >= 0                                            */
+  double alphas_mz;        /* alpha_s(M_Z) (> 0)                              */
+  double mz;               /* M_Z (> 0)                                       */
+  double mu_r_factor;      /* mu_R = mu_r_factor * H_T (> 0)                  */
+  double hist_lo, hist_hi; /* histogram range [lo, hi), uniform bins          */
+} tess_process;
+
+/* Per-call device outputs (caller-owned; NULL = not requested, except acc).
+ * Per-event arrays have n_events entries, indexed by event - first_event.
+ *   weight  event weight in pb (0 for events failing the cuts)
+ *   me2     helicity/colour estimator E of sum |A|^2 in GeV^(8-2n) (before
+ *           couplings, luminosity and phase space), computed for every event
+ *   pass    1 if the event passes the cuts (events are flagged, not dropped)
+ *   ht, ptlead, rmin   observables (H_T, leading-jet pT, min Delta R)
+ * acc  [TESS_ACC_LEN] doubles, ACCUMULATED into (zero it before the first
+ *      call): {sum w, sum w^2, n_pass, n_generated, compensation of sum w,
+ *      compensation of sum w^2, n_nonfinite, reserved}.  Repeated calls over
+ *      disjoint event ranges give the run total (checkpoint = copy of acc).
+ * hist [4 * (hist_bins + 2)] doubles, accumulated into: sum w per bin, then
+ *      sum w^2 per bin, then their two compensation terms.  Bin 0 is the
+ *      underflow, 1..hist_bins the uniform bins, hist_bins+1 the overflow.
+ *      Only events that pass the cuts are filled.                         */
+typedef struct tess_outputs {
+  double *weight;
+  double *me2;
+  uint8_t *pass;
+  double *ht;
+  double *ptlead;
+  double *rmin;
+  double *acc;
+  double *hist;
+} tess_outputs;
+
+typedef struct tess_ctx tess_ctx;
+
+/* Library version string, e.g. "tess-gb300 0.1". */
+const char *tess_version(void);
+
+/* Thread-local message for the last failing call on this thread ("" if none). */
+const char *tess_last_error(void);
+
+/* Create a context on CUDA device `device` (reads its properties; allocates
+ * no device memory).  *ctx receives the handle; free it with tess_destroy. */
+int tess_init(int device, tess_ctx **ctx);
+void tess_destroy(tess_ctx *ctx);
+
+/* Bytes of device workspace tess_generate needs for this process and event
+ * count (per-block partial sums of the accumulation).  0 is never returned
+ * for a valid process. */
+int tess_workspace_size(const tess_ctx *ctx, const tess_process *proc, uint64_t n_events, size_t *bytes);
+
+/* Generate events [first_event, first_event + n_events) of the counter-based
+ * stream `seed` (Sec. 3 stages: phase space, phase-space weight, matrix-
+ * element weight, epilogue; cross-section formula at the end of Sec. 3).
+ * Writes the requested per-event outputs and accumulates acc/hist.
+ * workspace: device buffer of at least tess_workspace_size() bytes, 256-byte
+ * aligned, not shared with a concurrent call.  n_events may be 0 (no-op).
+ * Errors: TESS_E_INVALID (bad process/pointers), TESS_E_UNSUPPORTED (n out of
+ * range, HEL_SUM with n > 5), TESS_E_WORKSPACE, TESS_E_CUDA (launch).     */
+int tess_generate(tess_ctx *ctx, const tess_process *proc, uint64_t seed, uint64_t first_event,
+                  uint64_t n_events, const tess_outputs *out, void *workspace, size_t workspace_bytes,
+                  void *stream);
+
+/* Colour-ordered matrix elements for caller-given kinematics (the
+ * matrix-element stage alone, Eq. (BG-recursion) and the amplitude
+ * equation of Sec. 3):  me2[e] = |A(order_e; hel_e)|^2 with
+ * A = m / 2^((n-2)/2) in the Tr(T^a T^b) = delta^ab normalisation.
+ *   k      device, [n_events][n][4] doubles: all-outgoing momenta
+ *          (k_1 = -p_1, k_2 = -p_2 incoming; sum_i k_i = 0), (E, px, py, pz)
+ *   order  device, [n_events][n] uint8: cyclic colour ordering, order[0] is
+ *          the leg contracted last; each row a permutation of 0..n-1
+ *   hel    device, [n_events] uint32: bit i = helicity label of leg i (0 ->
+ *          eps_+ of the leg's physical direction, 1 -> eps_-)
+ *   me2    device, [n_events] doubles (output)
+ * precision: TESS_FP64 or TESS_FP32_CURRENTS.                               */
+int tess_me2(tess_ctx *ctx, int n, int precision, uint64_t n_events, const double *k, const uint8_t *order,
+             const uint32_t *hel, double *me2, void *stream);
+
+/* Cross section from a device acc (synchronises the stream):
+ * host out[4] = {sigma_pb, mc_error_pb, n_pass, n_generated}.
+ * Returns TESS_E_NUMERICAL (after filling out) if non-finite weights were seen. */
+int tess_result(tess_ctx *ctx, const double *acc, double *out, void *stream);
+
+/* Copy per-event outputs to host buffers (synchronises the stream).  Any of
+ * the host pointers may be NULL. */
+int tess_weights(tess_ctx *ctx, const tess_outputs *dev, uint64_t n_events, double *host_weight,
+                 uint8_t *host_pass, double *host_me2, void *stream);
+
+/* Histogram from a device hist (synchronises): host sumw[hist_bins + 2] and
+ * sumw2[hist_bins + 2], compensation folded in. */
+int tess_histograms(tess_ctx *ctx, const tess_process *proc, const double *hist, double *host_sumw,
+                    double *host_sumw2, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TESS_H */

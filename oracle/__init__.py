@@ -91,6 +91,7 @@ def lib():
             h.orc_polvec.argtypes = [_D, ctypes.c_int, _D]
             h.orc_amp.argtypes = [ctypes.c_int, _I, _D, _D, ctypes.c_int, _D]
             h.orc_event_record.argtypes = [ctypes.POINTER(Process), ctypes.c_uint64, ctypes.c_uint64, _D]
+            h.orc_event_record_u.argtypes = [ctypes.POINTER(Process), _D, _D]
             h.orc_generate.argtypes = [ctypes.POINTER(Process), ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                        ctypes.c_int, _D, _D, _U8, _D, _D, _D, _D, _D]
             h.orc_hist_bin.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double]
@@ -185,6 +186,51 @@ def event(proc, seed, ev):
     d["perm"] = rec[14:14 + proc.n].astype(int)
     d["k"] = rec[14 + proc.n:].reshape(proc.n, 4).copy()
     return d
+
+
+def event_u(proc, u):
+    """Event from caller-given uniforms (layout as the counter-based draws)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    assert u.size >= n_uniforms(proc.n)
+    rec = np.zeros(14 + proc.n + 4 * proc.n)
+    if lib().orc_event_record_u(ctypes.byref(proc), _dp(u), _dp(rec)):
+        raise ValueError("oracle rejected the process")
+    d = {f: rec[i] for i, f in enumerate(EVENT_FIELDS)}
+    d["pass"] = bool(rec[12])
+    d["hel_bits"] = int(rec[13])
+    d["perm"] = rec[14:14 + proc.n].astype(int)
+    d["k"] = rec[14 + proc.n:].reshape(proc.n, 4).copy()
+    return d
+
+
+def ulp_sensitivity(proc, seed, ev, trials=6):
+    """Largest relative change of the oracle's |A|^2 and weight for event ev
+    when each x and Rambo uniform moves by at most one ulp: the difference a
+    one-ulp discrepancy in a transcendental function can cause downstream.
+    Events near a zero of the amplitude have large values."""
+    rng = np.random.default_rng(ev & 0xFFFFFFFF)
+    u = uniforms(proc, seed, ev)
+    base = event_u(proc, u)
+    m = proc.n - 2
+    worst = 0.0
+    for _ in range(trials):
+        up = u.copy()
+        for j in range(2 + 4 * m):
+            r = rng.integers(3)
+            if r:
+                up[j] = np.nextafter(up[j], 0.0 if r == 1 else 1.0)
+        e = event_u(proc, up)
+        if e["pass"] != base["pass"] or base["me2"] == 0:
+            continue
+        worst = max(worst, abs(e["me2"] - base["me2"]) / abs(base["me2"]))
+        if base["weight"] > 0:
+            worst = max(worst, abs(e["weight"] - base["weight"]) / base["weight"])
+    return worst
+
+
+def uniforms(proc_or_n, seed, ev):
+    n = proc_or_n if isinstance(proc_or_n, int) else proc_or_n.n
+    return np.array([uniform(seed, ev, j) for j in range(n_uniforms(n))])
 
 
 def generate(proc, seed, first, n_events, threads=None, per_event=True, hist=True):

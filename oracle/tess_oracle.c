@@ -419,10 +419,10 @@ typedef struct {
 #define GEV2_TO_PB 0.3893793721e9
 #define NC 3.0
 
-static void event_kinematics(const orc_process *pr, uint64_t seed, uint64_t ev, orc_event_out *o, double *u) {
+/* Kinematics, helicity word and colour ordering from the event's uniforms
+ * u[0 .. orc_n_uniforms(n)) in the layout of Sec. 1 above. */
+static void event_kinematics(const orc_process *pr, const double *u, orc_event_out *o) {
   const int n = pr->n, m = n - 2;
-  const int nu = orc_n_uniforms(n);
-  for (int j = 0; j < nu; ++j) u[j] = orc_uniform(seed, ev, (uint32_t)j);
   const double S = pr->sqrt_s * pr->sqrt_s;
   const double lnxmin = log((m * pr->pt_min) * (m * pr->pt_min) / S);
   o->x1 = exp(u[0] * lnxmin);
@@ -485,11 +485,10 @@ static int next_perm(int *v, int len) {
   return 1;
 }
 
-int orc_event(const orc_process *pr, uint64_t seed, uint64_t ev, orc_event_out *o) {
+static int event_from_uniforms(const orc_process *pr, const double *u, orc_event_out *o) {
   const int n = pr->n, m = n - 2;
   if (n < 4 || n > ORC_MAXN) return -1;
-  double u[64];
-  event_kinematics(pr, seed, ev, o, u);
+  event_kinematics(pr, u, o);
   double E = 0.0;
   if (pr->hel_mode == 0) {
     int order[ORC_MAXN];
@@ -515,6 +514,14 @@ int orc_event(const orc_process *pr, uint64_t seed, uint64_t ev, orc_event_out *
   }
   o->weight = w;
   return 0;
+}
+
+int orc_event(const orc_process *pr, uint64_t seed, uint64_t ev, orc_event_out *o) {
+  if (pr->n < 4 || pr->n > ORC_MAXN) return -1;
+  double u[64];
+  const int nu = orc_n_uniforms(pr->n);
+  for (int j = 0; j < nu; ++j) u[j] = orc_uniform(seed, ev, (uint32_t)j);
+  return event_from_uniforms(pr, u, o);
 }
 
 /* ========================================================================
@@ -650,6 +657,21 @@ int orc_generate(const orc_process *pr, uint64_t seed, uint64_t first, uint64_t 
 int orc_event_record(const orc_process *pr, uint64_t seed, uint64_t ev, double *rec) {
   orc_event_out o;
   const int rc = orc_event(pr, seed, ev, &o);
+  if (rc) return rc;
+  const double head[12] = {o.x1, o.x2, o.shat, o.y, o.alphas, o.ht, o.ptlead, o.rmin, o.me2, o.weight, o.pdf, o.phi};
+  memcpy(rec, head, sizeof head);
+  rec[12] = o.pass;
+  rec[13] = o.hel_bits;
+  for (int i = 0; i < pr->n; ++i) rec[14 + i] = o.perm[i];
+  for (int i = 0; i < pr->n; ++i)
+    for (int mu = 0; mu < 4; ++mu) rec[14 + pr->n + 4 * i + mu] = o.k[i][mu];
+  return 0;
+}
+
+/* The same record for caller-given uniforms u[0 .. orc_n_uniforms(n)). */
+int orc_event_record_u(const orc_process *pr, const double *u, double *rec) {
+  orc_event_out o;
+  const int rc = event_from_uniforms(pr, u, &o);
   if (rc) return rc;
   const double head[12] = {o.x1, o.x2, o.shat, o.y, o.alphas, o.ht, o.ptlead, o.rmin, o.me2, o.weight, o.pdf, o.phi};
   memcpy(rec, head, sizeof head);

@@ -1,0 +1,268 @@
+"""GB300-native leading-order, leading-colour multi-gluon event generator.
+
+Thin Python binding of the C ABI in ``include/tess.h`` (``_build/libtess.so``):
+argument marshalling only.  Every step of an event runs in the library's
+CUDA kernels; PyTorch is used for device memory and streams.  There is no
+CPU path: if the CUDA library cannot be loaded, every call raises.
+
+Names follow the C ABI (``tess_init``, ``tess_generate``, ...).  ``n`` is the
+total number of gluons (gg -> (n-2) g), as in the paper.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libtess.so")
+
+TESS_OK = 0
+TESS_E_INVALID = -1
+TESS_E_UNSUPPORTED = -2
+TESS_E_CUDA = -3
+TESS_E_WORKSPACE = -4
+TESS_E_NUMERICAL = -5
+TESS_MIN_N, TESS_MAX_N, TESS_MAX_BINS, TESS_ACC_LEN = 4, 12, 1024, 8
+TESS_FP64, TESS_FP32_CURRENTS = 0, 1
+TESS_HEL_SUM, TESS_HEL_SAMPLE = 0, 1
+TESS_OBS_PTLEAD, TESS_OBS_HT, TESS_OBS_RMIN = 0, 1, 2
+
+# Every symbol include/tess.h declares (checked by the ABI tests).
+EXPORTED = ["tess_version", "tess_last_error", "tess_init", "tess_destroy", "tess_workspace_size", "tess_generate",
+            "tess_me2", "tess_result", "tess_weights", "tess_histograms"]
+
+
+class TessError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"tess error {code}: {msg}")
+        self.code = code
+
+
+class tess_process(ctypes.Structure):
+    _fields_ = [
+        ("n_gluons", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("helicity_mode", ctypes.c_int32),
+        ("hist_observable", ctypes.c_int32),
+        ("hist_bins", ctypes.c_int32),
+        ("nf", ctypes.c_int32),
+        ("sqrt_s", ctypes.c_double),
+        ("pt_min", ctypes.c_double),
+        ("eta_max", ctypes.c_double),
+        ("dr_min", ctypes.c_double),
+        ("alphas_mz", ctypes.c_double),
+        ("mz", ctypes.c_double),
+        ("mu_r_factor", ctypes.c_double),
+        ("hist_lo", ctypes.c_double),
+        ("hist_hi", ctypes.c_double),
+    ]
+
+
+class tess_outputs(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_void_p) for name in ("weight", "me2", "pass_", "ht", "ptlead", "rmin", "acc", "hist")]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            from . import build as _build
+            _build.build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        vp, u64, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
+        P = ctypes.POINTER
+        lib.tess_version.restype = ctypes.c_char_p
+        lib.tess_last_error.restype = ctypes.c_char_p
+        lib.tess_init.argtypes = [i32, P(vp)]
+        lib.tess_destroy.argtypes = [vp]
+        lib.tess_destroy.restype = None
+        lib.tess_workspace_size.argtypes = [vp, P(tess_process), u64, P(ctypes.c_size_t)]
+        lib.tess_generate.argtypes = [vp, P(tess_process), u64, u64, u64, P(tess_outputs), vp, ctypes.c_size_t, vp]
+        lib.tess_me2.argtypes = [vp, i32, i32, u64, vp, vp, vp, vp, vp]
+        lib.tess_result.argtypes = [vp, vp, P(ctypes.c_double), vp]
+        lib.tess_weights.argtypes = [vp, P(tess_outputs), u64, vp, vp, vp, vp]
+        lib.tess_histograms.argtypes = [vp, P(tess_process), vp, vp, vp, vp]
+        for f in EXPORTED:
+            if f not in ("tess_version", "tess_last_error", "tess_destroy"):
+                getattr(lib, f).restype = i32
+        _lib = lib
+        return lib
+
+
+def library_path():
+    return _LIB_PATH
+
+
+def _check(rc):
+    if rc != TESS_OK:
+        raise TessError(rc, _load().tess_last_error().decode())
+    return rc
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ----------------------------------------------------------------- C ABI
+def tess_version():
+    return _load().tess_version().decode()
+
+
+def tess_last_error():
+    return _load().tess_last_error().decode()
+
+
+def tess_init(device=0):
+    h = ctypes.c_void_p()
+    _check(_load().tess_init(int(device), ctypes.byref(h)))
+    return h
+
+
+def tess_destroy(ctx):
+    _load().tess_destroy(ctx)
+
+
+def tess_workspace_size(ctx, proc, n_events):
+    b = ctypes.c_size_t()
+    _check(_load().tess_workspace_size(ctx, ctypes.byref(proc), int(n_events), ctypes.byref(b)))
+    return b.value
+
+
+def make_outputs(weight=None, me2=None, pass_=None, ht=None, ptlead=None, rmin=None, acc=None, hist=None):
+    return tess_outputs(*[t.data_ptr() if t is not None else None for t in (weight, me2, pass_, ht, ptlead, rmin,
+                                                                            acc, hist)])
+
+
+def tess_generate(ctx, proc, seed, first_event, n_events, outputs, workspace, stream=None):
+    ws = _ptr(workspace)
+    nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(_load().tess_generate(ctx, ctypes.byref(proc), int(seed), int(first_event), int(n_events),
+                                 ctypes.byref(outputs), ws, nbytes, _stream(stream)))
+
+
+def tess_me2(ctx, n, precision, k, order, hel, me2, stream=None):
+    _check(_load().tess_me2(ctx, int(n), int(precision), int(me2.numel()), _ptr(k), _ptr(order), _ptr(hel),
+                            _ptr(me2), _stream(stream)))
+
+
+def tess_result(ctx, acc, stream=None, allow_nonfinite=False):
+    out = (ctypes.c_double * 4)()
+    rc = _load().tess_result(ctx, _ptr(acc), out, _stream(stream))
+    if rc != TESS_OK and not (allow_nonfinite and rc == TESS_E_NUMERICAL):
+        _check(rc)
+    return out[0], out[1], int(out[2]), int(out[3])
+
+
+def tess_weights(ctx, outputs, n_events, host_weight=None, host_pass=None, host_me2=None, stream=None):
+    def hp(a):
+        return None if a is None else ctypes.c_void_p(a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr())
+    _check(_load().tess_weights(ctx, ctypes.byref(outputs), int(n_events), hp(host_weight), hp(host_pass),
+                                hp(host_me2), _stream(stream)))
+
+
+def tess_histograms(ctx, proc, hist, stream=None):
+    nb2 = proc.hist_bins + 2
+    sw = np.zeros(nb2)
+    sw2 = np.zeros(nb2)
+    _check(_load().tess_histograms(ctx, ctypes.byref(proc), _ptr(hist), ctypes.c_void_p(sw.ctypes.data),
+                                   ctypes.c_void_p(sw2.ctypes.data), _stream(stream)))
+    return sw, sw2
+
+
+# ----------------------------------------------------------------- helpers
+def process(n, precision=TESS_FP64, helicity_mode=TESS_HEL_SAMPLE, sqrt_s=14000.0, pt_min=20.0, eta_max=2.5,
+            dr_min=0.4, alphas_mz=0.118, mz=91.19, nf=5, mu_r_factor=0.5, hist_observable=TESS_OBS_PTLEAD,
+            hist_bins=0, hist_lo=20.0, hist_hi=1020.0):
+    return tess_process(n_gluons=n, precision=precision, helicity_mode=helicity_mode,
+                        hist_observable=hist_observable, hist_bins=hist_bins, nf=nf, sqrt_s=sqrt_s, pt_min=pt_min,
+                        eta_max=eta_max, dr_min=dr_min, alphas_mz=alphas_mz, mz=mz, mu_r_factor=mu_r_factor,
+                        hist_lo=hist_lo, hist_hi=hist_hi)
+
+
+# Workloads of the numerical study (Sec. 4), 14 TeV, toy gluon density.
+PRESETS = {
+    "gg2g": dict(n=4, precision=TESS_FP64, helicity_mode=TESS_HEL_SUM, hist_observable=TESS_OBS_PTLEAD,
+                 hist_bins=50, hist_lo=20.0, hist_hi=1020.0, n_events=1 << 20),
+    "gg4g": dict(n=6, precision=TESS_FP32_CURRENTS, helicity_mode=TESS_HEL_SAMPLE, n_events=1 << 24),
+    "gg8g": dict(n=10, precision=TESS_FP32_CURRENTS, helicity_mode=TESS_HEL_SAMPLE, pt_min=30.0,
+                 hist_observable=TESS_OBS_HT, hist_bins=40, hist_lo=200.0, hist_hi=3000.0, n_events=1 << 26),
+}
+
+
+class Run:
+    """Device buffers (torch) for one call of tess_generate plus its
+    accumulators; ``per_event`` selects which per-event arrays exist."""
+
+    def __init__(self, ctx, proc, n_events, device="cuda", per_event=("weight", "me2", "pass", "ht", "ptlead", "rmin")):
+        import torch
+        self.ctx, self.proc, self.n_events = ctx, proc, int(n_events)
+        dev = torch.device(device)
+        f64 = dict(dtype=torch.float64, device=dev)
+        self.t = {}
+        for name in ("weight", "me2", "ht", "ptlead", "rmin"):
+            self.t[name] = torch.empty(self.n_events, **f64) if name in per_event else None
+        self.t["pass"] = torch.empty(self.n_events, dtype=torch.uint8, device=dev) if "pass" in per_event else None
+        self.acc = torch.zeros(TESS_ACC_LEN, **f64)
+        self.hist = torch.zeros(4 * (proc.hist_bins + 2), **f64) if proc.hist_bins > 0 else None
+        ws = tess_workspace_size(ctx, proc, self.n_events)
+        self.workspace = torch.empty((ws + 7) // 8, **f64)
+        self.outputs = make_outputs(self.t["weight"], self.t["me2"], self.t["pass"], self.t["ht"], self.t["ptlead"],
+                                    self.t["rmin"], self.acc, self.hist)
+
+    def reset(self):
+        self.acc.zero_()
+        if self.hist is not None:
+            self.hist.zero_()
+
+    def generate(self, seed, first_event=0, stream=None):
+        tess_generate(self.ctx, self.proc, seed, first_event, self.n_events, self.outputs, self.workspace, stream)
+
+    def result(self, stream=None, allow_nonfinite=False):
+        return tess_result(self.ctx, self.acc, stream, allow_nonfinite)
+
+    def histograms(self, stream=None):
+        return tess_histograms(self.ctx, self.proc, self.hist, stream)
+
+
+# ----------------------------------------------------------------- cost model
+def bg_flops(n):
+    """Real floating-point operations (FMA = 2, add/mul/reciprocal = 1) of one
+    Berends-Giele amplitude as the kernels evaluate it (tess_bg.cuh): per
+    split 148 (+2 for each S term of a multi-leg side), per four-vertex triple
+    62, per set 20 plus 16 when propagated, and the final contraction 30."""
+    L = n - 1
+    total = 0
+    for ln in range(2, L + 1):
+        for a in range(0, L - ln + 1):
+            b = a + ln - 1
+            for i in range(a, b):
+                total += 148 + (2 if i > a else 0) + (2 if b > i + 1 else 0)
+            total += 62 * ((ln - 1) * (ln - 2) // 2)
+            total += 20 + (16 if ln < L else 0)
+    return total + 30
+
+
+def splits_and_triples(n):
+    L = n - 1
+    return math.comb(L + 1, 3), math.comb(L + 1, 4)

@@ -1,0 +1,367 @@
+// C ABI of the generator (declared in include/tess.h): argument validation,
+// error reporting, launch sequencing.  Allocates no device memory.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "tess.h"
+#include "tess_kernels.cuh"
+
+namespace tess {
+cudaError_t launch_generate_f64(int n, bool sum, const EventParams &P, double *partials, int grid, cudaStream_t s);
+cudaError_t launch_generate_f32(int n, bool sum, const EventParams &P, double *partials, int grid, cudaStream_t s);
+int grid_generate_f64(int n, bool sum, int sm_count, uint64_t n_events, int hist_bins);
+int grid_generate_f32(int n, bool sum, int sm_count, uint64_t n_events, int hist_bins);
+cudaError_t launch_me2_f64(int n, uint64_t n_events, const double *k, const uint8_t *order, const uint32_t *hel,
+                           double *me2, cudaStream_t s);
+cudaError_t launch_me2_f32(int n, uint64_t n_events, const double *k, const uint8_t *order, const uint32_t *hel,
+                           double *me2, cudaStream_t s);
+// Neumaier-compensated addition (s, c) += x.
+__device__ __forceinline__ void comp_add(double &s, double &c, double x) {
+  const double t = s + x;
+  if (fabs(s) >= fabs(x))
+    c += (s - t) + x;
+  else
+    c += (x - t) + s;
+  s = t;
+}
+
+// Folds the per-block partials, in block order with compensation, into the
+// caller's running accumulators (acc, hist), which carry their own
+// compensation terms between calls.
+__global__ void finalize_kernel(const double *__restrict__ partials, int nblocks, int hist_bins, uint64_t n_events,
+                                double *acc, double *hist) {
+  const int stride = partial_stride(hist_bins);
+  const int nb2 = hist_bins > 0 ? hist_bins + 2 : 0;
+  const int nq = kPartialHead + 2 * nb2;
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    double s = 0.0, c = 0.0;
+    for (int b = 0; b < nblocks; ++b) comp_add(s, c, partials[(size_t)b * stride + q]);
+    const double tot = s + c;
+    if (q == 0 || q == 1) {
+      double hs = acc[q], hc = acc[4 + q];
+      comp_add(hs, hc, tot);
+      acc[q] = hs;
+      acc[4 + q] = hc;
+    } else if (q == 2) {
+      acc[2] += tot;
+    } else if (q == 3) {
+      acc[6] += tot;
+    } else {
+      const int h = q - kPartialHead;  // 0..2 nb2 - 1: w bins then w^2 bins
+      double hs = hist[h], hc = hist[2 * nb2 + h];
+      comp_add(hs, hc, tot);
+      hist[h] = hs;
+      hist[2 * nb2 + h] = hc;
+    }
+  }
+  if (threadIdx.x == 0) acc[3] += (double)n_events;
+}
+
+}  // namespace tess
+
+struct tess_ctx {
+  int device;
+  int sm_count;
+};
+
+namespace {
+
+thread_local std::string g_error;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_error = buf;
+  return code;
+}
+
+int ok() {
+  g_error.clear();
+  return TESS_OK;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  return fail(TESS_E_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// Makes ctx's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) {
+      err = cudaSetDevice(dev);
+      changed = (err == cudaSuccess);
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+int check_process(const tess_process *p) {
+  if (!p) return fail(TESS_E_INVALID, "process is NULL");
+  if (p->n_gluons < TESS_MIN_N || p->n_gluons > TESS_MAX_N)
+    return fail(TESS_E_UNSUPPORTED, "n_gluons = %d outside %d..%d", p->n_gluons, TESS_MIN_N, TESS_MAX_N);
+  if (p->precision != TESS_FP64 && p->precision != TESS_FP32_CURRENTS)
+    return fail(TESS_E_INVALID, "precision = %d is not TESS_FP64 or TESS_FP32_CURRENTS", p->precision);
+  if (p->helicity_mode != TESS_HEL_SUM && p->helicity_mode != TESS_HEL_SAMPLE)
+    return fail(TESS_E_INVALID, "helicity_mode = %d is not TESS_HEL_SUM or TESS_HEL_SAMPLE", p->helicity_mode);
+  if (p->helicity_mode == TESS_HEL_SUM && p->n_gluons > 5)
+    return fail(TESS_E_UNSUPPORTED, "TESS_HEL_SUM is built for n <= 5 (n = %d)", p->n_gluons);
+  if (!finite_pos(p->sqrt_s)) return fail(TESS_E_INVALID, "sqrt_s must be finite and > 0");
+  if (!finite_pos(p->pt_min)) return fail(TESS_E_INVALID, "pt_min must be finite and > 0");
+  if (!finite_pos(p->eta_max)) return fail(TESS_E_INVALID, "eta_max must be finite and > 0");
+  if (!(std::isfinite(p->dr_min) && p->dr_min >= 0.0)) return fail(TESS_E_INVALID, "dr_min must be finite and >= 0");
+  if (!finite_pos(p->alphas_mz)) return fail(TESS_E_INVALID, "alphas_mz must be finite and > 0");
+  if (!finite_pos(p->mz)) return fail(TESS_E_INVALID, "mz must be finite and > 0");
+  if (!finite_pos(p->mu_r_factor)) return fail(TESS_E_INVALID, "mu_r_factor must be finite and > 0");
+  if (p->nf < 0 || p->nf > 6) return fail(TESS_E_INVALID, "nf = %d outside 0..6", p->nf);
+  if ((p->n_gluons - 2) * p->pt_min >= p->sqrt_s)
+    return fail(TESS_E_INVALID, "(n-2) * pt_min must be below sqrt_s (no phase space passes the cuts)");
+  if (p->hist_bins < 0 || p->hist_bins > TESS_MAX_BINS)
+    return fail(TESS_E_INVALID, "hist_bins = %d outside 0..%d", p->hist_bins, TESS_MAX_BINS);
+  if (p->hist_bins > 0) {
+    if (p->hist_observable < 0 || p->hist_observable > 2)
+      return fail(TESS_E_INVALID, "hist_observable = %d is not a TESS_OBS_* value", p->hist_observable);
+    if (!(std::isfinite(p->hist_lo) && std::isfinite(p->hist_hi) && p->hist_lo < p->hist_hi))
+      return fail(TESS_E_INVALID, "histogram range must satisfy finite hist_lo < hist_hi");
+  }
+  return TESS_OK;
+}
+
+// Rejects host or foreign-device pointers before any kernel dereferences them.
+int check_device_ptr(const void *p, int device, const char *name) {
+  if (!p) return TESS_OK;
+  cudaPointerAttributes a;
+  const cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(TESS_E_INVALID, "%s: not a CUDA pointer (%s)", name, cudaGetErrorName(e));
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+    return fail(TESS_E_INVALID, "%s: must be device memory", name);
+  if (a.type == cudaMemoryTypeDevice && a.device != device)
+    return fail(TESS_E_INVALID, "%s: lives on device %d, context is on device %d", name, a.device, device);
+  return TESS_OK;
+}
+
+int grid_for(const tess_ctx *ctx, const tess_process *p, uint64_t n_events) {
+  const bool sum = p->helicity_mode == TESS_HEL_SUM;
+  const uint64_t ne = n_events ? n_events : 1;
+  return p->precision == TESS_FP64 ? tess::grid_generate_f64(p->n_gluons, sum, ctx->sm_count, ne, p->hist_bins)
+                                   : tess::grid_generate_f32(p->n_gluons, sum, ctx->sm_count, ne, p->hist_bins);
+}
+
+double factorial(int k) {
+  double f = 1.0;
+  for (int i = 2; i <= k; ++i) f *= i;
+  return f;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tess_version(void) { return "tess-gb300 0.1"; }
+
+const char *tess_last_error(void) { return g_error.c_str(); }
+
+int tess_init(int device, tess_ctx **ctx) {
+  if (!ctx) return fail(TESS_E_INVALID, "ctx is NULL");
+  *ctx = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= count) return fail(TESS_E_INVALID, "device %d outside 0..%d", device, count - 1);
+  int major = 0, minor = 0, sms = 0;
+  if ((e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess)
+    return cuda_fail(e, "cudaDeviceGetAttribute");
+  if (major != 10 || minor != 3)
+    return fail(TESS_E_UNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a (GB300) only", device,
+                major, minor);
+  *ctx = new tess_ctx{device, sms};
+  return ok();
+}
+
+void tess_destroy(tess_ctx *ctx) { delete ctx; }
+
+int tess_workspace_size(const tess_ctx *ctx, const tess_process *proc, uint64_t n_events, size_t *bytes) {
+  if (!ctx || !bytes) return fail(TESS_E_INVALID, "ctx and bytes must not be NULL");
+  int rc = check_process(proc);
+  if (rc) return rc;
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  const int grid = grid_for(ctx, proc, n_events);
+  *bytes = (size_t)grid * (size_t)tess::partial_stride(proc->hist_bins) * sizeof(double);
+  return ok();
+}
+
+int tess_generate(tess_ctx *ctx, const tess_process *proc, uint64_t seed, uint64_t first_event, uint64_t n_events,
+                  const tess_outputs *out, void *workspace, size_t workspace_bytes, void *stream) {
+  if (!ctx) return fail(TESS_E_INVALID, "ctx is NULL");
+  int rc = check_process(proc);
+  if (rc) return rc;
+  if (!out || !out->acc) return fail(TESS_E_INVALID, "outputs and outputs->acc must not be NULL");
+  if (proc->hist_bins > 0 && !out->hist) return fail(TESS_E_INVALID, "hist_bins > 0 needs outputs->hist");
+  if (n_events > (UINT64_MAX - first_event)) return fail(TESS_E_INVALID, "event range overflows 64 bits");
+  if (n_events == 0) return ok();
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  const void *ptrs[] = {out->weight, out->me2, out->pass, out->ht, out->ptlead, out->rmin, out->acc, out->hist,
+                        workspace};
+  const char *names[] = {"weight", "me2", "pass", "ht", "ptlead", "rmin", "acc", "hist", "workspace"};
+  for (int i = 0; i < 9; ++i)
+    if ((rc = check_device_ptr(ptrs[i], ctx->device, names[i]))) return rc;
+  const int grid = grid_for(ctx, proc, n_events);
+  const size_t need = (size_t)grid * (size_t)tess::partial_stride(proc->hist_bins) * sizeof(double);
+  if (!workspace || workspace_bytes < need)
+    return fail(TESS_E_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, workspace ? workspace_bytes : 0);
+  if (((uintptr_t)workspace) % 256 != 0) return fail(TESS_E_WORKSPACE, "workspace must be 256-byte aligned");
+
+  const int n = proc->n_gluons, m = n - 2;
+  const bool sum = proc->helicity_mode == TESS_HEL_SUM;
+  tess::EventParams P;
+  memset(&P, 0, sizeof P);
+  P.seed = seed;
+  P.first_event = first_event;
+  P.n_events = n_events;
+  P.S = proc->sqrt_s * proc->sqrt_s;
+  P.lnxmin = std::log((m * proc->pt_min) * (m * proc->pt_min) / P.S);
+  P.pt_min = proc->pt_min;
+  P.eta_max = proc->eta_max;
+  P.dr2_min = proc->dr_min * proc->dr_min;
+  P.alphas_mz = proc->alphas_mz;
+  P.ln_mz2 = std::log(proc->mz * proc->mz);
+  P.b0 = (33.0 - 2.0 * proc->nf) / (12.0 * M_PI);
+  P.mu_r_factor = proc->mu_r_factor;
+  const double nc = 3.0;
+  P.wconst = std::pow(nc, n - 2) * (nc * nc - 1.0) / (256.0 * factorial(m)) * 0.3893793721e9;
+  P.phiconst = std::pow(2.0 * M_PI, 4.0 - 3.0 * m) * std::pow(M_PI / 2.0, m - 1.0) / (factorial(m - 1) * factorial(m - 2));
+  P.efac = sum ? 1.0 / std::ldexp(1.0, n - 2) : std::ldexp(1.0, n) * factorial(n - 1) / std::ldexp(1.0, n - 2);
+  P.hist_bins = proc->hist_bins;
+  P.hist_obs = proc->hist_observable;
+  P.hist_lo = proc->hist_lo;
+  P.hist_inv_width = proc->hist_bins > 0 ? proc->hist_bins / (proc->hist_hi - proc->hist_lo) : 0.0;
+  P.weight = out->weight;
+  P.me2 = out->me2;
+  P.pass = out->pass;
+  P.ht = out->ht;
+  P.ptlead = out->ptlead;
+  P.rmin = out->rmin;
+
+  cudaStream_t s = (cudaStream_t)stream;
+  double *partials = (double *)workspace;
+  cudaError_t e = proc->precision == TESS_FP64 ? tess::launch_generate_f64(n, sum, P, partials, grid, s)
+                                               : tess::launch_generate_f32(n, sum, P, partials, grid, s);
+  if (e != cudaSuccess) return cuda_fail(e, "event kernel launch");
+  tess::finalize_kernel<<<1, 256, 0, s>>>(partials, grid, proc->hist_bins, n_events, out->acc, out->hist);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "finalize kernel launch");
+  return ok();
+}
+
+int tess_me2(tess_ctx *ctx, int n, int precision, uint64_t n_events, const double *k, const uint8_t *order,
+             const uint32_t *hel, double *me2, void *stream) {
+  if (!ctx) return fail(TESS_E_INVALID, "ctx is NULL");
+  if (n < TESS_MIN_N || n > TESS_MAX_N) return fail(TESS_E_UNSUPPORTED, "n = %d outside %d..%d", n, TESS_MIN_N, TESS_MAX_N);
+  if (precision != TESS_FP64 && precision != TESS_FP32_CURRENTS) return fail(TESS_E_INVALID, "bad precision %d", precision);
+  if (n_events == 0) return ok();
+  if (!k || !order || !hel || !me2) return fail(TESS_E_INVALID, "k, order, hel and me2 must not be NULL");
+  if (n_events > (uint64_t)INT32_MAX * 128ull) return fail(TESS_E_INVALID, "n_events too large for one call");
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  int rc;
+  if ((rc = check_device_ptr(k, ctx->device, "k")) || (rc = check_device_ptr(order, ctx->device, "order")) ||
+      (rc = check_device_ptr(hel, ctx->device, "hel")) || (rc = check_device_ptr(me2, ctx->device, "me2")))
+    return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const cudaError_t e = precision == TESS_FP64 ? tess::launch_me2_f64(n, n_events, k, order, hel, me2, s)
+                                               : tess::launch_me2_f32(n, n_events, k, order, hel, me2, s);
+  if (e != cudaSuccess) return cuda_fail(e, "me2 kernel launch");
+  return ok();
+}
+
+int tess_result(tess_ctx *ctx, const double *acc, double *out, void *stream) {
+  if (!ctx || !acc || !out) return fail(TESS_E_INVALID, "ctx, acc and out must not be NULL");
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  int rc = check_device_ptr(acc, ctx->device, "acc");
+  if (rc) return rc;
+  double h[TESS_ACC_LEN];
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(h, acc, sizeof h, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "copy of acc");
+  const double n = h[3];
+  const double sw = h[0] + h[4], sw2 = h[1] + h[5];
+  const double mean = n > 0 ? sw / n : 0.0;
+  const double var = n > 1 ? (sw2 / n - mean * mean) / (n - 1.0) : 0.0;
+  out[0] = mean;
+  out[1] = std::sqrt(var > 0 ? var : 0.0);
+  out[2] = h[2];
+  out[3] = n;
+  if (h[6] > 0) return fail(TESS_E_NUMERICAL, "%.0f events had non-finite weights (counted as 0)", h[6]);
+  return ok();
+}
+
+int tess_weights(tess_ctx *ctx, const tess_outputs *dev, uint64_t n_events, double *host_weight, uint8_t *host_pass,
+                 double *host_me2, void *stream) {
+  if (!ctx || !dev) return fail(TESS_E_INVALID, "ctx and dev must not be NULL");
+  if (n_events == 0) return ok();
+  if ((host_weight && !dev->weight) || (host_pass && !dev->pass) || (host_me2 && !dev->me2))
+    return fail(TESS_E_INVALID, "a requested host output has no device array");
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (host_weight && e == cudaSuccess)
+    e = cudaMemcpyAsync(host_weight, dev->weight, n_events * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (host_pass && e == cudaSuccess)
+    e = cudaMemcpyAsync(host_pass, dev->pass, n_events, cudaMemcpyDeviceToHost, s);
+  if (host_me2 && e == cudaSuccess)
+    e = cudaMemcpyAsync(host_me2, dev->me2, n_events * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "copy of per-event outputs");
+  return ok();
+}
+
+int tess_histograms(tess_ctx *ctx, const tess_process *proc, const double *hist, double *host_sumw,
+                    double *host_sumw2, void *stream) {
+  if (!ctx || !hist || !host_sumw || !host_sumw2) return fail(TESS_E_INVALID, "NULL argument");
+  int rc = check_process(proc);
+  if (rc) return rc;
+  if (proc->hist_bins <= 0) return fail(TESS_E_INVALID, "process has no histogram");
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  if ((rc = check_device_ptr(hist, ctx->device, "hist"))) return rc;
+  const int nb2 = proc->hist_bins + 2;
+  double *h = new double[4 * nb2];
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(h, hist, 4 * nb2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    delete[] h;
+    return cuda_fail(e, "copy of hist");
+  }
+  for (int b = 0; b < nb2; ++b) {
+    host_sumw[b] = h[b] + h[2 * nb2 + b];
+    host_sumw2[b] = h[nb2 + b] + h[3 * nb2 + b];
+  }
+  delete[] h;
+  return ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,177 @@
+// Berends-Giele colour-ordered amplitude for one event, one thread.
+//
+// Recursion (Sec. 3, Eq. (BG-recursion) and its shorthand): for a contiguous
+// set X = [a..b] of the L = n-1 legs,
+//   J[X] = 1/K[X]^2 ( sum_splits [J_l, J_r] + sum_triples {J_l, J_m, J_r} ).
+// The triple (four-gluon vertex) sum is reorganised here without changing
+// its value.  With S[Y] = sum_{splits (l,r) of Y} J_l.J_r (a scalar per set),
+//   sum_{A,B,C} {A,B,C} = 2 sum_{A,B,C} (J_A.J_C) J_B
+//                         - sum_{splits (l,r) of X} ( S[l] J_r + S[r] J_l ),
+// so each split costs one three-vertex bracket plus two scalar multiply-adds
+// and only the (J_A.J_C) J_B term keeps the O(n^4) triple loop.  S[Y] is
+// accumulated for free while Y itself is built (it is the sum of the J_l.J_r
+// dot products the brackets already need).
+//
+// All loops have compile-time trip counts, so after full unrolling every
+// table index is a constant and the tables live in registers.
+#pragma once
+#include "tess_math.cuh"
+
+namespace tess {
+
+template <typename R, int L>
+struct BGTables {
+  CV4<R> J[L][L];  // J[a][b], a <= b: current of legs a..b
+  RV4<R> K[L][L];  // K[a][b]: sum of the momenta of legs a..b
+  Cx<R> S[L][L];   // S[a][b]: sum over splits of J_l . J_r (b > a)
+};
+
+// Un-propagated top current Num = K^2 J[0..L-1] for leg momenta k[0..L) and
+// polarisations e[0..L) (already in the colour order), then the amplitude
+// m = e0 . Num (amplitude equation of Sec. 3, leg 1 off-shell).
+template <typename R, int L>
+__device__ __forceinline__ Cx<R> bg_amplitude(const RV4<R> (&k)[L], const CV4<R> (&e)[L], const CV4<R> &e0) {
+  BGTables<R, L> t;
+#pragma unroll
+  for (int a = 0; a < L; ++a) {
+    t.J[a][a] = e[a];
+    t.K[a][a] = k[a];
+  }
+  CV4<R> num = cv_zero<R>();
+#pragma unroll
+  for (int len = 2; len <= L; ++len) {
+#pragma unroll
+    for (int a = 0; a + len - 1 < L; ++a) {
+      const int b = a + len - 1;
+      t.K[a][b] = radd(t.K[a][b - 1], k[b]);
+      CV4<R> acc = cv_zero<R>();
+      CV4<R> tri = cv_zero<R>();
+      Cx<R> s = cx<R>(R(0), R(0));
+#pragma unroll
+      for (int i = a; i < b; ++i) {
+        // split l = [a..i], r = [i+1..b]
+        const CV4<R> &Jl = t.J[a][i];
+        const CV4<R> &Jr = t.J[i + 1][b];
+        const Cx<R> d = mdot(Jl, Jr);
+        const Cx<R> jlkr = mdot(Jl, t.K[i + 1][b]);
+        const Cx<R> krjl = mdot(Jr, t.K[a][i]);
+        Cx<R> cr = cx<R>(R(2) * jlkr.re, R(2) * jlkr.im);
+        Cx<R> cl = cx<R>(R(-2) * krjl.re, R(-2) * krjl.im);
+        if (i > a) {
+          cr.re -= t.S[a][i].re;
+          cr.im -= t.S[a][i].im;
+        }
+        if (b > i + 1) {
+          cl.re -= t.S[i + 1][b].re;
+          cl.im -= t.S[i + 1][b].im;
+        }
+        axpy(acc, cr, Jr);
+        axpy(acc, cl, Jl);
+        axpy(acc, d, rsub(t.K[a][i], t.K[i + 1][b]));
+        s.re += d.re;
+        s.im += d.im;
+      }
+#pragma unroll
+      for (int i = a; i + 1 < b; ++i) {
+#pragma unroll
+        for (int j = i + 1; j < b; ++j) {
+          axpy(tri, mdot(t.J[a][i], t.J[j + 1][b]), t.J[i + 1][j]);
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        acc.c[m].re = fma(R(2), tri.c[m].re, acc.c[m].re);
+        acc.c[m].im = fma(R(2), tri.c[m].im, acc.c[m].im);
+      }
+      if (len < L) {
+        const R inv = R(1) / mdot(t.K[a][b], t.K[a][b]);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          t.J[a][b].c[m].re = acc.c[m].re * inv;
+          t.J[a][b].c[m].im = acc.c[m].im * inv;
+        }
+        t.S[a][b] = s;
+      } else {
+        num = acc;
+      }
+    }
+  }
+  return mdot(e0, num);
+}
+
+// ---------------------------------------------------------------------------
+// Loop form of the same recursion for large tables (FP64, and FP32 with
+// n >= 8): runtime loops over lengths, sets and splits, the table in
+// per-thread local memory indexed by tri(a, b).  Compiles in O(1) code size.
+// The caller fills the single-leg entries J[tri(a,a)] (polarisations) and
+// K[tri(a,a)] (momenta) in colour order, then calls run().
+// ---------------------------------------------------------------------------
+template <typename R, int L>
+struct BGLoop {
+  static constexpr int T = L * (L + 1) / 2;
+  CV4<R> J[T];
+  RV4<R> K[T];
+  Cx<R> S[T];
+
+  __device__ __forceinline__ static int tri(int a, int b) { return a * L - (a * (a - 1)) / 2 + (b - a); }
+
+  __device__ Cx<R> run(const CV4<R> &e0) {
+#pragma unroll 1
+    for (int a = 0; a < L; ++a) S[tri(a, a)] = cx<R>(R(0), R(0));
+    CV4<R> num = cv_zero<R>();
+#pragma unroll 1
+    for (int len = 2; len <= L; ++len) {
+#pragma unroll 1
+      for (int a = 0; a + len - 1 < L; ++a) {
+        const int b = a + len - 1;
+        const int X = tri(a, b);
+        K[X] = radd(K[tri(a, b - 1)], K[tri(b, b)]);
+        CV4<R> acc = cv_zero<R>();
+        CV4<R> trs = cv_zero<R>();
+        Cx<R> s = cx<R>(R(0), R(0));
+#pragma unroll 1
+        for (int i = a; i < b; ++i) {
+          const int l = tri(a, i), r = tri(i + 1, b);
+          const CV4<R> Jl = J[l], Jr = J[r];
+          const RV4<R> Kl = K[l], Kr = K[r];
+          const Cx<R> d = mdot(Jl, Jr);
+          const Cx<R> jlkr = mdot(Jl, Kr);
+          const Cx<R> krjl = mdot(Jr, Kl);
+          const Cx<R> Sl = S[l], Sr = S[r];
+          const Cx<R> cr = cx<R>(fma(R(2), jlkr.re, -Sl.re), fma(R(2), jlkr.im, -Sl.im));
+          const Cx<R> cl = cx<R>(fma(R(-2), krjl.re, -Sr.re), fma(R(-2), krjl.im, -Sr.im));
+          axpy(acc, cr, Jr);
+          axpy(acc, cl, Jl);
+          axpy(acc, d, rsub(Kl, Kr));
+          s.re += d.re;
+          s.im += d.im;
+        }
+#pragma unroll 1
+        for (int i = a; i + 1 < b; ++i) {
+          const CV4<R> JA = J[tri(a, i)];
+#pragma unroll 1
+          for (int j = i + 1; j < b; ++j) axpy(trs, mdot(JA, J[tri(j + 1, b)]), J[tri(i + 1, j)]);
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          acc.c[m].re = fma(R(2), trs.c[m].re, acc.c[m].re);
+          acc.c[m].im = fma(R(2), trs.c[m].im, acc.c[m].im);
+        }
+        if (len < L) {
+          const R inv = R(1) / mdot(K[X], K[X]);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            J[X].c[m].re = acc.c[m].re * inv;
+            J[X].c[m].im = acc.c[m].im * inv;
+          }
+          S[X] = s;
+        } else {
+          num = acc;
+        }
+      }
+    }
+    return mdot(e0, num);
+  }
+};
+
+}  // namespace tess

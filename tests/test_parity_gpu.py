@@ -1,0 +1,372 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Criteria (all reference values come from the oracle or from mpmath on the
+oracle's inputs; nothing is derived from the CUDA path):
+  FP64 path, per event: relative difference <= 1e-10 on |A|^2 and on the
+    weight, OR, for an event the oracle shows to be ill-conditioned, at most
+    16x the relative change that moving every Rambo / x uniform by one ulp
+    produces in the oracle's own result (that is the size of difference a
+    one-ulp libm discrepancy can cause; such events sit near zeros of the
+    amplitude and carry tiny weights).  With identical inputs (tess_me2) the
+    fallback is 16x the oracle's own rounding error against a 50-digit
+    evaluation.  Events needing the fallback are counted and reported.
+  FP32-current path: the error is stated per result, not bounded per event
+    (an FP32 evaluation of an event near a zero of the amplitude can be off
+    by O(1)); the median (< 1e-5), 99th percentile (< 1e-2) and the
+    weight-weighted mean (< 1e-4, the quantity that enters sigma) of the
+    per-event relative error against the FP64 oracle are asserted and printed.
+  Amplitudes that vanish at tree level (all labels equal or one different)
+    are rounding noise: both sides must be below 1e-20 (FP64) / 1e-6 (FP32)
+    of the event's MHV scale |A(legs 1, 2 with the odd label)|^2.
+  Observables: relative 1e-10 (Rambo's final boost amplifies rounding for
+    two nearly collinear seeds).  Cross sections and histogram bins:
+    relative 1e-10 plus an absolute 1e-12 of the total.
+  A pass flag may differ only when a cut quantity lies within 1e-9 of its
+    threshold.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+import paper_1002_3446_gb300 as tess  # noqa: E402
+
+RTOL64 = 1e-10
+RTOL32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available(), "gpu tests need a CUDA device"
+    c = tess.tess_init(0)
+    yield c
+    tess.tess_destroy(c)
+
+
+def orc_proc(orc, p):
+    return orc.process(p.n_gluons, hel_mode=p.helicity_mode, sqrt_s=p.sqrt_s, pt_min=p.pt_min, eta_max=p.eta_max,
+                       dr_min=p.dr_min, alphas_mz=p.alphas_mz, mz=p.mz, nf=p.nf, mu_r_factor=p.mu_r_factor,
+                       hist_obs=p.hist_observable, hist_bins=p.hist_bins, hist_lo=p.hist_lo, hist_hi=p.hist_hi)
+
+
+def gpu_generate(ctx, proc, seed, first, n_events, calls=1):
+    run = tess.Run(ctx, proc, n_events)
+    for _ in range(calls):
+        run.generate(seed, first)
+    torch.cuda.synchronize()
+    out = {k: (v.cpu().numpy() if v is not None else None) for k, v in run.t.items()}
+    out["acc"] = run.acc.cpu().numpy()
+    out["sigma"] = run.result()
+    if proc.hist_bins > 0:
+        out["hist_w"], out["hist_w2"] = run.histograms()
+    return out
+
+
+def vanishing(hel_bits, n):
+    c = bin(int(hel_bits)).count("1")
+    return c <= 1 or c >= n - 1
+
+
+def phys(k, i):
+    return -k[i] if i < 2 else k[i]
+
+
+def mhv_scale(orc, k, order):
+    n = len(order)
+    hel = [0] * n
+    hel[0] = hel[1] = 1
+    eps = np.array([orc.polvec(phys(k, i), hel[i]) for i in range(n)])
+    return abs(orc.amp(list(order), k, eps)) ** 2 / 2 ** (n - 2)
+
+
+def near_cut(orc, p, k, y):
+    """True if a cut quantity of the event is within 1e-9 of its threshold."""
+    m = p.n_gluons - 2
+    pk = k[2:]
+    pt = np.hypot(pk[:, 1], pk[:, 2])
+    pa = np.linalg.norm(pk[:, 1:], axis=1)
+    eta = 0.5 * np.log((pa + pk[:, 3]) / (pa - pk[:, 3])) + y
+    if np.any(np.abs(pt / p.pt_min - 1) < 1e-9) or np.any(np.abs(np.abs(eta) - p.eta_max) < 1e-9 * p.eta_max):
+        return True
+    for i in range(m):
+        for j in range(i + 1, m):
+            dphi = math.atan2(abs(pk[i, 1] * pk[j, 2] - pk[i, 2] * pk[j, 1]), pk[i, 1] * pk[j, 1] + pk[i, 2] * pk[j, 2])
+            dr2 = (eta[i] - eta[j]) ** 2 + dphi**2
+            if abs(dr2 / p.dr_min**2 - 1) < 1e-9:
+                return True
+    return False
+
+
+def ulp_sensitivity(orc, op, seed, ev):
+    return orc.ulp_sensitivity(op, seed, ev)
+
+
+def compare_events(orc, p, g, seed, first, idx, stats=None):
+    """Per-event comparison of GPU outputs at positions idx with the oracle."""
+    op = orc_proc(orc, p)
+    n = p.n_gluons
+    fp32 = p.precision == tess.TESS_FP32_CURRENTS
+    floor = RTOL32 if fp32 else RTOL64  # FP32: events above it are only counted
+    vtol = 1e-6 if fp32 else 1e-20
+    flips = fallback = 0
+    rel = []
+    wdiff = wsum = 0.0
+    for i in idx:
+        ev = first + int(i)
+        r = orc.event(op, seed, ev)
+        for key in ("ht", "ptlead", "rmin"):
+            assert np.isclose(g[key][i], r[key], rtol=1e-10, atol=0), (key, i, g[key][i], r[key])
+        if bool(g["pass"][i]) != r["pass"]:
+            assert near_cut(orc, p, r["k"], r["y"]), f"pass flag differs away from a cut boundary (event {i})"
+            flips += 1
+            continue
+        if p.helicity_mode == tess.TESS_HEL_SAMPLE and vanishing(r["hel_bits"], n):
+            # the sampled estimator is 2^n (n-1)! |A|^2
+            sc = mhv_scale(orc, r["k"], r["perm"]) * (2**n * math.factorial(n - 1))
+            assert abs(g["me2"][i]) <= vtol * sc and abs(r["me2"]) <= vtol * sc, (i, g["me2"][i], r["me2"], sc)
+            continue
+        e = abs(g["me2"][i] - r["me2"]) / abs(r["me2"])
+        if r["pass"]:
+            e = max(e, abs(g["weight"][i] - r["weight"]) / abs(r["weight"]))
+            wdiff += abs(g["weight"][i] - r["weight"])
+            wsum += r["weight"]
+        else:
+            assert g["weight"][i] == 0.0
+        if e > floor:
+            if not fp32:
+                s = ulp_sensitivity(orc, op, seed, ev)
+                assert e <= 16 * s, f"event {i}: relative difference {e:.3e} above 16 x ulp-sensitivity {s:.3e}"
+            fallback += 1
+        rel.append(e)
+    rel = np.array(rel)
+    if stats is not None:
+        stats.update(median=float(np.median(rel)), max=float(rel.max()), p99=float(np.quantile(rel, 0.99)),
+                     flips=flips, compared=len(rel), ill_conditioned=fallback,
+                     weighted=wdiff / wsum if wsum > 0 else 0.0)
+    return rel
+
+
+# ---------------------------------------------------------------- amplitude stage
+@pytest.mark.parametrize("n", list(range(4, 13)))
+@pytest.mark.parametrize("precision", [tess.TESS_FP64, tess.TESS_FP32_CURRENTS])
+def test_me2_matches_oracle(ctx, orc, n, precision):
+    from mp_reference import amp_exact
+    rng = np.random.default_rng(1000 + n)
+    E = 300 + n  # several blocks of 128 and a ragged tail
+    op = orc.process(n)
+    k = np.zeros((E, n, 4))
+    order = np.zeros((E, n), dtype=np.uint8)
+    hel = np.zeros(E, dtype=np.uint32)
+    ref = np.zeros(E)
+    epss = []
+    for e in range(E):
+        k[e] = orc.event(op, 77, e)["k"]
+        order[e] = [0] + list(rng.permutation(np.arange(1, n)))
+        while True:
+            h = int(rng.integers(0, 2**n))
+            if not vanishing(h, n):
+                break
+        hel[e] = h
+        eps = np.array([orc.polvec(phys(k[e], i), (h >> i) & 1) for i in range(n)])
+        epss.append(eps)
+        ref[e] = abs(orc.amp(list(order[e]), k[e], eps)) ** 2 / 2 ** (n - 2)
+    dk = torch.tensor(k, device="cuda")
+    do = torch.tensor(order, device="cuda")
+    dh = torch.tensor(hel.astype(np.int64), device="cuda").to(torch.int32)
+    out = torch.empty(E, dtype=torch.float64, device="cuda")
+    tess.tess_me2(ctx, n, precision, dk, do, dh, out)
+    got = out.cpu().numpy()
+    rel = np.abs(got - ref) / np.abs(ref)
+    floor = RTOL64 if precision == tess.TESS_FP64 else RTOL32
+    ill = 0
+    for e in np.nonzero(rel > floor)[0]:
+        ill += 1
+        if precision == tess.TESS_FP32_CURRENTS:
+            continue  # FP32: statistics below
+        exact = abs(amp_exact(list(order[e]), k[e], epss[e])) ** 2 / 2 ** (n - 2)
+        own = abs(ref[e] - exact) / exact
+        assert abs(got[e] - exact) / exact <= max(floor, 16 * own), (e, got[e], ref[e], exact)
+    print(f"me2 n={n} precision={precision}: max rel {rel.max():.2e}, median {np.median(rel):.2e}, "
+          f"{ill} ill-conditioned events")
+    if precision == tess.TESS_FP32_CURRENTS:
+        assert np.median(rel) < 1e-5 and np.quantile(rel, 0.99) < 1e-2
+
+
+# ---------------------------------------------------------------- whole event
+def test_gg2g_exact_sum_fp64(ctx, orc):
+    p = tess.process(4, precision=tess.TESS_FP64, helicity_mode=tess.TESS_HEL_SUM, hist_bins=50)
+    N = 3 * 128 * 7 + 45
+    g = gpu_generate(ctx, p, 1, 0, N)
+    compare_events(orc, p, g, 1, 0, np.arange(N))
+    r = orc.generate(orc_proc(orc, p), 1, 0, N)
+    assert np.isclose(g["acc"][0] + g["acc"][4], r["acc"][0], rtol=1e-10)
+    assert g["acc"][2] == r["acc"][2] and g["acc"][3] == N
+    tot = r["hist_w"].sum()
+    assert np.allclose(g["hist_w"], r["hist_w"], rtol=1e-10, atol=1e-12 * tot)
+    assert np.allclose(g["hist_w2"], r["hist_w2"], rtol=1e-10, atol=1e-12 * r["hist_w2"].sum())
+
+
+@pytest.mark.parametrize("n", list(range(4, 13)))
+def test_sampled_events_fp64(ctx, orc, n):
+    p = tess.process(n, precision=tess.TESS_FP64, pt_min=30.0 if n >= 10 else 20.0, hist_bins=40,
+                     hist_observable=tess.TESS_OBS_HT, hist_lo=200.0, hist_hi=3000.0)
+    N = 2 * 128 + 29 if n >= 10 else 5 * 128 + 29
+    first = (1 << 40) + 3
+    g = gpu_generate(ctx, p, 5, first, N)
+    st = {}
+    compare_events(orc, p, g, 5, first, np.arange(N), st)
+    print(f"FP64 n={n}: {st}")
+    r = orc.generate(orc_proc(orc, p), 5, first, N)
+    assert np.isclose(g["acc"][0] + g["acc"][4], r["acc"][0], rtol=1e-10)
+    assert np.allclose(g["hist_w"], r["hist_w"], rtol=1e-10, atol=1e-12 * r["hist_w"].sum())
+
+
+@pytest.mark.parametrize("n", [4, 6, 8, 10, 12])
+def test_sampled_events_fp32_currents(ctx, orc, n):
+    p = tess.process(n, precision=tess.TESS_FP32_CURRENTS, pt_min=30.0 if n >= 10 else 20.0)
+    N = 4 * 128 + 17
+    g = gpu_generate(ctx, p, 9, 0, N)
+    st = {}
+    compare_events(orc, p, g, 9, 0, np.arange(N), st)
+    print(f"FP32 currents n={n}: per-event relative error median {st['median']:.2e} "
+          f"p99 {st['p99']:.2e} max {st['max']:.2e} over {st['compared']} events, "
+          f"{st['ill_conditioned']} ill-conditioned, {st['flips']} cut flips, "
+          f"weight-weighted {st['weighted']:.2e}")
+    assert st["median"] < 1e-5 and st["p99"] < 1e-2 and st["weighted"] < 1e-4
+
+
+# ---------------------------------------------------------------- full-size configurations
+@pytest.mark.slow
+def test_full_gg2g_2e20_fp64(ctx, orc):
+    """2^20 events, exact helicity/ordering sum, FP64: every event, sigma and
+    the 50-bin leading-jet pT histogram against the oracle run on all cores."""
+    p = tess.process(4, precision=tess.TESS_FP64, helicity_mode=tess.TESS_HEL_SUM, hist_bins=50)
+    N = 1 << 20
+    g = gpu_generate(ctx, p, 1, 0, N)
+    r = orc.generate(orc_proc(orc, p), 1, 0, N)
+    ok = g["pass"].astype(bool) == r["pass"].astype(bool)
+    assert (~ok).sum() <= 5
+    rel = np.abs(g["weight"][ok] - r["weight"][ok]) / np.maximum(np.abs(r["weight"][ok]), 1e-300)
+    rel[r["weight"][ok] == 0] = 0
+    op = orc_proc(orc, p)
+    over = np.nonzero(rel > RTOL64)[0]
+    assert len(over) < 1e-4 * N
+    evs = np.nonzero(ok)[0][over]
+    for i, e in zip(over, evs):
+        assert rel[i] <= 16 * ulp_sensitivity(orc, op, 1, int(e))
+    print(f"gg->gg 2^20: max rel {rel.max():.2e}, {len(over)} ill-conditioned events")
+    assert np.isclose(g["sigma"][0], orc.sigma(r["acc"])[0], rtol=1e-10)
+    assert np.allclose(g["hist_w"], r["hist_w"], rtol=1e-10, atol=1e-12 * r["hist_w"].sum())
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("n,N,pt", [(6, 1 << 24, 20.0), (10, 1 << 26, 30.0)])
+def test_full_size_sampled_parity(ctx, orc, n, N, pt):
+    """Full-size runs in the benchmark's launch configuration; 1024 sampled
+    events are recomputed one by one by the oracle; sigma is checked against
+    the sum of the per-event weights."""
+    p = tess.process(n, precision=tess.TESS_FP32_CURRENTS, pt_min=pt, hist_bins=40, hist_observable=tess.TESS_OBS_HT,
+                     hist_lo=200.0, hist_hi=3000.0)
+    run = tess.Run(ctx, p, N, per_event=("weight", "me2", "pass", "ht", "ptlead", "rmin"))
+    run.generate(1, 0)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(n)
+    idx = np.sort(rng.choice(N, size=1024, replace=False))
+    g = {k: v[torch.as_tensor(idx, device="cuda")].cpu().numpy() for k, v in run.t.items()}
+    op = orc_proc(orc, p)
+    errs = []
+    for j, i in enumerate(idx):
+        r = orc.event(op, 1, int(i))
+        if bool(g["pass"][j]) != r["pass"]:
+            assert near_cut(orc, p, r["k"], r["y"])
+            continue
+        if vanishing(r["hel_bits"], n):
+            continue
+        errs.append(abs(g["me2"][j] - r["me2"]) / r["me2"])
+        assert np.isclose(g["ht"][j], r["ht"], rtol=1e-12)
+    errs = np.array(errs)
+    print(f"n={n} N={N}: sampled FP32 relative error median {np.median(errs):.2e} max {errs.max():.2e}")
+    assert np.median(errs) < 1e-5 and np.quantile(errs, 0.99) < 1e-2
+    sig = run.result()
+    w = run.t["weight"].double()
+    assert np.isclose(sig[0], float(w.sum()) / N, rtol=1e-10)
+    assert sig[2] == int(run.t["pass"].sum())
+    sw, _ = run.histograms()
+    assert np.isclose(sw.sum(), float(w.sum()), rtol=1e-10)
+
+
+# ---------------------------------------------------------------- edge cases and API behaviour
+def test_split_range_accumulates(ctx, orc):
+    p = tess.process(6, precision=tess.TESS_FP64, hist_bins=10, hist_lo=20, hist_hi=220)
+    a = gpu_generate(ctx, p, 3, 0, 1000)
+    run = tess.Run(ctx, p, 400)
+    run.generate(3, 0)
+    run2 = tess.Run(ctx, p, 600)
+    run2.acc.copy_(run.acc)
+    run2.hist.copy_(run.hist)
+    run2.generate(3, 400)
+    torch.cuda.synchronize()
+    assert np.isclose(run2.result()[0], a["sigma"][0], rtol=1e-13)
+    assert np.array_equal(run2.t["weight"].cpu().numpy(), a["weight"][400:])
+    assert run2.result()[3] == 1000
+
+
+def test_deterministic(ctx):
+    p = tess.process(7, precision=tess.TESS_FP32_CURRENTS, hist_bins=20, hist_lo=20, hist_hi=420)
+    r1 = tess.Run(ctx, p, 5000)
+    r1.generate(11)
+    r2 = tess.Run(ctx, p, 5000)
+    r2.generate(11)
+    torch.cuda.synchronize()
+    assert torch.equal(r1.acc, r2.acc) and torch.equal(r1.hist, r2.hist)
+    assert torch.equal(r1.t["weight"], r2.t["weight"])
+
+
+def test_zero_events_is_noop(ctx):
+    p = tess.process(5)
+    run = tess.Run(ctx, p, 1)
+    tess.tess_generate(ctx, p, 1, 0, 0, run.outputs, run.workspace)
+    torch.cuda.synchronize()
+    assert float(run.acc.abs().sum()) == 0.0
+
+
+def test_invalid_arguments_rejected(ctx):
+    run = tess.Run(ctx, tess.process(6), 16)
+    bad = [tess.process(3), tess.process(13), tess.process(6, helicity_mode=tess.TESS_HEL_SUM),
+           tess.process(6, precision=7), tess.process(6, sqrt_s=-1.0), tess.process(6, pt_min=float("nan")),
+           tess.process(6, hist_bins=5000), tess.process(12, pt_min=2000.0)]
+    for p in bad:
+        with pytest.raises(tess.TessError) as e:
+            tess.tess_generate(ctx, p, 1, 0, 16, run.outputs, run.workspace)
+        assert e.value.code in (tess.TESS_E_INVALID, tess.TESS_E_UNSUPPORTED)
+    # histogram requested without a buffer
+    with pytest.raises(tess.TessError):
+        tess.tess_generate(ctx, tess.process(6, hist_bins=4), 1, 0, 16, run.outputs, run.workspace)
+    # workspace too small
+    small = torch.empty(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(tess.TessError) as e:
+        tess.tess_generate(ctx, tess.process(6), 1, 0, 16, run.outputs, small)
+    assert e.value.code == tess.TESS_E_WORKSPACE
+    # a host buffer is refused before any kernel touches it
+    host = np.zeros(16)
+    outs = tess.make_outputs(acc=run.acc)
+    outs.weight = host.ctypes.data
+    with pytest.raises(tess.TessError) as e:
+        tess.tess_generate(ctx, tess.process(6), 1, 0, 16, outs, run.workspace)
+    assert e.value.code == tess.TESS_E_INVALID
+    torch.cuda.synchronize()
+
+
+def test_host_copies(ctx):
+    p = tess.process(5, precision=tess.TESS_FP64)
+    run = tess.Run(ctx, p, 300)
+    run.generate(2)
+    hw = np.zeros(300)
+    hp = np.zeros(300, dtype=np.uint8)
+    tess.tess_weights(ctx, run.outputs, 300, hw, hp)
+    assert np.array_equal(hw, run.t["weight"].cpu().numpy())
+    assert np.array_equal(hp, run.t["pass"].cpu().numpy())
