@@ -163,6 +163,31 @@ int tess_weights(tess_ctx *ctx, const tess_outputs *dev, uint64_t n_events, doub
 int tess_histograms(tess_ctx *ctx, const tess_process *proc, const double *hist, double *host_sumw,
                     double *host_sumw2, void *stream);
 
+/* ---- Allocation-free generation (no counterpart in the paper) ----------------
+ * Some callers cannot call cudaMalloc or give the library a workspace: for
+ * example a host program whose memory manager reserves the whole device at
+ * start-up and forbids other allocations, or a latency-critical loop that
+ * cannot afford an allocation's implicit device synchronisation.  For them,
+ * tess_generate_noalloc does exactly what tess_generate does (same outputs,
+ * same accumulation into acc / hist, which the caller still provides) but
+ * keeps its scratch -- the per-block partial sums -- in a fixed device array
+ * of TESS_NOALLOC_SCRATCH_BYTES that is part of the library.  Every GPU that
+ * loads the library holds that array until the process exits.
+ *   - It calls no cudaMalloc, cudaFree or allocating library routine.
+ *   - The first call on each device looks up the array's device address (a
+ *     one-time set-up with that device current); make that first call before
+ *     any stream capture.
+ *   - All calls share the one array: calls that overlap on the GPU (other
+ *     streams, other host threads) race and must be serialised by the caller.
+ *     Nothing in it needs clearing: each call writes every partial row that it
+ *     reads back.
+ *   - At most TESS_NOALLOC_MAX_BINS histogram bins; more is TESS_E_INVALID.
+ *     Other errors as tess_generate (no workspace errors).                  */
+#define TESS_NOALLOC_SCRATCH_BYTES (1u << 20)
+#define TESS_NOALLOC_MAX_BINS 254
+int tess_generate_noalloc(tess_ctx *ctx, const tess_process *proc, uint64_t seed, uint64_t first_event,
+                          uint64_t n_events, const tess_outputs *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,13 +27,14 @@ TESS_E_CUDA = -3
 TESS_E_WORKSPACE = -4
 TESS_E_NUMERICAL = -5
 TESS_MIN_N, TESS_MAX_N, TESS_MAX_BINS, TESS_ACC_LEN = 4, 12, 1024, 8
+TESS_NOALLOC_SCRATCH_BYTES, TESS_NOALLOC_MAX_BINS = 1 << 20, 254
 TESS_FP64, TESS_FP32_CURRENTS = 0, 1
 TESS_HEL_SUM, TESS_HEL_SAMPLE = 0, 1
 TESS_OBS_PTLEAD, TESS_OBS_HT, TESS_OBS_RMIN = 0, 1, 2
 
 # Every symbol include/tess.h declares (checked by the ABI tests).
 EXPORTED = ["tess_version", "tess_last_error", "tess_init", "tess_destroy", "tess_workspace_size", "tess_generate",
-            "tess_me2", "tess_result", "tess_weights", "tess_histograms"]
+            "tess_me2", "tess_result", "tess_weights", "tess_histograms", "tess_generate_noalloc"]
 
 
 class TessError(RuntimeError):
@@ -89,6 +90,7 @@ def _load():
         lib.tess_workspace_size.argtypes = [vp, P(tess_process), u64, P(ctypes.c_size_t)]
         lib.tess_generate.argtypes = [vp, P(tess_process), u64, u64, u64, P(tess_outputs), vp, ctypes.c_size_t, vp]
         lib.tess_me2.argtypes = [vp, i32, i32, u64, vp, vp, vp, vp, vp]
+        lib.tess_generate_noalloc.argtypes = [vp, P(tess_process), u64, u64, u64, P(tess_outputs), vp]
         lib.tess_result.argtypes = [vp, vp, P(ctypes.c_double), vp]
         lib.tess_weights.argtypes = [vp, P(tess_outputs), u64, vp, vp, vp, vp]
         lib.tess_histograms.argtypes = [vp, P(tess_process), vp, vp, vp, vp]
@@ -159,6 +161,13 @@ def tess_generate(ctx, proc, seed, first_event, n_events, outputs, workspace, st
     nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check(_load().tess_generate(ctx, ctypes.byref(proc), int(seed), int(first_event), int(n_events),
                                  ctypes.byref(outputs), ws, nbytes, _stream(stream)))
+
+
+def tess_generate_noalloc(ctx, proc, seed, first_event, n_events, outputs, stream=None):
+    """tess_generate without a workspace: for callers that cannot allocate
+    device memory (the scratch lives in a fixed array inside the library)."""
+    _check(_load().tess_generate_noalloc(ctx, ctypes.byref(proc), int(seed), int(first_event), int(n_events),
+                                         ctypes.byref(outputs), _stream(stream)))
 
 
 def tess_me2(ctx, n, precision, k, order, hel, me2, stream=None):

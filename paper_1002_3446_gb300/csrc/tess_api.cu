@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "tess.h"
@@ -365,3 +366,111 @@ int tess_histograms(tess_ctx *ctx, const tess_process *proc, const double *hist,
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free generation (tess_generate_noalloc).
+//
+// Callers that cannot call cudaMalloc or hand the library a workspace -- for
+// example a host program whose memory manager reserves the whole device at
+// start-up and forbids any other allocation, or a latency-critical loop that
+// cannot afford an allocation's implicit device synchronisation -- use this
+// variant.  It runs the fused event kernel with its per-block partial sums
+// in the fixed file-scope array below instead of a caller workspace.
+// The array (TESS_NOALLOC_SCRATCH_BYTES) lives on every GPU that loads this
+// library until the process exits.  In host code its name is only a host-side
+// stand-in, so its device address is looked up once per device (with that
+// device current) on the first call and cached.
+// ===========================================================================
+static __device__ __align__(256) double g_noalloc_partials[TESS_NOALLOC_SCRATCH_BYTES / sizeof(double)];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+// Device address of g_noalloc_partials on `device`, which must be current.
+int noalloc_scratch(int device, double **out) {
+  if (device < 0 || device >= kNoallocMaxDevices) return fail(TESS_E_INVALID, "device index %d too large", device);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[device]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+    g_noalloc_ptr[device] = (double *)p;
+  }
+  *out = g_noalloc_ptr[device];
+  return TESS_OK;
+}
+
+}  // namespace
+
+extern "C" int tess_generate_noalloc(tess_ctx *ctx, const tess_process *proc, uint64_t seed, uint64_t first_event,
+                                     uint64_t n_events, const tess_outputs *out, void *stream) {
+  if (!ctx) return fail(TESS_E_INVALID, "ctx is NULL");
+  int rc = check_process(proc);
+  if (rc) return rc;
+  if (proc->hist_bins > TESS_NOALLOC_MAX_BINS)
+    return fail(TESS_E_INVALID, "tess_generate_noalloc supports at most %d histogram bins (%d requested)",
+                TESS_NOALLOC_MAX_BINS, proc->hist_bins);
+  if (!out || !out->acc) return fail(TESS_E_INVALID, "outputs and outputs->acc must not be NULL");
+  if (proc->hist_bins > 0 && !out->hist) return fail(TESS_E_INVALID, "hist_bins > 0 needs outputs->hist");
+  if (n_events > (UINT64_MAX - first_event)) return fail(TESS_E_INVALID, "event range overflows 64 bits");
+  if (n_events == 0) return ok();
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  const void *ptrs[] = {out->weight, out->me2, out->pass, out->ht, out->ptlead, out->rmin, out->acc, out->hist};
+  const char *names[] = {"weight", "me2", "pass", "ht", "ptlead", "rmin", "acc", "hist"};
+  for (int i = 0; i < 8; ++i)
+    if ((rc = check_device_ptr(ptrs[i], ctx->device, names[i]))) return rc;
+  double *partials = nullptr;
+  if ((rc = noalloc_scratch(ctx->device, &partials))) return rc;
+
+  // Rows of partial sums that fit in the fixed array; every row the finalize
+  // step reads is written by this call's event kernel, so nothing in the
+  // array needs clearing between calls.
+  const int stride = tess::partial_stride(proc->hist_bins);
+  const int max_rows = (int)(TESS_NOALLOC_SCRATCH_BYTES / sizeof(double)) / stride;
+  int grid = grid_for(ctx, proc, n_events);
+  if (grid > max_rows) grid = max_rows;
+
+  const int n = proc->n_gluons, m = n - 2;
+  const bool sum = proc->helicity_mode == TESS_HEL_SUM;
+  tess::EventParams P;
+  memset(&P, 0, sizeof P);
+  P.seed = seed;
+  P.first_event = first_event;
+  P.n_events = n_events;
+  P.S = proc->sqrt_s * proc->sqrt_s;
+  P.lnxmin = std::log((m * proc->pt_min) * (m * proc->pt_min) / P.S);
+  P.pt_min = proc->pt_min;
+  P.eta_max = proc->eta_max;
+  P.dr2_min = proc->dr_min * proc->dr_min;
+  P.alphas_mz = proc->alphas_mz;
+  P.ln_mz2 = std::log(proc->mz * proc->mz);
+  P.b0 = (33.0 - 2.0 * proc->nf) / (12.0 * M_PI);
+  P.mu_r_factor = proc->mu_r_factor;
+  const double nc = 3.0;
+  P.wconst = std::pow(nc, n - 2) * (nc * nc - 1.0) / (256.0 * factorial(m)) * 0.3893793721e9;
+  P.phiconst = std::pow(2.0 * M_PI, 4.0 - 3.0 * m) * std::pow(M_PI / 2.0, m - 1.0) / (factorial(m - 1) * factorial(m - 2));
+  P.efac = sum ? 1.0 / std::ldexp(1.0, n - 2) : std::ldexp(1.0, n) * factorial(n - 1) / std::ldexp(1.0, n - 2);
+  P.hist_bins = proc->hist_bins;
+  P.hist_obs = proc->hist_observable;
+  P.hist_lo = proc->hist_lo;
+  P.hist_inv_width = proc->hist_bins > 0 ? proc->hist_bins / (proc->hist_hi - proc->hist_lo) : 0.0;
+  P.weight = out->weight;
+  P.me2 = out->me2;
+  P.pass = out->pass;
+  P.ht = out->ht;
+  P.ptlead = out->ptlead;
+  P.rmin = out->rmin;
+
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = proc->precision == TESS_FP64 ? tess::launch_generate_f64(n, sum, P, partials, grid, s)
+                                               : tess::launch_generate_f32(n, sum, P, partials, grid, s);
+  if (e != cudaSuccess) return cuda_fail(e, "event kernel launch");
+  tess::finalize_kernel<<<1, 256, 0, s>>>(partials, grid, proc->hist_bins, n_events, out->acc, out->hist);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "finalize kernel launch");
+  return ok();
+}
