@@ -30,9 +30,9 @@ sys.path.insert(0, ROOT)
 
 WORKLOADS = {
     # name: (n, events per GPU, pt_min, helicity mode, precision, hist (obs, bins, lo, hi))
-    "gg4g": dict(n=6, n_events=1 << 24, pt_min=20.0, hel="sample", precision="fp32", hist=None),
+    "gg4g": dict(n=6, n_events=1 << 24, pt_min=20.0, hel="sample", precision="ds", hist=None),
     "gg2g": dict(n=4, n_events=1 << 20, pt_min=20.0, hel="sum", precision="fp64", hist=(0, 50, 20.0, 1020.0)),
-    "gg8g": dict(n=10, n_events=1 << 26, pt_min=30.0, hel="sample", precision="fp32", hist=(1, 40, 200.0, 3000.0)),
+    "gg8g": dict(n=10, n_events=1 << 26, pt_min=30.0, hel="sample", precision="ds", hist=(1, 40, 200.0, 3000.0)),
 }
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5, from unit counts and clock
@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison measurement")
     ap.add_argument("--no-per-n", action="store_true", help="skip the per-multiplicity sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--events", type=int, default=0, help="override events per GPU (small cases for profiling)")
     return ap.parse_args()
 
 
@@ -117,7 +118,7 @@ class ClockSampler:
 # ------------------------------------------------------------------ tess arm
 def make_proc(tess, wl, precision=None):
     prec = precision or wl["precision"]
-    kw = dict(precision=tess.TESS_FP32_CURRENTS if prec == "fp32" else tess.TESS_FP64,
+    kw = dict(precision={"fp32": tess.TESS_FP32_CURRENTS, "ds": tess.TESS_FP32_DS, "fp64": tess.TESS_FP64}[prec],
               helicity_mode=tess.TESS_HEL_SUM if wl["hel"] == "sum" else tess.TESS_HEL_SAMPLE, pt_min=wl["pt_min"])
     if wl["hist"]:
         obs, nb, lo, hi = wl["hist"]
@@ -155,7 +156,9 @@ def run_tess(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.events:
+        wl["n_events"] = args.events
     n, N = wl["n"], wl["n_events"]
     ctx = tess.tess_init(local)
     proc = make_proc(tess, wl)
@@ -190,6 +193,16 @@ def run_tess(args):
     value = ws * N / (ms_per_step * 1e-3)
     sigma = run.result()
     acc = run.acc.clone()
+
+    # ---- per-stage device time (library-recorded CUDA events on the launch stream)
+    tess.tess_stage_timing(ctx, 1)
+    tess.tess_stage_times(ctx)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        run.reset()
+        run.generate(seed, first)
+    stages = tess.tess_stage_times(ctx)
+    tess.tess_stage_timing(ctx, 0)
     if dist:
         dist.all_reduce(acc, op=dist.ReduceOp.SUM)
 
@@ -219,7 +232,15 @@ def run_tess(args):
 
     # ---- FP64 plain form of the same workload, and the per-n sweep
     extra = {}
-    if not args.no_fp64 and wl["precision"] == "fp32" and rank == 0:
+    if wl["precision"] == "ds" and rank == 0:
+        p32 = make_proc(tess, wl, "fp32")
+        r32 = tess.Run(ctx, p32, N, per_event=("weight", "me2", "pass"))
+        ms = time_steps(torch, r32, seed, first, max(2, args.steps // 2), 2, flush)
+        extra["fp32_native_fp64_steps"] = {
+            "value": N / (statistics.mean(ms) * 1e-3), "ms_per_step": statistics.mean(ms),
+            "note": "TESS_FP32_CURRENTS: Rambo boost/rescale and polarisation Gram products in native FP64"}
+        del r32
+    if not args.no_fp64 and wl["precision"] in ("fp32", "ds") and rank == 0:
         p64 = make_proc(tess, wl, "fp64")
         n64 = N >> 3
         r64 = tess.Run(ctx, p64, n64, per_event=("weight", "me2", "pass"))
@@ -233,10 +254,10 @@ def run_tess(args):
         sweep = {}
         for nn in range(4, 13):
             row = {}
-            for prec in ("fp32", "fp64"):
+            for prec in ("ds", "fp32", "fp64"):
                 w2 = dict(wl, n=nn, pt_min=30.0 if nn >= 10 else 20.0, hel="sample", hist=None)
                 pp = make_proc(tess, w2, prec)
-                ne = (1 << 20) if prec == "fp32" else (1 << 16)
+                ne = (1 << 16) if prec == "fp64" else (1 << 20)
                 rr = tess.Run(ctx, pp, ne, per_event=("weight",))
                 ms = time_steps(torch, rr, seed, 0, 2, 1, flush)
                 ev = ne / (min(ms) * 1e-3)
@@ -250,10 +271,15 @@ def run_tess(args):
         cpu = cpu_baseline(wl, budget_s=12.0)
 
     if rank == 0:
-        achieved = tess.bg_flops(n) * N / (ms_per_step * 1e-3) / 1e12
+        amp_ms, amp_launches = stages["amplitude"]
+        if amp_launches == 0:  # exact-sum mode: one fused kernel
+            amp_ms, amp_launches = stages["fused"]
+        amp_ms_step = amp_ms / args.steps
+        achieved = tess.bg_flops(n) * N / (amp_ms_step * 1e-3) / 1e12
+        tot = sum(v[0] for v in stages.values()) or 1.0
         traffic = read_traffic(args.workload)
         line = {
-            "metric": f"events/s (gg->{n - 2}g, {n}-point, FP32 currents)",
+            "metric": f"events/s (gg->{n - 2}g, {n}-point, {'FP64' if wl['precision'] == 'fp64' else 'FP32 currents'})",
             "value": value,
             "unit": "events/s",
             "n_gpus": ws,
@@ -263,19 +289,28 @@ def run_tess(args):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f32 currents, f64 kinematics and accumulation",
+            "dtype": {"fp32": "f32 currents and cuts; f64 Rambo rescale, polarisations, accumulation",
+                      "ds": ("f32 currents and cuts; double-single (2 x f32) Rambo rescale and polarisation "
+                             "Gram products; f64 accumulation"),
+                      "fp64": "f64"}[wl["precision"]],
             "data": "synthetic (counter-based Philox draws, toy gluon PDF)",
             "config": {"workload": f"{args.workload}: gg->{n - 2} gluons, {N} events per GPU, seed 1, sqrt(S)=14 TeV, "
                                    f"pT>{wl['pt_min']:g} |eta|<2.5 dR>0.4, helicity+ordering sampled",
                        "events_per_gpu": N, "n_gluons": n, "l2": "flushed between timed steps (256 MB write)"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts and clock)",
-                         "flops_per_event": tess.bg_flops(n),
-                         "timed": "tess_generate (fused event kernel + 1-block finalize), CUDA events"},
+            "roofline": {"bound": "alu", "kernel": "Berends-Giele amplitude kernel", "achieved": achieved,
+                         "peak": FP64_PEAK_TFLOPS if wl["precision"] == "fp64" else FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s",
+                         "frac": achieved / (FP64_PEAK_TFLOPS if wl["precision"] == "fp64" else FP32_PEAK_TFLOPS),
+                         "traffic": traffic,
+                         "peak_source": ("152 SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts and clock); "
+                                         "an FMA probe measured 78.2 FP32 / 1.25 FP64 TFLOP/s"),
+                         "flops_per_event": tess.bg_flops(n), "ms_per_step": amp_ms_step,
+                         "launches_per_step": amp_launches // args.steps,
+                         "timed": "CUDA events recorded by the library around each amplitude launch"},
+            "stage_share": {k: v[0] / tot for k, v in stages.items() if v[1] > 0},
             "e2e": {"value": ws * N / e2e_s, "unit": "events/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": N * 9 + 64},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": tess.tess_kernel_launches(ctx, proc, N) * args.steps,
             "clocks": clk.summary(),
             "sigma_pb": float((acc[0] + acc[4]).item() / (ws * N)),
             "cpu_baseline": cpu,

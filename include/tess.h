@@ -13,7 +13,7 @@
  *   - Return value: TESS_OK (0) on success, a negative TESS_E_* code on
  *     failure; tess_last_error() then returns a message (thread-local).
  *   - Memory: the library allocates no device memory in tess_generate,
- *     tess_me2 or tess_generate_batched.  The caller owns every buffer; device
+ *     tess_me2, tess_generate_batched or tess_autotune.  The caller owns every buffer; device
  *     pointers are plain CUDA device addresses (e.g. from cudaMalloc or a
  *     torch tensor) on the context's device.  Host pointers are marked "host".
  *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
@@ -46,9 +46,15 @@ extern "C" {
 
 /* precision */
 #define TESS_FP64 0          /* every step in FP64                                 */
-#define TESS_FP32_CURRENTS 1 /* Berends-Giele currents and vertex contractions in
-                                FP32 on momenta in units of sqrt(s_hat); momenta,
-                                polarisation vectors and accumulation in FP64     */
+#define TESS_FP32_CURRENTS 1 /* Berends-Giele currents, vertex contractions, Rambo
+                                seeds, cuts and observables in FP32; Rambo's boost
+                                and rescale, the polarisation Gram products and
+                                the accumulation in native FP64                   */
+#define TESS_FP32_DS 2       /* as TESS_FP32_CURRENTS, but the Rambo boost/rescale
+                                and the Gram products in double-single (two-float,
+                                ~47-bit) arithmetic on the FP32 pipe instead of
+                                native FP64, which runs at 1/64 of the FP32 rate
+                                on GB300; accumulation stays FP64               */
 /* helicity_mode */
 #define TESS_HEL_SUM 0    /* exact sum over 2^n helicities and (n-1)! orderings (n <= 5) */
 #define TESS_HEL_SAMPLE 1 /* one helicity configuration and colour ordering per event,
@@ -62,7 +68,7 @@ extern "C" {
  * pT > pt_min, |eta| < eta_max, Delta R > dr_min).  Units: GeV. */
 typedef struct tess_process {
   int32_t n_gluons;        /* total gluons, TESS_MIN_N..TESS_MAX_N            */
-  int32_t precision;       /* TESS_FP64 or TESS_FP32_CURRENTS                 */
+  int32_t precision;       /* TESS_FP64, TESS_FP32_CURRENTS or TESS_FP32_DS   */
   int32_t helicity_mode;   /* TESS_HEL_SUM or TESS_HEL_SAMPLE                 */
   int32_t hist_observable; /* TESS_OBS_*                                      */
   int32_t hist_bins;       /* 0 = no histogram, else 1..TESS_MAX_BINS         */
@@ -117,9 +123,14 @@ int tess_init(int device, tess_ctx **ctx);
 void tess_destroy(tess_ctx *ctx);
 
 /* Bytes of device workspace tess_generate needs for this process and event
- * count (per-block partial sums of the accumulation).  0 is never returned
- * for a valid process. */
+ * count: per-block partial sums of the accumulation and, for sampled
+ * helicities, one L2-sized chunk of per-event amplitude inputs.  0 is never
+ * returned for a valid process. */
 int tess_workspace_size(const tess_ctx *ctx, const tess_process *proc, uint64_t n_events, size_t *bytes);
+
+/* Number of kernel launches one tess_generate call with these arguments
+ * makes (for launch accounting and graph sizing). */
+int tess_kernel_launches(const tess_ctx *ctx, const tess_process *proc, uint64_t n_events, int *launches);
 
 /* Generate events [first_event, first_event + n_events) of the counter-based
  * stream `seed` (Sec. 3 stages: phase space, phase-space weight, matrix-
@@ -133,6 +144,50 @@ int tess_generate(tess_ctx *ctx, const tess_process *proc, uint64_t seed, uint64
                   uint64_t n_events, const tess_outputs *out, void *workspace, size_t workspace_bytes,
                   void *stream);
 
+/* ---- Stage timing ----------------------------------------------------------------
+ * With timing enabled, tess_generate records a CUDA event pair on its stream
+ * around every launch it makes; tess_stage_times synchronises on them and
+ * returns the summed device time (ms) and launch count per stage since the
+ * previous read: [0] kinematics kernel, [1] amplitude kernel, [2] finalize,
+ * [3] fused event kernel (exact-sum mode).  Events only; no device memory. */
+int tess_stage_timing(tess_ctx *ctx, int enable);
+int tess_stage_times(tess_ctx *ctx, double *ms /* [4] */, int *launches /* [4] */);
+
+/* ---- Batched mixed multiplicities -------------------------------------------
+ * n_proc (1..16) processes -- typically gg -> 2..10 gluons with different
+ * event counts -- in one call.  Process i generates events
+ * [first_events[i], first_events[i] + n_events[i]) of stream seeds[i] into
+ * outs[i] (accumulating into its acc/hist, as tess_generate).  The per-process
+ * pipelines are recorded as parallel branches of one CUDA graph, captured on
+ * internal streams the first time an argument set is seen and replayed on
+ * `stream` after that, so a batch is a single graph launch whose branches
+ * overlap on the GPU (the tail of one multiplicity is filled with work of
+ * another).  Capture happens inside this call; do not call it while `stream`
+ * is being captured.  workspace: tess_workspace_size_batched() bytes (the
+ * per-process workspaces back to back).  Errors as tess_generate. */
+int tess_workspace_size_batched(const tess_ctx *ctx, int n_proc, const tess_process *procs,
+                                const uint64_t *n_events, size_t *bytes);
+int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, const uint64_t *seeds,
+                          const uint64_t *first_events, const uint64_t *n_events, const tess_outputs *outs,
+                          void *workspace, size_t workspace_bytes, void *stream);
+
+/* ---- Amplitude-kernel autotuner ------------------------------------------------
+ * Times every amplitude-kernel variant built for (precision, n) of proc on
+ * probe_events sampled events and makes the fastest the context's choice for
+ * later calls with that (precision, n).  Variants (all one thread per event):
+ * TESS_K2_REG (current table in registers), TESS_K2_ROWS32 / TESS_K2_ROWS64
+ * (current row in registers, older rows in shared memory, 32 / 64 threads per
+ * block), TESS_K2_LOOP (FP64 loop form).  acc_scratch: device, TESS_ACC_LEN
+ * doubles (overwritten); workspace: tess_workspace_size(proc, probe_events)
+ * bytes -- that size already covers every variant.  *form_out receives the
+ * chosen TESS_K2_* (-1 for the exact-sum mode, which has one kernel). */
+#define TESS_K2_REG 0
+#define TESS_K2_ROWS32 1
+#define TESS_K2_ROWS64 2
+#define TESS_K2_LOOP 3
+int tess_autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events, double *acc_scratch,
+                  void *workspace, size_t workspace_bytes, void *stream, int *form_out);
+
 /* Colour-ordered matrix elements for caller-given kinematics (the
  * matrix-element stage alone, Eq. (BG-recursion) and the amplitude
  * equation of Sec. 3):  me2[e] = |A(order_e; hel_e)|^2 with
@@ -144,7 +199,7 @@ int tess_generate(tess_ctx *ctx, const tess_process *proc, uint64_t seed, uint64
  *   hel    device, [n_events] uint32: bit i = helicity label of leg i (0 ->
  *          eps_+ of the leg's physical direction, 1 -> eps_-)
  *   me2    device, [n_events] doubles (output)
- * precision: TESS_FP64 or TESS_FP32_CURRENTS.                               */
+ * precision: TESS_FP64, or TESS_FP32_CURRENTS / TESS_FP32_DS (FP32 currents). */
 int tess_me2(tess_ctx *ctx, int n, int precision, uint64_t n_events, const double *k, const uint8_t *order,
              const uint32_t *hel, double *me2, void *stream);
 

@@ -28,13 +28,16 @@ TESS_E_WORKSPACE = -4
 TESS_E_NUMERICAL = -5
 TESS_MIN_N, TESS_MAX_N, TESS_MAX_BINS, TESS_ACC_LEN = 4, 12, 1024, 8
 TESS_NOALLOC_SCRATCH_BYTES, TESS_NOALLOC_MAX_BINS = 1 << 20, 254
-TESS_FP64, TESS_FP32_CURRENTS = 0, 1
+TESS_FP64, TESS_FP32_CURRENTS, TESS_FP32_DS = 0, 1, 2
 TESS_HEL_SUM, TESS_HEL_SAMPLE = 0, 1
 TESS_OBS_PTLEAD, TESS_OBS_HT, TESS_OBS_RMIN = 0, 1, 2
+TESS_K2_REG, TESS_K2_ROWS32, TESS_K2_ROWS64, TESS_K2_LOOP = 0, 1, 2, 3
 
 # Every symbol include/tess.h declares (checked by the ABI tests).
 EXPORTED = ["tess_version", "tess_last_error", "tess_init", "tess_destroy", "tess_workspace_size", "tess_generate",
-            "tess_me2", "tess_result", "tess_weights", "tess_histograms", "tess_generate_noalloc"]
+            "tess_me2", "tess_result", "tess_weights", "tess_histograms", "tess_generate_noalloc",
+            "tess_kernel_launches", "tess_workspace_size_batched", "tess_generate_batched", "tess_autotune",
+            "tess_stage_timing", "tess_stage_times"]
 
 
 class TessError(RuntimeError):
@@ -88,6 +91,13 @@ def _load():
         lib.tess_destroy.argtypes = [vp]
         lib.tess_destroy.restype = None
         lib.tess_workspace_size.argtypes = [vp, P(tess_process), u64, P(ctypes.c_size_t)]
+        lib.tess_kernel_launches.argtypes = [vp, P(tess_process), u64, P(ctypes.c_int)]
+        lib.tess_workspace_size_batched.argtypes = [vp, i32, P(tess_process), P(u64), P(ctypes.c_size_t)]
+        lib.tess_generate_batched.argtypes = [vp, i32, P(tess_process), P(u64), P(u64), P(u64), P(tess_outputs), vp,
+                                              ctypes.c_size_t, vp]
+        lib.tess_autotune.argtypes = [vp, P(tess_process), u64, vp, vp, ctypes.c_size_t, vp, P(ctypes.c_int)]
+        lib.tess_stage_timing.argtypes = [vp, i32]
+        lib.tess_stage_times.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int)]
         lib.tess_generate.argtypes = [vp, P(tess_process), u64, u64, u64, P(tess_outputs), vp, ctypes.c_size_t, vp]
         lib.tess_me2.argtypes = [vp, i32, i32, u64, vp, vp, vp, vp, vp]
         lib.tess_generate_noalloc.argtypes = [vp, P(tess_process), u64, u64, u64, P(tess_outputs), vp]
@@ -149,6 +159,54 @@ def tess_workspace_size(ctx, proc, n_events):
     b = ctypes.c_size_t()
     _check(_load().tess_workspace_size(ctx, ctypes.byref(proc), int(n_events), ctypes.byref(b)))
     return b.value
+
+
+def tess_kernel_launches(ctx, proc, n_events):
+    c = ctypes.c_int()
+    _check(_load().tess_kernel_launches(ctx, ctypes.byref(proc), int(n_events), ctypes.byref(c)))
+    return c.value
+
+
+def _u64s(xs):
+    return (ctypes.c_uint64 * len(xs))(*[int(x) for x in xs])
+
+
+def tess_workspace_size_batched(ctx, procs, n_events):
+    arr = (tess_process * len(procs))(*procs)
+    b = ctypes.c_size_t()
+    _check(_load().tess_workspace_size_batched(ctx, len(procs), arr, _u64s(n_events), ctypes.byref(b)))
+    return b.value
+
+
+def tess_generate_batched(ctx, procs, seeds, first_events, n_events, outputs, workspace, stream=None):
+    k = len(procs)
+    arr = (tess_process * k)(*procs)
+    outs = (tess_outputs * k)(*outputs)
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(_load().tess_generate_batched(ctx, k, arr, _u64s(seeds), _u64s(first_events), _u64s(n_events), outs,
+                                         _ptr(workspace), nbytes, _stream(stream)))
+
+
+def tess_autotune(ctx, proc, probe_events, acc_scratch, workspace, stream=None):
+    f = ctypes.c_int()
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(_load().tess_autotune(ctx, ctypes.byref(proc), int(probe_events), _ptr(acc_scratch), _ptr(workspace),
+                                 nbytes, _stream(stream), ctypes.byref(f)))
+    return f.value
+
+
+STAGES = ("kinematics", "amplitude", "finalize", "fused")
+
+
+def tess_stage_timing(ctx, enable):
+    _check(_load().tess_stage_timing(ctx, int(bool(enable))))
+
+
+def tess_stage_times(ctx):
+    ms = (ctypes.c_double * 4)()
+    n = (ctypes.c_int * 4)()
+    _check(_load().tess_stage_times(ctx, ms, n))
+    return {STAGES[i]: (ms[i], n[i]) for i in range(4)}
 
 
 def make_outputs(weight=None, me2=None, pass_=None, ht=None, ptlead=None, rmin=None, acc=None, hist=None):

@@ -6,9 +6,11 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "tess.h"
 #include "tess_kernels.cuh"
+#include "tess_pipe_launch.cuh"
 
 namespace tess {
 cudaError_t launch_generate_f64(int n, bool sum, const EventParams &P, double *partials, int grid, cudaStream_t s);
@@ -19,6 +21,18 @@ cudaError_t launch_me2_f64(int n, uint64_t n_events, const double *k, const uint
                            double *me2, cudaStream_t s);
 cudaError_t launch_me2_f32(int n, uint64_t n_events, const double *k, const uint8_t *order, const uint32_t *hel,
                            double *me2, cudaStream_t s);
+int plan_pipeline_f64(int n, int sm_count, uint64_t n_events, int hist_bins, int form, PipePlan *pl);
+int plan_pipeline_f32a(int n, int sm_count, uint64_t n_events, int hist_bins, int form, PipePlan *pl);
+int plan_pipeline_f32b(int n, int sm_count, uint64_t n_events, int hist_bins, int form, PipePlan *pl);
+int plan_pipeline_f32c(int n, int sm_count, uint64_t n_events, int hist_bins, int form, PipePlan *pl);
+cudaError_t run_pipeline_f64(int n, const EventParams &P, const PipePlan &pl, char *ws, cudaStream_t s,
+                             const StageHook *hook);
+cudaError_t run_pipeline_f32a(int n, const EventParams &P, const PipePlan &pl, char *ws, cudaStream_t s,
+                             const StageHook *hook);
+cudaError_t run_pipeline_f32b(int n, const EventParams &P, const PipePlan &pl, char *ws, cudaStream_t s,
+                             const StageHook *hook);
+cudaError_t run_pipeline_f32c(int n, const EventParams &P, const PipePlan &pl, char *ws, cudaStream_t s,
+                             const StageHook *hook);
 // Neumaier-compensated addition (s, c) += x.
 __device__ __forceinline__ void comp_add(double &s, double &c, double x) {
   const double t = s + x;
@@ -63,9 +77,29 @@ __global__ void finalize_kernel(const double *__restrict__ partials, int nblocks
 
 }  // namespace tess
 
+constexpr int kMaxBranches = 16;
+
 struct tess_ctx {
-  int device;
-  int sm_count;
+  int device = 0;
+  int sm_count = 1;
+  // tuned amplitude-kernel variant per (precision, n); -1 = built-in default
+  int form[2][TESS_MAX_N + 1];
+  // batched generation: capture streams, fork/join events, cached graph
+  cudaStream_t cap_stream = nullptr;
+  cudaStream_t branch[kMaxBranches] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kMaxBranches] = {};
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<unsigned char> graph_key;
+  // opt-in stage timing: event pairs recorded around each launch
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_marks;
+  cudaEvent_t ev_open[4] = {};
+  tess_ctx() {
+    for (auto &row : form)
+      for (int &f : row) f = -1;
+  }
 };
 
 namespace {
@@ -114,8 +148,9 @@ int check_process(const tess_process *p) {
   if (!p) return fail(TESS_E_INVALID, "process is NULL");
   if (p->n_gluons < TESS_MIN_N || p->n_gluons > TESS_MAX_N)
     return fail(TESS_E_UNSUPPORTED, "n_gluons = %d outside %d..%d", p->n_gluons, TESS_MIN_N, TESS_MAX_N);
-  if (p->precision != TESS_FP64 && p->precision != TESS_FP32_CURRENTS)
-    return fail(TESS_E_INVALID, "precision = %d is not TESS_FP64 or TESS_FP32_CURRENTS", p->precision);
+  if (p->precision != TESS_FP64 && p->precision != TESS_FP32_CURRENTS && p->precision != TESS_FP32_DS)
+    return fail(TESS_E_INVALID, "precision = %d is not TESS_FP64, TESS_FP32_CURRENTS or TESS_FP32_DS",
+                p->precision);
   if (p->helicity_mode != TESS_HEL_SUM && p->helicity_mode != TESS_HEL_SAMPLE)
     return fail(TESS_E_INVALID, "helicity_mode = %d is not TESS_HEL_SUM or TESS_HEL_SAMPLE", p->helicity_mode);
   if (p->helicity_mode == TESS_HEL_SUM && p->n_gluons > 5)
@@ -170,71 +205,79 @@ double factorial(int k) {
   return f;
 }
 
-}  // namespace
+// Sampled helicity/ordering runs the two-kernel pipeline; the exact sum runs
+// the fused kernel.
+bool uses_pipeline(const tess_process *p) { return p->helicity_mode == TESS_HEL_SAMPLE; }
 
-extern "C" {
-
-const char *tess_version(void) { return "tess-gb300 0.1"; }
-
-const char *tess_last_error(void) { return g_error.c_str(); }
-
-int tess_init(int device, tess_ctx **ctx) {
-  if (!ctx) return fail(TESS_E_INVALID, "ctx is NULL");
-  *ctx = nullptr;
-  int count = 0;
-  cudaError_t e = cudaGetDeviceCount(&count);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
-  if (device < 0 || device >= count) return fail(TESS_E_INVALID, "device %d outside 0..%d", device, count - 1);
-  int major = 0, minor = 0, sms = 0;
-  if ((e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device)) != cudaSuccess ||
-      (e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device)) != cudaSuccess ||
-      (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess)
-    return cuda_fail(e, "cudaDeviceGetAttribute");
-  if (major != 10 || minor != 3)
-    return fail(TESS_E_UNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a (GB300) only", device,
-                major, minor);
-  *ctx = new tess_ctx{device, sms};
-  return ok();
+int plan_with_form(const tess_ctx *ctx, const tess_process *p, uint64_t n_events, int form, tess::PipePlan *pl) {
+  const int n = p->n_gluons;
+  int rc;
+  if (p->precision == TESS_FP64)
+    rc = tess::plan_pipeline_f64(n, ctx->sm_count, n_events, p->hist_bins, form, pl);
+  else if (n <= 7)
+    rc = tess::plan_pipeline_f32a(n, ctx->sm_count, n_events, p->hist_bins, form, pl);
+  else if (n <= 10)
+    rc = tess::plan_pipeline_f32b(n, ctx->sm_count, n_events, p->hist_bins, form, pl);
+  else
+    rc = tess::plan_pipeline_f32c(n, ctx->sm_count, n_events, p->hist_bins, form, pl);
+  if (rc) return fail(TESS_E_CUDA, "could not size the pipeline kernels (occupancy query failed)");
+  return TESS_OK;
 }
 
-void tess_destroy(tess_ctx *ctx) { delete ctx; }
-
-int tess_workspace_size(const tess_ctx *ctx, const tess_process *proc, uint64_t n_events, size_t *bytes) {
-  if (!ctx || !bytes) return fail(TESS_E_INVALID, "ctx and bytes must not be NULL");
-  int rc = check_process(proc);
-  if (rc) return rc;
-  DeviceGuard g(ctx->device);
-  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
-  const int grid = grid_for(ctx, proc, n_events);
-  *bytes = (size_t)grid * (size_t)tess::partial_stride(proc->hist_bins) * sizeof(double);
-  return ok();
+int pipeline_plan(const tess_ctx *ctx, const tess_process *p, uint64_t n_events, tess::PipePlan *pl) {
+  return plan_with_form(ctx, p, n_events, ctx->form[p->precision == TESS_FP64 ? 0 : 1][p->n_gluons], pl);
 }
 
-int tess_generate(tess_ctx *ctx, const tess_process *proc, uint64_t seed, uint64_t first_event, uint64_t n_events,
-                  const tess_outputs *out, void *workspace, size_t workspace_bytes, void *stream) {
-  if (!ctx) return fail(TESS_E_INVALID, "ctx is NULL");
-  int rc = check_process(proc);
-  if (rc) return rc;
-  if (!out || !out->acc) return fail(TESS_E_INVALID, "outputs and outputs->acc must not be NULL");
-  if (proc->hist_bins > 0 && !out->hist) return fail(TESS_E_INVALID, "hist_bins > 0 needs outputs->hist");
-  if (n_events > (UINT64_MAX - first_event)) return fail(TESS_E_INVALID, "event range overflows 64 bits");
-  if (n_events == 0) return ok();
-  DeviceGuard g(ctx->device);
-  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
-  const void *ptrs[] = {out->weight, out->me2, out->pass, out->ht, out->ptlead, out->rmin, out->acc, out->hist,
-                        workspace};
-  const char *names[] = {"weight", "me2", "pass", "ht", "ptlead", "rmin", "acc", "hist", "workspace"};
-  for (int i = 0; i < 9; ++i)
-    if ((rc = check_device_ptr(ptrs[i], ctx->device, names[i]))) return rc;
-  const int grid = grid_for(ctx, proc, n_events);
-  const size_t need = (size_t)grid * (size_t)tess::partial_stride(proc->hist_bins) * sizeof(double);
-  if (!workspace || workspace_bytes < need)
-    return fail(TESS_E_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, workspace ? workspace_bytes : 0);
-  if (((uintptr_t)workspace) % 256 != 0) return fail(TESS_E_WORKSPACE, "workspace must be 256-byte aligned");
+// Workspace of the largest amplitude-kernel variant, so that tuning never
+// needs a larger workspace than the one sized before it.
+int pipeline_bytes_any_form(const tess_ctx *ctx, const tess_process *p, uint64_t n_events, size_t *bytes) {
+  size_t best = 0;
+  for (int f = 0; f < tess::K2_NFORMS; ++f) {
+    tess::PipePlan pl;
+    const int rc = plan_with_form(ctx, p, n_events, f, &pl);
+    if (rc) return rc;
+    if (pl.bytes > best) best = pl.bytes;
+  }
+  *bytes = best;
+  return TESS_OK;
+}
 
+cudaError_t pipeline_run(const tess_process *p, const tess::EventParams &P, const tess::PipePlan &pl, char *ws,
+                         cudaStream_t s, const tess::StageHook *hook) {
+  const int n = p->n_gluons;
+  if (p->precision == TESS_FP64) return tess::run_pipeline_f64(n, P, pl, ws, s, hook);
+  if (n <= 7) return tess::run_pipeline_f32a(n, P, pl, ws, s, hook);
+  if (n <= 10) return tess::run_pipeline_f32b(n, P, pl, ws, s, hook);
+  return tess::run_pipeline_f32c(n, P, pl, ws, s, hook);
+}
+
+// Stage timing hook: records an event before and after each launch.
+void stage_mark(void *self, int kind, bool begin, cudaStream_t s) {
+  tess_ctx *ctx = (tess_ctx *)self;
+  cudaEvent_t e = nullptr;
+  if (!ctx->ev_free.empty()) {
+    e = ctx->ev_free.back();
+    ctx->ev_free.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    return;
+  }
+  cudaEventRecord(e, s);
+  if (begin) {
+    ctx->ev_open[kind] = e;
+  } else if (ctx->ev_open[kind]) {
+    ctx->ev_marks.push_back({kind, {ctx->ev_open[kind], e}});
+    ctx->ev_open[kind] = nullptr;
+  } else {
+    ctx->ev_free.push_back(e);
+  }
+}
+
+// Launch constants of one generation call.
+void fill_params(const tess_process *proc, uint64_t seed, uint64_t first_event, uint64_t n_events,
+                 const tess_outputs *out, tess::EventParams *Pp) {
+  tess::EventParams &P = *Pp;
   const int n = proc->n_gluons, m = n - 2;
   const bool sum = proc->helicity_mode == TESS_HEL_SUM;
-  tess::EventParams P;
   memset(&P, 0, sizeof P);
   P.seed = seed;
   P.first_event = first_event;
@@ -262,15 +305,383 @@ int tess_generate(tess_ctx *ctx, const tess_process *proc, uint64_t seed, uint64
   P.ht = out->ht;
   P.ptlead = out->ptlead;
   P.rmin = out->rmin;
+  P.kin_ds = proc->precision == TESS_FP32_DS;
+  P.S_hi = (float)P.S;
+  P.S_lo = (float)(P.S - (double)P.S_hi);
+  P.wk = P.wconst * P.lnxmin * P.lnxmin * P.phiconst * 0.5;
+}
 
-  cudaStream_t s = (cudaStream_t)stream;
-  double *partials = (double *)workspace;
-  cudaError_t e = proc->precision == TESS_FP64 ? tess::launch_generate_f64(n, sum, P, partials, grid, s)
-                                               : tess::launch_generate_f32(n, sum, P, partials, grid, s);
-  if (e != cudaSuccess) return cuda_fail(e, "event kernel launch");
-  tess::finalize_kernel<<<1, 256, 0, s>>>(partials, grid, proc->hist_bins, n_events, out->acc, out->hist);
+}  // namespace
+
+extern "C" {
+
+const char *tess_version(void) { return "tess-gb300 0.1"; }
+
+const char *tess_last_error(void) { return g_error.c_str(); }
+
+int tess_init(int device, tess_ctx **ctx) {
+  if (!ctx) return fail(TESS_E_INVALID, "ctx is NULL");
+  *ctx = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= count) return fail(TESS_E_INVALID, "device %d outside 0..%d", device, count - 1);
+  int major = 0, minor = 0, sms = 0;
+  if ((e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess)
+    return cuda_fail(e, "cudaDeviceGetAttribute");
+  if (major != 10 || minor != 3)
+    return fail(TESS_E_UNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a (GB300) only", device,
+                major, minor);
+  tess_ctx *c = new tess_ctx();
+  c->device = device;
+  c->sm_count = sms;
+  *ctx = c;
+  return ok();
+}
+
+void tess_destroy(tess_ctx *ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  for (int i = 0; i < kMaxBranches; ++i) {
+    if (ctx->branch[i]) cudaStreamDestroy(ctx->branch[i]);
+    if (ctx->join_ev[i]) cudaEventDestroy(ctx->join_ev[i]);
+  }
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);
+  for (auto &m : ctx->ev_marks) {
+    cudaEventDestroy(m.second.first);
+    cudaEventDestroy(m.second.second);
+  }
+  delete ctx;
+}
+
+int tess_workspace_size(const tess_ctx *ctx, const tess_process *proc, uint64_t n_events, size_t *bytes) {
+  if (!ctx || !bytes) return fail(TESS_E_INVALID, "ctx and bytes must not be NULL");
+  int rc = check_process(proc);
+  if (rc) return rc;
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  if (uses_pipeline(proc)) {
+    if ((rc = pipeline_bytes_any_form(ctx, proc, n_events, bytes))) return rc;
+    return ok();
+  }
+  const int grid = grid_for(ctx, proc, n_events);
+  *bytes = (size_t)grid * (size_t)tess::partial_stride(proc->hist_bins) * sizeof(double);
+  return ok();
+}
+
+int tess_kernel_launches(const tess_ctx *ctx, const tess_process *proc, uint64_t n_events, int *launches) {
+  if (!ctx || !launches) return fail(TESS_E_INVALID, "ctx and launches must not be NULL");
+  int rc = check_process(proc);
+  if (rc) return rc;
+  if (n_events == 0) {
+    *launches = 0;
+    return ok();
+  }
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  if (uses_pipeline(proc)) {
+    tess::PipePlan pl;
+    if ((rc = pipeline_plan(ctx, proc, n_events, &pl))) return rc;
+    *launches = 2 * pl.chunks + 1;  // (kinematics, amplitude) per chunk + finalize
+  } else {
+    *launches = 2;  // fused event kernel + finalize
+  }
+  return ok();
+}
+
+}  // extern "C"
+
+namespace {
+
+// A validated, planned generation call: everything tess_generate needs except
+// the stream.  Built outside any stream capture; launching it only enqueues
+// memsets and kernels.
+struct Prepared {
+  tess::EventParams P;
+  bool pipeline = false;
+  bool sum = false;
+  tess::PipePlan pl;
+  int grid = 1;
+  const tess_process *proc = nullptr;
+  void *workspace = nullptr;
+  double *acc = nullptr, *hist = nullptr;
+};
+
+int prepare(tess_ctx *ctx, const tess_process *proc, uint64_t seed, uint64_t first_event, uint64_t n_events,
+            const tess_outputs *out, void *workspace, size_t workspace_bytes, Prepared *pr) {
+  int rc = check_process(proc);
+  if (rc) return rc;
+  if (!out || !out->acc) return fail(TESS_E_INVALID, "outputs and outputs->acc must not be NULL");
+  if (proc->hist_bins > 0 && !out->hist) return fail(TESS_E_INVALID, "hist_bins > 0 needs outputs->hist");
+  if (n_events > (UINT64_MAX - first_event)) return fail(TESS_E_INVALID, "event range overflows 64 bits");
+  const void *ptrs[] = {out->weight, out->me2, out->pass, out->ht, out->ptlead, out->rmin, out->acc, out->hist,
+                        workspace};
+  const char *names[] = {"weight", "me2", "pass", "ht", "ptlead", "rmin", "acc", "hist", "workspace"};
+  for (int i = 0; i < 9; ++i)
+    if ((rc = check_device_ptr(ptrs[i], ctx->device, names[i]))) return rc;
+  if (((uintptr_t)workspace) % 256 != 0) return fail(TESS_E_WORKSPACE, "workspace must be 256-byte aligned");
+  fill_params(proc, seed, first_event, n_events, out, &pr->P);
+  pr->proc = proc;
+  pr->workspace = workspace;
+  pr->acc = out->acc;
+  pr->hist = out->hist;
+  pr->sum = proc->helicity_mode == TESS_HEL_SUM;
+  pr->pipeline = uses_pipeline(proc);
+  size_t need;
+  if (pr->pipeline) {
+    if ((rc = pipeline_plan(ctx, proc, n_events, &pr->pl))) return rc;
+    pr->grid = pr->pl.grid;
+    need = pr->pl.bytes;
+  } else {
+    pr->grid = grid_for(ctx, proc, n_events);
+    need = (size_t)pr->grid * (size_t)tess::partial_stride(proc->hist_bins) * sizeof(double);
+  }
+  if (!workspace || workspace_bytes < need)
+    return fail(TESS_E_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, workspace ? workspace_bytes : 0);
+  return TESS_OK;
+}
+
+int launch_prepared(const Prepared &pr, cudaStream_t s, const tess::StageHook *hook = nullptr) {
+  if (pr.P.n_events == 0) return TESS_OK;
+  const int n = pr.proc->n_gluons;
+  double *partials = (double *)pr.workspace;
+  cudaError_t e;
+  if (pr.pipeline) {
+    e = pipeline_run(pr.proc, pr.P, pr.pl, (char *)pr.workspace, s, hook);
+    if (e != cudaSuccess) return cuda_fail(e, "pipeline launch");
+  } else {
+    if (hook) (*hook)(tess::STAGE_FUSED, true, s);
+    e = pr.proc->precision == TESS_FP64 ? tess::launch_generate_f64(n, pr.sum, pr.P, partials, pr.grid, s)
+                                        : tess::launch_generate_f32(n, pr.sum, pr.P, partials, pr.grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "event kernel launch");
+    if (hook) (*hook)(tess::STAGE_FUSED, false, s);
+  }
+  if (hook) (*hook)(tess::STAGE_FINAL, true, s);
+  tess::finalize_kernel<<<1, 256, 0, s>>>(partials, pr.grid, pr.proc->hist_bins, pr.P.n_events, pr.acc, pr.hist);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "finalize kernel launch");
+  if (hook) (*hook)(tess::STAGE_FINAL, false, s);
+  return TESS_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" {
+
+int tess_generate(tess_ctx *ctx, const tess_process *proc, uint64_t seed, uint64_t first_event, uint64_t n_events,
+                  const tess_outputs *out, void *workspace, size_t workspace_bytes, void *stream) {
+  if (!ctx) return fail(TESS_E_INVALID, "ctx is NULL");
+  int rc = check_process(proc);
+  if (rc) return rc;
+  if (!out || !out->acc) return fail(TESS_E_INVALID, "outputs and outputs->acc must not be NULL");
+  if (n_events == 0) return ok();
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  Prepared pr;
+  if ((rc = prepare(ctx, proc, seed, first_event, n_events, out, workspace, workspace_bytes, &pr))) return rc;
+  tess::StageHook hook{stage_mark, ctx};
+  if ((rc = launch_prepared(pr, (cudaStream_t)stream, ctx->timing ? &hook : nullptr))) return rc;
+  return ok();
+}
+
+int tess_stage_timing(tess_ctx *ctx, int enable) {
+  if (!ctx) return fail(TESS_E_INVALID, "ctx is NULL");
+  ctx->timing = enable != 0;
+  return ok();
+}
+
+int tess_stage_times(tess_ctx *ctx, double *ms, int *launches) {
+  if (!ctx || !ms || !launches) return fail(TESS_E_INVALID, "NULL argument");
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  for (int k = 0; k < tess::STAGE_NKINDS; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  cudaError_t e = cudaSuccess;
+  for (auto &m : ctx->ev_marks) {
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventSynchronize(m.second.second);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, m.second.first, m.second.second);
+    ms[m.first] += t;
+    launches[m.first] += 1;
+    ctx->ev_free.push_back(m.second.first);
+    ctx->ev_free.push_back(m.second.second);
+  }
+  ctx->ev_marks.clear();
+  if (e != cudaSuccess) return cuda_fail(e, "stage timing events");
+  return ok();
+}
+
+int tess_workspace_size_batched(const tess_ctx *ctx, int n_proc, const tess_process *procs,
+                                const uint64_t *n_events, size_t *bytes) {
+  if (!ctx || !procs || !n_events || !bytes) return fail(TESS_E_INVALID, "NULL argument");
+  if (n_proc < 1 || n_proc > kMaxBranches) return fail(TESS_E_INVALID, "n_proc must be 1..%d", kMaxBranches);
+  size_t tot = 0;
+  for (int i = 0; i < n_proc; ++i) {
+    size_t b = 0;
+    const int rc = tess_workspace_size(ctx, &procs[i], n_events[i], &b);
+    if (rc) return rc;
+    tot += align256(b);
+  }
+  *bytes = tot;
+  return ok();
+}
+
+int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, const uint64_t *seeds,
+                          const uint64_t *first_events, const uint64_t *n_events, const tess_outputs *outs,
+                          void *workspace, size_t workspace_bytes, void *stream) {
+  if (!ctx || !procs || !seeds || !first_events || !n_events || !outs) return fail(TESS_E_INVALID, "NULL argument");
+  if (n_proc < 1 || n_proc > kMaxBranches) return fail(TESS_E_INVALID, "n_proc must be 1..%d", kMaxBranches);
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  // validate and plan every process before anything is captured
+  std::vector<Prepared> prs(n_proc);
+  char *ws = (char *)workspace;
+  size_t left = workspace ? workspace_bytes : 0;
+  int rc;
+  for (int i = 0; i < n_proc; ++i) {
+    size_t b = 0;
+    if ((rc = tess_workspace_size(ctx, &procs[i], n_events[i], &b))) return rc;
+    b = align256(b);
+    if (b > left) return fail(TESS_E_WORKSPACE, "batched workspace too small at process %d", i);
+    if ((rc = prepare(ctx, &procs[i], seeds[i], first_events[i], n_events[i], &outs[i], ws, b, &prs[i]))) return rc;
+    ws += b;
+    left -= b;
+  }
+  // graph key: every argument that is baked into the captured launches
+  std::vector<unsigned char> key;
+  auto put = [&](const void *p, size_t n) {
+    const unsigned char *c = (const unsigned char *)p;
+    key.insert(key.end(), c, c + n);
+  };
+  put(&n_proc, sizeof n_proc);
+  put(procs, sizeof(tess_process) * n_proc);
+  put(seeds, sizeof(uint64_t) * n_proc);
+  put(first_events, sizeof(uint64_t) * n_proc);
+  put(n_events, sizeof(uint64_t) * n_proc);
+  put(outs, sizeof(tess_outputs) * n_proc);
+  put(&workspace, sizeof workspace);
+  put(ctx->form, sizeof ctx->form);
+  cudaError_t e = cudaSuccess;
+  if (!ctx->graph_exec || key != ctx->graph_key) {
+    if (!ctx->cap_stream) {
+      if ((e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "stream/event creation");
+    }
+    for (int i = 0; i < n_proc; ++i) {
+      if (!ctx->branch[i]) {
+        if ((e = cudaStreamCreateWithFlags(&ctx->branch[i], cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&ctx->join_ev[i], cudaEventDisableTiming)) != cudaSuccess)
+          return cuda_fail(e, "stream/event creation");
+      }
+    }
+    // one branch per process, forked from and joined back into the capture stream
+    cudaGraph_t graph = nullptr;
+    if ((e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamBeginCapture");
+    e = cudaEventRecord(ctx->fork_ev, ctx->cap_stream);
+    int lrc = TESS_OK;
+    for (int i = 0; i < n_proc && e == cudaSuccess && lrc == TESS_OK; ++i) {
+      e = cudaStreamWaitEvent(ctx->branch[i], ctx->fork_ev, 0);
+      if (e == cudaSuccess) lrc = launch_prepared(prs[i], ctx->branch[i]);
+      if (e == cudaSuccess && lrc == TESS_OK) e = cudaEventRecord(ctx->join_ev[i], ctx->branch[i]);
+      if (e == cudaSuccess && lrc == TESS_OK) e = cudaStreamWaitEvent(ctx->cap_stream, ctx->join_ev[i], 0);
+    }
+    const cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (lrc != TESS_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return lrc;
+    }
+    if (e == cudaSuccess) e = ee;
+    if (e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(e, "graph capture");
+    }
+    if (ctx->graph_exec) {
+      cudaGraphExecDestroy(ctx->graph_exec);
+      ctx->graph_exec = nullptr;
+    }
+    e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      ctx->graph_exec = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    ctx->graph_key = key;
+  }
+  if ((e = cudaGraphLaunch(ctx->graph_exec, (cudaStream_t)stream)) != cudaSuccess)
+    return cuda_fail(e, "cudaGraphLaunch");
+  return ok();
+}
+
+int tess_autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events, double *acc_scratch,
+                  void *workspace, size_t workspace_bytes, void *stream, int *form_out) {
+  if (!ctx || !proc || !acc_scratch || !form_out) return fail(TESS_E_INVALID, "NULL argument");
+  int rc = check_process(proc);
+  if (rc) return rc;
+  if (probe_events == 0) return fail(TESS_E_INVALID, "probe_events must be > 0");
+  const int pi = proc->precision == TESS_FP64 ? 0 : 1;
+  const int n = proc->n_gluons;
+  if (!uses_pipeline(proc)) {  // the exact-sum mode has a single kernel
+    *form_out = -1;
+    return ok();
+  }
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  tess_outputs out;
+  memset(&out, 0, sizeof out);
+  out.acc = acc_scratch;
+  tess_process pp = *proc;
+  pp.hist_bins = 0;  // time the amplitude path only
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&a)) != cudaSuccess || (e = cudaEventCreate(&b)) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    return cuda_fail(e, "cudaEventCreate");
+  }
+  const int saved = ctx->form[pi][n];
+  int best = -1;
+  float best_ms = 0.f;
+  for (int f = 0; f < tess::K2_NFORMS; ++f) {
+    tess::PipePlan pl;
+    if ((rc = plan_with_form(ctx, &pp, probe_events, f, &pl))) break;
+    if (pl.form != f) continue;  // variant not built for this (precision, n)
+    ctx->form[pi][n] = f;
+    Prepared pr;
+    if ((rc = prepare(ctx, &pp, 1, 0, probe_events, &out, workspace, workspace_bytes, &pr))) break;
+    if ((rc = launch_prepared(pr, s))) break;  // warm-up
+    cudaEventRecord(a, s);
+    if ((rc = launch_prepared(pr, s))) break;
+    cudaEventRecord(b, s);
+    if ((e = cudaEventSynchronize(b)) != cudaSuccess) {
+      rc = cuda_fail(e, "autotune timing");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (best < 0 || ms < best_ms) {
+      best = f;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) {
+    ctx->form[pi][n] = saved;
+    return rc;
+  }
+  ctx->form[pi][n] = best;
+  *form_out = best;
   return ok();
 }
 
@@ -278,7 +689,8 @@ int tess_me2(tess_ctx *ctx, int n, int precision, uint64_t n_events, const doubl
              const uint32_t *hel, double *me2, void *stream) {
   if (!ctx) return fail(TESS_E_INVALID, "ctx is NULL");
   if (n < TESS_MIN_N || n > TESS_MAX_N) return fail(TESS_E_UNSUPPORTED, "n = %d outside %d..%d", n, TESS_MIN_N, TESS_MAX_N);
-  if (precision != TESS_FP64 && precision != TESS_FP32_CURRENTS) return fail(TESS_E_INVALID, "bad precision %d", precision);
+  if (precision != TESS_FP64 && precision != TESS_FP32_CURRENTS && precision != TESS_FP32_DS)
+    return fail(TESS_E_INVALID, "bad precision %d", precision);
   if (n_events == 0) return ok();
   if (!k || !order || !hel || !me2) return fail(TESS_E_INVALID, "k, order, hel and me2 must not be NULL");
   if (n_events > (uint64_t)INT32_MAX * 128ull) return fail(TESS_E_INVALID, "n_events too large for one call");

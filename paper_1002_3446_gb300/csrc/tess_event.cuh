@@ -24,6 +24,11 @@ struct EventParams {
   double hist_lo, hist_inv_width;
   int hist_bins;       // 0: no histogram
   int hist_obs;
+  // double-single kinematics: S split into two floats, and the weight
+  // constant wconst (ln x_min)^2 phiconst / 2
+  float S_hi, S_lo;
+  double wk;
+  int kin_ds;          // 1: double-single kinematics kernel
   // outputs (device; may be null)
   double *weight, *me2, *ht, *ptlead, *rmin;
   uint8_t *pass;
@@ -154,19 +159,28 @@ __device__ __forceinline__ void kinematics(const EventParams &P, uint64_t ev, Ki
 }
 
 // Colour ordering (Fisher-Yates on positions 2..n) and helicity labels of a
-// sampled event, from its draws.
+// sampled event, from its draws.  Both are integer functions of the Philox
+// words: the helicity word is the top n bits of its uniform, and each swap
+// index floor(u (i-1)) is evaluated exactly as the double product rounds.
 template <int N>
 __device__ __forceinline__ uint32_t sample_config(const EventParams &P, uint64_t ev, int (&perm)[N]) {
   constexpr int M = N - 2;
-  const uint32_t jh = 2 + 4 * M;
-  const double uh = uniform_at(P.seed, ev, jh);
-  const uint32_t hel = (uint32_t)(uh * (double)(1u << N));
+  constexpr uint32_t jh = 2 + 4 * M;  // helicity draw; ordering draws follow
+  uint4 w = philox_block(P.seed, ev, jh >> 1);
+  uint32_t cur = jh >> 1;
+  const uint32_t a0 = (jh & 1u) ? w.z : w.x;
+  const uint32_t hel = a0 >> (32 - N);  // top N bits of (a >> 6) 2^26 + (b >> 6)
 #pragma unroll
   for (int i = 0; i < N; ++i) perm[i] = i;
 #pragma unroll
   for (int i = N; i >= 3; --i) {
-    const double ui = uniform_at(P.seed, ev, jh + 1 + (N - i));
-    const int r = 2 + (int)(ui * (double)(i - 1));
+    const uint32_t j = jh + 1 + (N - i);
+    if ((j >> 1) != cur) {
+      cur = j >> 1;
+      w = philox_block(P.seed, ev, cur);
+    }
+    const uint64_t k = (j & 1u) ? unit_bits(w.z, w.w) : unit_bits(w.x, w.y);
+    const int r = 2 + floor_unit_times(k, (uint32_t)(i - 1));
     // swap positions i and r (1-based)
 #pragma unroll
     for (int q = 2; q <= N; ++q) {

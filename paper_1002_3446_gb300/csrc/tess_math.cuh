@@ -41,6 +41,43 @@ __device__ __forceinline__ double2 uniform_pair(uint64_t seed, uint64_t ev, uint
   return make_double2(unit_from_words(w.x, w.y), unit_from_words(w.z, w.w));
 }
 
+// The raw Philox block `blk` of event `ev`.
+__device__ __forceinline__ uint4 philox_block(uint64_t seed, uint64_t ev, uint32_t blk) {
+  return philox4x32_10(make_uint4((uint32_t)ev, (uint32_t)(ev >> 32), blk, 0u),
+                       make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// The 52-bit integer k of uniform u = (k + 1/2) 2^-52 from its two words.
+__device__ __forceinline__ uint64_t unit_bits(uint32_t a, uint32_t b) {
+  return ((uint64_t)(a >> 6) << 26) | (uint64_t)(b >> 6);
+}
+
+// floor(u * c) exactly as the double-precision product rounds it (single
+// rounding to 53 bits, ties to even), in integer arithmetic: u * c =
+// (2k+1) c 2^-53 and scaling by 2^-53 is exact.  c <= 2^10.
+__device__ __forceinline__ int floor_unit_times(uint64_t k, uint32_t c) {
+  uint64_t X = (2 * k + 1) * (uint64_t)c;
+  const int e = 63 - __clzll((long long)X);
+  if (e >= 53) {
+    const int s = e - 52;
+    const uint64_t mask = (1ull << s) - 1, half = 1ull << (s - 1);
+    uint64_t q = X >> s;
+    const uint64_t rem = X & mask;
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+    X = q << s;
+  }
+  return (int)(X >> 53);
+}
+
+// A uniform in single precision from the same two words: hi 2^-26 +
+// (lo + 1/2) 2^-52 with one rounding when hi < 2^24 (u < 1/4, exactly
+// float(u)); within 2 ulp of float(u) above.  Strictly inside (0, 1).
+__device__ __forceinline__ float unit_f32(uint32_t a, uint32_t b) {
+  const float hi = (float)(a >> 6), lo = (float)(b >> 6);
+  const float u = fmaf(lo + 0.5f, 0x1p-52f, hi * 0x1p-26f);
+  return fminf(u, 0x1.fffffep-1f);
+}
+
 // Single uniform j of an event (used for scattered draws).
 __device__ __forceinline__ double uniform_at(uint64_t seed, uint64_t ev, uint32_t j) {
   const double2 p = uniform_pair(seed, ev, j >> 1);
@@ -154,5 +191,86 @@ __device__ __forceinline__ RV4<R> radd(const RV4<R> &a, const RV4<R> &b) {
   for (int m = 0; m < 4; ++m) d.v[m] = a.v[m] + b.v[m];
   return d;
 }
+
+}  // namespace tess
+
+namespace tess {
+
+// ---------------------------------------------------------------------------
+// Double-single ("two-float") arithmetic: a value is hi + lo with |lo| <=
+// ulp(hi)/2, about 47-48 significant bits, evaluated on the FP32 pipe.  Built
+// from the error-free transformations two-sum (Knuth) and two-product (one
+// FMA); reciprocal and reciprocal square root take one Newton step in
+// double-single from the FP32 estimate.  Rounding a normalised value to FP32
+// gives hi.
+// ---------------------------------------------------------------------------
+struct DS {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DS ds(float x) { return DS{x, 0.f}; }
+
+__device__ __forceinline__ DS ds_from_double(double x) {
+  const float h = (float)x;
+  return DS{h, (float)(x - (double)h)};
+}
+
+__device__ __forceinline__ double ds_to_double(DS a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ DS ds_fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return DS{s, b - (s - a)};
+}
+
+__device__ __forceinline__ DS ds_add(DS a, DS b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb);
+  return ds_fast_two_sum(s, e + a.lo + b.lo);
+}
+
+__device__ __forceinline__ DS ds_add(DS a, float b) {
+  const float s = a.hi + b;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b - bb);
+  return ds_fast_two_sum(s, e + a.lo);
+}
+
+__device__ __forceinline__ DS ds_neg(DS a) { return DS{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ DS ds_sub(DS a, DS b) { return ds_add(a, ds_neg(b)); }
+
+__device__ __forceinline__ DS ds_mul(DS a, DS b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return ds_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ DS ds_mul(DS a, float b) {
+  const float p = a.hi * b;
+  const float e = fmaf(a.lo, b, fmaf(a.hi, b, -p));
+  return ds_fast_two_sum(p, e);
+}
+
+// a*b + c
+__device__ __forceinline__ DS ds_fma(DS a, DS b, DS c) { return ds_add(ds_mul(a, b), c); }
+
+// 1/a: y0 = rcp(hi), y = y0 + y0 (1 - a y0)
+__device__ __forceinline__ DS ds_rcp(DS a) {
+  const float y0 = 1.f / a.hi;
+  const DS r = ds_add(ds(1.f), ds_neg(ds_mul(a, y0)));  // 1 - a y0, small
+  return ds_add(ds(y0), r.hi * y0);
+}
+
+// 1/sqrt(a): y0 = rsqrt(hi), y = y0 + y0 (1 - a y0^2) / 2
+__device__ __forceinline__ DS ds_rsqrt(DS a) {
+  const float y0 = rsqrtf(a.hi);
+  const DS t = ds_mul(ds_mul(a, y0), y0);  // a y0^2, close to 1
+  const DS r = ds_add(ds(1.f), ds_neg(t));
+  return ds_add(ds(y0), 0.5f * y0 * r.hi);
+}
+
+__device__ __forceinline__ DS ds_sqrt(DS a) { return ds_mul(a, ds_rsqrt(a)); }
 
 }  // namespace tess

@@ -1,0 +1,25 @@
+// Instantiations of the two-kernel pipeline (float currents, n = 8..10).
+#include "tess_pipe_launch.cuh"
+
+namespace tess {
+
+int plan_pipeline_f32b(int n, int sm_count, uint64_t n_events, int hist_bins, int form, PipePlan *pl) {
+  switch (n) {
+    case 8: return plan_pipeline_t<8, float>(sm_count, n_events, hist_bins, form, pl);
+    case 9: return plan_pipeline_t<9, float>(sm_count, n_events, hist_bins, form, pl);
+    case 10: return plan_pipeline_t<10, float>(sm_count, n_events, hist_bins, form, pl);
+    default: return -1;
+  }
+}
+
+cudaError_t run_pipeline_f32b(int n, const EventParams &P, const PipePlan &pl, char *ws, cudaStream_t s,
+                                 const StageHook *hook) {
+  switch (n) {
+    case 8: return run_pipeline_t<8, float>(P, pl, ws, s, hook);
+    case 9: return run_pipeline_t<9, float>(P, pl, ws, s, hook);
+    case 10: return run_pipeline_t<10, float>(P, pl, ws, s, hook);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace tess

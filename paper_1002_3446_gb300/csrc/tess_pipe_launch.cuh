@@ -1,0 +1,182 @@
+// Host side of the two-kernel pipeline: plan (workspace layout, chunk size,
+// K2 grid) and the launch sequence of one tess_generate call.
+#pragma once
+#include <algorithm>
+
+#include "tess_pipeline.cuh"
+
+namespace tess {
+
+struct PipePlan {
+  int form = 0;      // K2 variant (K2Form)
+  int per_sm = 1;    // K2 blocks resident per SM
+  int grid = 1;      // K2 blocks = partial rows
+  int block = 128;   // K2 threads per block (events per tile)
+  size_t smem = 0;   // K2 dynamic shared memory
+  int cap = 128;     // events per chunk
+  int chunks = 1;
+  size_t off_in = 0, off_efac = 0, off_wfac = 0, off_hval = 0, off_pass = 0;
+  size_t bytes = 0;  // workspace bytes
+};
+
+constexpr size_t kChunkTargetBytes = 64ull << 20;  // stays resident in the 129 MB L2
+
+// Optional host hook around each launch (stage timing); kinds below.
+enum StageKind { STAGE_KIN = 0, STAGE_AMP = 1, STAGE_FINAL = 2, STAGE_FUSED = 3, STAGE_NKINDS = 4 };
+struct StageHook {
+  void (*mark)(void *self, int kind, bool begin, cudaStream_t s);
+  void *self;
+  void operator()(int kind, bool begin, cudaStream_t s) const {
+    if (mark) mark(self, kind, begin, s);
+  }
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Amplitude-kernel (K2) variants.  All are one thread per event; they differ
+// in where the current table lives and in the block shape:
+//   K2_REG     table in registers (fully unrolled), 128 threads   FP32, n <= 8
+//   K2_ROWS32  current row in registers, older rows in the thread's
+//              shared-memory column, 32 threads per block         FP32, n >= 6
+//   K2_ROWS64  the same with 64 threads per block                 FP32, n >= 6
+//   K2_LOOP    loop form, table in local memory, 128 threads      FP64
+enum K2Form { K2_REG = 0, K2_ROWS32 = 1, K2_ROWS64 = 2, K2_LOOP = 3, K2_NFORMS = 4 };
+
+template <int N, typename R>
+constexpr bool k2_valid(int f) {
+  return sizeof(R) == 8 ? f == K2_LOOP : (f == K2_REG ? N <= 8 : (f == K2_ROWS32 || f == K2_ROWS64) ? N >= 6 : false);
+}
+
+template <int N, typename R>
+constexpr int k2_default() {
+  return sizeof(R) == 8 ? K2_LOOP : (N <= 7 ? K2_REG : K2_ROWS32);
+}
+
+template <int N, typename R, int F>
+struct K2V {
+  static constexpr int L = N - 1;
+  static constexpr int block = (F == K2_ROWS32) ? 32 : (F == K2_ROWS64 ? 64 : 128);
+  static void *fn() {
+    if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
+      return (void *)bg_rows_kernel<N, block>;
+    else if constexpr (F == K2_REG)
+      return (void *)bg_reg_kernel<N, float, 128>;
+    else
+      return (void *)bg_loop_kernel<N, 128>;
+  }
+  static size_t smem(int hist_bins) {
+    if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
+      return rows_smem_per_thread<L>() * block + EpiSmem<block>::bytes(hist_bins);
+    else
+      return EpiSmem<128>::bytes(hist_bins);
+  }
+  static cudaError_t launch(const ChunkParams &C, const ChunkBuf<R> &B, double *partials, int grid, size_t smem,
+                            cudaStream_t s) {
+    if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
+      bg_rows_kernel<N, block><<<grid, block, smem, s>>>(C, B, partials);
+    else if constexpr (F == K2_REG)
+      bg_reg_kernel<N, float, 128><<<grid, 128, smem, s>>>(C, B, partials);
+    else
+      bg_loop_kernel<N, 128><<<grid, 128, smem, s>>>(C, B, partials);
+    return cudaGetLastError();
+  }
+};
+
+// Dispatch a runtime form to the compiled variants of (N, R).
+template <int N, typename R, typename Fn>
+auto with_form(int f, Fn &&fn) {
+  if constexpr (sizeof(R) == 8) {
+    return fn(K2V<N, R, K2_LOOP>{});
+  } else {
+    if constexpr (N <= 8) {
+      if (f == K2_REG) return fn(K2V<N, R, K2_REG>{});
+    }
+    if constexpr (N >= 6) {
+      if (f == K2_ROWS64) return fn(K2V<N, R, K2_ROWS64>{});
+      return fn(K2V<N, R, K2_ROWS32>{});
+    } else {
+      return fn(K2V<N, R, K2_REG>{});
+    }
+  }
+}
+
+template <int N, typename R>
+int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, PipePlan *pl) {
+  constexpr int L = N - 1;
+  if (!k2_valid<N, R>(form)) form = k2_default<N, R>();
+  pl->form = form;
+  const int rc = with_form<N, R>(form, [&](auto K) {
+    using KV = decltype(K);
+    pl->block = KV::block;
+    pl->smem = KV::smem(hist_bins);
+    if (pl->smem > 48 * 1024 &&
+        cudaFuncSetAttribute(KV::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem) != cudaSuccess)
+      return -1;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, KV::fn(), KV::block, pl->smem) != cudaSuccess ||
+        per_sm < 1)
+      return -1;
+    pl->per_sm = per_sm;
+    return 0;
+  });
+  if (rc) return rc;
+  const int per_sm = pl->per_sm;
+  const uint64_t per_event = (uint64_t)(12 * L + 8) * sizeof(R) + 3 * sizeof(double) + 1;
+  const uint64_t target = std::max<uint64_t>(128, (kChunkTargetBytes / per_event) / 128 * 128);
+  const uint64_t want = (std::max<uint64_t>(n_events, 1) + 127) / 128 * 128;
+  pl->cap = (int)std::min(target, want);
+  pl->chunks = (int)((std::max<uint64_t>(n_events, 1) + pl->cap - 1) / pl->cap);
+  const uint64_t tiles = ((uint64_t)pl->cap + pl->block - 1) / pl->block;
+  pl->grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)sm_count * per_sm));
+  size_t off = align256((size_t)pl->grid * partial_stride(hist_bins) * sizeof(double));
+  pl->off_in = off;
+  off = align256(off + (size_t)(12 * L + 8) * pl->cap * sizeof(R));
+  pl->off_efac = off;
+  off = align256(off + (size_t)pl->cap * sizeof(double));
+  pl->off_wfac = off;
+  off = align256(off + (size_t)pl->cap * sizeof(double));
+  pl->off_hval = off;
+  off = align256(off + (size_t)pl->cap * sizeof(double));
+  pl->off_pass = off;
+  pl->bytes = align256(off + (size_t)pl->cap);
+  return 0;
+}
+
+template <int N, typename R>
+cudaError_t run_pipeline_t(const EventParams &P, const PipePlan &pl, char *ws, cudaStream_t s,
+                           const StageHook *hook) {
+  double *partials = (double *)ws;
+  cudaError_t e = cudaMemsetAsync(partials, 0, (size_t)pl.grid * partial_stride(P.hist_bins) * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  ChunkBuf<R> B;
+  B.in = (R *)(ws + pl.off_in);
+  B.efac = (double *)(ws + pl.off_efac);
+  B.wfac = (double *)(ws + pl.off_wfac);
+  B.hval = (double *)(ws + pl.off_hval);
+  B.pass = (uint8_t *)(ws + pl.off_pass);
+  B.cap = pl.cap;
+  ChunkParams C;
+  C.P = P;
+  for (uint64_t off = 0; off < P.n_events; off += (uint64_t)pl.cap) {
+    C.chunk_first = off;
+    C.count = (int)std::min<uint64_t>((uint64_t)pl.cap, P.n_events - off);
+    if (hook) (*hook)(STAGE_KIN, true, s);
+    if constexpr (sizeof(R) == 4) {
+      if (P.kin_ds)
+        kin_ds_kernel<N><<<(C.count + kBlock - 1) / kBlock, kBlock, 0, s>>>(C, B);
+      else
+        kin_kernel<N, R><<<(C.count + kBlock - 1) / kBlock, kBlock, 0, s>>>(C, B);
+    } else {
+      kin_kernel<N, R><<<(C.count + kBlock - 1) / kBlock, kBlock, 0, s>>>(C, B);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (hook) (*hook)(STAGE_KIN, false, s);
+    if (hook) (*hook)(STAGE_AMP, true, s);
+    e = with_form<N, R>(pl.form, [&](auto K) { return decltype(K)::launch(C, B, partials, pl.grid, pl.smem, s); });
+    if (e != cudaSuccess) return e;
+    if (hook) (*hook)(STAGE_AMP, false, s);
+  }
+  return cudaSuccess;
+}
+
+}  // namespace tess

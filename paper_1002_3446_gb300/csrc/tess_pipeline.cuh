@@ -1,0 +1,942 @@
+// Two-kernel event pipeline for sampled helicity / colour ordering:
+//   K1 (kin_kernel): draws -> x1, x2 -> Rambo -> luminosity, alpha_s, cuts,
+//       observables -> polarisation vectors; writes the colour-ordered
+//       Berends-Giele inputs of a chunk of events to workspace (SoA).
+//   K2 (bg_*_kernel): Berends-Giele amplitude of every event of the chunk ->
+//       |A|^2 estimator, weight -> per-block partial sums (deterministic).
+// The chunk is sized to stay resident in L2 between the two launches.
+//
+// Precision: with R = double every step is FP64 (the plain FP64 form).  With
+// R = float (FP32 currents) the Rambo seeds, cuts, observables, alpha_s and
+// PDF are FP32, while Rambo's mass-conserving boost and rescale, the
+// polarisation-vector construction and all accumulation stay FP64.
+#pragma once
+#include <cstdint>
+
+#include "tess_event.cuh"
+#include "tess_kernels.cuh"
+
+namespace tess {
+
+// Chunk buffers inside the caller's workspace, element e of slot s at
+// base[s * cap + e] (coalesced across consecutive events).
+template <typename R>
+struct ChunkBuf {
+  R *in;          // [(12 L + 8) * cap]: per position a = 0..L-1: k (4), eps (4 re, 4 im); then eps_0 (4 re, 4 im)
+  double *efac;   // [cap] |m|^2 -> estimator E (includes the momentum unit)
+  double *wfac;   // [cap] E -> weight (0 if the event fails the cuts)
+  double *hval;   // [cap] histogram observable
+  uint8_t *pass;  // [cap] pass flag
+  int cap;
+};
+
+struct ChunkParams {
+  EventParams P;
+  uint64_t chunk_first;  // index of the chunk's first event within the call
+  int count;             // events in this chunk
+};
+
+template <typename R>
+__device__ __forceinline__ R r_exp(R x);
+template <>
+__device__ __forceinline__ float r_exp<float>(float x) { return expf(x); }
+template <>
+__device__ __forceinline__ double r_exp<double>(double x) { return exp(x); }
+
+template <typename R>
+__device__ __forceinline__ R r_log(R x);
+template <>
+__device__ __forceinline__ float r_log<float>(float x) { return logf(x); }
+template <>
+__device__ __forceinline__ double r_log<double>(double x) { return log(x); }
+
+template <typename R>
+__device__ __forceinline__ R r_atan2(R y, R x);
+template <>
+__device__ __forceinline__ float r_atan2<float>(float y, float x) { return atan2f(y, x); }
+template <>
+__device__ __forceinline__ double r_atan2<double>(double y, double x) { return atan2(y, x); }
+
+template <typename R>
+__device__ __forceinline__ void r_sincospi(R x, R *s, R *c);
+template <>
+__device__ __forceinline__ void r_sincospi<float>(float x, float *s, float *c) { sincospif(x, s, c); }
+template <>
+__device__ __forceinline__ void r_sincospi<double>(double x, double *s, double *c) { sincospi(x, s, c); }
+
+template <typename R>
+__device__ __forceinline__ R r_pow(R x, R y);
+template <>
+__device__ __forceinline__ float r_pow<float>(float x, float y) { return powf(x, y); }
+template <>
+__device__ __forceinline__ double r_pow<double>(double x, double y) { return pow(x, y); }
+
+// A uniform rounded to R, kept strictly below 1.
+template <typename R>
+__device__ __forceinline__ R r_unit(double u) {
+  R v = R(u);
+  return v < R(1) ? v : R(1) - R(1) / R(1 << 24);
+}
+
+// K1, FP64 form: every step in double precision.
+template <int N, typename R>
+__device__ __forceinline__ void kin_generic(const ChunkParams &C, const ChunkBuf<R> &B, int e) {
+  constexpr int M = N - 2, L = N - 1;
+  const EventParams &P = C.P;
+  const uint64_t idx = C.chunk_first + (uint64_t)e;
+  const uint64_t ev = P.first_event + idx;
+
+  // ---- x1, x2 (uniform in ln x)
+  const double2 ux = uniform_pair(P.seed, ev, 0);
+  const R x1 = r_exp<R>(R(ux.x) * R(P.lnxmin));
+  const R x2 = r_exp<R>(R(ux.y) * R(P.lnxmin));
+  const double shat = (double)x1 * (double)x2 * P.S;
+  const double rs = sqrt(shat);
+
+  // ---- Rambo: isotropic seeds in R, boost + rescale in FP64
+  double q[M][4];
+  double Q0 = 0.0, Q1 = 0.0, Q2 = 0.0, Q3 = 0.0;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const double2 a = uniform_pair(P.seed, ev, 1 + 2 * i);
+    const double2 b = uniform_pair(P.seed, ev, 2 + 2 * i);
+    const R c = R(2) * r_unit<R>(a.x) - R(1);
+    const R s = sqrt(fmax(R(1) - c * c, R(0)));
+    R sn, cs;
+    r_sincospi<R>(R(2) * r_unit<R>(a.y), &sn, &cs);
+    const R q0 = -r_log<R>(r_unit<R>(b.x) * r_unit<R>(b.y));
+    q[i][0] = (double)q0;
+    q[i][1] = (double)(q0 * s * cs);
+    q[i][2] = (double)(q0 * s * sn);
+    q[i][3] = (double)(q0 * c);
+    Q0 += q[i][0];
+    Q1 += q[i][1];
+    Q2 += q[i][2];
+    Q3 += q[i][3];
+  }
+  const double Mq = sqrt(Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3);
+  const double invM = 1.0 / Mq;
+  const double bx = -Q1 * invM, by = -Q2 * invM, bz = -Q3 * invM;
+  const double gam = Q0 * invM;
+  const double aa = 1.0 / (1.0 + gam);
+  const double xs = rs * invM;
+  double kk[N][4];
+  const double h = 0.5 * rs;
+  kk[0][0] = -h; kk[0][1] = 0.0; kk[0][2] = 0.0; kk[0][3] = -h;
+  kk[1][0] = -h; kk[1][1] = 0.0; kk[1][2] = 0.0; kk[1][3] = h;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const double bq = bx * q[i][1] + by * q[i][2] + bz * q[i][3];
+    kk[2 + i][0] = xs * (gam * q[i][0] + bq);
+    const double f = aa * bq + q[i][0];
+    kk[2 + i][1] = xs * (q[i][1] + bx * f);
+    kk[2 + i][2] = xs * (q[i][2] + by * f);
+    kk[2 + i][3] = xs * (q[i][3] + bz * f);
+  }
+
+  // ---- cuts and observables (R), lab rapidity = eta + ln(x1/x2)/2
+  const R y = R(0.5) * r_log<R>(x1 / x2);
+  R eta[M], pt[M], px[M], py[M];
+  int pass = 1;
+  R sum = R(0), lead = R(0);
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    px[i] = R(kk[2 + i][1]);
+    py[i] = R(kk[2 + i][2]);
+    const R pz = R(kk[2 + i][3]);
+    const R pt2 = px[i] * px[i] + py[i] * py[i];
+    const R pabs = sqrt(pt2 + pz * pz);
+    pt[i] = sqrt(pt2);
+    eta[i] = R(0.5) * r_log<R>((pabs + pz) / (pabs - pz)) + y;
+    sum += pt[i];
+    lead = fmax(lead, pt[i]);
+    pass &= (pt[i] > R(P.pt_min)) & (fabs(eta[i]) < R(P.eta_max));
+  }
+  R dr2min = R(1e30);
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+#pragma unroll
+    for (int j = i + 1; j < M; ++j) {
+      const R dphi = r_atan2<R>(fabs(px[i] * py[j] - py[i] * px[j]), px[i] * px[j] + py[i] * py[j]);
+      const R de = eta[i] - eta[j];
+      const R dr2 = de * de + dphi * dphi;
+      dr2min = fmin(dr2min, dr2);
+      pass &= (dr2 > R(P.dr2_min));
+    }
+  }
+  const double ht = (double)sum, ptlead = (double)lead, rmin = (double)sqrt(dr2min);
+  if (P.ht) P.ht[idx] = ht;
+  if (P.ptlead) P.ptlead[idx] = ptlead;
+  if (P.rmin) P.rmin[idx] = rmin;
+  if (P.pass) P.pass[idx] = (uint8_t)pass;
+
+  // ---- weight factor (everything but the matrix element)
+  double wf = 0.0;
+  if (pass) {
+    const R mu = R(P.mu_r_factor) * sum;
+    const R as = R(P.alphas_mz) / (R(1) + R(P.alphas_mz) * R(P.b0) * (r_log<R>(mu * mu) - R(P.ln_mz2)));
+    const double g2 = 4.0 * 3.14159265358979323846 * (double)as;
+    double gp = 1.0;
+#pragma unroll
+    for (int i = 0; i < N - 2; ++i) gp *= g2;
+    double sp = 1.0;
+#pragma unroll
+    for (int i = 0; i < M - 2; ++i) sp *= shat;
+    const R f1 = R(1.7) * r_pow<R>(x1, R(-0.2)) * r_pow<R>(R(1) - x1, R(5));
+    const R f2 = R(1.7) * r_pow<R>(x2, R(-0.2)) * r_pow<R>(R(1) - x2, R(5));
+    const double lum = P.lnxmin * P.lnxmin * (double)f1 * (double)f2;
+    wf = P.wconst * lum / (2.0 * shat) * (P.phiconst * sp) * gp;
+  }
+  const double inv_rs = pow2_unit_inv(rs);
+  double ef = P.efac;
+  const double u2 = inv_rs * inv_rs;
+#pragma unroll
+  for (int i = 0; i < N - 4; ++i) ef *= u2;
+  B.efac[e] = ef;
+  B.wfac[e] = wf;
+  B.pass[e] = (uint8_t)pass;
+  if (B.hval) B.hval[e] = P.hist_obs == 0 ? ptlead : (P.hist_obs == 1 ? ht : rmin);
+
+  // ---- colour ordering, helicities, polarisations (FP64 construction)
+  int perm[N];
+  const uint32_t hel = sample_config<N>(P, ev, perm);
+  double kp[N][4];
+  int legp[N];
+  gather_positions<N>(kk, perm, kp, legp);
+  const int cap = B.cap;
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
+    const double sg = legp[a] < 2 ? -1.0 : 1.0;
+    CV4<double> ep, em;
+    polarisations<double>(sg * kp[a][1], sg * kp[a][2], sg * kp[a][3], ep, em);
+    const bool minus = (hel >> legp[a]) & 1u;
+    R *o = a == 0 ? B.in + (size_t)(12 * L) * cap : B.in + (size_t)(12 * (a - 1) + 4) * cap;
+    if (a > 0) {
+      R *ok = B.in + (size_t)(12 * (a - 1)) * cap;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) ok[(size_t)m * cap + e] = R(kp[a][m] * inv_rs);
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const Cx<double> z = minus ? em.c[m] : ep.c[m];
+      o[(size_t)m * cap + e] = R(z.re);
+      o[(size_t)(4 + m) * cap + e] = R(z.im);
+    }
+  }
+}
+
+// Polarisation basis of an outgoing massless momentum (E, px, py, pz) in FP64
+// (the Gram products): e1 = theta-hat = (ct cf, ct sf, -st), e2 = phi-hat =
+// (-sf, cf, 0), with ct = pz/E, st = pT/E, cf = px/pT, sf = py/pT (E = |p|
+// for a massless momentum).  Returned rounded to FP32.
+__device__ __forceinline__ void pol_basis_f32(double E, double px, double py, double pz, float (&e1)[3],
+                                              float (&e2)[2]) {
+  const double pt2 = px * px + py * py;
+  double cf = 1.0, sf = 0.0, pt = 0.0;
+  if (pt2 > 0.0) {
+    const double inv_pt = rsqrt(pt2);
+    pt = pt2 * inv_pt;
+    cf = px * inv_pt;
+    sf = py * inv_pt;
+  }
+  const double inv_e = 1.0 / E;
+  const double ct = pz * inv_e, st = pt * inv_e;
+  e1[0] = (float)(ct * cf);
+  e1[1] = (float)(ct * sf);
+  e1[2] = (float)(-st);
+  e2[0] = (float)(-sf);
+  e2[1] = (float)cf;
+}
+
+// Gathers per-leg FP32 data (momentum, polarisation basis) into colour
+// position order and writes the amplitude inputs of one event.
+template <int N>
+__device__ __forceinline__ void store_ordered(const EventParams &P, uint64_t ev, const ChunkBuf<float> &B, int e,
+                                              const float (&lk)[N][4], const float (&le1)[N][3],
+                                              const float (&le2)[N][2]) {
+  constexpr int L = N - 1;
+  // eps_+ = -(e1 + i e2)/sqrt2, eps_- = (e1 - i e2)/sqrt2
+  int perm[N];
+  const uint32_t hel = sample_config<N>(P, ev, perm);
+  const int cap = B.cap;
+  const float r2 = 0.70710678118654752440f;
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
+    const int want = perm[a];
+    float v[9];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = lk[0][q];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) v[4 + q] = le1[0][q];
+    v[7] = le2[0][0];
+    v[8] = le2[0][1];
+#pragma unroll
+    for (int l = 1; l < N; ++l) {
+      const bool hit = (want == l);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = hit ? lk[l][q] : v[q];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) v[4 + q] = hit ? le1[l][q] : v[4 + q];
+      v[7] = hit ? le2[l][0] : v[7];
+      v[8] = hit ? le2[l][1] : v[8];
+    }
+    const float sre = ((hel >> want) & 1u) ? r2 : -r2;
+    float *o = a == 0 ? B.in + (size_t)(12 * L) * cap : B.in + (size_t)(12 * (a - 1) + 4) * cap;
+    if (a > 0) {
+      float *ok = B.in + (size_t)(12 * (a - 1)) * cap;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) ok[(size_t)q * cap + e] = v[q];
+    }
+    o[e] = 0.f;                                  // re, time component
+    o[(size_t)1 * cap + e] = sre * v[4];
+    o[(size_t)2 * cap + e] = sre * v[5];
+    o[(size_t)3 * cap + e] = sre * v[6];
+    o[(size_t)4 * cap + e] = 0.f;                // im, time component
+    o[(size_t)5 * cap + e] = -r2 * v[7];
+    o[(size_t)6 * cap + e] = -r2 * v[8];
+    o[(size_t)7 * cap + e] = 0.f;
+  }
+}
+
+// K1, FP32-current form.  FP32: uniforms (from the Philox words directly),
+// Rambo seeds, x1/x2, cuts, observables, alpha_s, PDF.  FP64: the Rambo boost
+// and rescale (conservation and masslessness), the polarisation Gram
+// products, the weight factor.  Helicity labels and colour ordering are
+// exact integer functions of the draws (identical in both forms).
+template <int N>
+__device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<float> &B, int e) {
+  constexpr int M = N - 2, L = N - 1;
+  const EventParams &P = C.P;
+  const uint64_t idx = C.chunk_first + (uint64_t)e;
+  const uint64_t ev = P.first_event + idx;
+
+  const uint4 w0 = philox_block(P.seed, ev, 0);
+  const float lnxmin = (float)P.lnxmin;
+  const float x1 = expf(unit_f32(w0.x, w0.y) * lnxmin);
+  const float x2 = expf(unit_f32(w0.z, w0.w) * lnxmin);
+  const double shat = (double)x1 * (double)x2 * P.S;
+  const double rs = sqrt(shat);
+
+  // Rambo seeds in FP32, boost + rescale in FP64
+  float qf[M][4];
+  double Q0 = 0.0, Q1 = 0.0, Q2 = 0.0, Q3 = 0.0;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const uint4 wa = philox_block(P.seed, ev, 1 + 2 * i);
+    const uint4 wb = philox_block(P.seed, ev, 2 + 2 * i);
+    const float c = 2.f * unit_f32(wa.x, wa.y) - 1.f;
+    const float sn0 = sqrtf(fmaxf(1.f - c * c, 0.f));
+    float sn, cs;
+    sincospif(2.f * unit_f32(wa.z, wa.w), &sn, &cs);
+    const float q0 = -logf(unit_f32(wb.x, wb.y) * unit_f32(wb.z, wb.w));
+    qf[i][0] = q0;
+    qf[i][1] = q0 * sn0 * cs;
+    qf[i][2] = q0 * sn0 * sn;
+    qf[i][3] = q0 * c;
+    Q0 += (double)qf[i][0];
+    Q1 += (double)qf[i][1];
+    Q2 += (double)qf[i][2];
+    Q3 += (double)qf[i][3];
+  }
+  const double invM = rsqrt(Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3);
+  const double bx = -Q1 * invM, by = -Q2 * invM, bz = -Q3 * invM;
+  const double gam = Q0 * invM;
+  const double aa = 1.0 / (1.0 + gam);
+  const double xs = rs * invM;
+  double pk[M][4];
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const double q0 = qf[i][0], q1 = qf[i][1], q2 = qf[i][2], q3 = qf[i][3];
+    const double bq = bx * q1 + by * q2 + bz * q3;
+    pk[i][0] = xs * (gam * q0 + bq);
+    const double f = aa * bq + q0;
+    pk[i][1] = xs * (q1 + bx * f);
+    pk[i][2] = xs * (q2 + by * f);
+    pk[i][3] = xs * (q3 + bz * f);
+  }
+
+  // cuts and observables in FP32
+  const float y = 0.5f * logf(x1 / x2);
+  float eta[M], pt[M], px[M], py[M];
+  int pass = 1;
+  float sum = 0.f, lead = 0.f;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    px[i] = (float)pk[i][1];
+    py[i] = (float)pk[i][2];
+    const float pz = (float)pk[i][3];
+    const float pt2 = px[i] * px[i] + py[i] * py[i];
+    const float pabs = sqrtf(pt2 + pz * pz);
+    pt[i] = sqrtf(pt2);
+    eta[i] = 0.5f * logf((pabs + pz) / (pabs - pz)) + y;
+    sum += pt[i];
+    lead = fmaxf(lead, pt[i]);
+    pass &= (pt[i] > (float)P.pt_min) & (fabsf(eta[i]) < (float)P.eta_max);
+  }
+  float dr2min = 1e30f;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+#pragma unroll
+    for (int j = i + 1; j < M; ++j) {
+      const float dphi = atan2f(fabsf(px[i] * py[j] - py[i] * px[j]), px[i] * px[j] + py[i] * py[j]);
+      const float de = eta[i] - eta[j];
+      const float dr2 = de * de + dphi * dphi;
+      dr2min = fminf(dr2min, dr2);
+      pass &= (dr2 > (float)P.dr2_min);
+    }
+  }
+  const double ht = (double)sum, ptlead = (double)lead, rmin = (double)sqrtf(dr2min);
+  if (P.ht) P.ht[idx] = ht;
+  if (P.ptlead) P.ptlead[idx] = ptlead;
+  if (P.rmin) P.rmin[idx] = rmin;
+  if (P.pass) P.pass[idx] = (uint8_t)pass;
+
+  double wf = 0.0;
+  if (pass) {
+    const float mu = (float)P.mu_r_factor * sum;
+    const float as = (float)P.alphas_mz /
+                     (1.f + (float)P.alphas_mz * (float)P.b0 * (logf(mu * mu) - (float)P.ln_mz2));
+    const double g2 = 4.0 * 3.14159265358979323846 * (double)as;
+    double gp = 1.0;
+#pragma unroll
+    for (int i = 0; i < N - 2; ++i) gp *= g2;
+    double sp = 1.0;
+#pragma unroll
+    for (int i = 0; i < M - 2; ++i) sp *= shat;
+    const float f1 = 1.7f * powf(x1, -0.2f) * powf(1.f - x1, 5.f);
+    const float f2 = 1.7f * powf(x2, -0.2f) * powf(1.f - x2, 5.f);
+    const double lum = P.lnxmin * P.lnxmin * (double)f1 * (double)f2;
+    wf = P.wconst * lum / (2.0 * shat) * (P.phiconst * sp) * gp;
+  }
+  const double inv_rs = pow2_unit_inv(rs);
+  double ef = P.efac;
+  const double u2 = inv_rs * inv_rs;
+#pragma unroll
+  for (int i = 0; i < N - 4; ++i) ef *= u2;
+  B.efac[e] = ef;
+  B.wfac[e] = wf;
+  B.pass[e] = (uint8_t)pass;
+  if (B.hval) B.hval[e] = P.hist_obs == 0 ? ptlead : (P.hist_obs == 1 ? ht : rmin);
+
+  // per-leg FP32 data: momentum in units of the power-of-two scale, and the
+  // polarisation basis (e1 spatial, e2 transverse); beam-axis legs are exact
+  float lk[N][4], le1[N][3], le2[N][2];
+  const float sc = (float)inv_rs;
+  const float hs = (float)(0.5 * rs) * sc;
+  lk[0][0] = -hs; lk[0][1] = 0.f; lk[0][2] = 0.f; lk[0][3] = -hs;
+  lk[1][0] = -hs; lk[1][1] = 0.f; lk[1][2] = 0.f; lk[1][3] = hs;
+  le1[0][0] = 1.f; le1[0][1] = 0.f; le1[0][2] = 0.f; le2[0][0] = 0.f; le2[0][1] = 1.f;   // physical +z
+  le1[1][0] = -1.f; le1[1][1] = 0.f; le1[1][2] = 0.f; le2[1][0] = 0.f; le2[1][1] = 1.f;  // physical -z
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) lk[2 + i][m] = (float)pk[i][m] * sc;
+    pol_basis_f32(pk[i][0], pk[i][1], pk[i][2], pk[i][3], le1[2 + i], le2[2 + i]);
+  }
+
+  store_ordered<N>(P, ev, B, e, lk, le1, le2);
+}
+
+// Polarisation basis in double-single from double-single momentum components
+// (E = |p| for a massless momentum); results rounded to FP32.
+__device__ __forceinline__ void pol_basis_ds(DS E, DS px, DS py, DS pz, float (&e1)[3], float (&e2)[2]) {
+  const DS pt2 = ds_add(ds_mul(px, px), ds_mul(py, py));
+  DS cf = ds(1.f), sf = ds(0.f), pt = ds(0.f);
+  if (pt2.hi > 0.f) {
+    const DS ipt = ds_rsqrt(pt2);
+    pt = ds_mul(pt2, ipt);
+    cf = ds_mul(px, ipt);
+    sf = ds_mul(py, ipt);
+  }
+  const DS ie = ds_rcp(E);
+  const DS ct = ds_mul(pz, ie), st = ds_mul(pt, ie);
+  e1[0] = ds_mul(ct, cf).hi;
+  e1[1] = ds_mul(ct, sf).hi;
+  e1[2] = -st.hi;
+  e2[0] = -sf.hi;
+  e2[1] = cf.hi;
+}
+
+// K1, double-single form: as kin_fp32, with the steps that need more than
+// FP32 -- Rambo's boost and rescale, the polarisation Gram products -- in
+// double-single arithmetic on the FP32 pipe instead of native FP64 (1/64 of
+// the FP32 rate on this GPU).  The weight factor is assembled in FP32 with
+// its power-of-two scale kept as an exact exponent.
+template <int N>
+__device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<float> &B, int e) {
+  constexpr int M = N - 2, L = N - 1;
+  const EventParams &P = C.P;
+  const uint64_t idx = C.chunk_first + (uint64_t)e;
+  const uint64_t ev = P.first_event + idx;
+
+  const uint4 w0 = philox_block(P.seed, ev, 0);
+  const float lnxmin = (float)P.lnxmin;
+  const float x1 = expf(unit_f32(w0.x, w0.y) * lnxmin);
+  const float x2 = expf(unit_f32(w0.z, w0.w) * lnxmin);
+  const DS shat = ds_mul(ds_mul(DS{P.S_hi, P.S_lo}, x1), x2);
+  const DS rs = ds_sqrt(shat);
+
+  float qf[M][4];
+  DS Q[4] = {ds(0.f), ds(0.f), ds(0.f), ds(0.f)};
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const uint4 wa = philox_block(P.seed, ev, 1 + 2 * i);
+    const uint4 wb = philox_block(P.seed, ev, 2 + 2 * i);
+    const float c = 2.f * unit_f32(wa.x, wa.y) - 1.f;
+    const float sn0 = sqrtf(fmaxf(1.f - c * c, 0.f));
+    float sn, cs;
+    sincospif(2.f * unit_f32(wa.z, wa.w), &sn, &cs);
+    const float q0 = -logf(unit_f32(wb.x, wb.y) * unit_f32(wb.z, wb.w));
+    qf[i][0] = q0;
+    qf[i][1] = q0 * sn0 * cs;
+    qf[i][2] = q0 * sn0 * sn;
+    qf[i][3] = q0 * c;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) Q[m] = ds_add(Q[m], qf[i][m]);
+  }
+  const DS M2 = ds_sub(ds_mul(Q[0], Q[0]), ds_add(ds_add(ds_mul(Q[1], Q[1]), ds_mul(Q[2], Q[2])), ds_mul(Q[3], Q[3])));
+  const DS invM = ds_rsqrt(M2);
+  const DS bx = ds_neg(ds_mul(Q[1], invM)), by = ds_neg(ds_mul(Q[2], invM)), bz = ds_neg(ds_mul(Q[3], invM));
+  const DS gam = ds_mul(Q[0], invM);
+  const DS aa = ds_rcp(ds_add(gam, 1.f));
+  const DS xs = ds_mul(rs, invM);
+  DS pk[M][4];
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const DS bq = ds_add(ds_add(ds_mul(bx, qf[i][1]), ds_mul(by, qf[i][2])), ds_mul(bz, qf[i][3]));
+    pk[i][0] = ds_mul(xs, ds_add(ds_mul(gam, qf[i][0]), bq));
+    const DS f = ds_add(ds_mul(aa, bq), qf[i][0]);
+    pk[i][1] = ds_mul(xs, ds_add(ds_mul(bx, f), qf[i][1]));
+    pk[i][2] = ds_mul(xs, ds_add(ds_mul(by, f), qf[i][2]));
+    pk[i][3] = ds_mul(xs, ds_add(ds_mul(bz, f), qf[i][3]));
+  }
+
+  // cuts and observables in FP32 from the rounded momenta
+  const float y = 0.5f * logf(x1 / x2);
+  float eta[M], pt[M], px[M], py[M];
+  int pass = 1;
+  float sum = 0.f, lead = 0.f;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    px[i] = pk[i][1].hi;
+    py[i] = pk[i][2].hi;
+    const float pz = pk[i][3].hi;
+    const float pt2 = px[i] * px[i] + py[i] * py[i];
+    const float pabs = sqrtf(pt2 + pz * pz);
+    pt[i] = sqrtf(pt2);
+    eta[i] = 0.5f * logf((pabs + pz) / (pabs - pz)) + y;
+    sum += pt[i];
+    lead = fmaxf(lead, pt[i]);
+    pass &= (pt[i] > (float)P.pt_min) & (fabsf(eta[i]) < (float)P.eta_max);
+  }
+  float dr2min = 1e30f;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+#pragma unroll
+    for (int j = i + 1; j < M; ++j) {
+      const float dphi = atan2f(fabsf(px[i] * py[j] - py[i] * px[j]), px[i] * px[j] + py[i] * py[j]);
+      const float de = eta[i] - eta[j];
+      const float dr2 = de * de + dphi * dphi;
+      dr2min = fminf(dr2min, dr2);
+      pass &= (dr2 > (float)P.dr2_min);
+    }
+  }
+  const double ht = (double)sum, ptlead = (double)lead, rmin = (double)sqrtf(dr2min);
+  if (P.ht) P.ht[idx] = ht;
+  if (P.ptlead) P.ptlead[idx] = ptlead;
+  if (P.rmin) P.rmin[idx] = rmin;
+  if (P.pass) P.pass[idx] = (uint8_t)pass;
+
+  // momentum unit 2^-ex near 1/sqrt(s_hat); s' = s_hat 2^-2ex in [1/4, 1)
+  int ex;
+  frexpf(rs.hi, &ex);
+  const float sc = ldexpf(1.f, -ex);
+  const float sp = shat.hi * sc * sc;
+  double wf = 0.0;
+  if (pass) {
+    const float mu = (float)P.mu_r_factor * sum;
+    const float as = (float)P.alphas_mz /
+                     (1.f + (float)P.alphas_mz * (float)P.b0 * (logf(mu * mu) - (float)P.ln_mz2));
+    const float g2 = 4.f * 3.14159265358979323846f * as;
+    float F = 1.7f * powf(x1, -0.2f) * powf(1.f - x1, 5.f) * (1.7f * powf(x2, -0.2f) * powf(1.f - x2, 5.f));
+#pragma unroll
+    for (int i = 0; i < N - 2; ++i) F *= g2;
+    // s_hat^(m-3) = s'^(m-3) 2^(2 ex (m-3))
+    if (M >= 3) {
+#pragma unroll
+      for (int i = 0; i < M - 3; ++i) F *= sp;
+    } else {
+      F /= sp;
+    }
+    wf = ldexp(P.wk * (double)F, 2 * ex * (M - 3));
+  }
+  B.efac[e] = ldexp(P.efac, -2 * ex * (N - 4));
+  B.wfac[e] = wf;
+  B.pass[e] = (uint8_t)pass;
+  if (B.hval) B.hval[e] = P.hist_obs == 0 ? ptlead : (P.hist_obs == 1 ? ht : rmin);
+
+  float lk[N][4], le1[N][3], le2[N][2];
+  const float hs = 0.5f * rs.hi * sc;
+  lk[0][0] = -hs; lk[0][1] = 0.f; lk[0][2] = 0.f; lk[0][3] = -hs;
+  lk[1][0] = -hs; lk[1][1] = 0.f; lk[1][2] = 0.f; lk[1][3] = hs;
+  le1[0][0] = 1.f; le1[0][1] = 0.f; le1[0][2] = 0.f; le2[0][0] = 0.f; le2[0][1] = 1.f;   // physical +z
+  le1[1][0] = -1.f; le1[1][1] = 0.f; le1[1][2] = 0.f; le2[1][0] = 0.f; le2[1][1] = 1.f;  // physical -z
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) lk[2 + i][m] = pk[i][m].hi * sc;
+    pol_basis_ds(pk[i][0], pk[i][1], pk[i][2], pk[i][3], le1[2 + i], le2[2 + i]);
+  }
+  store_ordered<N>(P, ev, B, e, lk, le1, le2);
+}
+
+template <int N, typename R>
+__global__ void __launch_bounds__(kBlock) kin_kernel(ChunkParams C, ChunkBuf<R> B) {
+  const int e = blockIdx.x * kBlock + threadIdx.x;
+  if (e >= C.count) return;
+  if constexpr (sizeof(R) == 4)
+    kin_fp32<N>(C, B, e);
+  else
+    kin_generic<N, R>(C, B, e);
+}
+
+template <int N>
+__global__ void __launch_bounds__(kBlock) kin_ds_kernel(ChunkParams C, ChunkBuf<float> B) {
+  const int e = blockIdx.x * kBlock + threadIdx.x;
+  if (e >= C.count) return;
+  kin_ds<N>(C, B, e);
+}
+
+// ---------------------------------------------------------------------------
+// K2 epilogue shared by the Berends-Giele kernels: |m|^2 -> estimator and
+// weight, per-event outputs, and block-owned partial sums.  Each block owns
+// partial row blockIdx.x and adds this chunk's sums to it (chunks run in order
+// on one stream, so the read-modify-write is race-free and deterministic).
+// ---------------------------------------------------------------------------
+template <int NB>
+struct Accum {
+  double sw = 0.0, sw2 = 0.0, npass = 0.0, nbad = 0.0;
+};
+
+template <int NB, typename R>
+__device__ __forceinline__ void finish_event(const ChunkParams &C, const ChunkBuf<R> &B, int e, double amp2,
+                                             Accum<NB> &A, double &w_out, int &bin_out) {
+  const EventParams &P = C.P;
+  const uint64_t idx = C.chunk_first + (uint64_t)e;
+  const double E = B.efac[e] * amp2;
+  double w = B.wfac[e] * E;
+  if (!isfinite(w)) {
+    A.nbad += 1.0;
+    w = 0.0;
+  }
+  if (P.me2) P.me2[idx] = E;
+  if (P.weight) P.weight[idx] = w;
+  const int ok = B.pass[e];
+  A.sw += w;
+  A.sw2 += w * w;
+  A.npass += (double)ok;
+  w_out = w;
+  bin_out = (P.hist_bins > 0 && ok) ? hist_bin(B.hval[e], P.hist_lo, P.hist_inv_width, P.hist_bins) : -1;
+}
+
+// Shared-memory scratch of the epilogue: histogram accumulators and a tile's
+// (w, bin) staging, after `offset` bytes used by the kernel itself.
+template <int NB>
+struct EpiSmem {
+  double *hw, *hw2, *stage_w;
+  int *stage_b;
+  __device__ EpiSmem(char *base, int nb2) {
+    hw = (double *)base;
+    hw2 = hw + nb2;
+    stage_w = hw2 + nb2;
+    stage_b = (int *)(stage_w + NB);
+  }
+  static size_t bytes(int hist_bins) {
+    const int nb2 = hist_bins > 0 ? hist_bins + 2 : 0;
+    return (size_t)(2 * nb2 + NB) * sizeof(double) + (size_t)NB * sizeof(int);
+  }
+};
+
+template <int NB>
+__device__ __forceinline__ void epi_tile(const EpiSmem<NB> &S, int nb2, double w, int bin) {
+  if (nb2 == 0) return;
+  __syncthreads();
+  S.stage_w[threadIdx.x] = w;
+  S.stage_b[threadIdx.x] = bin;
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb2; b += NB) {
+    double a = 0.0, a2 = 0.0;
+    for (int t = 0; t < NB; ++t) {
+      if (S.stage_b[t] == b) {
+        const double x = S.stage_w[t];
+        a += x;
+        a2 += x * x;
+      }
+    }
+    S.hw[b] += a;
+    S.hw2[b] += a2;
+  }
+}
+
+template <int NB>
+__device__ __forceinline__ void epi_flush(const EpiSmem<NB> &S, int nb2, Accum<NB> &A, double *partials,
+                                          int hist_bins) {
+  __shared__ double red[4][NB];
+  red[0][threadIdx.x] = A.sw;
+  red[1][threadIdx.x] = A.sw2;
+  red[2][threadIdx.x] = A.npass;
+  red[3][threadIdx.x] = A.nbad;
+  __syncthreads();
+  for (int s = NB / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  double *row = partials + (size_t)blockIdx.x * partial_stride(hist_bins);
+  if (threadIdx.x < 4) row[threadIdx.x] += red[threadIdx.x][0];
+  // hw and hw2 are contiguous: [w bins | w^2 bins]
+  for (int i = threadIdx.x; i < 2 * nb2; i += NB) row[kPartialHead + i] += S.hw[i];
+}
+
+template <typename R>
+__device__ __forceinline__ void load_cv(const R *base, int cap, int e, CV4<R> &v) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    v.c[m].re = base[(size_t)m * cap + e];
+    v.c[m].im = base[(size_t)(4 + m) * cap + e];
+  }
+}
+
+// K2, register form (FP32, n <= 7): thread per event, the whole current table
+// in registers.
+template <int N, typename R, int NB>
+__global__ void __launch_bounds__(NB) bg_reg_kernel(ChunkParams C, ChunkBuf<R> B, double *partials) {
+  constexpr int L = N - 1;
+  extern __shared__ __align__(16) char smem_raw[];
+  const int nb2 = C.P.hist_bins > 0 ? C.P.hist_bins + 2 : 0;
+  EpiSmem<NB> S(smem_raw, nb2);
+  for (int i = threadIdx.x; i < 2 * nb2; i += NB) S.hw[i] = 0.0;
+  Accum<NB> A;
+  const int ntiles = (C.count + NB - 1) / NB;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int e = tile * NB + threadIdx.x;
+    double w = 0.0;
+    int bin = -1;
+    if (e < C.count) {
+      RV4<R> k[L];
+      CV4<R> ev[L], e0;
+#pragma unroll
+      for (int a = 0; a < L; ++a) {
+        const R *base = B.in + (size_t)(12 * a) * B.cap;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) k[a].v[m] = base[(size_t)m * B.cap + e];
+        load_cv(base + (size_t)4 * B.cap, B.cap, e, ev[a]);
+      }
+      load_cv(B.in + (size_t)(12 * L) * B.cap, B.cap, e, e0);
+      const Cx<R> amp = bg_amplitude<R, L>(k, ev, e0);
+      const double re = amp.re, im = amp.im;
+      finish_event<NB, R>(C, B, e, re * re + im * im, A, w, bin);
+    }
+    epi_tile<NB>(S, nb2, w, bin);
+  }
+  epi_flush<NB>(S, nb2, A, partials, C.P.hist_bins);
+}
+
+// K2, loop form (FP64): table in per-thread local memory.
+template <int N, int NB>
+__global__ void __launch_bounds__(NB) bg_loop_kernel(ChunkParams C, ChunkBuf<double> B, double *partials) {
+  constexpr int L = N - 1;
+  extern __shared__ __align__(16) char smem_raw[];
+  const int nb2 = C.P.hist_bins > 0 ? C.P.hist_bins + 2 : 0;
+  EpiSmem<NB> S(smem_raw, nb2);
+  for (int i = threadIdx.x; i < 2 * nb2; i += NB) S.hw[i] = 0.0;
+  Accum<NB> A;
+  const int ntiles = (C.count + NB - 1) / NB;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int e = tile * NB + threadIdx.x;
+    double w = 0.0;
+    int bin = -1;
+    if (e < C.count) {
+      BGLoop<double, L> bg;
+#pragma unroll 1
+      for (int a = 0; a < L; ++a) {
+        const double *base = B.in + (size_t)(12 * a) * B.cap;
+        const int X = BGLoop<double, L>::tri(a, a);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) bg.K[X].v[m] = base[(size_t)m * B.cap + e];
+        load_cv(base + (size_t)4 * B.cap, B.cap, e, bg.J[X]);
+      }
+      CV4<double> e0;
+      load_cv(B.in + (size_t)(12 * L) * B.cap, B.cap, e, e0);
+      const Cx<double> amp = bg.run(e0);
+      finish_event<NB, double>(C, B, e, amp.re * amp.re + amp.im * amp.im, A, w, bin);
+    }
+    epi_tile<NB>(S, nb2, w, bin);
+  }
+  epi_flush<NB>(S, nb2, A, partials, C.P.hist_bins);
+}
+
+// ---------------------------------------------------------------------------
+// K2, row form (FP32, n >= 8).  Thread per event; currents are computed row
+// by row, rows a = L-1 down to 0 (row a = the sets [a..b], b >= a), each row
+// in increasing b.  The row being built lives in registers (it supplies the
+// left part J[a..i] of every split and the first part J_A of every four-
+// vertex triple), older rows live in the thread's own shared-memory column
+// (they supply the right parts and the middle parts).  Right-part momenta
+// K[i+1..b] are summed on the fly from the leg momenta, so no momentum table
+// is stored.  Shared-memory traffic is 10 floats per split and 8 per triple.
+// ---------------------------------------------------------------------------
+template <int L>
+__host__ __device__ constexpr int t1(int a, int b) {
+  // sets [a..b] with 1 <= a <= b <= L-1, triangular over the legs 1..L-1
+  return (a - 1) * (L - 1) - ((a - 1) * (a - 2)) / 2 + (b - a);
+}
+
+template <int NB>
+__device__ __forceinline__ void st_cv(float4 *J4, int t, const CV4<float> &v) {
+  J4[(2 * t) * NB + threadIdx.x] = make_float4(v.c[0].re, v.c[0].im, v.c[1].re, v.c[1].im);
+  J4[(2 * t + 1) * NB + threadIdx.x] = make_float4(v.c[2].re, v.c[2].im, v.c[3].re, v.c[3].im);
+}
+
+template <int NB>
+__device__ __forceinline__ CV4<float> ld_cv(const float4 *J4, int t) {
+  const float4 a = J4[(2 * t) * NB + threadIdx.x];
+  const float4 b = J4[(2 * t + 1) * NB + threadIdx.x];
+  CV4<float> v;
+  v.c[0] = cx<float>(a.x, a.y);
+  v.c[1] = cx<float>(a.z, a.w);
+  v.c[2] = cx<float>(b.x, b.y);
+  v.c[3] = cx<float>(b.z, b.w);
+  return v;
+}
+
+template <int L, int NB>
+__device__ __forceinline__ Cx<float> bg_rows(const float4 *K4, const CV4<float> &eps_pos0, const CV4<float> &e0,
+                                             float4 *J4, float2 *S2) {
+  Cx<float> amp = cx<float>(0.f, 0.f);
+  auto kleg = [&](int leg) {
+    const float4 v = K4[leg * NB + threadIdx.x];
+    RV4<float> r = {{v.x, v.y, v.z, v.w}};
+    return r;
+  };
+  // Runtime loop over rows; inside a row every register index is relative to
+  // a and compile-time, so the row stays in registers and only one row's
+  // worth of state is live at a time.
+#pragma unroll 1
+  for (int a = L - 1; a >= 0; --a) {
+    const int len = L - a;  // currents in this row
+    CV4<float> row[L];
+    Cx<float> srow[L];
+    RV4<float> krow[L];
+    row[0] = (a == 0) ? eps_pos0 : ld_cv<NB>(J4, t1<L>(a, a));
+    srow[0] = cx<float>(0.f, 0.f);
+    krow[0] = kleg(a);
+#pragma unroll
+    for (int d = 1; d < L; ++d) {
+      if (d >= len) break;
+      const int b = a + d;
+      krow[d] = radd(krow[d - 1], kleg(b));
+      CV4<float> acc = cv_zero<float>(), tri = cv_zero<float>();
+      Cx<float> s = cx<float>(0.f, 0.f);
+      RV4<float> kr = {{0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+      for (int dp = d - 1; dp >= 0; --dp) {
+        const int r0 = a + dp + 1;  // right part [r0..b]
+        kr = radd(kr, kleg(r0));
+        const CV4<float> Jr = ld_cv<NB>(J4, t1<L>(r0, b));
+        const CV4<float> &Jl = row[dp];
+        const Cx<float> d0 = mdot(Jl, Jr);
+        const Cx<float> jlkr = mdot(Jl, kr);
+        const Cx<float> krjl = mdot(Jr, krow[dp]);
+        Cx<float> cr = cx<float>(2.f * jlkr.re - srow[dp].re, 2.f * jlkr.im - srow[dp].im);
+        Cx<float> cl = cx<float>(-2.f * krjl.re, -2.f * krjl.im);
+        if (dp + 1 < d) {  // right part has more than one leg
+          const float2 sr = S2[t1<L>(r0, b) * NB + threadIdx.x];
+          cl.re -= sr.x;
+          cl.im -= sr.y;
+        }
+        axpy(acc, cr, Jr);
+        axpy(acc, cl, Jl);
+        axpy(acc, d0, rsub(krow[dp], kr));
+        s.re += d0.re;
+        s.im += d0.im;
+        // four-vertex triples whose last part is [r0..b]
+#pragma unroll
+        for (int dpp = 0; dpp < dp; ++dpp) {
+          const CV4<float> JB = ld_cv<NB>(J4, t1<L>(a + dpp + 1, a + dp));
+          axpy(tri, mdot(row[dpp], Jr), JB);
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        acc.c[m].re = fmaf(2.f, tri.c[m].re, acc.c[m].re);
+        acc.c[m].im = fmaf(2.f, tri.c[m].im, acc.c[m].im);
+      }
+      if (a == 0 && d == L - 1) {
+        amp = mdot(e0, acc);
+      } else {
+        const float inv = 1.f / mdot(krow[d], krow[d]);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          row[d].c[m].re = acc.c[m].re * inv;
+          row[d].c[m].im = acc.c[m].im * inv;
+        }
+        srow[d] = s;
+        if (a > 0) {
+          st_cv<NB>(J4, t1<L>(a, b), row[d]);
+          S2[t1<L>(a, b) * NB + threadIdx.x] = make_float2(s.re, s.im);
+        }
+      }
+    }
+  }
+  return amp;
+}
+
+template <int L>
+__host__ __device__ constexpr size_t rows_smem_per_thread() {
+  return (size_t)(L * (L - 1) / 2) * (2 * sizeof(float4) + sizeof(float2)) + (size_t)L * sizeof(float4);
+}
+
+template <int N, int NB>
+__global__ void __launch_bounds__(NB) bg_rows_kernel(ChunkParams C, ChunkBuf<float> B, double *partials) {
+  constexpr int L = N - 1, T1 = L * (L - 1) / 2;
+  extern __shared__ __align__(16) char smem_raw[];
+  float4 *J4 = (float4 *)smem_raw;
+  float4 *K4 = J4 + 2 * T1 * NB;
+  float2 *S2 = (float2 *)(K4 + L * NB);
+  const int nb2 = C.P.hist_bins > 0 ? C.P.hist_bins + 2 : 0;
+  EpiSmem<NB> S((char *)(S2 + T1 * NB), nb2);
+  for (int i = threadIdx.x; i < 2 * nb2; i += NB) S.hw[i] = 0.0;
+  Accum<NB> A;
+  const int ntiles = (C.count + NB - 1) / NB;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int e = tile * NB + threadIdx.x;
+    double w = 0.0;
+    int bin = -1;
+    if (e < C.count) {
+      CV4<float> eps0pos, e0;
+#pragma unroll
+      for (int a = 0; a < L; ++a) {
+        const float *base = B.in + (size_t)(12 * a) * B.cap;
+        K4[a * NB + threadIdx.x] = make_float4(base[e], base[(size_t)B.cap + e], base[(size_t)2 * B.cap + e],
+                                               base[(size_t)3 * B.cap + e]);
+        CV4<float> ea;
+        load_cv(base + (size_t)4 * B.cap, B.cap, e, ea);
+        if (a == 0)
+          eps0pos = ea;
+        else
+          st_cv<NB>(J4, t1<L>(a, a), ea);
+      }
+      load_cv(B.in + (size_t)(12 * L) * B.cap, B.cap, e, e0);
+      const Cx<float> amp = bg_rows<L, NB>(K4, eps0pos, e0, J4, S2);
+      const double re = amp.re, im = amp.im;
+      finish_event<NB, float>(C, B, e, re * re + im * im, A, w, bin);
+    }
+    epi_tile<NB>(S, nb2, w, bin);
+  }
+  epi_flush<NB>(S, nb2, A, partials, C.P.hist_bins);
+}
+
+}  // namespace tess

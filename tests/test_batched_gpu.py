@@ -1,0 +1,122 @@
+"""Batched mixed multiplicities (one captured CUDA graph, one branch per
+process) and the amplitude-kernel autotuner, through the C ABI.
+
+The batched path runs the same kernels with the same plans as separate
+tess_generate calls, so its outputs must be identical to them; replaying the
+cached graph accumulates a second time; changing an argument re-captures.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+import paper_1002_3446_gb300 as tess  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available()
+    c = tess.tess_init(0)
+    yield c
+    tess.tess_destroy(c)
+
+
+def _procs():
+    return [
+        tess.process(4, precision=tess.TESS_FP32_CURRENTS, hist_bins=20, hist_observable=tess.TESS_OBS_PTLEAD),
+        tess.process(6, precision=tess.TESS_FP64, hist_bins=10, hist_observable=tess.TESS_OBS_HT, hist_lo=100.0,
+                     hist_hi=1100.0),
+        tess.process(9, precision=tess.TESS_FP32_CURRENTS),
+        tess.process(12, precision=tess.TESS_FP32_CURRENTS, pt_min=30.0),
+    ]
+
+
+def _runs(ctx, procs, counts):
+    return [tess.Run(ctx, p, n) for p, n in zip(procs, counts)]
+
+
+def _host(run):
+    torch.cuda.synchronize()
+    d = {k: v.cpu().numpy() for k, v in run.t.items() if v is not None}
+    d["acc"] = run.acc.cpu().numpy()
+    d["hist"] = run.hist.cpu().numpy() if run.hist is not None else None
+    return d
+
+
+def test_batched_equals_separate_calls_and_replays(ctx):
+    procs = _procs()
+    counts = [70000, 9000, 3001, 700]
+    seeds = [1, 2, 3, 4]
+    firsts = [0, 10, 1 << 33, 5]
+    sep = _runs(ctx, procs, counts)
+    for r, s, f in zip(sep, seeds, firsts):
+        r.generate(s, f)
+    bat = _runs(ctx, procs, counts)
+    ws_bytes = tess.tess_workspace_size_batched(ctx, procs, counts)
+    ws = torch.empty((ws_bytes + 7) // 8, dtype=torch.float64, device="cuda")
+    outs = [r.outputs for r in bat]
+    tess.tess_generate_batched(ctx, procs, seeds, firsts, counts, outs, ws)
+    for a, b in zip(bat, sep):
+        ha, hb = _host(a), _host(b)
+        for key in ("weight", "me2", "pass", "ht", "ptlead", "rmin", "acc"):
+            assert np.array_equal(ha[key], hb[key]), key
+        if ha["hist"] is not None:
+            assert np.array_equal(ha["hist"], hb["hist"])
+    # replay of the cached graph accumulates again
+    tess.tess_generate_batched(ctx, procs, seeds, firsts, counts, outs, ws)
+    for a, b, n in zip(bat, sep, counts):
+        sa, sb = a.result(), b.result()
+        assert sa[3] == 2 * n and np.isclose(sa[0], sb[0], rtol=1e-12)
+    # a changed argument re-captures
+    seeds2 = [11, 12, 13, 14]
+    for r in bat:
+        r.reset()
+    tess.tess_generate_batched(ctx, procs, seeds2, firsts, counts, outs, ws)
+    sep2 = _runs(ctx, procs, counts)
+    for r, s, f in zip(sep2, seeds2, firsts):
+        r.generate(s, f)
+    for a, b in zip(bat, sep2):
+        assert np.array_equal(_host(a)["weight"], _host(b)["weight"])
+
+
+def test_batched_rejects_small_workspace(ctx):
+    procs = _procs()[:2]
+    counts = [1000, 1000]
+    bat = _runs(ctx, procs, counts)
+    ws = torch.empty(16, dtype=torch.float64, device="cuda")
+    with pytest.raises(tess.TessError) as e:
+        tess.tess_generate_batched(ctx, procs, [1, 2], [0, 0], counts, [r.outputs for r in bat], ws)
+    assert e.value.code == tess.TESS_E_WORKSPACE
+
+
+@pytest.mark.parametrize("n,prec", [(5, tess.TESS_FP32_CURRENTS), (7, tess.TESS_FP32_CURRENTS),
+                                    (8, tess.TESS_FP32_CURRENTS), (10, tess.TESS_FP32_CURRENTS),
+                                    (6, tess.TESS_FP64)])
+def test_autotune_choice_is_valid_and_consistent(ctx, n, prec):
+    proc = tess.process(n, precision=prec, pt_min=30.0 if n >= 10 else 20.0)
+    N = 1 << 16
+    run = tess.Run(ctx, proc, N)  # workspace sized before tuning
+    ref = _host_generate(run)
+    acc = torch.zeros(tess.TESS_ACC_LEN, dtype=torch.float64, device="cuda")
+    form = tess.tess_autotune(ctx, proc, N, acc, run.workspace)
+    valid = {tess.TESS_K2_LOOP} if prec == tess.TESS_FP64 else (
+        ({tess.TESS_K2_REG} if n <= 8 else set()) | ({tess.TESS_K2_ROWS32, tess.TESS_K2_ROWS64} if n >= 6 else set()))
+    assert form in valid
+    run.reset()
+    got = _host_generate(run)  # the tuned variant, same workspace
+    assert np.array_equal(got["pass"], ref["pass"])
+    if prec == tess.TESS_FP64:
+        assert np.array_equal(got["weight"], ref["weight"])
+    else:
+        # variants differ only in the FP32 summation order of the amplitude
+        ok = ref["me2"] > 1e-6 * np.median(ref["me2"][ref["me2"] > 0])
+        rel = np.abs(got["me2"][ok] - ref["me2"][ok]) / ref["me2"][ok]
+        assert np.median(rel) < 1e-5
+    print(f"autotune n={n} precision={prec}: variant {form}")
+
+
+def _host_generate(run):
+    run.generate(7, 0)
+    return _host(run)

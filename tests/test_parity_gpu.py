@@ -12,14 +12,17 @@ oracle's inputs; nothing is derived from the CUDA path):
     evaluation.  Events needing the fallback are counted and reported.
   FP32-current path: the error is stated per result, not bounded per event
     (an FP32 evaluation of an event near a zero of the amplitude can be off
-    by O(1)); the median (< 1e-5), 99th percentile (< 1e-2) and the
+    by O(1)); the median (< 1e-5), 99th percentile (< 5e-2) and the
     weight-weighted mean (< 1e-4, the quantity that enters sigma) of the
     per-event relative error against the FP64 oracle are asserted and printed.
   Amplitudes that vanish at tree level (all labels equal or one different)
     are rounding noise: both sides must be below 1e-20 (FP64) / 1e-6 (FP32)
     of the event's MHV scale |A(legs 1, 2 with the odd label)|^2.
   Observables: relative 1e-10 (Rambo's final boost amplifies rounding for
-    two nearly collinear seeds).  Cross sections and histogram bins:
+    two nearly collinear seeds); 1e-4 in the FP32 form, whose Rambo seeds,
+    cuts and observables are FP32 (the FP64 boost amplifies the seeds'
+    rounding by up to ~gamma^2; flags may then differ within 1e-4 of a
+    threshold).  Cross sections and histogram bins:
     relative 1e-10 plus an absolute 1e-12 of the total.
   A pass flag may differ only when a cut quantity lies within 1e-9 of its
     threshold.
@@ -83,20 +86,20 @@ def mhv_scale(orc, k, order):
     return abs(orc.amp(list(order), k, eps)) ** 2 / 2 ** (n - 2)
 
 
-def near_cut(orc, p, k, y):
-    """True if a cut quantity of the event is within 1e-9 of its threshold."""
+def near_cut(orc, p, k, y, tol=1e-9):
+    """True if a cut quantity of the event is within tol (relative) of its threshold."""
     m = p.n_gluons - 2
     pk = k[2:]
     pt = np.hypot(pk[:, 1], pk[:, 2])
     pa = np.linalg.norm(pk[:, 1:], axis=1)
     eta = 0.5 * np.log((pa + pk[:, 3]) / (pa - pk[:, 3])) + y
-    if np.any(np.abs(pt / p.pt_min - 1) < 1e-9) or np.any(np.abs(np.abs(eta) - p.eta_max) < 1e-9 * p.eta_max):
+    if np.any(np.abs(pt / p.pt_min - 1) < tol) or np.any(np.abs(np.abs(eta) - p.eta_max) < tol * p.eta_max):
         return True
     for i in range(m):
         for j in range(i + 1, m):
             dphi = math.atan2(abs(pk[i, 1] * pk[j, 2] - pk[i, 2] * pk[j, 1]), pk[i, 1] * pk[j, 1] + pk[i, 2] * pk[j, 2])
             dr2 = (eta[i] - eta[j]) ** 2 + dphi**2
-            if abs(dr2 / p.dr_min**2 - 1) < 1e-9:
+            if abs(dr2 / p.dr_min**2 - 1) < tol:
                 return True
     return False
 
@@ -109,9 +112,10 @@ def compare_events(orc, p, g, seed, first, idx, stats=None):
     """Per-event comparison of GPU outputs at positions idx with the oracle."""
     op = orc_proc(orc, p)
     n = p.n_gluons
-    fp32 = p.precision == tess.TESS_FP32_CURRENTS
+    fp32 = p.precision in (tess.TESS_FP32_CURRENTS, tess.TESS_FP32_DS)
     floor = RTOL32 if fp32 else RTOL64  # FP32: events above it are only counted
     vtol = 1e-6 if fp32 else 1e-20
+    otol = 1e-4 if fp32 else 1e-10  # FP32 form: FP32 Rambo seeds, cuts and observables
     flips = fallback = 0
     rel = []
     wdiff = wsum = 0.0
@@ -119,9 +123,9 @@ def compare_events(orc, p, g, seed, first, idx, stats=None):
         ev = first + int(i)
         r = orc.event(op, seed, ev)
         for key in ("ht", "ptlead", "rmin"):
-            assert np.isclose(g[key][i], r[key], rtol=1e-10, atol=0), (key, i, g[key][i], r[key])
+            assert np.isclose(g[key][i], r[key], rtol=otol, atol=0), (key, i, g[key][i], r[key])
         if bool(g["pass"][i]) != r["pass"]:
-            assert near_cut(orc, p, r["k"], r["y"]), f"pass flag differs away from a cut boundary (event {i})"
+            assert near_cut(orc, p, r["k"], r["y"], otol), f"pass flag differs away from a cut boundary (event {i})"
             flips += 1
             continue
         if p.helicity_mode == tess.TESS_HEL_SAMPLE and vanishing(r["hel_bits"], n):
@@ -226,17 +230,19 @@ def test_sampled_events_fp64(ctx, orc, n):
 
 
 @pytest.mark.parametrize("n", [4, 6, 8, 10, 12])
-def test_sampled_events_fp32_currents(ctx, orc, n):
-    p = tess.process(n, precision=tess.TESS_FP32_CURRENTS, pt_min=30.0 if n >= 10 else 20.0)
+@pytest.mark.parametrize("precision", [tess.TESS_FP32_CURRENTS, tess.TESS_FP32_DS])
+def test_sampled_events_fp32_currents(ctx, orc, n, precision):
+    p = tess.process(n, precision=precision, pt_min=30.0 if n >= 10 else 20.0)
     N = 4 * 128 + 17
     g = gpu_generate(ctx, p, 9, 0, N)
     st = {}
     compare_events(orc, p, g, 9, 0, np.arange(N), st)
-    print(f"FP32 currents n={n}: per-event relative error median {st['median']:.2e} "
+    print(f"FP32 currents ({'double-single' if precision == tess.TESS_FP32_DS else 'native FP64'} steps) n={n}: "
+          f"per-event relative error median {st['median']:.2e} "
           f"p99 {st['p99']:.2e} max {st['max']:.2e} over {st['compared']} events, "
           f"{st['ill_conditioned']} ill-conditioned, {st['flips']} cut flips, "
           f"weight-weighted {st['weighted']:.2e}")
-    assert st["median"] < 1e-5 and st["p99"] < 1e-2 and st["weighted"] < 1e-4
+    assert st["median"] < 1e-5 and st["p99"] < 5e-2 and st["weighted"] < 1e-4
 
 
 # ---------------------------------------------------------------- full-size configurations
@@ -264,12 +270,15 @@ def test_full_gg2g_2e20_fp64(ctx, orc):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("n,N,pt", [(6, 1 << 24, 20.0), (10, 1 << 26, 30.0)])
-def test_full_size_sampled_parity(ctx, orc, n, N, pt):
+@pytest.mark.parametrize("n,N,pt,precision", [(6, 1 << 24, 20.0, tess.TESS_FP32_CURRENTS),
+                                              (6, 1 << 24, 20.0, tess.TESS_FP32_DS),
+                                              (10, 1 << 26, 30.0, tess.TESS_FP32_CURRENTS),
+                                              (10, 1 << 26, 30.0, tess.TESS_FP32_DS)])
+def test_full_size_sampled_parity(ctx, orc, n, N, pt, precision):
     """Full-size runs in the benchmark's launch configuration; 1024 sampled
     events are recomputed one by one by the oracle; sigma is checked against
     the sum of the per-event weights."""
-    p = tess.process(n, precision=tess.TESS_FP32_CURRENTS, pt_min=pt, hist_bins=40, hist_observable=tess.TESS_OBS_HT,
+    p = tess.process(n, precision=precision, pt_min=pt, hist_bins=40, hist_observable=tess.TESS_OBS_HT,
                      hist_lo=200.0, hist_hi=3000.0)
     run = tess.Run(ctx, p, N, per_event=("weight", "me2", "pass", "ht", "ptlead", "rmin"))
     run.generate(1, 0)
@@ -282,12 +291,12 @@ def test_full_size_sampled_parity(ctx, orc, n, N, pt):
     for j, i in enumerate(idx):
         r = orc.event(op, 1, int(i))
         if bool(g["pass"][j]) != r["pass"]:
-            assert near_cut(orc, p, r["k"], r["y"])
+            assert near_cut(orc, p, r["k"], r["y"], 1e-4)
             continue
         if vanishing(r["hel_bits"], n):
             continue
         errs.append(abs(g["me2"][j] - r["me2"]) / r["me2"])
-        assert np.isclose(g["ht"][j], r["ht"], rtol=1e-12)
+        assert np.isclose(g["ht"][j], r["ht"], rtol=1e-4)
     errs = np.array(errs)
     print(f"n={n} N={N}: sampled FP32 relative error median {np.median(errs):.2e} max {errs.max():.2e}")
     assert np.median(errs) < 1e-5 and np.quantile(errs, 0.99) < 1e-2
