@@ -188,6 +188,32 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
 int tess_autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events, double *acc_scratch,
                   void *workspace, size_t workspace_bytes, void *stream, int *form_out);
 
+/* ---- Draws and gradients (no counterpart in the paper's method) --------------
+ * tess_draws writes the generator's own random inputs of events
+ * [first_event, first_event + n_events) of stream `seed`:
+ *   u      device [n_events][2 + 4(n-2)] doubles: u_x1, u_x2, then four Rambo
+ *          uniforms per final-state gluon (layout of the counter-based draws)
+ *   hel    device [n_events] uint32 helicity labels (bit i: leg i)
+ *   order  device [n_events][n] uint8 colour orderings (order[0] = 0)
+ * tess_gradients evaluates, for caller-given (u, hel, order) -- e.g. from
+ * tess_draws, or uniforms transformed by a phase-space map -- the event weight
+ * w (pb) of the sampled-mode estimator and its gradients:
+ *   dw_du     [n_events][2 + 4(n-2)]  total derivative w.r.t. the uniforms
+ *   dw_dk     [n_events][n][4]        w.r.t. the all-outgoing momenta at fixed
+ *                                     x1, x2 (polarisation vectors and K sums
+ *                                     follow k; beam-axis legs keep their basis)
+ *   dw_dlnmu  [n_events]              w.r.t. ln mu_R (one-loop running)
+ * all multiplied by dL_dw[e] when dL_dw is given (a vector-Jacobian product).
+ * The cuts are a step function: events failing them have w = 0 and zero
+ * gradients.  Kinematics and their adjoints are FP64; the Berends-Giele
+ * forward pass and its adjoint are FP64 for TESS_FP64 and FP32 otherwise.
+ * Any output pointer may be NULL. */
+int tess_draws(tess_ctx *ctx, int n, uint64_t seed, uint64_t first_event, uint64_t n_events, double *u,
+               uint32_t *hel, uint8_t *order, void *stream);
+int tess_gradients(tess_ctx *ctx, const tess_process *proc, uint64_t n_events, const double *u, const uint32_t *hel,
+                   const uint8_t *order, const double *dL_dw, double *w, double *dw_du, double *dw_dk,
+                   double *dw_dlnmu, void *stream);
+
 /* Colour-ordered matrix elements for caller-given kinematics (the
  * matrix-element stage alone, Eq. (BG-recursion) and the amplitude
  * equation of Sec. 3):  me2[e] = |A(order_e; hel_e)|^2 with

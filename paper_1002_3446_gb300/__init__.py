@@ -37,7 +37,7 @@ TESS_K2_REG, TESS_K2_ROWS32, TESS_K2_ROWS64, TESS_K2_LOOP = 0, 1, 2, 3
 EXPORTED = ["tess_version", "tess_last_error", "tess_init", "tess_destroy", "tess_workspace_size", "tess_generate",
             "tess_me2", "tess_result", "tess_weights", "tess_histograms", "tess_generate_noalloc",
             "tess_kernel_launches", "tess_workspace_size_batched", "tess_generate_batched", "tess_autotune",
-            "tess_stage_timing", "tess_stage_times"]
+            "tess_stage_timing", "tess_stage_times", "tess_draws", "tess_gradients"]
 
 
 class TessError(RuntimeError):
@@ -97,6 +97,8 @@ def _load():
                                               ctypes.c_size_t, vp]
         lib.tess_autotune.argtypes = [vp, P(tess_process), u64, vp, vp, ctypes.c_size_t, vp, P(ctypes.c_int)]
         lib.tess_stage_timing.argtypes = [vp, i32]
+        lib.tess_draws.argtypes = [vp, i32, u64, u64, u64, vp, vp, vp, vp]
+        lib.tess_gradients.argtypes = [vp, P(tess_process), u64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.tess_stage_times.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int)]
         lib.tess_generate.argtypes = [vp, P(tess_process), u64, u64, u64, P(tess_outputs), vp, ctypes.c_size_t, vp]
         lib.tess_me2.argtypes = [vp, i32, i32, u64, vp, vp, vp, vp, vp]
@@ -207,6 +209,75 @@ def tess_stage_times(ctx):
     n = (ctypes.c_int * 4)()
     _check(_load().tess_stage_times(ctx, ms, n))
     return {STAGES[i]: (ms[i], n[i]) for i in range(4)}
+
+
+def n_uniforms(n):
+    """x1, x2 and four Rambo uniforms per final-state gluon."""
+    return 2 + 4 * (n - 2)
+
+
+def tess_draws(ctx, n, seed, first_event, n_events, stream=None):
+    """The generator's own random inputs (u, hel, order) of an event range."""
+    import torch
+    u = torch.empty((n_events, n_uniforms(n)), dtype=torch.float64, device="cuda")
+    hel = torch.empty(n_events, dtype=torch.int32, device="cuda")
+    order = torch.empty((n_events, n), dtype=torch.uint8, device="cuda")
+    _check(_load().tess_draws(ctx, int(n), int(seed), int(first_event), int(n_events), _ptr(u), _ptr(hel),
+                              _ptr(order), _stream(stream)))
+    return u, hel, order
+
+
+def tess_gradients(ctx, proc, u, hel, order, dL_dw=None, want=("w", "dw_du", "dw_dk", "dw_dlnmu"), stream=None):
+    """Event weights and their gradients (see include/tess.h); returns a dict of
+    device tensors for the requested outputs."""
+    import torch
+    E = u.shape[0]
+    n = proc.n_gluons
+    f64 = dict(dtype=torch.float64, device=u.device)
+    out = {"w": torch.empty(E, **f64) if "w" in want else None,
+           "dw_du": torch.empty((E, n_uniforms(n)), **f64) if "dw_du" in want else None,
+           "dw_dk": torch.empty((E, n, 4), **f64) if "dw_dk" in want else None,
+           "dw_dlnmu": torch.empty(E, **f64) if "dw_dlnmu" in want else None}
+    _check(_load().tess_gradients(ctx, ctypes.byref(proc), int(E), _ptr(u.contiguous()), _ptr(hel), _ptr(order),
+                                  _ptr(dL_dw), _ptr(out["w"]), _ptr(out["dw_du"]), _ptr(out["dw_dk"]),
+                                  _ptr(out["dw_dlnmu"]), _stream(stream)))
+    return {k: v for k, v in out.items() if v is not None}
+
+
+def _weight_function():
+    import torch
+
+    class EventWeight(torch.autograd.Function):
+        """w(u, log_xi) for fixed helicity labels and colour orderings, with
+        mu_R = xi H_T / 2; the backward pass is the library's adjoint kernel
+        (a vector-Jacobian product with the upstream gradient)."""
+
+        @staticmethod
+        def forward(fctx, u, log_xi, tctx, proc, hel, order):
+            p = tess_process.from_buffer_copy(proc)
+            p.mu_r_factor = proc.mu_r_factor * float(torch.exp(log_xi))
+            fctx.save_for_backward(u)
+            fctx.meta = (tctx, p, hel, order)
+            return tess_gradients(tctx, p, u.detach(), hel, order, want=("w",))["w"]
+
+        @staticmethod
+        def backward(fctx, grad_w):
+            (u,) = fctx.saved_tensors
+            tctx, p, hel, order = fctx.meta
+            g = tess_gradients(tctx, p, u.detach(), hel, order, dL_dw=grad_w.contiguous(),
+                               want=("dw_du", "dw_dlnmu"))
+            return g["dw_du"], g["dw_dlnmu"].sum().reshape(()), None, None, None, None
+
+    return EventWeight
+
+
+def event_weight(tctx, proc, u, hel, order, log_xi=None):
+    """Differentiable event weights: torch.autograd sees w as a function of the
+    uniforms u (and of log_xi = ln(mu_R / (H_T/2)) when given)."""
+    import torch
+    if log_xi is None:
+        log_xi = torch.zeros((), dtype=torch.float64, device=u.device)
+    return _weight_function().apply(u, log_xi, tctx, proc, hel, order)
 
 
 def make_outputs(weight=None, me2=None, pass_=None, ht=None, ptlead=None, rmin=None, acc=None, hist=None):

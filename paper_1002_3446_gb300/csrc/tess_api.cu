@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "tess.h"
+#include "tess_grad.cuh"
 #include "tess_kernels.cuh"
 #include "tess_pipe_launch.cuh"
 
@@ -21,6 +22,12 @@ cudaError_t launch_me2_f64(int n, uint64_t n_events, const double *k, const uint
                            double *me2, cudaStream_t s);
 cudaError_t launch_me2_f32(int n, uint64_t n_events, const double *k, const uint8_t *order, const uint32_t *hel,
                            double *me2, cudaStream_t s);
+cudaError_t launch_grad_a(int n, bool fp64, const GradParams &G, cudaStream_t s);
+cudaError_t launch_grad_b(int n, bool fp64, const GradParams &G, cudaStream_t s);
+cudaError_t launch_grad_c(int n, bool fp64, const GradParams &G, cudaStream_t s);
+cudaError_t launch_draws_a(int n, const EventParams &P, double *u, uint32_t *hel, uint8_t *order, cudaStream_t s);
+cudaError_t launch_draws_b(int n, const EventParams &P, double *u, uint32_t *hel, uint8_t *order, cudaStream_t s);
+cudaError_t launch_draws_c(int n, const EventParams &P, double *u, uint32_t *hel, uint8_t *order, cudaStream_t s);
 int plan_pipeline_f64(int n, int sm_count, uint64_t n_events, int hist_bins, int form, PipePlan *pl);
 int plan_pipeline_f32a(int n, int sm_count, uint64_t n_events, int hist_bins, int form, PipePlan *pl);
 int plan_pipeline_f32b(int n, int sm_count, uint64_t n_events, int hist_bins, int form, PipePlan *pl);
@@ -682,6 +689,73 @@ int tess_autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events
   }
   ctx->form[pi][n] = best;
   *form_out = best;
+  return ok();
+}
+
+int tess_draws(tess_ctx *ctx, int n, uint64_t seed, uint64_t first_event, uint64_t n_events, double *u,
+               uint32_t *hel, uint8_t *order, void *stream) {
+  if (!ctx) return fail(TESS_E_INVALID, "ctx is NULL");
+  if (n < TESS_MIN_N || n > TESS_MAX_N) return fail(TESS_E_UNSUPPORTED, "n = %d outside %d..%d", n, TESS_MIN_N, TESS_MAX_N);
+  if (n_events == 0) return ok();
+  if (!u || !hel || !order) return fail(TESS_E_INVALID, "u, hel and order must not be NULL");
+  if (n_events > (uint64_t)INT32_MAX * 128ull || n_events > (UINT64_MAX - first_event))
+    return fail(TESS_E_INVALID, "event range too large for one call");
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  int rc;
+  if ((rc = check_device_ptr(u, ctx->device, "u")) || (rc = check_device_ptr(hel, ctx->device, "hel")) ||
+      (rc = check_device_ptr(order, ctx->device, "order")))
+    return rc;
+  tess::EventParams P;
+  memset(&P, 0, sizeof P);
+  P.seed = seed;
+  P.first_event = first_event;
+  P.n_events = n_events;
+  cudaStream_t s = (cudaStream_t)stream;
+  const cudaError_t e = n <= 8 ? tess::launch_draws_a(n, P, u, hel, order, s)
+                               : (n <= 10 ? tess::launch_draws_b(n, P, u, hel, order, s)
+                                          : tess::launch_draws_c(n, P, u, hel, order, s));
+  if (e != cudaSuccess) return cuda_fail(e, "draws kernel launch");
+  return ok();
+}
+
+int tess_gradients(tess_ctx *ctx, const tess_process *proc, uint64_t n_events, const double *u, const uint32_t *hel,
+                   const uint8_t *order, const double *dL_dw, double *w, double *dw_du, double *dw_dk,
+                   double *dw_dlnmu, void *stream) {
+  if (!ctx) return fail(TESS_E_INVALID, "ctx is NULL");
+  int rc = check_process(proc);
+  if (rc) return rc;
+  if (proc->helicity_mode != TESS_HEL_SAMPLE)
+    return fail(TESS_E_UNSUPPORTED, "gradients are built for sampled helicity and ordering (TESS_HEL_SAMPLE)");
+  if (n_events == 0) return ok();
+  if (!u || !hel || !order) return fail(TESS_E_INVALID, "u, hel and order must not be NULL");
+  if (n_events > (uint64_t)INT32_MAX * 128ull) return fail(TESS_E_INVALID, "n_events too large for one call");
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  const void *ptrs[] = {u, hel, order, dL_dw, w, dw_du, dw_dk, dw_dlnmu};
+  const char *names[] = {"u", "hel", "order", "dL_dw", "w", "dw_du", "dw_dk", "dw_dlnmu"};
+  for (int i = 0; i < 8; ++i)
+    if ((rc = check_device_ptr(ptrs[i], ctx->device, names[i]))) return rc;
+  tess::GradParams G;
+  memset(&G, 0, sizeof G);
+  tess_outputs none;
+  memset(&none, 0, sizeof none);
+  fill_params(proc, 0, 0, n_events, &none, &G.P);
+  G.u = u;
+  G.hel = hel;
+  G.order = order;
+  G.dL_dw = dL_dw;
+  G.w = w;
+  G.dw_du = dw_du;
+  G.dw_dk = dw_dk;
+  G.dw_dlnmu = dw_dlnmu;
+  G.n_events = n_events;
+  const int n = proc->n_gluons;
+  const bool fp64 = proc->precision == TESS_FP64;
+  cudaStream_t s = (cudaStream_t)stream;
+  const cudaError_t e = n <= 8 ? tess::launch_grad_a(n, fp64, G, s)
+                               : (n <= 10 ? tess::launch_grad_b(n, fp64, G, s) : tess::launch_grad_c(n, fp64, G, s));
+  if (e != cudaSuccess) return cuda_fail(e, "gradient kernel launch");
   return ok();
 }
 
