@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-per-n", action="store_true", help="skip the per-multiplicity sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--events", type=int, default=0, help="override events per GPU (small cases for profiling)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the mixed-multiplicity batched measurement")
+    ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
     return ap.parse_args()
 
 
@@ -164,7 +166,8 @@ def run_tess(args):
     proc = make_proc(tess, wl)
     run = tess.Run(ctx, proc, N, per_event=("weight", "me2", "pass"))
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB > L2
-    first = rank * N
+    from paper_1002_3446_gb300 import dist as tdist
+    first, _ = tdist.event_range(rank, ws, N)
     seed = 1
 
     def barrier():
@@ -250,6 +253,10 @@ def run_tess(args):
                          "achieved_tflops": tess.bg_flops(n) * n64 / (statistics.mean(ms) * 1e-3) / 1e12,
                          "peak_tflops": FP64_PEAK_TFLOPS}
         del r64
+    if not args.no_batched and rank == 0:
+        extra["batched_mixed"] = bench_batched(torch, tess, ctx, flush, max(2, args.steps // 2))
+    if not args.no_grad and rank == 0:
+        extra["gradients_gg6g"] = bench_gradients(torch, tess, ctx, max(2, args.steps // 2))
     if not args.no_per_n and rank == 0:
         sweep = {}
         for nn in range(4, 13):
@@ -320,6 +327,83 @@ def run_tess(args):
     tess.tess_destroy(ctx)
     if dist:
         dist.destroy_process_group()
+
+
+def bench_batched(torch, tess, ctx, flush, steps):
+    """gg -> 2..10 gluons (n = 4..12) with 2^24 .. 2^16 events, FP32 currents:
+    one graph launch of the batched call vs 9 separate tess_generate calls,
+    before and after autotuning the amplitude kernel per n."""
+    ns = list(range(4, 13))
+    counts = [1 << (24 - i) for i in range(9)]
+    procs = [tess.process(n, precision=tess.TESS_FP32_DS, pt_min=30.0 if n >= 10 else 20.0) for n in ns]
+    runs = [tess.Run(ctx, p, c, per_event=("weight",)) for p, c in zip(procs, counts)]
+    ws_bytes = tess.tess_workspace_size_batched(ctx, procs, counts)
+    ws = torch.empty((ws_bytes + 7) // 8, dtype=torch.float64, device="cuda")
+    outs = [r.outputs for r in runs]
+    seeds, firsts = [1] * 9, [0] * 9
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.mean(ts)
+
+    def batched():
+        tess.tess_generate_batched(ctx, procs, seeds, firsts, counts, outs, ws)
+
+    def plain():
+        for r in runs:
+            r.generate(1, 0)
+
+    total = sum(counts)
+    res = {"events": total, "n": ns, "events_per_n": counts}
+    ms = timed(plain)
+    res["plain_9_launches"] = {"value": total / (ms * 1e-3), "ms": ms}
+    ms = timed(batched)
+    res["graph_batched"] = {"value": total / (ms * 1e-3), "ms": ms}
+    acc = torch.zeros(tess.TESS_ACC_LEN, dtype=torch.float64, device="cuda")
+    chosen = {}
+    for p, r in zip(procs, runs):
+        probe = min(r.n_events, 1 << 18)
+        chosen[p.n_gluons] = tess.tess_autotune(ctx, p, probe, acc, r.workspace)
+    ms = timed(batched)
+    res["graph_batched_autotuned"] = {"value": total / (ms * 1e-3), "ms": ms, "variants": chosen}
+    ms = timed(plain)
+    res["plain_9_launches_autotuned"] = {"value": total / (ms * 1e-3), "ms": ms}
+    res["unit"] = "events/s"
+    return res
+
+
+def bench_gradients(torch, tess, ctx, steps):
+    """gg -> 6 gluons (n = 8), 2^22 events: weights and d w/d u, d w/d k,
+    d w/d ln mu_R (FP32 forward + adjoint amplitude, FP64 kinematics)."""
+    n, E = 8, 1 << 22
+    u, hel, order = tess.tess_draws(ctx, n, 1, 0, E)
+    proc = tess.process(n, precision=tess.TESS_FP32_CURRENTS)
+    f = lambda: tess.tess_gradients(ctx, proc, u, hel, order)
+    f()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ts = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        f()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = statistics.mean(ts)
+    return {"value": E / (ms * 1e-3), "unit": "events/s (weight + all gradients)", "events": E, "ms": ms}
 
 
 def read_traffic(workload):
