@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--events", type=int, default=0, help="override events per GPU (small cases for profiling)")
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-multiplicity batched measurement")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
+    ap.add_argument("--no-autotune", action="store_true", help="time the built-in default amplitude variant")
     return ap.parse_args()
 
 
@@ -165,6 +166,10 @@ def run_tess(args):
     ctx = tess.tess_init(local)
     proc = make_proc(tess, wl)
     run = tess.Run(ctx, proc, N, per_event=("weight", "me2", "pass"))
+    variant = None
+    if not args.no_autotune and wl["hel"] == "sample":
+        probe_acc = torch.zeros(tess.TESS_ACC_LEN, dtype=torch.float64, device="cuda")
+        variant = tess.tess_autotune(ctx, proc, min(N, 1 << 22), probe_acc, run.workspace)
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB > L2
     from paper_1002_3446_gb300 import dist as tdist
     first, _ = tdist.event_range(rank, ws, N)
@@ -197,7 +202,14 @@ def run_tess(args):
     sigma = run.result()
     acc = run.acc.clone()
 
-    # ---- per-stage device time (library-recorded CUDA events on the launch stream)
+    # ---- per-stage device time (library-recorded CUDA events on the launch stream).
+    # Under an overlapped schedule the two kernels share the SMs, so the stages
+    # are timed with the same kernel variants run serially (each kernel alone).
+    plan = tess.tess_plan_info(ctx, proc, N)
+    serial_of = {tess.TESS_SCHED_OVERLAP: tess.TESS_SCHED_SERIAL,
+                 tess.TESS_SCHED_OVERLAP_TILES: tess.TESS_SCHED_SERIAL_TILES}
+    if plan["schedule"] in serial_of:
+        tess.tess_select_variant(ctx, proc, plan["variant"], serial_of[plan["schedule"]])
     tess.tess_stage_timing(ctx, 1)
     tess.tess_stage_times(ctx)
     for _ in range(args.steps):
@@ -206,6 +218,8 @@ def run_tess(args):
         run.generate(seed, first)
     stages = tess.tess_stage_times(ctx)
     tess.tess_stage_timing(ctx, 0)
+    if plan["schedule"] in serial_of:
+        tess.tess_select_variant(ctx, proc, plan["variant"], plan["schedule"])
     if dist:
         dist.all_reduce(acc, op=dist.ReduceOp.SUM)
 
@@ -266,9 +280,14 @@ def run_tess(args):
                 pp = make_proc(tess, w2, prec)
                 ne = (1 << 16) if prec == "fp64" else (1 << 20)
                 rr = tess.Run(ctx, pp, ne, per_event=("weight",))
+                if not args.no_autotune:
+                    tess.tess_autotune(ctx, pp, ne, torch.zeros(tess.TESS_ACC_LEN, dtype=torch.float64,
+                                                                device="cuda"), rr.workspace)
                 ms = time_steps(torch, rr, seed, 0, 2, 1, flush)
                 ev = ne / (min(ms) * 1e-3)
-                row[prec] = {"events_per_s": ev, "tflops": tess.bg_flops(nn) * ev / 1e12}
+                info = tess.tess_plan_info(ctx, pp, ne)
+                row[prec] = {"events_per_s": ev, "tflops": tess.bg_flops(nn) * ev / 1e12,
+                             "variant_schedule": [info["variant"], info["schedule"]]}
                 del rr
             sweep[str(nn)] = row
         extra["per_n"] = sweep
@@ -312,8 +331,12 @@ def run_tess(args):
                          "peak_source": ("152 SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts and clock); "
                                          "an FMA probe measured 78.2 FP32 / 1.25 FP64 TFLOP/s"),
                          "flops_per_event": tess.bg_flops(n), "ms_per_step": amp_ms_step,
+                         "variant": variant,
+                         "plan": plan,
                          "launches_per_step": amp_launches // args.steps,
-                         "timed": "CUDA events recorded by the library around each amplitude launch"},
+                         "timed": ("CUDA events recorded by the library around each amplitude launch"
+                                   + (", kernels run serially (same variants)" if plan["schedule"] in serial_of
+                                      else ""))},
             "stage_share": {k: v[0] / tot for k, v in stages.items() if v[1] > 0},
             "e2e": {"value": ws * N / e2e_s, "unit": "events/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": N * 9 + 64},
@@ -374,10 +397,12 @@ def bench_batched(torch, tess, ctx, flush, steps):
     acc = torch.zeros(tess.TESS_ACC_LEN, dtype=torch.float64, device="cuda")
     chosen = {}
     for p, r in zip(procs, runs):
-        probe = min(r.n_events, 1 << 18)
-        chosen[p.n_gluons] = tess.tess_autotune(ctx, p, probe, acc, r.workspace)
+        probe = min(r.n_events, 1 << 21)
+        tess.tess_autotune(ctx, p, probe, acc, r.workspace)
+        info = tess.tess_plan_info(ctx, p, r.n_events)
+        chosen[p.n_gluons] = [info["variant"], info["schedule"]]
     ms = timed(batched)
-    res["graph_batched_autotuned"] = {"value": total / (ms * 1e-3), "ms": ms, "variants": chosen}
+    res["graph_batched_autotuned"] = {"value": total / (ms * 1e-3), "ms": ms, "variant_schedule": chosen}
     ms = timed(plain)
     res["plain_9_launches_autotuned"] = {"value": total / (ms * 1e-3), "ms": ms}
     res["unit"] = "events/s"

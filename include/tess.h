@@ -92,7 +92,10 @@ typedef struct tess_process {
  *   ht, ptlead, rmin   observables (H_T, leading-jet pT, min Delta R)
  * acc  [TESS_ACC_LEN] doubles, ACCUMULATED into (zero it before the first
  *      call): {sum w, sum w^2, n_pass, n_generated, compensation of sum w,
- *      compensation of sum w^2, n_nonfinite, reserved}.  Repeated calls over
+ *      compensation of sum w^2, n_nonfinite, n_stalled}; n_stalled counts
+ *      amplitude blocks that gave up waiting (after about a second) for a
+ *      staged input copy, whose remaining events are missing from the sums
+ *      (tess_result then fails with TESS_E_CUDA).  Repeated calls over
  *      disjoint event ranges give the run total (checkpoint = copy of acc).
  * hist [4 * (hist_bins + 2)] doubles, accumulated into: sum w per bin, then
  *      sum w^2 per bin, then their two compensation terms.  Bin 0 is the
@@ -173,20 +176,61 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
 
 /* ---- Amplitude-kernel autotuner ------------------------------------------------
  * Times every amplitude-kernel variant built for (precision, n) of proc on
- * probe_events sampled events and makes the fastest the context's choice for
- * later calls with that (precision, n).  Variants (all one thread per event):
+ * probe_events sampled events (one warm-up, median of three timed runs, no
+ * histogram) and makes the fastest the context's choice for later calls with
+ * that (precision, n).  Choose probe_events to span several chunks (a few
+ * million events) so that the overlapped schedules can show their gain.  Variants (all one thread per event):
  * TESS_K2_REG (current table in registers), TESS_K2_ROWS32 / TESS_K2_ROWS64
  * (current row in registers, older rows in shared memory, 32 / 64 threads per
- * block), TESS_K2_LOOP (FP64 loop form).  acc_scratch: device, TESS_ACC_LEN
- * doubles (overwritten); workspace: tess_workspace_size(proc, probe_events)
- * bytes -- that size already covers every variant.  *form_out receives the
- * chosen TESS_K2_* (-1 for the exact-sum mode, which has one kernel). */
+ * block), TESS_K2_LOOP (FP64 loop form), TESS_K2_REG_HI (register form
+ * compiled for more resident blocks) -- each under every chunk schedule
+ * TESS_SCHED_* below.  acc_scratch: device, TESS_ACC_LEN doubles
+ * (overwritten); workspace: tess_workspace_size(proc, probe_events) bytes --
+ * that size already covers every variant and schedule.  *form_out receives
+ * the chosen TESS_K2_* (-1 for the exact-sum mode, which has one kernel);
+ * tess_plan_info reports the chosen schedule.  Per-event outputs do not
+ * depend on the choice beyond FP32 summation order inside the amplitude
+ * (identical in FP64); the accumulated sums can differ in the last bits,
+ * since the amplitude grid sets their summation order.
+ *
+ * Chunk schedules (events are processed in chunks sized to stay in L2, each
+ * by a kinematics kernel and an amplitude kernel):
+ *   TESS_SCHED_SERIAL         both kernels of a chunk back to back on
+ *                             `stream`; amplitude grid = resident blocks
+ *   TESS_SCHED_OVERLAP        kinematics of chunk c+1 on `stream` while the
+ *                             amplitude kernel of chunk c runs on a second
+ *                             stream owned by the context (two chunk buffers;
+ *                             needs more than one chunk, else serial)
+ *   TESS_SCHED_OVERLAP_TILES  overlapped, one amplitude block per tile of
+ *                             events (bounded so that the blocks' partial-sum
+ *                             flushes stay small next to the chunk's traffic)
+ *   TESS_SCHED_SERIAL_TILES   serial, one amplitude block per tile */
 #define TESS_K2_REG 0
 #define TESS_K2_ROWS32 1
 #define TESS_K2_ROWS64 2
 #define TESS_K2_LOOP 3
+#define TESS_K2_REG_HI 4 /* register form compiled for 3-4 resident blocks per SM (FP32, n <= 7) */
+#define TESS_K2_REG_TMA 5 /* register form, tile inputs staged in shared memory by bulk copies one
+                             tile ahead (FP32, n <= 8) */
+#define TESS_SCHED_SERIAL 0
+#define TESS_SCHED_OVERLAP 1
+#define TESS_SCHED_OVERLAP_TILES 2
+#define TESS_SCHED_SERIAL_TILES 3
 int tess_autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events, double *acc_scratch,
                   void *workspace, size_t workspace_bytes, void *stream, int *form_out);
+
+/* Sets the variant for (precision, n) of proc without timing: form one of
+ * TESS_K2_* (-1: built-in default; a form not built for (precision, n) falls
+ * back to the default), schedule one of TESS_SCHED_* (-1: default, serial).
+ * Takes effect for later calls; TESS_E_INVALID for values out of range.  A
+ * workspace sized by tess_workspace_size covers every choice. */
+int tess_select_variant(tess_ctx *ctx, const tess_process *proc, int form, int schedule);
+
+/* What a call with (proc, n_events) would run: info[0] amplitude variant
+ * (TESS_K2_*, -1 for the exact-sum mode), info[1] the schedule in effect
+ * (TESS_SCHED_*), info[2] number of chunks, info[3] amplitude-kernel grid
+ * (blocks).  info: host, 4 ints.  Launches nothing. */
+int tess_plan_info(const tess_ctx *ctx, const tess_process *proc, uint64_t n_events, int *info);
 
 /* ---- Draws and gradients (no counterpart in the paper's method) --------------
  * tess_draws writes the generator's own random inputs of events
@@ -231,7 +275,8 @@ int tess_me2(tess_ctx *ctx, int n, int precision, uint64_t n_events, const doubl
 
 /* Cross section from a device acc (synchronises the stream):
  * host out[4] = {sigma_pb, mc_error_pb, n_pass, n_generated}.
- * Returns TESS_E_NUMERICAL (after filling out) if non-finite weights were seen. */
+ * Returns TESS_E_CUDA (after filling out) if acc counts stalled blocks,
+ * else TESS_E_NUMERICAL (after filling out) if non-finite weights were seen. */
 int tess_result(tess_ctx *ctx, const double *acc, double *out, void *stream);
 
 /* Copy per-event outputs to host buffers (synchronises the stream).  Any of

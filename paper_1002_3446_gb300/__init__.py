@@ -31,13 +31,15 @@ TESS_NOALLOC_SCRATCH_BYTES, TESS_NOALLOC_MAX_BINS = 1 << 20, 254
 TESS_FP64, TESS_FP32_CURRENTS, TESS_FP32_DS = 0, 1, 2
 TESS_HEL_SUM, TESS_HEL_SAMPLE = 0, 1
 TESS_OBS_PTLEAD, TESS_OBS_HT, TESS_OBS_RMIN = 0, 1, 2
-TESS_K2_REG, TESS_K2_ROWS32, TESS_K2_ROWS64, TESS_K2_LOOP = 0, 1, 2, 3
+TESS_K2_REG, TESS_K2_ROWS32, TESS_K2_ROWS64, TESS_K2_LOOP, TESS_K2_REG_HI, TESS_K2_REG_TMA = 0, 1, 2, 3, 4, 5
+TESS_SCHED_SERIAL, TESS_SCHED_OVERLAP, TESS_SCHED_OVERLAP_TILES, TESS_SCHED_SERIAL_TILES = 0, 1, 2, 3
 
 # Every symbol include/tess.h declares (checked by the ABI tests).
 EXPORTED = ["tess_version", "tess_last_error", "tess_init", "tess_destroy", "tess_workspace_size", "tess_generate",
             "tess_me2", "tess_result", "tess_weights", "tess_histograms", "tess_generate_noalloc",
             "tess_kernel_launches", "tess_workspace_size_batched", "tess_generate_batched", "tess_autotune",
-            "tess_stage_timing", "tess_stage_times", "tess_draws", "tess_gradients"]
+            "tess_stage_timing", "tess_stage_times", "tess_draws", "tess_gradients", "tess_select_variant",
+            "tess_plan_info"]
 
 
 class TessError(RuntimeError):
@@ -97,6 +99,8 @@ def _load():
                                               ctypes.c_size_t, vp]
         lib.tess_autotune.argtypes = [vp, P(tess_process), u64, vp, vp, ctypes.c_size_t, vp, P(ctypes.c_int)]
         lib.tess_stage_timing.argtypes = [vp, i32]
+        lib.tess_select_variant.argtypes = [vp, P(tess_process), i32, i32]
+        lib.tess_plan_info.argtypes = [vp, P(tess_process), u64, P(ctypes.c_int)]
         lib.tess_draws.argtypes = [vp, i32, u64, u64, u64, vp, vp, vp, vp]
         lib.tess_gradients.argtypes = [vp, P(tess_process), u64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.tess_stage_times.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int)]
@@ -195,6 +199,17 @@ def tess_autotune(ctx, proc, probe_events, acc_scratch, workspace, stream=None):
     _check(_load().tess_autotune(ctx, ctypes.byref(proc), int(probe_events), _ptr(acc_scratch), _ptr(workspace),
                                  nbytes, _stream(stream), ctypes.byref(f)))
     return f.value
+
+
+def tess_select_variant(ctx, proc, form=-1, schedule=-1):
+    _check(_load().tess_select_variant(ctx, ctypes.byref(proc), int(form), int(schedule)))
+
+
+def tess_plan_info(ctx, proc, n_events):
+    """Amplitude variant, schedule in effect, chunks and amplitude grid of a call with n_events."""
+    info = (ctypes.c_int * 4)()
+    _check(_load().tess_plan_info(ctx, ctypes.byref(proc), int(n_events), info))
+    return {"variant": info[0], "schedule": info[1], "chunks": info[2], "grid": info[3]}
 
 
 STAGES = ("kinematics", "amplitude", "finalize", "fused")

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -28,18 +29,22 @@ cudaError_t launch_grad_c(int n, bool fp64, const GradParams &G, cudaStream_t s)
 cudaError_t launch_draws_a(int n, const EventParams &P, double *u, uint32_t *hel, uint8_t *order, cudaStream_t s);
 cudaError_t launch_draws_b(int n, const EventParams &P, double *u, uint32_t *hel, uint8_t *order, cudaStream_t s);
 cudaError_t launch_draws_c(int n, const EventParams &P, double *u, uint32_t *hel, uint8_t *order, cudaStream_t s);
-int plan_pipeline_f64(int n, int sm_count, uint64_t n_events, int hist_bins, int form, PipePlan *pl);
-int plan_pipeline_f32a(int n, int sm_count, uint64_t n_events, int hist_bins, int form, PipePlan *pl);
-int plan_pipeline_f32b(int n, int sm_count, uint64_t n_events, int hist_bins, int form, PipePlan *pl);
-int plan_pipeline_f32c(int n, int sm_count, uint64_t n_events, int hist_bins, int form, PipePlan *pl);
+int plan_pipeline_f64(int n, int sm_count, uint64_t n_events, int hist_bins, int form, int sched,
+                      PipePlan *pl);
+int plan_pipeline_f32a(int n, int sm_count, uint64_t n_events, int hist_bins, int form, int sched,
+                      PipePlan *pl);
+int plan_pipeline_f32b(int n, int sm_count, uint64_t n_events, int hist_bins, int form, int sched,
+                      PipePlan *pl);
+int plan_pipeline_f32c(int n, int sm_count, uint64_t n_events, int hist_bins, int form, int sched,
+                      PipePlan *pl);
 cudaError_t run_pipeline_f64(int n, const EventParams &P, const PipePlan &pl, char *ws, cudaStream_t s,
-                             const StageHook *hook);
+                             const StageHook *hook, const OverlapRes *ov);
 cudaError_t run_pipeline_f32a(int n, const EventParams &P, const PipePlan &pl, char *ws, cudaStream_t s,
-                             const StageHook *hook);
+                             const StageHook *hook, const OverlapRes *ov);
 cudaError_t run_pipeline_f32b(int n, const EventParams &P, const PipePlan &pl, char *ws, cudaStream_t s,
-                             const StageHook *hook);
+                             const StageHook *hook, const OverlapRes *ov);
 cudaError_t run_pipeline_f32c(int n, const EventParams &P, const PipePlan &pl, char *ws, cudaStream_t s,
-                             const StageHook *hook);
+                             const StageHook *hook, const OverlapRes *ov);
 // Neumaier-compensated addition (s, c) += x.
 __device__ __forceinline__ void comp_add(double &s, double &c, double x) {
   const double t = s + x;
@@ -71,6 +76,8 @@ __global__ void finalize_kernel(const double *__restrict__ partials, int nblocks
       acc[2] += tot;
     } else if (q == 3) {
       acc[6] += tot;
+    } else if (q == 4) {
+      acc[7] += tot;
     } else {
       const int h = q - kPartialHead;  // 0..2 nb2 - 1: w bins then w^2 bins
       double hs = hist[h], hc = hist[2 * nb2 + h];
@@ -89,8 +96,12 @@ constexpr int kMaxBranches = 16;
 struct tess_ctx {
   int device = 0;
   int sm_count = 1;
-  // tuned amplitude-kernel variant per (precision, n); -1 = built-in default
+  // tuned amplitude-kernel variant and chunk schedule per (precision, n);
+  // -1 = built-in default
   int form[2][TESS_MAX_N + 1];
+  int sched[2][TESS_MAX_N + 1];
+  // streams/events of the overlapped pipeline: [0] plain calls, [1 + i] batch branch i
+  tess::OverlapRes ovl[kMaxBranches + 1];
   // batched generation: capture streams, fork/join events, cached graph
   cudaStream_t cap_stream = nullptr;
   cudaStream_t branch[kMaxBranches] = {};
@@ -105,6 +116,8 @@ struct tess_ctx {
   cudaEvent_t ev_open[4] = {};
   tess_ctx() {
     for (auto &row : form)
+      for (int &f : row) f = -1;
+    for (auto &row : sched)
       for (int &f : row) f = -1;
   }
 };
@@ -216,46 +229,64 @@ double factorial(int k) {
 // the fused kernel.
 bool uses_pipeline(const tess_process *p) { return p->helicity_mode == TESS_HEL_SAMPLE; }
 
-int plan_with_form(const tess_ctx *ctx, const tess_process *p, uint64_t n_events, int form, tess::PipePlan *pl) {
+int plan_with_form(const tess_ctx *ctx, const tess_process *p, uint64_t n_events, int form, int sched,
+                   tess::PipePlan *pl) {
   const int n = p->n_gluons;
   int rc;
   if (p->precision == TESS_FP64)
-    rc = tess::plan_pipeline_f64(n, ctx->sm_count, n_events, p->hist_bins, form, pl);
+    rc = tess::plan_pipeline_f64(n, ctx->sm_count, n_events, p->hist_bins, form, sched, pl);
   else if (n <= 7)
-    rc = tess::plan_pipeline_f32a(n, ctx->sm_count, n_events, p->hist_bins, form, pl);
+    rc = tess::plan_pipeline_f32a(n, ctx->sm_count, n_events, p->hist_bins, form, sched, pl);
   else if (n <= 10)
-    rc = tess::plan_pipeline_f32b(n, ctx->sm_count, n_events, p->hist_bins, form, pl);
+    rc = tess::plan_pipeline_f32b(n, ctx->sm_count, n_events, p->hist_bins, form, sched, pl);
   else
-    rc = tess::plan_pipeline_f32c(n, ctx->sm_count, n_events, p->hist_bins, form, pl);
+    rc = tess::plan_pipeline_f32c(n, ctx->sm_count, n_events, p->hist_bins, form, sched, pl);
   if (rc) return fail(TESS_E_CUDA, "could not size the pipeline kernels (occupancy query failed)");
   return TESS_OK;
 }
 
 int pipeline_plan(const tess_ctx *ctx, const tess_process *p, uint64_t n_events, tess::PipePlan *pl) {
-  return plan_with_form(ctx, p, n_events, ctx->form[p->precision == TESS_FP64 ? 0 : 1][p->n_gluons], pl);
+  const int pi = p->precision == TESS_FP64 ? 0 : 1;
+  return plan_with_form(ctx, p, n_events, ctx->form[pi][p->n_gluons], ctx->sched[pi][p->n_gluons], pl);
 }
 
-// Workspace of the largest amplitude-kernel variant, so that tuning never
-// needs a larger workspace than the one sized before it.
+// Workspace of the largest amplitude-kernel variant and schedule (the
+// overlapped ones hold two chunk buffers), so that tuning never needs a larger
+// workspace than the one sized before it.
 int pipeline_bytes_any_form(const tess_ctx *ctx, const tess_process *p, uint64_t n_events, size_t *bytes) {
   size_t best = 0;
-  for (int f = 0; f < tess::K2_NFORMS; ++f) {
-    tess::PipePlan pl;
-    const int rc = plan_with_form(ctx, p, n_events, f, &pl);
-    if (rc) return rc;
-    if (pl.bytes > best) best = pl.bytes;
-  }
+  for (int f = 0; f < tess::K2_NFORMS; ++f)
+    for (int o = 0; o < tess::SCHED_N; ++o) {
+      tess::PipePlan pl;
+      const int rc = plan_with_form(ctx, p, n_events, f, o, &pl);
+      if (rc) return rc;
+      if (pl.bytes > best) best = pl.bytes;
+    }
   *bytes = best;
   return TESS_OK;
 }
 
+// Lazily created streams and events of the overlapped pipeline.
+int overlap_res(tess_ctx *ctx, int slot, tess::OverlapRes **out) {
+  tess::OverlapRes &o = ctx->ovl[slot];
+  if (!o.aux) {
+    cudaError_t e = cudaStreamCreateWithFlags(&o.aux, cudaStreamNonBlocking);
+    cudaEvent_t *evs[] = {&o.fork, &o.join, &o.k1done[0], &o.k1done[1], &o.k2done[0], &o.k2done[1]};
+    for (cudaEvent_t *ev : evs)
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "overlap stream/event creation");
+  }
+  *out = &o;
+  return TESS_OK;
+}
+
 cudaError_t pipeline_run(const tess_process *p, const tess::EventParams &P, const tess::PipePlan &pl, char *ws,
-                         cudaStream_t s, const tess::StageHook *hook) {
+                         cudaStream_t s, const tess::StageHook *hook, const tess::OverlapRes *ov) {
   const int n = p->n_gluons;
-  if (p->precision == TESS_FP64) return tess::run_pipeline_f64(n, P, pl, ws, s, hook);
-  if (n <= 7) return tess::run_pipeline_f32a(n, P, pl, ws, s, hook);
-  if (n <= 10) return tess::run_pipeline_f32b(n, P, pl, ws, s, hook);
-  return tess::run_pipeline_f32c(n, P, pl, ws, s, hook);
+  if (p->precision == TESS_FP64) return tess::run_pipeline_f64(n, P, pl, ws, s, hook, ov);
+  if (n <= 7) return tess::run_pipeline_f32a(n, P, pl, ws, s, hook, ov);
+  if (n <= 10) return tess::run_pipeline_f32b(n, P, pl, ws, s, hook, ov);
+  return tess::run_pipeline_f32c(n, P, pl, ws, s, hook, ov);
 }
 
 // Stage timing hook: records an event before and after each launch.
@@ -316,6 +347,14 @@ void fill_params(const tess_process *proc, uint64_t seed, uint64_t first_event, 
   P.S_hi = (float)P.S;
   P.S_lo = (float)(P.S - (double)P.S_hi);
   P.wk = P.wconst * P.lnxmin * P.lnxmin * P.phiconst * 0.5;
+  P.f_lnxmin = (float)P.lnxmin;
+  P.f_pt_min = (float)P.pt_min;
+  P.f_eta_max = (float)P.eta_max;
+  P.f_dr2_min = (float)P.dr2_min;
+  P.f_alphas_mz = (float)P.alphas_mz;
+  P.f_asb0 = (float)P.alphas_mz * (float)P.b0;
+  P.f_ln_mz2 = (float)P.ln_mz2;
+  P.f_mu_r_factor = (float)P.mu_r_factor;
 }
 
 }  // namespace
@@ -358,6 +397,12 @@ void tess_destroy(tess_ctx *ctx) {
   }
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  for (auto &o : ctx->ovl) {
+    if (o.aux) cudaStreamDestroy(o.aux);
+    cudaEvent_t evs[] = {o.fork, o.join, o.k1done[0], o.k1done[1], o.k2done[0], o.k2done[1]};
+    for (cudaEvent_t e : evs)
+      if (e) cudaEventDestroy(e);
+  }
   for (cudaEvent_t e : ctx->ev_free) cudaEventDestroy(e);
   for (auto &m : ctx->ev_marks) {
     cudaEventDestroy(m.second.first);
@@ -453,13 +498,14 @@ int prepare(tess_ctx *ctx, const tess_process *proc, uint64_t seed, uint64_t fir
   return TESS_OK;
 }
 
-int launch_prepared(const Prepared &pr, cudaStream_t s, const tess::StageHook *hook = nullptr) {
+int launch_prepared(const Prepared &pr, cudaStream_t s, const tess::StageHook *hook = nullptr,
+                    const tess::OverlapRes *ov = nullptr) {
   if (pr.P.n_events == 0) return TESS_OK;
   const int n = pr.proc->n_gluons;
   double *partials = (double *)pr.workspace;
   cudaError_t e;
   if (pr.pipeline) {
-    e = pipeline_run(pr.proc, pr.P, pr.pl, (char *)pr.workspace, s, hook);
+    e = pipeline_run(pr.proc, pr.P, pr.pl, (char *)pr.workspace, s, hook, ov);
     if (e != cudaSuccess) return cuda_fail(e, "pipeline launch");
   } else {
     if (hook) (*hook)(tess::STAGE_FUSED, true, s);
@@ -493,8 +539,10 @@ int tess_generate(tess_ctx *ctx, const tess_process *proc, uint64_t seed, uint64
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
   Prepared pr;
   if ((rc = prepare(ctx, proc, seed, first_event, n_events, out, workspace, workspace_bytes, &pr))) return rc;
+  tess::OverlapRes *ov = nullptr;
+  if (pr.pipeline && pr.pl.overlap && (rc = overlap_res(ctx, 0, &ov))) return rc;
   tess::StageHook hook{stage_mark, ctx};
-  if ((rc = launch_prepared(pr, (cudaStream_t)stream, ctx->timing ? &hook : nullptr))) return rc;
+  if ((rc = launch_prepared(pr, (cudaStream_t)stream, ctx->timing ? &hook : nullptr, ov))) return rc;
   return ok();
 }
 
@@ -577,6 +625,7 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
   put(outs, sizeof(tess_outputs) * n_proc);
   put(&workspace, sizeof workspace);
   put(ctx->form, sizeof ctx->form);
+  put(ctx->sched, sizeof ctx->sched);
   cudaError_t e = cudaSuccess;
   if (!ctx->graph_exec || key != ctx->graph_key) {
     if (!ctx->cap_stream) {
@@ -585,6 +634,8 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
         return cuda_fail(e, "stream/event creation");
     }
     for (int i = 0; i < n_proc; ++i) {
+      tess::OverlapRes *ov = nullptr;
+      if (prs[i].pipeline && prs[i].pl.overlap && (rc = overlap_res(ctx, 1 + i, &ov))) return rc;
       if (!ctx->branch[i]) {
         if ((e = cudaStreamCreateWithFlags(&ctx->branch[i], cudaStreamNonBlocking)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&ctx->join_ev[i], cudaEventDisableTiming)) != cudaSuccess)
@@ -599,7 +650,8 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
     int lrc = TESS_OK;
     for (int i = 0; i < n_proc && e == cudaSuccess && lrc == TESS_OK; ++i) {
       e = cudaStreamWaitEvent(ctx->branch[i], ctx->fork_ev, 0);
-      if (e == cudaSuccess) lrc = launch_prepared(prs[i], ctx->branch[i]);
+      const tess::OverlapRes *ov = (prs[i].pipeline && prs[i].pl.overlap) ? &ctx->ovl[1 + i] : nullptr;
+      if (e == cudaSuccess) lrc = launch_prepared(prs[i], ctx->branch[i], nullptr, ov);
       if (e == cudaSuccess && lrc == TESS_OK) e = cudaEventRecord(ctx->join_ev[i], ctx->branch[i]);
       if (e == cudaSuccess && lrc == TESS_OK) e = cudaStreamWaitEvent(ctx->cap_stream, ctx->join_ev[i], 0);
     }
@@ -630,6 +682,45 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
   return ok();
 }
 
+int tess_select_variant(tess_ctx *ctx, const tess_process *proc, int form, int schedule) {
+  if (!ctx || !proc) return fail(TESS_E_INVALID, "NULL argument");
+  int rc = check_process(proc);
+  if (rc) return rc;
+  if (form < -1 || form >= tess::K2_NFORMS) return fail(TESS_E_INVALID, "form out of range");
+  if (schedule < -1 || schedule >= tess::SCHED_N) return fail(TESS_E_INVALID, "schedule out of range");
+  const int pi = proc->precision == TESS_FP64 ? 0 : 1;
+  ctx->form[pi][proc->n_gluons] = form;
+  ctx->sched[pi][proc->n_gluons] = schedule;
+  return ok();
+}
+
+int tess_plan_info(const tess_ctx *ctx, const tess_process *proc, uint64_t n_events, int *info) {
+  if (!ctx || !proc || !info) return fail(TESS_E_INVALID, "NULL argument");
+  int rc = check_process(proc);
+  if (rc) return rc;
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  if (!uses_pipeline(proc)) {
+    info[0] = -1;
+    info[1] = tess::SCHED_SERIAL;
+    info[2] = 1;
+    info[3] = grid_for(ctx, proc, n_events);
+    return ok();
+  }
+  tess::PipePlan pl;
+  if ((rc = pipeline_plan(ctx, proc, n_events, &pl))) return rc;
+  info[0] = pl.form;
+  // the schedule in effect: an overlapped one runs serially on a single chunk
+  info[1] = pl.overlap || pl.sched == tess::SCHED_SERIAL || pl.sched == tess::SCHED_SERIAL_TILES
+                ? pl.sched
+                : (pl.sched == tess::SCHED_OVERLAP ? tess::SCHED_SERIAL : tess::SCHED_SERIAL_TILES);
+  info[2] = pl.chunks;
+  info[3] = pl.grid;
+  return ok();
+}
+
+constexpr int kTuneReps = 3;  // timed runs per candidate (median)
+
 int tess_autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events, double *acc_scratch,
                   void *workspace, size_t workspace_bytes, void *stream, int *form_out) {
   if (!ctx || !proc || !acc_scratch || !form_out) return fail(TESS_E_INVALID, "NULL argument");
@@ -656,37 +747,53 @@ int tess_autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events
     if (a) cudaEventDestroy(a);
     return cuda_fail(e, "cudaEventCreate");
   }
-  const int saved = ctx->form[pi][n];
-  int best = -1;
+  const int saved = ctx->form[pi][n], saved_sched = ctx->sched[pi][n];
+  int best = -1, best_sched = 0;
   float best_ms = 0.f;
-  for (int f = 0; f < tess::K2_NFORMS; ++f) {
-    tess::PipePlan pl;
-    if ((rc = plan_with_form(ctx, &pp, probe_events, f, &pl))) break;
-    if (pl.form != f) continue;  // variant not built for this (precision, n)
-    ctx->form[pi][n] = f;
-    Prepared pr;
-    if ((rc = prepare(ctx, &pp, 1, 0, probe_events, &out, workspace, workspace_bytes, &pr))) break;
-    if ((rc = launch_prepared(pr, s))) break;  // warm-up
-    cudaEventRecord(a, s);
-    if ((rc = launch_prepared(pr, s))) break;
-    cudaEventRecord(b, s);
-    if ((e = cudaEventSynchronize(b)) != cudaSuccess) {
-      rc = cuda_fail(e, "autotune timing");
-      break;
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
-    if (best < 0 || ms < best_ms) {
-      best = f;
-      best_ms = ms;
+  for (int f = 0; f < tess::K2_NFORMS && !rc; ++f) {
+    for (int o = 0; o < tess::SCHED_N && !rc; ++o) {
+      tess::PipePlan pl;
+      if ((rc = plan_with_form(ctx, &pp, probe_events, f, o, &pl))) break;
+      if (pl.form != f) continue;  // not built for (precision, n)
+      const bool wants_overlap = o == tess::SCHED_OVERLAP || o == tess::SCHED_OVERLAP_TILES;
+      if (wants_overlap && !pl.overlap) continue;  // a single chunk: nothing to overlap
+      ctx->form[pi][n] = f;
+      ctx->sched[pi][n] = o;
+      Prepared pr;
+      if ((rc = prepare(ctx, &pp, 1, 0, probe_events, &out, workspace, workspace_bytes, &pr))) break;
+      tess::OverlapRes *ov = nullptr;
+      if (pl.overlap && (rc = overlap_res(ctx, 0, &ov))) break;
+      if ((rc = launch_prepared(pr, s, nullptr, ov))) break;  // warm-up
+      float t[kTuneReps];
+      for (int r = 0; r < kTuneReps && !rc; ++r) {
+        cudaEventRecord(a, s);
+        if ((rc = launch_prepared(pr, s, nullptr, ov))) break;
+        cudaEventRecord(b, s);
+        if ((e = cudaEventSynchronize(b)) != cudaSuccess) {
+          rc = cuda_fail(e, "autotune timing");
+          break;
+        }
+        t[r] = 0.f;
+        cudaEventElapsedTime(&t[r], a, b);
+      }
+      if (rc) break;
+      std::sort(t, t + kTuneReps);
+      const float ms = t[kTuneReps / 2];  // median
+      if (best < 0 || ms < best_ms) {
+        best = f;
+        best_sched = o;
+        best_ms = ms;
+      }
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (rc) {
     ctx->form[pi][n] = saved;
+    ctx->sched[pi][n] = saved_sched;
     return rc;
   }
+  ctx->sched[pi][n] = best_sched;
   ctx->form[pi][n] = best;
   *form_out = best;
   return ok();
@@ -800,6 +907,9 @@ int tess_result(tess_ctx *ctx, const double *acc, double *out, void *stream) {
   out[1] = std::sqrt(var > 0 ? var : 0.0);
   out[2] = h[2];
   out[3] = n;
+  if (h[7] > 0)
+    return fail(TESS_E_CUDA, "%.0f amplitude blocks timed out waiting for a staged input copy (sums incomplete)",
+                h[7]);
   if (h[6] > 0) return fail(TESS_E_NUMERICAL, "%.0f events had non-finite weights (counted as 0)", h[6]);
   return ok();
 }

@@ -28,6 +28,8 @@ struct EventParams {
   // constant wconst (ln x_min)^2 phiconst / 2
   float S_hi, S_lo;
   double wk;
+  // single-precision copies of the constants the FP32 kinematics read
+  float f_lnxmin, f_pt_min, f_eta_max, f_dr2_min, f_alphas_mz, f_asb0, f_ln_mz2, f_mu_r_factor;
   int kin_ds;          // 1: double-single kinematics kernel
   // outputs (device; may be null)
   double *weight, *me2, *ht, *ptlead, *rmin;
@@ -280,6 +282,13 @@ __device__ __forceinline__ double pow2_unit_inv(double rs) {
   int e;
   frexp(rs, &e);
   return ldexp(1.0, -e);
+}
+
+// x 2^s by adding s to the exponent field: equal to ldexp(x, s) for a normal
+// nonzero x whose result is normal (the callers' factors are far inside the
+// double range), in two integer operations instead of FP64 work.
+__device__ __forceinline__ double scale_pow2(double x, int s) {
+  return __longlong_as_double(__double_as_longlong(x) + ((long long)s << 52));
 }
 
 template <int N, typename R, bool SUM>

@@ -227,7 +227,7 @@ __device__ __forceinline__ void polvec_adjoint(const double (&p)[3], bool minus,
   const double pt2 = px * px + py * py;
   const double pt = sqrt(pt2), r = sqrt(pt2 + pz * pz);
   if (!(pt > 0.0)) return;  // beam axis: the basis is fixed by convention
-  const double ct = pz / r, st = pt / r, cf = px / pt, sf = py / pt;
+  const double ct = pz / r, cf = px / pt, sf = py / pt;
   const double s2 = 0.70710678118654752440;
   // Re eps = sgn e1 / sqrt2, Im eps = -e2 / sqrt2 with sgn = -1 (eps_+) or +1 (eps_-)
   const double sg = minus ? 1.0 : -1.0;

@@ -8,10 +8,11 @@
 namespace tess {
 
 constexpr int kBlock = 128;       // threads (= events) per tile
-constexpr int kPartialHead = 4;   // sum w, sum w^2, n_pass, n_nonfinite
+constexpr int kPartialHead = 5;   // sum w, sum w^2, n_pass, n_nonfinite, n_stalled
 
 // Workspace layout: one row of partials per block,
-//   [sum w, sum w^2, n_pass, n_nonfinite, hist w (nb2), hist w^2 (nb2)].
+//   [sum w, sum w^2, n_pass, n_nonfinite, n_stalled, hist w (nb2), hist w^2 (nb2)].
+// n_stalled counts blocks that gave up waiting for a staged input copy.
 __host__ __device__ inline int partial_stride(int hist_bins) {
   return kPartialHead + (hist_bins > 0 ? 2 * (hist_bins + 2) : 0);
 }
@@ -100,6 +101,7 @@ __global__ void __launch_bounds__(kBlock) event_kernel(EventParams P, double *__
   }
   double *row = partials + (size_t)blockIdx.x * partial_stride(nb);
   if (threadIdx.x < 4) row[threadIdx.x] = red[threadIdx.x][0];
+  if (threadIdx.x == 4) row[4] = 0.0;
   for (int i = threadIdx.x; i < 2 * nb2; i += kBlock) row[kPartialHead + i] = smem[i];
 }
 

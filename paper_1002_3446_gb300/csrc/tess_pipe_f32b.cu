@@ -3,21 +3,22 @@
 
 namespace tess {
 
-int plan_pipeline_f32b(int n, int sm_count, uint64_t n_events, int hist_bins, int form, PipePlan *pl) {
+int plan_pipeline_f32b(int n, int sm_count, uint64_t n_events, int hist_bins, int form, int sched,
+                          PipePlan *pl) {
   switch (n) {
-    case 8: return plan_pipeline_t<8, float>(sm_count, n_events, hist_bins, form, pl);
-    case 9: return plan_pipeline_t<9, float>(sm_count, n_events, hist_bins, form, pl);
-    case 10: return plan_pipeline_t<10, float>(sm_count, n_events, hist_bins, form, pl);
+    case 8: return plan_pipeline_t<8, float>(sm_count, n_events, hist_bins, form, sched, pl);
+    case 9: return plan_pipeline_t<9, float>(sm_count, n_events, hist_bins, form, sched, pl);
+    case 10: return plan_pipeline_t<10, float>(sm_count, n_events, hist_bins, form, sched, pl);
     default: return -1;
   }
 }
 
 cudaError_t run_pipeline_f32b(int n, const EventParams &P, const PipePlan &pl, char *ws, cudaStream_t s,
-                                 const StageHook *hook) {
+                                 const StageHook *hook, const OverlapRes *ov) {
   switch (n) {
-    case 8: return run_pipeline_t<8, float>(P, pl, ws, s, hook);
-    case 9: return run_pipeline_t<9, float>(P, pl, ws, s, hook);
-    case 10: return run_pipeline_t<10, float>(P, pl, ws, s, hook);
+    case 8: return run_pipeline_t<8, float>(P, pl, ws, s, hook, ov);
+    case 9: return run_pipeline_t<9, float>(P, pl, ws, s, hook, ov);
+    case 10: return run_pipeline_t<10, float>(P, pl, ws, s, hook, ov);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -3,19 +3,20 @@
 
 namespace tess {
 
-int plan_pipeline_f32c(int n, int sm_count, uint64_t n_events, int hist_bins, int form, PipePlan *pl) {
+int plan_pipeline_f32c(int n, int sm_count, uint64_t n_events, int hist_bins, int form, int sched,
+                          PipePlan *pl) {
   switch (n) {
-    case 11: return plan_pipeline_t<11, float>(sm_count, n_events, hist_bins, form, pl);
-    case 12: return plan_pipeline_t<12, float>(sm_count, n_events, hist_bins, form, pl);
+    case 11: return plan_pipeline_t<11, float>(sm_count, n_events, hist_bins, form, sched, pl);
+    case 12: return plan_pipeline_t<12, float>(sm_count, n_events, hist_bins, form, sched, pl);
     default: return -1;
   }
 }
 
 cudaError_t run_pipeline_f32c(int n, const EventParams &P, const PipePlan &pl, char *ws, cudaStream_t s,
-                                 const StageHook *hook) {
+                                 const StageHook *hook, const OverlapRes *ov) {
   switch (n) {
-    case 11: return run_pipeline_t<11, float>(P, pl, ws, s, hook);
-    case 12: return run_pipeline_t<12, float>(P, pl, ws, s, hook);
+    case 11: return run_pipeline_t<11, float>(P, pl, ws, s, hook, ov);
+    case 12: return run_pipeline_t<12, float>(P, pl, ws, s, hook, ov);
     default: return cudaErrorInvalidValue;
   }
 }

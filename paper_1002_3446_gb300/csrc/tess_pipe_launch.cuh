@@ -16,7 +16,31 @@ struct PipePlan {
   int cap = 128;     // events per chunk
   int chunks = 1;
   size_t off_in = 0, off_efac = 0, off_wfac = 0, off_hval = 0, off_pass = 0;
-  size_t bytes = 0;  // workspace bytes
+  size_t kin_smem = 0;   // K1 dynamic shared memory (FP32 forms: the output tile)
+  size_t buf_bytes = 0;  // one chunk buffer
+  int sched = 0;         // Schedule
+  bool overlap = false;  // double-buffered, K1 and K2 on two streams
+  size_t bytes = 0;      // workspace bytes
+};
+
+// How the chunks are launched.
+//   SCHED_SERIAL         K1 then K2 per chunk on the caller's stream; K2 grid
+//                        = resident blocks (persistent, loops over tiles)
+//   SCHED_OVERLAP        K1 of chunk c+1 on the caller's stream while K2 of
+//                        chunk c runs on a second stream; two chunk buffers
+//   SCHED_OVERLAP_TILES  as SCHED_OVERLAP with one K2 block per tile, so that
+//                        K1 blocks are scheduled as K2 blocks retire
+//   SCHED_SERIAL_TILES   serial with one K2 block per tile
+// The per-tile grid is bounded so that the blocks' partial-row flushes stay
+// under 1/50 of the chunk's own traffic (large histograms keep the
+// persistent grid).
+enum Schedule { SCHED_SERIAL = 0, SCHED_OVERLAP = 1, SCHED_OVERLAP_TILES = 2, SCHED_SERIAL_TILES = 3, SCHED_N = 4 };
+
+// Streams and events of the overlapped pipeline (owned by the context).
+struct OverlapRes {
+  cudaStream_t aux = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t k1done[2] = {nullptr, nullptr}, k2done[2] = {nullptr, nullptr};
 };
 
 constexpr size_t kChunkTargetBytes = 64ull << 20;  // stays resident in the 129 MB L2
@@ -40,11 +64,26 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 //              shared-memory column, 32 threads per block         FP32, n >= 6
 //   K2_ROWS64  the same with 64 threads per block                 FP32, n >= 6
 //   K2_LOOP    loop form, table in local memory, 128 threads      FP64
-enum K2Form { K2_REG = 0, K2_ROWS32 = 1, K2_ROWS64 = 2, K2_LOOP = 3, K2_NFORMS = 4 };
+//   K2_REG_HI  register form compiled for more resident blocks (3 per SM
+//              for n >= 6, 4 below: fewer registers, a few spilled) FP32, n <= 7
+//   K2_REG_TMA register form with the tile inputs staged in shared memory
+//              by bulk copies one tile ahead, 128 threads         FP32, n <= 8
+enum K2Form { K2_REG = 0, K2_ROWS32 = 1, K2_ROWS64 = 2, K2_LOOP = 3, K2_REG_HI = 4, K2_REG_TMA = 5, K2_NFORMS = 6 };
 
 template <int N, typename R>
 constexpr bool k2_valid(int f) {
-  return sizeof(R) == 8 ? f == K2_LOOP : (f == K2_REG ? N <= 8 : (f == K2_ROWS32 || f == K2_ROWS64) ? N >= 6 : false);
+  if constexpr (sizeof(R) == 8) {
+    return f == K2_LOOP;
+  } else {
+    switch (f) {
+      case K2_REG:
+      case K2_REG_TMA: return N <= 8;
+      case K2_REG_HI: return N <= 7;
+      case K2_ROWS32:
+      case K2_ROWS64: return N >= 6;
+      default: return false;
+    }
+  }
 }
 
 template <int N, typename R>
@@ -56,17 +95,24 @@ template <int N, typename R, int F>
 struct K2V {
   static constexpr int L = N - 1;
   static constexpr int block = (F == K2_ROWS32) ? 32 : (F == K2_ROWS64 ? 64 : 128);
+  static constexpr int hi_blocks = N >= 6 ? 3 : 4;
   static void *fn() {
     if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
       return (void *)bg_rows_kernel<N, block>;
+    else if constexpr (F == K2_REG_TMA)
+      return (void *)bg_reg_tma_kernel<N, 128>;
     else if constexpr (F == K2_REG)
       return (void *)bg_reg_kernel<N, float, 128>;
+    else if constexpr (F == K2_REG_HI)
+      return (void *)bg_reg_kernel<N, float, 128, hi_blocks>;
     else
       return (void *)bg_loop_kernel<N, 128>;
   }
   static size_t smem(int hist_bins) {
     if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
       return rows_smem_per_thread<L>() * block + EpiSmem<block>::bytes(hist_bins);
+    else if constexpr (F == K2_REG_TMA)
+      return RegStage<L, 128>::head + EpiSmem<128>::bytes(hist_bins);
     else
       return EpiSmem<128>::bytes(hist_bins);
   }
@@ -74,8 +120,12 @@ struct K2V {
                             cudaStream_t s) {
     if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
       bg_rows_kernel<N, block><<<grid, block, smem, s>>>(C, B, partials);
+    else if constexpr (F == K2_REG_TMA)
+      bg_reg_tma_kernel<N, 128><<<grid, 128, smem, s>>>(C, B, partials);
     else if constexpr (F == K2_REG)
       bg_reg_kernel<N, float, 128><<<grid, 128, smem, s>>>(C, B, partials);
+    else if constexpr (F == K2_REG_HI)
+      bg_reg_kernel<N, float, 128, hi_blocks><<<grid, 128, smem, s>>>(C, B, partials);
     else
       bg_loop_kernel<N, 128><<<grid, 128, smem, s>>>(C, B, partials);
     return cudaGetLastError();
@@ -88,8 +138,12 @@ auto with_form(int f, Fn &&fn) {
   if constexpr (sizeof(R) == 8) {
     return fn(K2V<N, R, K2_LOOP>{});
   } else {
+    if constexpr (N <= 7) {
+      if (f == K2_REG_HI) return fn(K2V<N, R, K2_REG_HI>{});
+    }
     if constexpr (N <= 8) {
       if (f == K2_REG) return fn(K2V<N, R, K2_REG>{});
+      if (f == K2_REG_TMA) return fn(K2V<N, R, K2_REG_TMA>{});
     }
     if constexpr (N >= 6) {
       if (f == K2_ROWS64) return fn(K2V<N, R, K2_ROWS64>{});
@@ -101,7 +155,7 @@ auto with_form(int f, Fn &&fn) {
 }
 
 template <int N, typename R>
-int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, PipePlan *pl) {
+int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, int sched, PipePlan *pl) {
   constexpr int L = N - 1;
   if (!k2_valid<N, R>(form)) form = k2_default<N, R>();
   pl->form = form;
@@ -120,6 +174,17 @@ int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, Pi
     return 0;
   });
   if (rc) return rc;
+  if constexpr (sizeof(R) == 4) {
+    pl->kin_smem = kin_tile_bytes<N>();
+    if (pl->kin_smem > 48 * 1024 &&
+        (cudaFuncSetAttribute((void *)kin_ds_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)pl->kin_smem) != cudaSuccess ||
+         cudaFuncSetAttribute((void *)kin_kernel<N, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)pl->kin_smem) != cudaSuccess))
+      return -1;
+  } else {
+    pl->kin_smem = 0;
+  }
   const int per_sm = pl->per_sm;
   const uint64_t per_event = (uint64_t)(12 * L + 8) * sizeof(R) + 3 * sizeof(double) + 1;
   const uint64_t target = std::max<uint64_t>(128, (kChunkTargetBytes / per_event) / 128 * 128);
@@ -127,7 +192,15 @@ int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, Pi
   pl->cap = (int)std::min(target, want);
   pl->chunks = (int)((std::max<uint64_t>(n_events, 1) + pl->cap - 1) / pl->cap);
   const uint64_t tiles = ((uint64_t)pl->cap + pl->block - 1) / pl->block;
-  pl->grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)sm_count * per_sm));
+  if (sched < 0 || sched >= SCHED_N) sched = SCHED_SERIAL;
+  pl->sched = sched;
+  pl->overlap = (sched == SCHED_OVERLAP || sched == SCHED_OVERLAP_TILES) && pl->chunks > 1;
+  uint64_t resident = (uint64_t)sm_count * per_sm;
+  if (sched == SCHED_OVERLAP_TILES || sched == SCHED_SERIAL_TILES) {
+    const uint64_t flush_budget = (uint64_t)pl->cap * per_event / 50 / (partial_stride(hist_bins) * sizeof(double));
+    resident = std::max(resident, flush_budget);
+  }
+  pl->grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles, resident));
   size_t off = align256((size_t)pl->grid * partial_stride(hist_bins) * sizeof(double));
   pl->off_in = off;
   off = align256(off + (size_t)(12 * L + 8) * pl->cap * sizeof(R));
@@ -138,36 +211,76 @@ int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, Pi
   pl->off_hval = off;
   off = align256(off + (size_t)pl->cap * sizeof(double));
   pl->off_pass = off;
-  pl->bytes = align256(off + (size_t)pl->cap);
+  off = align256(off + (size_t)pl->cap);
+  pl->buf_bytes = off - pl->off_in;
+  pl->bytes = pl->overlap ? off + pl->buf_bytes : off;  // second chunk buffer
   return 0;
 }
 
 template <int N, typename R>
 cudaError_t run_pipeline_t(const EventParams &P, const PipePlan &pl, char *ws, cudaStream_t s,
-                           const StageHook *hook) {
+                           const StageHook *hook, const OverlapRes *ov = nullptr) {
   double *partials = (double *)ws;
   cudaError_t e = cudaMemsetAsync(partials, 0, (size_t)pl.grid * partial_stride(P.hist_bins) * sizeof(double), s);
   if (e != cudaSuccess) return e;
-  ChunkBuf<R> B;
-  B.in = (R *)(ws + pl.off_in);
-  B.efac = (double *)(ws + pl.off_efac);
-  B.wfac = (double *)(ws + pl.off_wfac);
-  B.hval = (double *)(ws + pl.off_hval);
-  B.pass = (uint8_t *)(ws + pl.off_pass);
-  B.cap = pl.cap;
+  ChunkBuf<R> BB[2];
+  for (int b = 0; b < 2; ++b) {
+    char *base = ws + (b ? pl.buf_bytes : 0);
+    BB[b].in = (R *)(base + pl.off_in);
+    BB[b].efac = (double *)(base + pl.off_efac);
+    BB[b].wfac = (double *)(base + pl.off_wfac);
+    BB[b].hval = (double *)(base + pl.off_hval);
+    BB[b].pass = (uint8_t *)(base + pl.off_pass);
+    BB[b].cap = pl.cap;
+  }
   ChunkParams C;
   C.P = P;
+  if (pl.overlap && ov) {
+    // K1 of chunk c+1 (caller's stream) runs while K2 of chunk c (aux stream)
+    // does; buffer c % 2 is reused only after K2 of chunk c-2 is done.
+    cudaStream_t a = ov->aux;
+    if ((e = cudaEventRecord(ov->fork, s)) != cudaSuccess || (e = cudaStreamWaitEvent(a, ov->fork, 0)) != cudaSuccess)
+      return e;
+    int c = 0;
+    for (uint64_t off = 0; off < P.n_events; off += (uint64_t)pl.cap, ++c) {
+      const int b = c & 1;
+      C.chunk_first = off;
+      C.count = (int)std::min<uint64_t>((uint64_t)pl.cap, P.n_events - off);
+      if (c >= 2 && (e = cudaStreamWaitEvent(s, ov->k2done[b], 0)) != cudaSuccess) return e;
+      if (hook) (*hook)(STAGE_KIN, true, s);
+      if constexpr (sizeof(R) == 4) {
+        if (P.kin_ds)
+          kin_ds_kernel<N><<<(C.count + kBlock - 1) / kBlock, kBlock, pl.kin_smem, s>>>(C, BB[b]);
+        else
+          kin_kernel<N, R><<<(C.count + kBlock - 1) / kBlock, kBlock, pl.kin_smem, s>>>(C, BB[b]);
+      } else {
+        kin_kernel<N, R><<<(C.count + kBlock - 1) / kBlock, kBlock, pl.kin_smem, s>>>(C, BB[b]);
+      }
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if (hook) (*hook)(STAGE_KIN, false, s);
+      if ((e = cudaEventRecord(ov->k1done[b], s)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(a, ov->k1done[b], 0)) != cudaSuccess) return e;
+      if (hook) (*hook)(STAGE_AMP, true, a);
+      e = with_form<N, R>(pl.form, [&](auto K) { return decltype(K)::launch(C, BB[b], partials, pl.grid, pl.smem, a); });
+      if (e != cudaSuccess) return e;
+      if (hook) (*hook)(STAGE_AMP, false, a);
+      if ((e = cudaEventRecord(ov->k2done[b], a)) != cudaSuccess) return e;
+    }
+    if ((e = cudaEventRecord(ov->join, a)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(s, ov->join, 0);
+  }
+  const ChunkBuf<R> &B = BB[0];
   for (uint64_t off = 0; off < P.n_events; off += (uint64_t)pl.cap) {
     C.chunk_first = off;
     C.count = (int)std::min<uint64_t>((uint64_t)pl.cap, P.n_events - off);
     if (hook) (*hook)(STAGE_KIN, true, s);
     if constexpr (sizeof(R) == 4) {
       if (P.kin_ds)
-        kin_ds_kernel<N><<<(C.count + kBlock - 1) / kBlock, kBlock, 0, s>>>(C, B);
+        kin_ds_kernel<N><<<(C.count + kBlock - 1) / kBlock, kBlock, pl.kin_smem, s>>>(C, B);
       else
-        kin_kernel<N, R><<<(C.count + kBlock - 1) / kBlock, kBlock, 0, s>>>(C, B);
+        kin_kernel<N, R><<<(C.count + kBlock - 1) / kBlock, kBlock, pl.kin_smem, s>>>(C, B);
     } else {
-      kin_kernel<N, R><<<(C.count + kBlock - 1) / kBlock, kBlock, 0, s>>>(C, B);
+      kin_kernel<N, R><<<(C.count + kBlock - 1) / kBlock, kBlock, pl.kin_smem, s>>>(C, B);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (hook) (*hook)(STAGE_KIN, false, s);

@@ -13,6 +13,7 @@
 #pragma once
 #include <cstdint>
 
+#include "tess_async.cuh"
 #include "tess_event.cuh"
 #include "tess_kernels.cuh"
 
@@ -248,53 +249,69 @@ __device__ __forceinline__ void pol_basis_f32(double E, double px, double py, do
   e2[1] = (float)cf;
 }
 
-// Gathers per-leg FP32 data (momentum, polarisation basis) into colour
-// position order and writes the amplitude inputs of one event.
+// Writes the amplitude inputs of one event -- per colour position a: the leg
+// momentum (positions 1..L) and eps (eps_+ = -(e1 + i e2)/sqrt2, eps_- =
+// (e1 - i e2)/sqrt2 by the leg's helicity label) -- into a shared-memory tile
+// of the block's kBlock events ([12 L + 8 rows][kBlock]).  Each leg's values
+// go straight to the rows of its colour position; store_tile then writes the
+// tile's rows to the chunk buffer with bulk copies.
 template <int N>
-__device__ __forceinline__ void store_ordered(const EventParams &P, uint64_t ev, const ChunkBuf<float> &B, int e,
-                                              const float (&lk)[N][4], const float (&le1)[N][3],
-                                              const float (&le2)[N][2]) {
+constexpr size_t kin_tile_bytes() {
+  return (size_t)(12 * (N - 1) + 8) * kBlock * sizeof(float);
+}
+
+template <int N>
+__device__ __forceinline__ void scatter_ordered(const EventParams &P, uint64_t ev, float *tile,
+                                                const float (&lk)[N][4], const float (&le1)[N][3],
+                                                const float (&le2)[N][2]) {
   constexpr int L = N - 1;
-  // eps_+ = -(e1 + i e2)/sqrt2, eps_- = (e1 - i e2)/sqrt2
   int perm[N];
   const uint32_t hel = sample_config<N>(P, ev, perm);
-  const int cap = B.cap;
+  int pos[N];  // colour position of each leg
+#pragma unroll
+  for (int l = 0; l < N; ++l) pos[l] = 0;
+#pragma unroll
+  for (int a = 1; a < N; ++a) {
+#pragma unroll
+    for (int l = 0; l < N; ++l) pos[l] = perm[a] == l ? a : pos[l];
+  }
+  float *col = tile + threadIdx.x;
   const float r2 = 0.70710678118654752440f;
 #pragma unroll
-  for (int a = 0; a < N; ++a) {
-    const int want = perm[a];
-    float v[9];
+  for (int l = 0; l < N; ++l) {
+    const int p = pos[l];
+    const float sre = ((hel >> l) & 1u) ? r2 : -r2;
+    float *o = col + (p == 0 ? 12 * L : 12 * (p - 1) + 4) * kBlock;
+    if (p > 0) {
+      float *ok = col + 12 * (p - 1) * kBlock;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = lk[0][q];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) v[4 + q] = le1[0][q];
-    v[7] = le2[0][0];
-    v[8] = le2[0][1];
-#pragma unroll
-    for (int l = 1; l < N; ++l) {
-      const bool hit = (want == l);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) v[q] = hit ? lk[l][q] : v[q];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) v[4 + q] = hit ? le1[l][q] : v[4 + q];
-      v[7] = hit ? le2[l][0] : v[7];
-      v[8] = hit ? le2[l][1] : v[8];
+      for (int q = 0; q < 4; ++q) ok[q * kBlock] = lk[l][q];
     }
-    const float sre = ((hel >> want) & 1u) ? r2 : -r2;
-    float *o = a == 0 ? B.in + (size_t)(12 * L) * cap : B.in + (size_t)(12 * (a - 1) + 4) * cap;
-    if (a > 0) {
-      float *ok = B.in + (size_t)(12 * (a - 1)) * cap;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) ok[(size_t)q * cap + e] = v[q];
-    }
-    o[e] = 0.f;                                  // re, time component
-    o[(size_t)1 * cap + e] = sre * v[4];
-    o[(size_t)2 * cap + e] = sre * v[5];
-    o[(size_t)3 * cap + e] = sre * v[6];
-    o[(size_t)4 * cap + e] = 0.f;                // im, time component
-    o[(size_t)5 * cap + e] = -r2 * v[7];
-    o[(size_t)6 * cap + e] = -r2 * v[8];
-    o[(size_t)7 * cap + e] = 0.f;
+    o[0] = 0.f;  // re, time component
+    o[1 * kBlock] = sre * le1[l][0];
+    o[2 * kBlock] = sre * le1[l][1];
+    o[3 * kBlock] = sre * le1[l][2];
+    o[4 * kBlock] = 0.f;  // im, time component
+    o[5 * kBlock] = -r2 * le2[l][0];
+    o[6 * kBlock] = -r2 * le2[l][1];
+    o[7 * kBlock] = 0.f;
+  }
+}
+
+// Rows of the block's tile -> chunk buffer, one bulk copy per row issued by
+// warp 0.  The chunk buffers hold cap events, cap a multiple of kBlock, so a
+// whole tile is in bounds (columns of threads without an event carry no data
+// the amplitude kernel reads); row segments start on 512-byte boundaries.
+template <int N>
+__device__ __forceinline__ void store_tile(const ChunkBuf<float> &B, const float *tile) {
+  constexpr int rows = 12 * (N - 1) + 8;
+  fence_proxy_async();  // this thread's tile writes, visible to the bulk-copy engine
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const size_t e0 = (size_t)blockIdx.x * kBlock;
+    for (int r = threadIdx.x; r < rows; r += 32)
+      bulk_s2g(B.in + (size_t)r * B.cap + e0, tile + (size_t)r * kBlock, kBlock * sizeof(float));
+    bulk_commit_and_wait_read();
   }
 }
 
@@ -304,14 +321,14 @@ __device__ __forceinline__ void store_ordered(const EventParams &P, uint64_t ev,
 // products, the weight factor.  Helicity labels and colour ordering are
 // exact integer functions of the draws (identical in both forms).
 template <int N>
-__device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<float> &B, int e) {
-  constexpr int M = N - 2, L = N - 1;
+__device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<float> &B, int e, float *tile) {
+  constexpr int M = N - 2;
   const EventParams &P = C.P;
   const uint64_t idx = C.chunk_first + (uint64_t)e;
   const uint64_t ev = P.first_event + idx;
 
   const uint4 w0 = philox_block(P.seed, ev, 0);
-  const float lnxmin = (float)P.lnxmin;
+  const float lnxmin = P.f_lnxmin;
   const float x1 = expf(unit_f32(w0.x, w0.y) * lnxmin);
   const float x2 = expf(unit_f32(w0.z, w0.w) * lnxmin);
   const double shat = (double)x1 * (double)x2 * P.S;
@@ -371,7 +388,7 @@ __device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<fl
     eta[i] = 0.5f * logf((pabs + pz) / (pabs - pz)) + y;
     sum += pt[i];
     lead = fmaxf(lead, pt[i]);
-    pass &= (pt[i] > (float)P.pt_min) & (fabsf(eta[i]) < (float)P.eta_max);
+    pass &= (pt[i] > P.f_pt_min) & (fabsf(eta[i]) < P.f_eta_max);
   }
   float dr2min = 1e30f;
 #pragma unroll
@@ -382,7 +399,7 @@ __device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<fl
       const float de = eta[i] - eta[j];
       const float dr2 = de * de + dphi * dphi;
       dr2min = fminf(dr2min, dr2);
-      pass &= (dr2 > (float)P.dr2_min);
+      pass &= (dr2 > P.f_dr2_min);
     }
   }
   const double ht = (double)sum, ptlead = (double)lead, rmin = (double)sqrtf(dr2min);
@@ -393,9 +410,8 @@ __device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<fl
 
   double wf = 0.0;
   if (pass) {
-    const float mu = (float)P.mu_r_factor * sum;
-    const float as = (float)P.alphas_mz /
-                     (1.f + (float)P.alphas_mz * (float)P.b0 * (logf(mu * mu) - (float)P.ln_mz2));
+    const float mu = P.f_mu_r_factor * sum;
+    const float as = P.f_alphas_mz / (1.f + P.f_asb0 * (logf(mu * mu) - P.f_ln_mz2));
     const double g2 = 4.0 * 3.14159265358979323846 * (double)as;
     double gp = 1.0;
 #pragma unroll
@@ -434,27 +450,29 @@ __device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<fl
     pol_basis_f32(pk[i][0], pk[i][1], pk[i][2], pk[i][3], le1[2 + i], le2[2 + i]);
   }
 
-  store_ordered<N>(P, ev, B, e, lk, le1, le2);
+  scatter_ordered<N>(P, ev, tile, lk, le1, le2);
 }
 
-// Polarisation basis in double-single from double-single momentum components
-// (E = |p| for a massless momentum); results rounded to FP32.
-__device__ __forceinline__ void pol_basis_ds(DS E, DS px, DS py, DS pz, float (&e1)[3], float (&e2)[2]) {
-  const DS pt2 = ds_add(ds_mul(px, px), ds_mul(py, py));
-  DS cf = ds(1.f), sf = ds(0.f), pt = ds(0.f);
-  if (pt2.hi > 0.f) {
-    const DS ipt = ds_rsqrt(pt2);
-    pt = ds_mul(pt2, ipt);
-    cf = ds_mul(px, ipt);
-    sf = ds_mul(py, ipt);
+// Polarisation basis in FP32 from the FP32-rounded momentum components (each
+// within half an ulp of the double-single value, so every product here has
+// FP32 relative accuracy: no cancellation occurs); E = |p|.
+__device__ __forceinline__ void pol_basis_rounded(float E, float px, float py, float pz, float (&e1)[3],
+                                                  float (&e2)[2]) {
+  const float pt2 = fmaf(px, px, py * py);
+  float cf = 1.f, sf = 0.f, pt = 0.f;
+  if (pt2 > 0.f) {
+    const float ipt = rsqrtf(pt2);
+    pt = pt2 * ipt;
+    cf = px * ipt;
+    sf = py * ipt;
   }
-  const DS ie = ds_rcp(E);
-  const DS ct = ds_mul(pz, ie), st = ds_mul(pt, ie);
-  e1[0] = ds_mul(ct, cf).hi;
-  e1[1] = ds_mul(ct, sf).hi;
-  e1[2] = -st.hi;
-  e2[0] = -sf.hi;
-  e2[1] = cf.hi;
+  const float ie = 1.f / E;
+  const float ct = pz * ie, st = pt * ie;
+  e1[0] = ct * cf;
+  e1[1] = ct * sf;
+  e1[2] = -st;
+  e2[0] = -sf;
+  e2[1] = cf;
 }
 
 // K1, double-single form: as kin_fp32, with the steps that need more than
@@ -463,16 +481,17 @@ __device__ __forceinline__ void pol_basis_ds(DS E, DS px, DS py, DS pz, float (&
 // the FP32 rate on this GPU).  The weight factor is assembled in FP32 with
 // its power-of-two scale kept as an exact exponent.
 template <int N>
-__device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<float> &B, int e) {
-  constexpr int M = N - 2, L = N - 1;
+__device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<float> &B, int e, float *tile) {
+  constexpr int M = N - 2;
   const EventParams &P = C.P;
   const uint64_t idx = C.chunk_first + (uint64_t)e;
   const uint64_t ev = P.first_event + idx;
 
   const uint4 w0 = philox_block(P.seed, ev, 0);
-  const float lnxmin = (float)P.lnxmin;
-  const float x1 = expf(unit_f32(w0.x, w0.y) * lnxmin);
-  const float x2 = expf(unit_f32(w0.z, w0.w) * lnxmin);
+  const float lnxmin = P.f_lnxmin;
+  const float ux1 = unit_f32(w0.x, w0.y), ux2 = unit_f32(w0.z, w0.w);
+  const float x1 = expf(ux1 * lnxmin);  // ln x = u ln x_min
+  const float x2 = expf(ux2 * lnxmin);
   const DS shat = ds_mul(ds_mul(DS{P.S_hi, P.S_lo}, x1), x2);
   const DS rs = ds_sqrt(shat);
 
@@ -511,8 +530,9 @@ __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<floa
     pk[i][3] = ds_mul(xs, ds_add(ds_mul(bz, f), qf[i][3]));
   }
 
-  // cuts and observables in FP32 from the rounded momenta
-  const float y = 0.5f * logf(x1 / x2);
+  // cuts and observables in FP32 from the rounded momenta; the partonic
+  // rapidity 0.5 ln(x1 / x2) from the logarithms drawn above
+  const float y = 0.5f * lnxmin * (ux1 - ux2);
   float eta[M], pt[M], px[M], py[M];
   int pass = 1;
   float sum = 0.f, lead = 0.f;
@@ -527,7 +547,7 @@ __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<floa
     eta[i] = 0.5f * logf((pabs + pz) / (pabs - pz)) + y;
     sum += pt[i];
     lead = fmaxf(lead, pt[i]);
-    pass &= (pt[i] > (float)P.pt_min) & (fabsf(eta[i]) < (float)P.eta_max);
+    pass &= (pt[i] > P.f_pt_min) & (fabsf(eta[i]) < P.f_eta_max);
   }
   float dr2min = 1e30f;
 #pragma unroll
@@ -538,13 +558,13 @@ __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<floa
       const float de = eta[i] - eta[j];
       const float dr2 = de * de + dphi * dphi;
       dr2min = fminf(dr2min, dr2);
-      pass &= (dr2 > (float)P.dr2_min);
+      pass &= (dr2 > P.f_dr2_min);
     }
   }
-  const double ht = (double)sum, ptlead = (double)lead, rmin = (double)sqrtf(dr2min);
-  if (P.ht) P.ht[idx] = ht;
-  if (P.ptlead) P.ptlead[idx] = ptlead;
-  if (P.rmin) P.rmin[idx] = rmin;
+  const float rmin = sqrtf(dr2min);
+  if (P.ht) P.ht[idx] = (double)sum;
+  if (P.ptlead) P.ptlead[idx] = (double)lead;
+  if (P.rmin) P.rmin[idx] = (double)rmin;
   if (P.pass) P.pass[idx] = (uint8_t)pass;
 
   // momentum unit 2^-ex near 1/sqrt(s_hat); s' = s_hat 2^-2ex in [1/4, 1)
@@ -554,11 +574,13 @@ __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<floa
   const float sp = shat.hi * sc * sc;
   double wf = 0.0;
   if (pass) {
-    const float mu = (float)P.mu_r_factor * sum;
-    const float as = (float)P.alphas_mz /
-                     (1.f + (float)P.alphas_mz * (float)P.b0 * (logf(mu * mu) - (float)P.ln_mz2));
+    const float mu = P.f_mu_r_factor * sum;
+    const float as = P.f_alphas_mz / (1.f + P.f_asb0 * (logf(mu * mu) - P.f_ln_mz2));
     const float g2 = 4.f * 3.14159265358979323846f * as;
-    float F = 1.7f * powf(x1, -0.2f) * powf(1.f - x1, 5.f) * (1.7f * powf(x2, -0.2f) * powf(1.f - x2, 5.f));
+    // f(x1) f(x2) with f(x) = 1.7 x^-0.2 (1 - x)^5: (x1 x2)^-0.2 from ln x1 + ln x2
+    const float t1 = 1.f - x1, t2 = 1.f - x2;
+    const float t1s = t1 * t1, t2s = t2 * t2;
+    float F = 2.89f * expf(-0.2f * lnxmin * (ux1 + ux2)) * (t1s * t1s * t1) * (t2s * t2s * t2);
 #pragma unroll
     for (int i = 0; i < N - 2; ++i) F *= g2;
     // s_hat^(m-3) = s'^(m-3) 2^(2 ex (m-3))
@@ -568,12 +590,12 @@ __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<floa
     } else {
       F /= sp;
     }
-    wf = ldexp(P.wk * (double)F, 2 * ex * (M - 3));
+    if (F > 0.f) wf = scale_pow2(P.wk * (double)F, 2 * ex * (M - 3));
   }
-  B.efac[e] = ldexp(P.efac, -2 * ex * (N - 4));
+  B.efac[e] = scale_pow2(P.efac, -2 * ex * (N - 4));
   B.wfac[e] = wf;
   B.pass[e] = (uint8_t)pass;
-  if (B.hval) B.hval[e] = P.hist_obs == 0 ? ptlead : (P.hist_obs == 1 ? ht : rmin);
+  if (B.hval) B.hval[e] = (double)(P.hist_obs == 0 ? lead : (P.hist_obs == 1 ? sum : rmin));
 
   float lk[N][4], le1[N][3], le2[N][2];
   const float hs = 0.5f * rs.hi * sc;
@@ -585,26 +607,32 @@ __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<floa
   for (int i = 0; i < M; ++i) {
 #pragma unroll
     for (int m = 0; m < 4; ++m) lk[2 + i][m] = pk[i][m].hi * sc;
-    pol_basis_ds(pk[i][0], pk[i][1], pk[i][2], pk[i][3], le1[2 + i], le2[2 + i]);
+    pol_basis_rounded(pk[i][0].hi, pk[i][1].hi, pk[i][2].hi, pk[i][3].hi, le1[2 + i], le2[2 + i]);
   }
-  store_ordered<N>(P, ev, B, e, lk, le1, le2);
+  scatter_ordered<N>(P, ev, tile, lk, le1, le2);
 }
 
+// K1 kernels.  The FP32 forms take kin_tile_bytes<N>() of dynamic shared
+// memory for the block's output tile.
 template <int N, typename R>
 __global__ void __launch_bounds__(kBlock) kin_kernel(ChunkParams C, ChunkBuf<R> B) {
   const int e = blockIdx.x * kBlock + threadIdx.x;
-  if (e >= C.count) return;
-  if constexpr (sizeof(R) == 4)
-    kin_fp32<N>(C, B, e);
-  else
+  if constexpr (sizeof(R) == 4) {
+    extern __shared__ __align__(128) float kin_tile[];
+    if (e < C.count) kin_fp32<N>(C, B, e, kin_tile);
+    store_tile<N>(B, kin_tile);
+  } else {
+    if (e >= C.count) return;
     kin_generic<N, R>(C, B, e);
+  }
 }
 
 template <int N>
 __global__ void __launch_bounds__(kBlock) kin_ds_kernel(ChunkParams C, ChunkBuf<float> B) {
+  extern __shared__ __align__(128) float kin_tile[];
   const int e = blockIdx.x * kBlock + threadIdx.x;
-  if (e >= C.count) return;
-  kin_ds<N>(C, B, e);
+  if (e < C.count) kin_ds<N>(C, B, e, kin_tile);
+  store_tile<N>(B, kin_tile);
 }
 
 // ---------------------------------------------------------------------------
@@ -618,25 +646,33 @@ struct Accum {
   double sw = 0.0, sw2 = 0.0, npass = 0.0, nbad = 0.0;
 };
 
-template <int NB, typename R>
-__device__ __forceinline__ void finish_event(const ChunkParams &C, const ChunkBuf<R> &B, int e, double amp2,
-                                             Accum<NB> &A, double &w_out, int &bin_out) {
+// Event epilogue from the chunk factors of event e (chunk index): efac, wfac,
+// pass and the histogram value *hval (read only when histogramming).
+template <int NB>
+__device__ __forceinline__ void finish_values(const ChunkParams &C, int e, double efac, double wfac, int ok,
+                                              const double *hval, double amp2, Accum<NB> &A, double &w_out,
+                                              int &bin_out) {
   const EventParams &P = C.P;
   const uint64_t idx = C.chunk_first + (uint64_t)e;
-  const double E = B.efac[e] * amp2;
-  double w = B.wfac[e] * E;
+  const double E = efac * amp2;
+  double w = wfac * E;
   if (!isfinite(w)) {
     A.nbad += 1.0;
     w = 0.0;
   }
   if (P.me2) P.me2[idx] = E;
   if (P.weight) P.weight[idx] = w;
-  const int ok = B.pass[e];
   A.sw += w;
   A.sw2 += w * w;
   A.npass += (double)ok;
   w_out = w;
-  bin_out = (P.hist_bins > 0 && ok) ? hist_bin(B.hval[e], P.hist_lo, P.hist_inv_width, P.hist_bins) : -1;
+  bin_out = (P.hist_bins > 0 && ok) ? hist_bin(*hval, P.hist_lo, P.hist_inv_width, P.hist_bins) : -1;
+}
+
+template <int NB, typename R>
+__device__ __forceinline__ void finish_event(const ChunkParams &C, const ChunkBuf<R> &B, int e, double amp2,
+                                             Accum<NB> &A, double &w_out, int &bin_out) {
+  finish_values<NB>(C, e, B.efac[e], B.wfac[e], B.pass[e], B.hval + e, amp2, A, w_out, bin_out);
 }
 
 // Shared-memory scratch of the epilogue: histogram accumulators and a tile's
@@ -680,7 +716,7 @@ __device__ __forceinline__ void epi_tile(const EpiSmem<NB> &S, int nb2, double w
 
 template <int NB>
 __device__ __forceinline__ void epi_flush(const EpiSmem<NB> &S, int nb2, Accum<NB> &A, double *partials,
-                                          int hist_bins) {
+                                          int hist_bins, int stalled = 0) {
   __shared__ double red[4][NB];
   red[0][threadIdx.x] = A.sw;
   red[1][threadIdx.x] = A.sw2;
@@ -696,6 +732,7 @@ __device__ __forceinline__ void epi_flush(const EpiSmem<NB> &S, int nb2, Accum<N
   }
   double *row = partials + (size_t)blockIdx.x * partial_stride(hist_bins);
   if (threadIdx.x < 4) row[threadIdx.x] += red[threadIdx.x][0];
+  if (threadIdx.x == 4 && stalled) row[4] += 1.0;
   // hw and hw2 are contiguous: [w bins | w^2 bins]
   for (int i = threadIdx.x; i < 2 * nb2; i += NB) row[kPartialHead + i] += S.hw[i];
 }
@@ -711,8 +748,8 @@ __device__ __forceinline__ void load_cv(const R *base, int cap, int e, CV4<R> &v
 
 // K2, register form (FP32, n <= 7): thread per event, the whole current table
 // in registers.
-template <int N, typename R, int NB>
-__global__ void __launch_bounds__(NB) bg_reg_kernel(ChunkParams C, ChunkBuf<R> B, double *partials) {
+template <int N, typename R, int NB, int MINB = 1>
+__global__ void __launch_bounds__(NB, MINB) bg_reg_kernel(ChunkParams C, ChunkBuf<R> B, double *partials) {
   constexpr int L = N - 1;
   extern __shared__ __align__(16) char smem_raw[];
   const int nb2 = C.P.hist_bins > 0 ? C.P.hist_bins + 2 : 0;
@@ -742,6 +779,156 @@ __global__ void __launch_bounds__(NB) bg_reg_kernel(ChunkParams C, ChunkBuf<R> B
     epi_tile<NB>(S, nb2, w, bin);
   }
   epi_flush<NB>(S, nb2, A, partials, C.P.hist_bins);
+}
+
+// K2, staged register form (FP32, n <= 8): as bg_reg_kernel, with each
+// warp's inputs (its 32 events' slice of the 12 L + 8 rows of the chunk
+// buffer and of the event factors) brought into shared memory by bulk copies
+// (the TMA unit's linear form) one tile ahead.  Every warp owns two stages and
+// their mbarriers (which count the copied bytes) and runs its own pipeline:
+// it issues the copies of its slice of tile t + gridDim.x, then waits for
+// tile t, so the next inputs arrive while this tile is computed, and warps
+// never wait for one another (the block synchronises per tile only to fill a
+// histogram).  A wait that does not complete within kStageWaitNs retires the
+// warp: it computes nothing more, waits once more (bounded) for its copies in
+// flight, and the block counts a stall in its partial row.
+template <int L>
+struct WarpStage {
+  static constexpr int rows = 12 * L + 8;
+  static constexpr size_t in_bytes = (size_t)rows * 32 * sizeof(float);
+  static constexpr size_t off_efac = in_bytes;
+  static constexpr size_t off_wfac = off_efac + 32 * sizeof(double);
+  static constexpr size_t off_hval = off_wfac + 32 * sizeof(double);
+  static constexpr size_t off_pass = off_hval + 32 * sizeof(double);
+  static constexpr size_t bytes = (off_pass + 32 + 127) / 128 * 128;
+  static constexpr uint32_t tx = (uint32_t)(in_bytes + 3 * 32 * sizeof(double) + 32);
+};
+
+template <int L, int NB>
+struct RegStage {
+  static constexpr int warps = NB / 32;
+  static constexpr size_t head = (size_t)warps * 2 * WarpStage<L>::bytes + 128;  // stages, then mbarriers
+  static_assert(warps * 2 * sizeof(uint64_t) <= 128, "mbarrier area");
+};
+
+// Copies of the 32 events starting at chunk index e0 into stage `st`.  The
+// chunk buffers hold cap events, cap a multiple of 128, so a whole slice of
+// a tile is always in bounds; every segment starts on a 16-byte boundary (cap
+// * 4 and e0 * 4 are multiples of 128) and is a multiple of 16 bytes long.
+template <int L>
+__device__ __forceinline__ void issue_slice(const ChunkBuf<float> &B, size_t e0, char *st, uint64_t *bar) {
+  using W = WarpStage<L>;
+  const int lane = threadIdx.x & 31;
+  fence_proxy_async();  // this warp's earlier reads of the stage precede the copies
+  if (lane == 0) mbar_arrive_expect_tx(bar, W::tx);
+  __syncwarp();
+  for (int r = lane; r < W::rows + 4; r += 32) {
+    if (r < W::rows)
+      bulk_g2s(st + (size_t)r * 32 * sizeof(float), B.in + (size_t)r * B.cap + e0, 32 * sizeof(float), bar);
+    else if (r == W::rows)
+      bulk_g2s(st + W::off_efac, B.efac + e0, 32 * sizeof(double), bar);
+    else if (r == W::rows + 1)
+      bulk_g2s(st + W::off_wfac, B.wfac + e0, 32 * sizeof(double), bar);
+    else if (r == W::rows + 2)
+      bulk_g2s(st + W::off_hval, B.hval + e0, 32 * sizeof(double), bar);
+    else
+      bulk_g2s(st + W::off_pass, B.pass + e0, 32, bar);
+  }
+}
+
+template <int N, int NB>
+__global__ void __launch_bounds__(NB, 1) bg_reg_tma_kernel(ChunkParams C, ChunkBuf<float> B, double *partials) {
+  constexpr int L = N - 1;
+  using W = WarpStage<L>;
+  static_assert(NB == kBlock, "tiles must match the chunk-capacity granularity");
+  extern __shared__ __align__(128) char smem_stage[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  char *const my0 = smem_stage + (size_t)warp * 2 * W::bytes, *const my1 = my0 + W::bytes;
+  uint64_t *const bar = (uint64_t *)(smem_stage + (size_t)RegStage<L, NB>::warps * 2 * W::bytes) + 2 * warp;
+  const int nb2 = C.P.hist_bins > 0 ? C.P.hist_bins + 2 : 0;
+  EpiSmem<NB> ES(smem_stage + RegStage<L, NB>::head, nb2);
+  for (int i = threadIdx.x; i < 2 * nb2; i += NB) ES.hw[i] = 0.0;
+  if (lane == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_proxy_async();
+  }
+  __syncthreads();
+  Accum<NB> A;
+  const int ntiles = (C.count + NB - 1) / NB;
+  // bit q of `parity`: phase of stage q's next completion; of `pending`: copies into q in flight
+  uint32_t parity = 0u, pending = 0u;
+  bool dead = false;
+  if ((int)blockIdx.x < ntiles) {
+    const size_t e0 = (size_t)blockIdx.x * NB + warp * 32;
+    if (e0 < (size_t)C.count) {
+      issue_slice<L>(B, e0, my0, &bar[0]);
+      pending = 1u;
+    }
+  }
+  int k = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+    const int sb = k & 1;
+    const int next = tile + gridDim.x;
+    if (!dead && next < ntiles) {  // the other stage was read by this warp in the previous iteration
+      const size_t e0n = (size_t)next * NB + warp * 32;
+      if (e0n < (size_t)C.count) {
+        issue_slice<L>(B, e0n, sb ? my0 : my1, &bar[sb ^ 1]);
+        pending |= 1u << (sb ^ 1);
+      }
+    }
+    const size_t e0 = (size_t)tile * NB + warp * 32;
+    double w = 0.0;
+    int bin = -1;
+    if (!dead && e0 < (size_t)C.count) {
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[sb], (parity >> sb) & 1u));
+      if (!ok) {
+        dead = true;
+      } else {
+        parity ^= 1u << sb;
+        pending &= ~(1u << sb);
+        const int e = (int)e0 + lane;
+        if (e < C.count) {
+          const char *st = sb ? my1 : my0;
+          const float *in = (const float *)st + lane;
+          RV4<float> kk[L];
+          CV4<float> ev[L], e0v;
+#pragma unroll
+          for (int a = 0; a < L; ++a) {
+            const float *base = in + (size_t)(12 * a) * 32;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+              kk[a].v[m] = base[m * 32];
+              ev[a].c[m].re = base[(4 + m) * 32];
+              ev[a].c[m].im = base[(8 + m) * 32];
+            }
+          }
+          const float *b0 = in + (size_t)(12 * L) * 32;
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            e0v.c[m].re = b0[m * 32];
+            e0v.c[m].im = b0[(4 + m) * 32];
+          }
+          const Cx<float> amp = bg_amplitude<float, L>(kk, ev, e0v);
+          const double re = amp.re, im = amp.im;
+          const double *efac = (const double *)(st + W::off_efac), *wfac = (const double *)(st + W::off_wfac);
+          const double *hval = (const double *)(st + W::off_hval);
+          const uint8_t *pass = (const uint8_t *)(st + W::off_pass);
+          finish_values<NB>(C, e, efac[lane], wfac[lane], pass[lane], hval + lane, re * re + im * im, A, w, bin);
+        }
+      }
+    }
+    epi_tile<NB>(ES, nb2, w, bin);  // block barrier only when filling a histogram
+    __syncwarp();                   // this warp's reads of the stage precede its refill
+  }
+  if (dead) {
+    // copies still in flight into this warp's stages: wait once more (bounded)
+    for (int q = 0; q < 2; ++q)
+      if ((pending >> q) & 1u) (void)mbar_wait_bounded(&bar[q], (parity >> q) & 1u);
+    __syncwarp();
+  }
+  const int stalled = __syncthreads_or(dead) ? 1 : 0;
+  epi_flush<NB>(ES, nb2, A, partials, C.P.hist_bins, stalled);
 }
 
 // K2, loop form (FP64): table in per-thread local memory.

@@ -26,6 +26,16 @@ def test_header_declares_binding_names():
     assert declared_functions() == sorted(tess.EXPORTED)
 
 
+def test_header_constants_match_binding():
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    defs = {}
+    for m in re.finditer(r"#define\s+(TESS_[A-Z0-9_]+)\s+\(?(-?[0-9]+)u?(?:\s*<<\s*([0-9]+))?", src):
+        defs[m.group(1)] = int(m.group(2)) << int(m.group(3) or 0)
+    assert len(defs) >= 29
+    for name, value in defs.items():
+        assert getattr(tess, name) == value, name
+
+
 def test_library_exports_every_declared_symbol():
     lib = tess._load()
     out = subprocess.run(["nm", "-D", "--defined-only", tess.library_path()], capture_output=True, text=True,
