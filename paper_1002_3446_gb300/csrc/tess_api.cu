@@ -347,6 +347,7 @@ void fill_params(const tess_process *proc, uint64_t seed, uint64_t first_event, 
   P.S_hi = (float)P.S;
   P.S_lo = (float)(P.S - (double)P.S_hi);
   P.wk = P.wconst * P.lnxmin * P.lnxmin * P.phiconst * 0.5;
+  tess::philox_round_keys(seed, P.rk);
   P.f_lnxmin = (float)P.lnxmin;
   P.f_pt_min = (float)P.pt_min;
   P.f_eta_max = (float)P.eta_max;
@@ -818,6 +819,7 @@ int tess_draws(tess_ctx *ctx, int n, uint64_t seed, uint64_t first_event, uint64
   P.seed = seed;
   P.first_event = first_event;
   P.n_events = n_events;
+  tess::philox_round_keys(seed, P.rk);
   cudaStream_t s = (cudaStream_t)stream;
   const cudaError_t e = n <= 8 ? tess::launch_draws_a(n, P, u, hel, order, s)
                                : (n <= 10 ? tess::launch_draws_b(n, P, u, hel, order, s)
@@ -1037,6 +1039,7 @@ extern "C" int tess_generate_noalloc(tess_ctx *ctx, const tess_process *proc, ui
   P.seed = seed;
   P.first_event = first_event;
   P.n_events = n_events;
+  tess::philox_round_keys(seed, P.rk);
   P.S = proc->sqrt_s * proc->sqrt_s;
   P.lnxmin = std::log((m * proc->pt_min) * (m * proc->pt_min) / P.S);
   P.pt_min = proc->pt_min;

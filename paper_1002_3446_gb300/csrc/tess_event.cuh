@@ -28,6 +28,7 @@ struct EventParams {
   // constant wconst (ln x_min)^2 phiconst / 2
   float S_hi, S_lo;
   double wk;
+  uint32_t rk[20];     // Philox round keys of `seed`
   // single-precision copies of the constants the FP32 kinematics read
   float f_lnxmin, f_pt_min, f_eta_max, f_dr2_min, f_alphas_mz, f_asb0, f_ln_mz2, f_mu_r_factor;
   int kin_ds;          // 1: double-single kinematics kernel
@@ -164,11 +165,17 @@ __device__ __forceinline__ void kinematics(const EventParams &P, uint64_t ev, Ki
 // sampled event, from its draws.  Both are integer functions of the Philox
 // words: the helicity word is the top n bits of its uniform, and each swap
 // index floor(u (i-1)) is evaluated exactly as the double product rounds.
+// Philox block `blk` of event `ev` of the launch's stream (round keys from
+// the launch constants).
+__device__ __forceinline__ uint4 event_block(const EventParams &P, uint64_t ev, uint32_t blk) {
+  return philox4x32_10_rk(make_uint4((uint32_t)ev, (uint32_t)(ev >> 32), blk, 0u), P.rk);
+}
+
 template <int N>
 __device__ __forceinline__ uint32_t sample_config(const EventParams &P, uint64_t ev, int (&perm)[N]) {
   constexpr int M = N - 2;
   constexpr uint32_t jh = 2 + 4 * M;  // helicity draw; ordering draws follow
-  uint4 w = philox_block(P.seed, ev, jh >> 1);
+  uint4 w = event_block(P, ev, jh >> 1);
   uint32_t cur = jh >> 1;
   const uint32_t a0 = (jh & 1u) ? w.z : w.x;
   const uint32_t hel = a0 >> (32 - N);  // top N bits of (a >> 6) 2^26 + (b >> 6)
@@ -179,7 +186,7 @@ __device__ __forceinline__ uint32_t sample_config(const EventParams &P, uint64_t
     const uint32_t j = jh + 1 + (N - i);
     if ((j >> 1) != cur) {
       cur = j >> 1;
-      w = philox_block(P.seed, ev, cur);
+      w = event_block(P, ev, cur);
     }
     const uint64_t k = (j & 1u) ? unit_bits(w.z, w.w) : unit_bits(w.x, w.y);
     const int r = 2 + floor_unit_times(k, (uint32_t)(i - 1));
@@ -193,6 +200,43 @@ __device__ __forceinline__ uint32_t sample_config(const EventParams &P, uint64_t
       }
     }
   }
+  return hel;
+}
+
+// The same draws as sample_config, with the permutation kept packed: nibble
+// a of the working word holds the leg at colour position a (a swap is a few
+// shifts and xors instead of selects over positions).  Returns the helicity
+// word; *posw receives the inverse, nibble l = colour position of leg l.
+template <int N>
+__device__ __forceinline__ uint32_t sample_positions(const EventParams &P, uint64_t ev, uint64_t *posw) {
+  static_assert(N <= 16, "4-bit positions");
+  constexpr int M = N - 2;
+  constexpr uint32_t jh = 2 + 4 * M;  // helicity draw; ordering draws follow
+  uint4 w = event_block(P, ev, jh >> 1);
+  uint32_t cur = jh >> 1;
+  const uint32_t a0 = (jh & 1u) ? w.z : w.x;
+  const uint32_t hel = a0 >> (32 - N);
+  uint64_t pw = 0;
+#pragma unroll
+  for (int a = 0; a < N; ++a) pw |= (uint64_t)a << (4 * a);
+#pragma unroll
+  for (int i = N; i >= 3; --i) {
+    const uint32_t j = jh + 1 + (N - i);
+    if ((j >> 1) != cur) {
+      cur = j >> 1;
+      w = event_block(P, ev, cur);
+    }
+    const uint64_t k = (j & 1u) ? unit_bits(w.z, w.w) : unit_bits(w.x, w.y);
+    const int r = 2 + floor_unit_times(k, (uint32_t)(i - 1));
+    // swap positions i and r (1-based)
+    const int si = 4 * (i - 1), sr = 4 * (r - 1);
+    const uint64_t x = ((pw >> si) ^ (pw >> sr)) & 15ull;
+    pw ^= (x << si) | (x << sr);
+  }
+  uint64_t qw = 0;
+#pragma unroll
+  for (int a = 0; a < N; ++a) qw |= (uint64_t)a << (4 * (int)((pw >> (4 * a)) & 15ull));
+  *posw = qw;
   return hel;
 }
 

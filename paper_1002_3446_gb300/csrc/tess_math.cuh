@@ -48,6 +48,31 @@ __device__ __forceinline__ uint4 philox_block(uint64_t seed, uint64_t ev, uint32
                        make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
 }
 
+// Philox4x32-10 with the ten round keys given (rk[2r], rk[2r+1] = key of
+// round r); the same function of (counter, key) as philox4x32_10.  Kernels
+// take the round keys from their launch constants, so the key schedule is
+// not recomputed per block.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t *rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk[2 * r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ rk[2 * r + 1],
+                   (uint32_t)p0);
+  }
+  return c;
+}
+
+// Round keys of philox4x32_10 for key (seed_lo, seed_hi).
+__host__ __device__ inline void philox_round_keys(uint64_t seed, uint32_t *rk) {
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk[2 * r] = k0;
+    rk[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
 // The 52-bit integer k of uniform u = (k + 1/2) 2^-52 from its two words.
 __device__ __forceinline__ uint64_t unit_bits(uint32_t a, uint32_t b) {
   return ((uint64_t)(a >> 6) << 26) | (uint64_t)(b >> 6);
@@ -273,5 +298,36 @@ __device__ __forceinline__ DS ds_rsqrt(DS a) {
 }
 
 __device__ __forceinline__ DS ds_sqrt(DS a) { return ds_mul(a, ds_rsqrt(a)); }
+
+// Unnormalised pairs (h, l) for chains whose result is needed only rounded to
+// FP32: error-free products and sums as above, without renormalising between
+// steps (|l| stays within a few ulp of h), rounded once at the end.
+__device__ __forceinline__ float two_sum(float a, float b, float &t) {  // s + t = a + b exactly
+  const float s = a + b;
+  const float bb = s - a;
+  t = (a - (s - bb)) + (b - bb);
+  return s;
+}
+
+// (ah, al) (bh, bl) as a pair
+__device__ __forceinline__ float pair_mul(float ah, float al, float bh, float bl, float &l) {
+  const float h = ah * bh;
+  l = fmaf(ah, bl, fmaf(al, bh, fmaf(ah, bh, -h)));
+  return h;
+}
+
+// (ah, al) b as a pair
+__device__ __forceinline__ float pair_mul(float ah, float al, float b, float &l) {
+  const float h = ah * b;
+  l = fmaf(al, b, fmaf(ah, b, -h));
+  return h;
+}
+
+// FP32 rounding of (ah, al) (bh, bl)
+__device__ __forceinline__ float pair_mul_round(float ah, float al, float bh, float bl) {
+  float l;
+  const float h = pair_mul(ah, al, bh, bl, l);
+  return h + l;
+}
 
 }  // namespace tess

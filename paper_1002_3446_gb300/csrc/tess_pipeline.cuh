@@ -265,21 +265,13 @@ __device__ __forceinline__ void scatter_ordered(const EventParams &P, uint64_t e
                                                 const float (&lk)[N][4], const float (&le1)[N][3],
                                                 const float (&le2)[N][2]) {
   constexpr int L = N - 1;
-  int perm[N];
-  const uint32_t hel = sample_config<N>(P, ev, perm);
-  int pos[N];  // colour position of each leg
-#pragma unroll
-  for (int l = 0; l < N; ++l) pos[l] = 0;
-#pragma unroll
-  for (int a = 1; a < N; ++a) {
-#pragma unroll
-    for (int l = 0; l < N; ++l) pos[l] = perm[a] == l ? a : pos[l];
-  }
+  uint64_t posw;
+  const uint32_t hel = sample_positions<N>(P, ev, &posw);
   float *col = tile + threadIdx.x;
   const float r2 = 0.70710678118654752440f;
 #pragma unroll
   for (int l = 0; l < N; ++l) {
-    const int p = pos[l];
+    const int p = (int)((posw >> (4 * l)) & 15ull);  // colour position of leg l
     const float sre = ((hel >> l) & 1u) ? r2 : -r2;
     float *o = col + (p == 0 ? 12 * L : 12 * (p - 1) + 4) * kBlock;
     if (p > 0) {
@@ -327,7 +319,7 @@ __device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<fl
   const uint64_t idx = C.chunk_first + (uint64_t)e;
   const uint64_t ev = P.first_event + idx;
 
-  const uint4 w0 = philox_block(P.seed, ev, 0);
+  const uint4 w0 = event_block(P, ev, 0);
   const float lnxmin = P.f_lnxmin;
   const float x1 = expf(unit_f32(w0.x, w0.y) * lnxmin);
   const float x2 = expf(unit_f32(w0.z, w0.w) * lnxmin);
@@ -339,8 +331,8 @@ __device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<fl
   double Q0 = 0.0, Q1 = 0.0, Q2 = 0.0, Q3 = 0.0;
 #pragma unroll
   for (int i = 0; i < M; ++i) {
-    const uint4 wa = philox_block(P.seed, ev, 1 + 2 * i);
-    const uint4 wb = philox_block(P.seed, ev, 2 + 2 * i);
+    const uint4 wa = event_block(P, ev, 1 + 2 * i);
+    const uint4 wb = event_block(P, ev, 2 + 2 * i);
     const float c = 2.f * unit_f32(wa.x, wa.y) - 1.f;
     const float sn0 = sqrtf(fmaxf(1.f - c * c, 0.f));
     float sn, cs;
@@ -487,7 +479,7 @@ __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<floa
   const uint64_t idx = C.chunk_first + (uint64_t)e;
   const uint64_t ev = P.first_event + idx;
 
-  const uint4 w0 = philox_block(P.seed, ev, 0);
+  const uint4 w0 = event_block(P, ev, 0);
   const float lnxmin = P.f_lnxmin;
   const float ux1 = unit_f32(w0.x, w0.y), ux2 = unit_f32(w0.z, w0.w);
   const float x1 = expf(ux1 * lnxmin);  // ln x = u ln x_min
@@ -496,11 +488,11 @@ __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<floa
   const DS rs = ds_sqrt(shat);
 
   float qf[M][4];
-  DS Q[4] = {ds(0.f), ds(0.f), ds(0.f), ds(0.f)};
+  float Qh[4] = {0.f, 0.f, 0.f, 0.f}, Ql[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 0; i < M; ++i) {
-    const uint4 wa = philox_block(P.seed, ev, 1 + 2 * i);
-    const uint4 wb = philox_block(P.seed, ev, 2 + 2 * i);
+    const uint4 wa = event_block(P, ev, 1 + 2 * i);
+    const uint4 wb = event_block(P, ev, 2 + 2 * i);
     const float c = 2.f * unit_f32(wa.x, wa.y) - 1.f;
     const float sn0 = sqrtf(fmaxf(1.f - c * c, 0.f));
     float sn, cs;
@@ -511,23 +503,49 @@ __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<floa
     qf[i][2] = q0 * sn0 * sn;
     qf[i][3] = q0 * c;
 #pragma unroll
-    for (int m = 0; m < 4; ++m) Q[m] = ds_add(Q[m], qf[i][m]);
+    for (int m = 0; m < 4; ++m) {
+      float t;
+      Qh[m] = two_sum(Qh[m], qf[i][m], t);
+      Ql[m] += t;
+    }
   }
+  DS Q[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) Q[m] = ds_fast_two_sum(Qh[m], Ql[m]);
   const DS M2 = ds_sub(ds_mul(Q[0], Q[0]), ds_add(ds_add(ds_mul(Q[1], Q[1]), ds_mul(Q[2], Q[2])), ds_mul(Q[3], Q[3])));
   const DS invM = ds_rsqrt(M2);
-  const DS bx = ds_neg(ds_mul(Q[1], invM)), by = ds_neg(ds_mul(Q[2], invM)), bz = ds_neg(ds_mul(Q[3], invM));
+  const DS b[3] = {ds_neg(ds_mul(Q[1], invM)), ds_neg(ds_mul(Q[2], invM)), ds_neg(ds_mul(Q[3], invM))};
   const DS gam = ds_mul(Q[0], invM);
   const DS aa = ds_rcp(ds_add(gam, 1.f));
   const DS xs = ds_mul(rs, invM);
-  DS pk[M][4];
+  // boost and rescale of each seed, k = xs (gam q0 + b.q, q + b f), f = aa b.q
+  // + q0, in unnormalised pairs, each component rounded once to FP32
+  float pk[M][4];
 #pragma unroll
   for (int i = 0; i < M; ++i) {
-    const DS bq = ds_add(ds_add(ds_mul(bx, qf[i][1]), ds_mul(by, qf[i][2])), ds_mul(bz, qf[i][3]));
-    pk[i][0] = ds_mul(xs, ds_add(ds_mul(gam, qf[i][0]), bq));
-    const DS f = ds_add(ds_mul(aa, bq), qf[i][0]);
-    pk[i][1] = ds_mul(xs, ds_add(ds_mul(bx, f), qf[i][1]));
-    pk[i][2] = ds_mul(xs, ds_add(ds_mul(by, f), qf[i][2]));
-    pk[i][3] = ds_mul(xs, ds_add(ds_mul(bz, f), qf[i][3]));
+    float t, l1, l2, l3;
+    const float p1 = pair_mul(b[0].hi, b[0].lo, qf[i][1], l1);
+    const float p2 = pair_mul(b[1].hi, b[1].lo, qf[i][2], l2);
+    const float p3 = pair_mul(b[2].hi, b[2].lo, qf[i][3], l3);
+    float uh = two_sum(p1, p2, t);
+    float ul = t + l1 + l2 + l3;
+    uh = two_sum(uh, p3, t);
+    ul += t;  // (uh, ul) = b.q
+    float gl;
+    const float gh = pair_mul(gam.hi, gam.lo, qf[i][0], gl);
+    const float eh = two_sum(gh, uh, t);
+    pk[i][0] = pair_mul_round(xs.hi, xs.lo, eh, t + gl + ul);
+    float fl;
+    const float fp = pair_mul(aa.hi, aa.lo, uh, ul, fl);
+    const float fh = two_sum(fp, qf[i][0], t);
+    fl += t;  // (fh, fl) = f
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float bl;
+      const float bh = pair_mul(b[j].hi, b[j].lo, fh, fl, bl);
+      const float sh = two_sum(qf[i][1 + j], bh, t);
+      pk[i][1 + j] = pair_mul_round(xs.hi, xs.lo, sh, t + bl);
+    }
   }
 
   // cuts and observables in FP32 from the rounded momenta; the partonic
@@ -538,9 +556,9 @@ __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<floa
   float sum = 0.f, lead = 0.f;
 #pragma unroll
   for (int i = 0; i < M; ++i) {
-    px[i] = pk[i][1].hi;
-    py[i] = pk[i][2].hi;
-    const float pz = pk[i][3].hi;
+    px[i] = pk[i][1];
+    py[i] = pk[i][2];
+    const float pz = pk[i][3];
     const float pt2 = px[i] * px[i] + py[i] * py[i];
     const float pabs = sqrtf(pt2 + pz * pz);
     pt[i] = sqrtf(pt2);
@@ -606,8 +624,8 @@ __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<floa
 #pragma unroll
   for (int i = 0; i < M; ++i) {
 #pragma unroll
-    for (int m = 0; m < 4; ++m) lk[2 + i][m] = pk[i][m].hi * sc;
-    pol_basis_rounded(pk[i][0].hi, pk[i][1].hi, pk[i][2].hi, pk[i][3].hi, le1[2 + i], le2[2 + i]);
+    for (int m = 0; m < 4; ++m) lk[2 + i][m] = pk[i][m] * sc;
+    pol_basis_rounded(pk[i][0], pk[i][1], pk[i][2], pk[i][3], le1[2 + i], le2[2 + i]);
   }
   scatter_ordered<N>(P, ev, tile, lk, le1, le2);
 }
