@@ -186,7 +186,7 @@ int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, in
     pl->kin_smem = 0;
   }
   const int per_sm = pl->per_sm;
-  const uint64_t per_event = (uint64_t)(12 * L + 8) * sizeof(R) + 3 * sizeof(double) + 1;
+  const uint64_t per_event = (uint64_t)InRows<L>::rows * sizeof(R) + 3 * sizeof(double) + 1;
   const uint64_t target = std::max<uint64_t>(128, (kChunkTargetBytes / per_event) / 128 * 128);
   const uint64_t want = (std::max<uint64_t>(n_events, 1) + 127) / 128 * 128;
   pl->cap = (int)std::min(target, want);
@@ -203,7 +203,7 @@ int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, in
   pl->grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles, resident));
   size_t off = align256((size_t)pl->grid * partial_stride(hist_bins) * sizeof(double));
   pl->off_in = off;
-  off = align256(off + (size_t)(12 * L + 8) * pl->cap * sizeof(R));
+  off = align256(off + (size_t)InRows<L>::rows * pl->cap * sizeof(R));
   pl->off_efac = off;
   off = align256(off + (size_t)pl->cap * sizeof(double));
   pl->off_wfac = off;

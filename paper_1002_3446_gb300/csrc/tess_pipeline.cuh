@@ -23,7 +23,7 @@ namespace tess {
 // base[s * cap + e] (coalesced across consecutive events).
 template <typename R>
 struct ChunkBuf {
-  R *in;          // [(12 L + 8) * cap]: per position a = 0..L-1: k (4), eps (4 re, 4 im); then eps_0 (4 re, 4 im)
+  R *in;          // [InRows<L>::rows * cap] amplitude inputs, rows as InRows
   double *efac;   // [cap] |m|^2 -> estimator E (includes the momentum unit)
   double *wfac;   // [cap] E -> weight (0 if the event fails the cuts)
   double *hval;   // [cap] histogram observable
@@ -36,6 +36,39 @@ struct ChunkParams {
   uint64_t chunk_first;  // index of the chunk's first event within the call
   int count;             // events in this chunk
 };
+
+// Rows of the amplitude inputs in a chunk buffer (each row cap events).  For
+// colour positions 1..L (block b = position - 1): k^0..k^3, Re eps^x, eps^y,
+// eps^z, Im eps^x, eps^y; then for position 0: Re eps^x, eps^y, eps^z, Im
+// eps^x, eps^y.  eps^0 = 0 and Im eps^z = 0 in the helicity basis of the
+// polarisation vectors (eps_+- = (-+e1 - i e2)/sqrt2 with e1, e2 spatial and
+// e2 transverse to z), so those components are not stored.
+template <int L>
+struct InRows {
+  static constexpr int rows = 9 * L + 5;
+  __host__ __device__ static constexpr int k(int b) { return 9 * b; }
+  __host__ __device__ static constexpr int eps(int b) { return 9 * b + 4; }
+  static constexpr int eps0 = 9 * L;
+};
+
+// Momentum and polarisation vector from their rows (row stride s elements).
+template <typename R>
+__device__ __forceinline__ void load_k(const R *p, size_t s, RV4<R> &k) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) k.v[m] = p[m * s];
+}
+
+template <typename R>
+__device__ __forceinline__ void load_eps(const R *p, size_t s, CV4<R> &v) {
+  v.c[0].re = R(0);
+  v.c[0].im = R(0);
+  v.c[1].re = p[0];
+  v.c[2].re = p[s];
+  v.c[3].re = p[2 * s];
+  v.c[1].im = p[3 * s];
+  v.c[2].im = p[4 * s];
+  v.c[3].im = R(0);
+}
 
 template <typename R>
 __device__ __forceinline__ R r_exp(R x);
@@ -211,18 +244,19 @@ __device__ __forceinline__ void kin_generic(const ChunkParams &C, const ChunkBuf
     CV4<double> ep, em;
     polarisations<double>(sg * kp[a][1], sg * kp[a][2], sg * kp[a][3], ep, em);
     const bool minus = (hel >> legp[a]) & 1u;
-    R *o = a == 0 ? B.in + (size_t)(12 * L) * cap : B.in + (size_t)(12 * (a - 1) + 4) * cap;
+    using IR = InRows<L>;
+    R *o = B.in + (size_t)(a == 0 ? IR::eps0 : IR::eps(a - 1)) * cap + e;
     if (a > 0) {
-      R *ok = B.in + (size_t)(12 * (a - 1)) * cap;
+      R *ok = B.in + (size_t)IR::k(a - 1) * cap + e;
 #pragma unroll
-      for (int m = 0; m < 4; ++m) ok[(size_t)m * cap + e] = R(kp[a][m] * inv_rs);
+      for (int m = 0; m < 4; ++m) ok[(size_t)m * cap] = R(kp[a][m] * inv_rs);
     }
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const Cx<double> z = minus ? em.c[m] : ep.c[m];
-      o[(size_t)m * cap + e] = R(z.re);
-      o[(size_t)(4 + m) * cap + e] = R(z.im);
-    }
+    const CV4<double> &z = minus ? em : ep;
+    o[0] = R(z.c[1].re);
+    o[(size_t)cap] = R(z.c[2].re);
+    o[(size_t)2 * cap] = R(z.c[3].re);
+    o[(size_t)3 * cap] = R(z.c[1].im);
+    o[(size_t)4 * cap] = R(z.c[2].im);
   }
 }
 
@@ -257,7 +291,7 @@ __device__ __forceinline__ void pol_basis_f32(double E, double px, double py, do
 // tile's rows to the chunk buffer with bulk copies.
 template <int N>
 constexpr size_t kin_tile_bytes() {
-  return (size_t)(12 * (N - 1) + 8) * kBlock * sizeof(float);
+  return (size_t)InRows<N - 1>::rows * kBlock * sizeof(float);
 }
 
 template <int N>
@@ -273,20 +307,17 @@ __device__ __forceinline__ void scatter_ordered(const EventParams &P, uint64_t e
   for (int l = 0; l < N; ++l) {
     const int p = (int)((posw >> (4 * l)) & 15ull);  // colour position of leg l
     const float sre = ((hel >> l) & 1u) ? r2 : -r2;
-    float *o = col + (p == 0 ? 12 * L : 12 * (p - 1) + 4) * kBlock;
+    float *o = col + (p == 0 ? InRows<L>::eps0 : InRows<L>::eps(p - 1)) * kBlock;
     if (p > 0) {
-      float *ok = col + 12 * (p - 1) * kBlock;
+      float *ok = col + InRows<L>::k(p - 1) * kBlock;
 #pragma unroll
       for (int q = 0; q < 4; ++q) ok[q * kBlock] = lk[l][q];
     }
-    o[0] = 0.f;  // re, time component
-    o[1 * kBlock] = sre * le1[l][0];
-    o[2 * kBlock] = sre * le1[l][1];
-    o[3 * kBlock] = sre * le1[l][2];
-    o[4 * kBlock] = 0.f;  // im, time component
-    o[5 * kBlock] = -r2 * le2[l][0];
-    o[6 * kBlock] = -r2 * le2[l][1];
-    o[7 * kBlock] = 0.f;
+    o[0] = sre * le1[l][0];
+    o[1 * kBlock] = sre * le1[l][1];
+    o[2 * kBlock] = sre * le1[l][2];
+    o[3 * kBlock] = -r2 * le2[l][0];
+    o[4 * kBlock] = -r2 * le2[l][1];
   }
 }
 
@@ -296,7 +327,7 @@ __device__ __forceinline__ void scatter_ordered(const EventParams &P, uint64_t e
 // the amplitude kernel reads); row segments start on 512-byte boundaries.
 template <int N>
 __device__ __forceinline__ void store_tile(const ChunkBuf<float> &B, const float *tile) {
-  constexpr int rows = 12 * (N - 1) + 8;
+  constexpr int rows = InRows<N - 1>::rows;
   fence_proxy_async();  // this thread's tile writes, visible to the bulk-copy engine
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -755,15 +786,6 @@ __device__ __forceinline__ void epi_flush(const EpiSmem<NB> &S, int nb2, Accum<N
   for (int i = threadIdx.x; i < 2 * nb2; i += NB) row[kPartialHead + i] += S.hw[i];
 }
 
-template <typename R>
-__device__ __forceinline__ void load_cv(const R *base, int cap, int e, CV4<R> &v) {
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    v.c[m].re = base[(size_t)m * cap + e];
-    v.c[m].im = base[(size_t)(4 + m) * cap + e];
-  }
-}
-
 // K2, register form (FP32, n <= 7): thread per event, the whole current table
 // in registers.
 template <int N, typename R, int NB, int MINB = 1>
@@ -784,12 +806,10 @@ __global__ void __launch_bounds__(NB, MINB) bg_reg_kernel(ChunkParams C, ChunkBu
       CV4<R> ev[L], e0;
 #pragma unroll
       for (int a = 0; a < L; ++a) {
-        const R *base = B.in + (size_t)(12 * a) * B.cap;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) k[a].v[m] = base[(size_t)m * B.cap + e];
-        load_cv(base + (size_t)4 * B.cap, B.cap, e, ev[a]);
+        load_k(B.in + (size_t)InRows<L>::k(a) * B.cap + e, (size_t)B.cap, k[a]);
+        load_eps(B.in + (size_t)InRows<L>::eps(a) * B.cap + e, (size_t)B.cap, ev[a]);
       }
-      load_cv(B.in + (size_t)(12 * L) * B.cap, B.cap, e, e0);
+      load_eps(B.in + (size_t)InRows<L>::eps0 * B.cap + e, (size_t)B.cap, e0);
       const Cx<R> amp = bg_amplitude<R, L>(k, ev, e0);
       const double re = amp.re, im = amp.im;
       finish_event<NB, R>(C, B, e, re * re + im * im, A, w, bin);
@@ -800,7 +820,7 @@ __global__ void __launch_bounds__(NB, MINB) bg_reg_kernel(ChunkParams C, ChunkBu
 }
 
 // K2, staged register form (FP32, n <= 8): as bg_reg_kernel, with each
-// warp's inputs (its 32 events' slice of the 12 L + 8 rows of the chunk
+// warp's inputs (its 32 events' slice of the InRows rows of the chunk
 // buffer and of the event factors) brought into shared memory by bulk copies
 // (the TMA unit's linear form) one tile ahead.  Every warp owns two stages and
 // their mbarriers (which count the copied bytes) and runs its own pipeline:
@@ -812,7 +832,7 @@ __global__ void __launch_bounds__(NB, MINB) bg_reg_kernel(ChunkParams C, ChunkBu
 // flight, and the block counts a stall in its partial row.
 template <int L>
 struct WarpStage {
-  static constexpr int rows = 12 * L + 8;
+  static constexpr int rows = InRows<L>::rows;
   static constexpr size_t in_bytes = (size_t)rows * 32 * sizeof(float);
   static constexpr size_t off_efac = in_bytes;
   static constexpr size_t off_wfac = off_efac + 32 * sizeof(double);
@@ -913,20 +933,10 @@ __global__ void __launch_bounds__(NB, 1) bg_reg_tma_kernel(ChunkParams C, ChunkB
           CV4<float> ev[L], e0v;
 #pragma unroll
           for (int a = 0; a < L; ++a) {
-            const float *base = in + (size_t)(12 * a) * 32;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-              kk[a].v[m] = base[m * 32];
-              ev[a].c[m].re = base[(4 + m) * 32];
-              ev[a].c[m].im = base[(8 + m) * 32];
-            }
+            load_k(in + (size_t)InRows<L>::k(a) * 32, 32, kk[a]);
+            load_eps(in + (size_t)InRows<L>::eps(a) * 32, 32, ev[a]);
           }
-          const float *b0 = in + (size_t)(12 * L) * 32;
-#pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            e0v.c[m].re = b0[m * 32];
-            e0v.c[m].im = b0[(4 + m) * 32];
-          }
+          load_eps(in + (size_t)InRows<L>::eps0 * 32, 32, e0v);
           const Cx<float> amp = bg_amplitude<float, L>(kk, ev, e0v);
           const double re = amp.re, im = amp.im;
           const double *efac = (const double *)(st + W::off_efac), *wfac = (const double *)(st + W::off_wfac);
@@ -967,14 +977,12 @@ __global__ void __launch_bounds__(NB) bg_loop_kernel(ChunkParams C, ChunkBuf<dou
       BGLoop<double, L> bg;
 #pragma unroll 1
       for (int a = 0; a < L; ++a) {
-        const double *base = B.in + (size_t)(12 * a) * B.cap;
         const int X = BGLoop<double, L>::tri(a, a);
-#pragma unroll
-        for (int m = 0; m < 4; ++m) bg.K[X].v[m] = base[(size_t)m * B.cap + e];
-        load_cv(base + (size_t)4 * B.cap, B.cap, e, bg.J[X]);
+        load_k(B.in + (size_t)InRows<L>::k(a) * B.cap + e, (size_t)B.cap, bg.K[X]);
+        load_eps(B.in + (size_t)InRows<L>::eps(a) * B.cap + e, (size_t)B.cap, bg.J[X]);
       }
       CV4<double> e0;
-      load_cv(B.in + (size_t)(12 * L) * B.cap, B.cap, e, e0);
+      load_eps(B.in + (size_t)InRows<L>::eps0 * B.cap + e, (size_t)B.cap, e0);
       const Cx<double> amp = bg.run(e0);
       finish_event<NB, double>(C, B, e, amp.re * amp.re + amp.im * amp.im, A, w, bin);
     }
@@ -1124,17 +1132,17 @@ __global__ void __launch_bounds__(NB) bg_rows_kernel(ChunkParams C, ChunkBuf<flo
       CV4<float> eps0pos, e0;
 #pragma unroll
       for (int a = 0; a < L; ++a) {
-        const float *base = B.in + (size_t)(12 * a) * B.cap;
-        K4[a * NB + threadIdx.x] = make_float4(base[e], base[(size_t)B.cap + e], base[(size_t)2 * B.cap + e],
-                                               base[(size_t)3 * B.cap + e]);
+        const float *base = B.in + (size_t)InRows<L>::k(a) * B.cap + e;
+        K4[a * NB + threadIdx.x] =
+            make_float4(base[0], base[(size_t)B.cap], base[(size_t)2 * B.cap], base[(size_t)3 * B.cap]);
         CV4<float> ea;
-        load_cv(base + (size_t)4 * B.cap, B.cap, e, ea);
+        load_eps(B.in + (size_t)InRows<L>::eps(a) * B.cap + e, (size_t)B.cap, ea);
         if (a == 0)
           eps0pos = ea;
         else
           st_cv<NB>(J4, t1<L>(a, a), ea);
       }
-      load_cv(B.in + (size_t)(12 * L) * B.cap, B.cap, e, e0);
+      load_eps(B.in + (size_t)InRows<L>::eps0 * B.cap + e, (size_t)B.cap, e0);
       const Cx<float> amp = bg_rows<L, NB>(K4, eps0pos, e0, J4, S2);
       const double re = amp.re, im = amp.im;
       finish_event<NB, float>(C, B, e, re * re + im * im, A, w, bin);
