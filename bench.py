@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-multiplicity batched measurement")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
     ap.add_argument("--no-autotune", action="store_true", help="time the built-in default amplitude variant")
+    ap.add_argument("--variant", default="", help="FORM,SCHEDULE: use this amplitude variant and chunk schedule "
+                                                 "instead of autotuning (reproducible profiling)")
     return ap.parse_args()
 
 
@@ -167,7 +169,10 @@ def run_tess(args):
     proc = make_proc(tess, wl)
     run = tess.Run(ctx, proc, N, per_event=("weight", "me2", "pass"))
     variant = None
-    if not args.no_autotune and wl["hel"] == "sample":
+    if args.variant:
+        form, sched = (int(x) for x in args.variant.split(","))
+        tess.tess_select_variant(ctx, proc, form, sched)
+    elif not args.no_autotune and wl["hel"] == "sample":
         probe_acc = torch.zeros(tess.TESS_ACC_LEN, dtype=torch.float64, device="cuda")
         variant = tess.tess_autotune(ctx, proc, min(N, 1 << 22), probe_acc, run.workspace)
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB > L2
@@ -303,7 +308,7 @@ def run_tess(args):
         amp_ms_step = amp_ms / args.steps
         achieved = tess.bg_flops(n) * N / (amp_ms_step * 1e-3) / 1e12
         tot = sum(v[0] for v in stages.values()) or 1.0
-        traffic = read_traffic(args.workload)
+        traffic = read_traffic(args.workload, plan["variant"], min(N, plan_cap(tess, ctx, proc, N)))
         line = {
             "metric": f"events/s (gg->{n - 2}g, {n}-point, {'FP64' if wl['precision'] == 'fp64' else 'FP32 currents'})",
             "value": value,
@@ -431,14 +436,41 @@ def bench_gradients(torch, tess, ctx, steps):
     return {"value": E / (ms * 1e-3), "unit": "events/s (weight + all gradients)", "events": E, "ms": ms}
 
 
-def read_traffic(workload):
-    """DRAM bytes per launch of the event kernel from the committed ncu summary, if any."""
+def plan_cap(tess, ctx, proc, n_events):
+    """Events per amplitude launch (the chunk capacity) of a call with n_events."""
+    info = tess.tess_plan_info(ctx, proc, n_events)
+    return -(-n_events // max(info["chunks"], 1))
+
+
+def kernel_source_hash():
+    """sha256 over the CUDA sources of the library: a committed ncu figure is
+    used only while the kernels it was taken from are unchanged."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1002_3446_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def read_traffic(workload, variant, events_per_launch):
+    """DRAM bytes per launch of the amplitude kernel from the committed ncu
+    capture (profiles/traffic_<workload>.json), scaled to this launch size, or
+    None when there is none for this variant or the kernels changed since."""
     path = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
     try:
         with open(path) as f:
-            return json.load(f).get("dram_bytes_per_launch")
+            rec = json.load(f)
     except (OSError, ValueError):
         return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    entry = rec.get("by_variant", {}).get(str(variant))
+    if not entry:
+        return None
+    return entry["dram_bytes_per_launch"] * events_per_launch / entry["events_per_launch"]
 
 
 # ------------------------------------------------------------------ oracle (CPU) arm

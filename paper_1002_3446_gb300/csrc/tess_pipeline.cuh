@@ -692,8 +692,21 @@ __global__ void __launch_bounds__(kBlock) kin_ds_kernel(ChunkParams C, ChunkBuf<
 // ---------------------------------------------------------------------------
 template <int NB>
 struct Accum {
-  double sw = 0.0, sw2 = 0.0, npass = 0.0, nbad = 0.0;
+  double sw = 0.0, sw2 = 0.0;
+  int npass = 0, nbad = 0;
 };
+
+// |A|^2 as the epilogue's FP64 input.  FP32 amplitudes: squared in FP32 (one
+// rounding, far below the FP32 amplitude's own error) when that stays in the
+// normal range, else in FP64.
+__device__ __forceinline__ double amp2_of(const Cx<float> &a) {
+  const float s = fmaf(a.re, a.re, a.im * a.im);
+  if (s < 3.0e38f && s > 1.0e-30f) return (double)s;
+  const double re = a.re, im = a.im;
+  return re * re + im * im;
+}
+
+__device__ __forceinline__ double amp2_of(const Cx<double> &a) { return a.re * a.re + a.im * a.im; }
 
 // Event epilogue from the chunk factors of event e (chunk index): efac, wfac,
 // pass and the histogram value *hval (read only when histogramming).
@@ -706,14 +719,14 @@ __device__ __forceinline__ void finish_values(const ChunkParams &C, int e, doubl
   const double E = efac * amp2;
   double w = wfac * E;
   if (!isfinite(w)) {
-    A.nbad += 1.0;
+    A.nbad += 1;
     w = 0.0;
   }
   if (P.me2) P.me2[idx] = E;
   if (P.weight) P.weight[idx] = w;
   A.sw += w;
   A.sw2 += w * w;
-  A.npass += (double)ok;
+  A.npass += ok;
   w_out = w;
   bin_out = (P.hist_bins > 0 && ok) ? hist_bin(*hval, P.hist_lo, P.hist_inv_width, P.hist_bins) : -1;
 }
@@ -769,8 +782,8 @@ __device__ __forceinline__ void epi_flush(const EpiSmem<NB> &S, int nb2, Accum<N
   __shared__ double red[4][NB];
   red[0][threadIdx.x] = A.sw;
   red[1][threadIdx.x] = A.sw2;
-  red[2][threadIdx.x] = A.npass;
-  red[3][threadIdx.x] = A.nbad;
+  red[2][threadIdx.x] = (double)A.npass;
+  red[3][threadIdx.x] = (double)A.nbad;
   __syncthreads();
   for (int s = NB / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) {
@@ -811,8 +824,7 @@ __global__ void __launch_bounds__(NB, MINB) bg_reg_kernel(ChunkParams C, ChunkBu
       }
       load_eps(B.in + (size_t)InRows<L>::eps0 * B.cap + e, (size_t)B.cap, e0);
       const Cx<R> amp = bg_amplitude<R, L>(k, ev, e0);
-      const double re = amp.re, im = amp.im;
-      finish_event<NB, R>(C, B, e, re * re + im * im, A, w, bin);
+      finish_event<NB, R>(C, B, e, amp2_of(amp), A, w, bin);
     }
     epi_tile<NB>(S, nb2, w, bin);
   }
@@ -938,11 +950,10 @@ __global__ void __launch_bounds__(NB, 1) bg_reg_tma_kernel(ChunkParams C, ChunkB
           }
           load_eps(in + (size_t)InRows<L>::eps0 * 32, 32, e0v);
           const Cx<float> amp = bg_amplitude<float, L>(kk, ev, e0v);
-          const double re = amp.re, im = amp.im;
           const double *efac = (const double *)(st + W::off_efac), *wfac = (const double *)(st + W::off_wfac);
           const double *hval = (const double *)(st + W::off_hval);
           const uint8_t *pass = (const uint8_t *)(st + W::off_pass);
-          finish_values<NB>(C, e, efac[lane], wfac[lane], pass[lane], hval + lane, re * re + im * im, A, w, bin);
+          finish_values<NB>(C, e, efac[lane], wfac[lane], pass[lane], hval + lane, amp2_of(amp), A, w, bin);
         }
       }
     }
@@ -1144,8 +1155,7 @@ __global__ void __launch_bounds__(NB) bg_rows_kernel(ChunkParams C, ChunkBuf<flo
       }
       load_eps(B.in + (size_t)InRows<L>::eps0 * B.cap + e, (size_t)B.cap, e0);
       const Cx<float> amp = bg_rows<L, NB>(K4, eps0pos, e0, J4, S2);
-      const double re = amp.re, im = amp.im;
-      finish_event<NB, float>(C, B, e, re * re + im * im, A, w, bin);
+      finish_event<NB, float>(C, B, e, amp2_of(amp), A, w, bin);
     }
     epi_tile<NB>(S, nb2, w, bin);
   }
