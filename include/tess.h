@@ -176,22 +176,26 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
 
 /* ---- Amplitude-kernel autotuner ------------------------------------------------
  * Times every amplitude-kernel variant built for (precision, n) of proc on
- * probe_events sampled events (one warm-up, median of three timed runs, no
- * histogram) and makes the fastest the context's choice for later calls with
- * that (precision, n).  Choose probe_events to span several chunks (a few
- * million events) so that the overlapped schedules can show their gain.  Variants (all one thread per event):
- * TESS_K2_REG (current table in registers), TESS_K2_ROWS32 / TESS_K2_ROWS64
- * (current row in registers, older rows in shared memory, 32 / 64 threads per
- * block), TESS_K2_LOOP (FP64 loop form), TESS_K2_REG_HI (register form
- * compiled for more resident blocks) -- each under every chunk schedule
- * TESS_SCHED_* below.  acc_scratch: device, TESS_ACC_LEN doubles
- * (overwritten); workspace: tess_workspace_size(proc, probe_events) bytes --
- * that size already covers every variant and schedule.  *form_out receives
- * the chosen TESS_K2_* (-1 for the exact-sum mode, which has one kernel);
- * tess_plan_info reports the chosen schedule.  Per-event outputs do not
- * depend on the choice beyond FP32 summation order inside the amplitude
- * (identical in FP64); the accumulated sums can differ in the last bits,
- * since the amplitude grid sets their summation order.
+ * probe_events sampled events (one warm-up, median of three timed runs, with
+ * proc's histogram settings) and makes the fastest the context's choice for
+ * later calls with that (precision, n); the choice is keyed by (precision, n)
+ * only, so tune with the histogram settings the calls will use.  Choose
+ * probe_events to span several chunks (a few million events) so that the
+ * overlapped schedules can show their gain.  Variants (all one thread per
+ * event): TESS_K2_REG (current table in registers), TESS_K2_ROWS32 /
+ * TESS_K2_ROWS64 (current row in registers, older rows in shared memory, 32 /
+ * 64 threads per block), TESS_K2_LOOP (FP64 loop form), TESS_K2_REG_HI
+ * (register form compiled for more resident blocks), TESS_K2_REG_TMA (inputs
+ * staged in shared memory by bulk copies) -- each under every chunk schedule
+ * TESS_SCHED_* below.  acc_scratch: device, TESS_ACC_LEN doubles (not
+ * written: the timed runs stop before folding their sums); workspace:
+ * tess_workspace_size(proc, probe_events) bytes -- that size already covers
+ * every variant and schedule.  *form_out receives the chosen TESS_K2_* (-1
+ * for the exact-sum mode, which has one kernel); tess_plan_info reports the
+ * chosen schedule.  Per-event outputs do not depend on the choice beyond FP32
+ * summation order inside the amplitude (identical in FP64); the accumulated
+ * sums can differ in the last bits, since the amplitude grid sets their
+ * summation order.
  *
  * Chunk schedules (events are processed in chunks sized to stay in L2, each
  * by a kinematics kernel and an amplitude kernel):

@@ -55,6 +55,29 @@ __device__ __forceinline__ void comp_add(double &s, double &c, double x) {
   s = t;
 }
 
+// Adds the total of partial-row column q into the caller's running
+// accumulators (acc, hist), which carry their own compensation terms.
+__device__ __forceinline__ void fold_column(int q, double tot, int nb2, double *acc, double *hist) {
+  if (q == 0 || q == 1) {
+    double hs = acc[q], hc = acc[4 + q];
+    comp_add(hs, hc, tot);
+    acc[q] = hs;
+    acc[4 + q] = hc;
+  } else if (q == 2) {
+    acc[2] += tot;
+  } else if (q == 3) {
+    acc[6] += tot;
+  } else if (q == 4) {
+    acc[7] += tot;
+  } else {
+    const int h = q - kPartialHead;  // 0..2 nb2 - 1: w bins then w^2 bins
+    double hs = hist[h], hc = hist[2 * nb2 + h];
+    comp_add(hs, hc, tot);
+    hist[h] = hs;
+    hist[2 * nb2 + h] = hc;
+  }
+}
+
 // Folds the per-block partials, in block order with compensation, into the
 // caller's running accumulators (acc, hist), which carry their own
 // compensation terms between calls.
@@ -66,27 +89,43 @@ __global__ void finalize_kernel(const double *__restrict__ partials, int nblocks
   for (int q = threadIdx.x; q < nq; q += blockDim.x) {
     double s = 0.0, c = 0.0;
     for (int b = 0; b < nblocks; ++b) comp_add(s, c, partials[(size_t)b * stride + q]);
-    const double tot = s + c;
-    if (q == 0 || q == 1) {
-      double hs = acc[q], hc = acc[4 + q];
-      comp_add(hs, hc, tot);
-      acc[q] = hs;
-      acc[4 + q] = hc;
-    } else if (q == 2) {
-      acc[2] += tot;
-    } else if (q == 3) {
-      acc[6] += tot;
-    } else if (q == 4) {
-      acc[7] += tot;
-    } else {
-      const int h = q - kPartialHead;  // 0..2 nb2 - 1: w bins then w^2 bins
-      double hs = hist[h], hc = hist[2 * nb2 + h];
-      comp_add(hs, hc, tot);
-      hist[h] = hs;
-      hist[2 * nb2 + h] = hc;
-    }
+    fold_column(q, s + c, nb2, acc, hist);
   }
   if (threadIdx.x == 0) acc[3] += (double)n_events;
+}
+
+// The same fold with the work spread over the GPU: block q sums column q,
+// its kFinThreads threads each over the rows t, t + kFinThreads, ... with
+// compensation, then a fixed-shape compensated tree.  Deterministic (fixed
+// assignment and order); FP64 issue is 1/64 rate here, so a single thread
+// per column would spend ~64 cycles per row.
+constexpr int kFinThreads = 64;
+
+__global__ void __launch_bounds__(kFinThreads) finalize_cols_kernel(const double *__restrict__ partials, int nrows,
+                                                                    int hist_bins, uint64_t n_events, double *acc,
+                                                                    double *hist) {
+  const int stride = partial_stride(hist_bins);
+  const int nb2 = hist_bins > 0 ? hist_bins + 2 : 0;
+  const int q = blockIdx.x, t = threadIdx.x;
+  double s = 0.0, c = 0.0;
+  for (int r = t; r < nrows; r += kFinThreads) comp_add(s, c, partials[(size_t)r * stride + q]);
+  __shared__ double ss[kFinThreads], cc[kFinThreads];
+  ss[t] = s;
+  cc[t] = c;
+  __syncthreads();
+  for (int w = kFinThreads / 2; w > 0; w >>= 1) {
+    if (t < w) {
+      double a = ss[t], ac = cc[t];
+      comp_add(a, ac, ss[t + w]);
+      ss[t] = a;
+      cc[t] = ac + cc[t + w];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    fold_column(q, ss[0] + cc[0], nb2, acc, hist);
+    if (q == 0) acc[3] += (double)n_events;
+  }
 }
 
 }  // namespace tess
@@ -499,8 +538,9 @@ int prepare(tess_ctx *ctx, const tess_process *proc, uint64_t seed, uint64_t fir
   return TESS_OK;
 }
 
+// fold = false: leave the sums in the workspace's partial rows (timing runs).
 int launch_prepared(const Prepared &pr, cudaStream_t s, const tess::StageHook *hook = nullptr,
-                    const tess::OverlapRes *ov = nullptr) {
+                    const tess::OverlapRes *ov = nullptr, bool fold = true) {
   if (pr.P.n_events == 0) return TESS_OK;
   const int n = pr.proc->n_gluons;
   double *partials = (double *)pr.workspace;
@@ -515,8 +555,11 @@ int launch_prepared(const Prepared &pr, cudaStream_t s, const tess::StageHook *h
     if (e != cudaSuccess) return cuda_fail(e, "event kernel launch");
     if (hook) (*hook)(tess::STAGE_FUSED, false, s);
   }
+  if (!fold) return TESS_OK;
   if (hook) (*hook)(tess::STAGE_FINAL, true, s);
-  tess::finalize_kernel<<<1, 256, 0, s>>>(partials, pr.grid, pr.proc->hist_bins, pr.P.n_events, pr.acc, pr.hist);
+  tess::finalize_cols_kernel<<<tess::kPartialHead + 2 * (pr.proc->hist_bins > 0 ? pr.proc->hist_bins + 2 : 0),
+                                tess::kFinThreads, 0, s>>>(partials, pr.grid, pr.proc->hist_bins, pr.P.n_events, pr.acc,
+                                                           pr.hist);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "finalize kernel launch");
   if (hook) (*hook)(tess::STAGE_FINAL, false, s);
@@ -736,11 +779,15 @@ int tess_autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events
   }
   DeviceGuard g(ctx->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  // timed with the process's own histogram settings (the epilogue cost
+  // differs between variants); the runs stop before the final fold, so
+  // nothing is written through `out` beyond the per-event outputs, which are
+  // not requested
   tess_outputs out;
   memset(&out, 0, sizeof out);
   out.acc = acc_scratch;
-  tess_process pp = *proc;
-  pp.hist_bins = 0;  // time the amplitude path only
+  out.hist = acc_scratch;  // never written: no fold
+  const tess_process pp = *proc;
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t a = nullptr, b = nullptr;
   cudaError_t e;
@@ -764,11 +811,11 @@ int tess_autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events
       if ((rc = prepare(ctx, &pp, 1, 0, probe_events, &out, workspace, workspace_bytes, &pr))) break;
       tess::OverlapRes *ov = nullptr;
       if (pl.overlap && (rc = overlap_res(ctx, 0, &ov))) break;
-      if ((rc = launch_prepared(pr, s, nullptr, ov))) break;  // warm-up
+      if ((rc = launch_prepared(pr, s, nullptr, ov, false))) break;  // warm-up
       float t[kTuneReps];
       for (int r = 0; r < kTuneReps && !rc; ++r) {
         cudaEventRecord(a, s);
-        if ((rc = launch_prepared(pr, s, nullptr, ov))) break;
+        if ((rc = launch_prepared(pr, s, nullptr, ov, false))) break;
         cudaEventRecord(b, s);
         if ((e = cudaEventSynchronize(b)) != cudaSuccess) {
           rc = cuda_fail(e, "autotune timing");
