@@ -186,7 +186,8 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
  * TESS_K2_ROWS64 (current row in registers, older rows in shared memory, 32 /
  * 64 threads per block), TESS_K2_LOOP (FP64 loop form), TESS_K2_REG_HI
  * (register form compiled for more resident blocks), TESS_K2_REG_TMA (inputs
- * staged in shared memory by bulk copies) -- each under every chunk schedule
+ * staged in shared memory by bulk copies), TESS_K2_REG_TMA_HI (the same for
+ * more resident blocks) -- each under every chunk schedule
  * TESS_SCHED_* below.  acc_scratch: device, TESS_ACC_LEN doubles (not
  * written: the timed runs stop before folding their sums); workspace:
  * tess_workspace_size(proc, probe_events) bytes -- that size already covers
@@ -216,6 +217,7 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
 #define TESS_K2_REG_HI 4 /* register form compiled for 3-4 resident blocks per SM (FP32, n <= 7) */
 #define TESS_K2_REG_TMA 5 /* register form, tile inputs staged in shared memory by bulk copies one
                              tile ahead (FP32, n <= 8) */
+#define TESS_K2_REG_TMA_HI 6 /* the staged form compiled for 3 resident blocks per SM (FP32, n <= 7) */
 #define TESS_SCHED_SERIAL 0
 #define TESS_SCHED_OVERLAP 1
 #define TESS_SCHED_OVERLAP_TILES 2

@@ -68,7 +68,17 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 //              for n >= 6, 4 below: fewer registers, a few spilled) FP32, n <= 7
 //   K2_REG_TMA register form with the tile inputs staged in shared memory
 //              by bulk copies one tile ahead, 128 threads         FP32, n <= 8
-enum K2Form { K2_REG = 0, K2_ROWS32 = 1, K2_ROWS64 = 2, K2_LOOP = 3, K2_REG_HI = 4, K2_REG_TMA = 5, K2_NFORMS = 6 };
+//   K2_REG_TMA_HI  the staged form compiled for 3 resident blocks   FP32, n <= 7
+enum K2Form {
+  K2_REG = 0,
+  K2_ROWS32 = 1,
+  K2_ROWS64 = 2,
+  K2_LOOP = 3,
+  K2_REG_HI = 4,
+  K2_REG_TMA = 5,
+  K2_REG_TMA_HI = 6,
+  K2_NFORMS = 7
+};
 
 template <int N, typename R>
 constexpr bool k2_valid(int f) {
@@ -78,7 +88,8 @@ constexpr bool k2_valid(int f) {
     switch (f) {
       case K2_REG:
       case K2_REG_TMA: return N <= 8;
-      case K2_REG_HI: return N <= 7;
+      case K2_REG_HI:
+      case K2_REG_TMA_HI: return N <= 7;
       case K2_ROWS32:
       case K2_ROWS64: return N >= 6;
       default: return false;
@@ -101,6 +112,8 @@ struct K2V {
       return (void *)bg_rows_kernel<N, block>;
     else if constexpr (F == K2_REG_TMA)
       return (void *)bg_reg_tma_kernel<N, 128>;
+    else if constexpr (F == K2_REG_TMA_HI)
+      return (void *)bg_reg_tma_kernel<N, 128, 3>;
     else if constexpr (F == K2_REG)
       return (void *)bg_reg_kernel<N, float, 128>;
     else if constexpr (F == K2_REG_HI)
@@ -111,7 +124,7 @@ struct K2V {
   static size_t smem(int hist_bins) {
     if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
       return rows_smem_per_thread<L>() * block + EpiSmem<block>::bytes(hist_bins);
-    else if constexpr (F == K2_REG_TMA)
+    else if constexpr (F == K2_REG_TMA || F == K2_REG_TMA_HI)
       return RegStage<L, 128>::head + EpiSmem<128>::bytes(hist_bins);
     else
       return EpiSmem<128>::bytes(hist_bins);
@@ -122,6 +135,8 @@ struct K2V {
       bg_rows_kernel<N, block><<<grid, block, smem, s>>>(C, B, partials);
     else if constexpr (F == K2_REG_TMA)
       bg_reg_tma_kernel<N, 128><<<grid, 128, smem, s>>>(C, B, partials);
+    else if constexpr (F == K2_REG_TMA_HI)
+      bg_reg_tma_kernel<N, 128, 3><<<grid, 128, smem, s>>>(C, B, partials);
     else if constexpr (F == K2_REG)
       bg_reg_kernel<N, float, 128><<<grid, 128, smem, s>>>(C, B, partials);
     else if constexpr (F == K2_REG_HI)
@@ -140,6 +155,7 @@ auto with_form(int f, Fn &&fn) {
   } else {
     if constexpr (N <= 7) {
       if (f == K2_REG_HI) return fn(K2V<N, R, K2_REG_HI>{});
+      if (f == K2_REG_TMA_HI) return fn(K2V<N, R, K2_REG_TMA_HI>{});
     }
     if constexpr (N <= 8) {
       if (f == K2_REG) return fn(K2V<N, R, K2_REG>{});

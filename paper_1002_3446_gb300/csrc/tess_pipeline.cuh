@@ -886,8 +886,8 @@ __device__ __forceinline__ void issue_slice(const ChunkBuf<float> &B, size_t e0,
   }
 }
 
-template <int N, int NB>
-__global__ void __launch_bounds__(NB, 1) bg_reg_tma_kernel(ChunkParams C, ChunkBuf<float> B, double *partials) {
+template <int N, int NB, int MINB = 1>
+__global__ void __launch_bounds__(NB, MINB) bg_reg_tma_kernel(ChunkParams C, ChunkBuf<float> B, double *partials) {
   constexpr int L = N - 1;
   using W = WarpStage<L>;
   static_assert(NB == kBlock, "tiles must match the chunk-capacity granularity");

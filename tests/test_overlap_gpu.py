@@ -42,6 +42,7 @@ CASES = [
     (10, tess.TESS_FP32_DS, tess.TESS_K2_ROWS32, 300_001),
     (6, tess.TESS_FP32_DS, tess.TESS_K2_REG_TMA, 600_001),
     (8, tess.TESS_FP32_CURRENTS, tess.TESS_K2_REG_TMA, 400_003),
+    (7, tess.TESS_FP32_DS, tess.TESS_K2_REG_TMA_HI, 500_009),
 ]
 
 
@@ -88,19 +89,22 @@ def test_staged_form_matches_register_form(ctx, n):
     N = 300_007
     res = {}
     try:
-        for form in (tess.TESS_K2_REG, tess.TESS_K2_REG_TMA):
+        forms = (tess.TESS_K2_REG, tess.TESS_K2_REG_TMA) + ((tess.TESS_K2_REG_TMA_HI,) if n <= 7 else ())
+        for form in forms:
             tess.tess_select_variant(ctx, proc, form, tess.TESS_SCHED_SERIAL)
             run = tess.Run(ctx, proc, N)
             run.generate(9, 77)
             res[form] = (_host(run), run.result())
     finally:
         tess.tess_select_variant(ctx, proc)
-    a, b = res[tess.TESS_K2_REG_TMA], res[tess.TESS_K2_REG]
-    assert np.array_equal(a[0]["pass"], b[0]["pass"])
-    ok = b[0]["me2"] > 0
-    rel = np.abs(a[0]["me2"][ok] - b[0]["me2"][ok]) / b[0]["me2"][ok]
-    assert np.median(rel) < 1e-6 and np.quantile(rel, 0.99) < 1e-3
-    assert a[1][2:] == b[1][2:] and np.isclose(a[1][0], b[1][0], rtol=1e-4)
+    b = res[tess.TESS_K2_REG]
+    for form in forms[1:]:
+        a = res[form]
+        assert np.array_equal(a[0]["pass"], b[0]["pass"])
+        ok = b[0]["me2"] > 0
+        rel = np.abs(a[0]["me2"][ok] - b[0]["me2"][ok]) / b[0]["me2"][ok]
+        assert np.median(rel) < 1e-6 and np.quantile(rel, 0.99) < 1e-3
+        assert a[1][2:] == b[1][2:] and np.isclose(a[1][0], b[1][0], rtol=1e-4)
 
 
 def test_single_chunk_overlap_runs_serially(ctx):
