@@ -187,7 +187,9 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
  * 64 threads per block), TESS_K2_LOOP (FP64 loop form), TESS_K2_REG_HI
  * (register form compiled for more resident blocks), TESS_K2_REG_TMA (inputs
  * staged in shared memory by bulk copies), TESS_K2_REG_TMA_HI (the same for
- * more resident blocks) -- each under every chunk schedule
+ * more resident blocks), TESS_K2_PAIR32 / TESS_K2_PAIR64 (two threads per
+ * event sharing its current table in shared memory) -- each under every chunk
+ * schedule
  * TESS_SCHED_* below.  acc_scratch: device, TESS_ACC_LEN doubles (not
  * written: the timed runs stop before folding their sums); workspace:
  * tess_workspace_size(proc, probe_events) bytes -- that size already covers
@@ -218,6 +220,8 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
 #define TESS_K2_REG_TMA 5 /* register form, tile inputs staged in shared memory by bulk copies one
                              tile ahead (FP32, n <= 8) */
 #define TESS_K2_REG_TMA_HI 6 /* the staged form compiled for 3 resident blocks per SM (FP32, n <= 7) */
+#define TESS_K2_PAIR32 7     /* two threads per event, table in shared memory, 32 events per block (FP32) */
+#define TESS_K2_PAIR64 8     /* the same with 64 events per block (FP32) */
 #define TESS_SCHED_SERIAL 0
 #define TESS_SCHED_OVERLAP 1
 #define TESS_SCHED_OVERLAP_TILES 2

@@ -32,7 +32,7 @@ TESS_FP64, TESS_FP32_CURRENTS, TESS_FP32_DS = 0, 1, 2
 TESS_HEL_SUM, TESS_HEL_SAMPLE = 0, 1
 TESS_OBS_PTLEAD, TESS_OBS_HT, TESS_OBS_RMIN = 0, 1, 2
 TESS_K2_REG, TESS_K2_ROWS32, TESS_K2_ROWS64, TESS_K2_LOOP, TESS_K2_REG_HI, TESS_K2_REG_TMA = 0, 1, 2, 3, 4, 5
-TESS_K2_REG_TMA_HI = 6
+TESS_K2_REG_TMA_HI, TESS_K2_PAIR32, TESS_K2_PAIR64 = 6, 7, 8
 TESS_SCHED_SERIAL, TESS_SCHED_OVERLAP, TESS_SCHED_OVERLAP_TILES, TESS_SCHED_SERIAL_TILES = 0, 1, 2, 3
 
 # Every symbol include/tess.h declares (checked by the ABI tests).

@@ -280,7 +280,10 @@ int plan_with_form(const tess_ctx *ctx, const tess_process *p, uint64_t n_events
     rc = tess::plan_pipeline_f32b(n, ctx->sm_count, n_events, p->hist_bins, form, sched, pl);
   else
     rc = tess::plan_pipeline_f32c(n, ctx->sm_count, n_events, p->hist_bins, form, sched, pl);
-  if (rc) return fail(TESS_E_CUDA, "could not size the pipeline kernels (occupancy query failed)");
+  if (rc)
+    return fail(TESS_E_CUDA, "could not size the pipeline kernels (n %d, amplitude variant %d, schedule %d: %s)", n,
+                form, sched,
+                rc == tess::kPlanNoResidentBlock ? "no block fits on an SM" : cudaGetErrorString((cudaError_t)rc));
   return TESS_OK;
 }
 

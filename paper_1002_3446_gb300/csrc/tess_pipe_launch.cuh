@@ -3,6 +3,7 @@
 #pragma once
 #include <algorithm>
 
+#include "tess_pair.cuh"
 #include "tess_pipeline.cuh"
 
 namespace tess {
@@ -11,7 +12,7 @@ struct PipePlan {
   int form = 0;      // K2 variant (K2Form)
   int per_sm = 1;    // K2 blocks resident per SM
   int grid = 1;      // K2 blocks = partial rows
-  int block = 128;   // K2 threads per block (events per tile)
+  int block = 128;   // events per K2 tile (= threads per block except the lane-pair forms)
   size_t smem = 0;   // K2 dynamic shared memory
   int cap = 128;     // events per chunk
   int chunks = 1;
@@ -45,6 +46,25 @@ struct OverlapRes {
 
 constexpr size_t kChunkTargetBytes = 64ull << 20;  // stays resident in the 129 MB L2
 
+// plan_pipeline_t result: 0, a cudaError_t of a failed attribute / occupancy
+// call, or this code when no block of the variant fits on an SM
+constexpr int kPlanNoResidentBlock = -2;
+
+// Lets `fn` launch with up to the device's opt-in maximum of shared memory
+// per block (dynamic + static).  Always the same value for a kernel, so plans
+// of different sizes for one kernel (batched processes, histograms) never
+// lower each other's limit.
+inline cudaError_t allow_max_smem(const void *fn) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  return e;
+}
+
 // Optional host hook around each launch (stage timing); kinds below.
 enum StageKind { STAGE_KIN = 0, STAGE_AMP = 1, STAGE_FINAL = 2, STAGE_FUSED = 3, STAGE_NKINDS = 4 };
 struct StageHook {
@@ -69,6 +89,9 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 //   K2_REG_TMA register form with the tile inputs staged in shared memory
 //              by bulk copies one tile ahead, 128 threads         FP32, n <= 8
 //   K2_REG_TMA_HI  the staged form compiled for 3 resident blocks   FP32, n <= 7
+//   K2_PAIR32  two threads per event, table in shared memory, 32 events
+//              per block (64 threads)                            FP32, any n
+//   K2_PAIR64  the same with 64 events per block (128 threads)   FP32, any n
 enum K2Form {
   K2_REG = 0,
   K2_ROWS32 = 1,
@@ -77,7 +100,9 @@ enum K2Form {
   K2_REG_HI = 4,
   K2_REG_TMA = 5,
   K2_REG_TMA_HI = 6,
-  K2_NFORMS = 7
+  K2_PAIR32 = 7,
+  K2_PAIR64 = 8,
+  K2_NFORMS = 9
 };
 
 template <int N, typename R>
@@ -92,6 +117,8 @@ constexpr bool k2_valid(int f) {
       case K2_REG_TMA_HI: return N <= 7;
       case K2_ROWS32:
       case K2_ROWS64: return N >= 6;
+      case K2_PAIR32:
+      case K2_PAIR64: return true;
       default: return false;
     }
   }
@@ -105,10 +132,14 @@ constexpr int k2_default() {
 template <int N, typename R, int F>
 struct K2V {
   static constexpr int L = N - 1;
-  static constexpr int block = (F == K2_ROWS32) ? 32 : (F == K2_ROWS64 ? 64 : 128);
+  static constexpr int block = (F == K2_ROWS32 || F == K2_PAIR32) ? 32 : ((F == K2_ROWS64 || F == K2_PAIR64) ? 64 : 128);
+  static constexpr bool pair = F == K2_PAIR32 || F == K2_PAIR64;
+  static constexpr int threads = pair ? 2 * block : block;  // block = events per tile
   static constexpr int hi_blocks = N >= 6 ? 3 : 4;
   static void *fn() {
-    if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
+    if constexpr (pair)
+      return (void *)bg_pair_kernel<N, block>;
+    else if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
       return (void *)bg_rows_kernel<N, block>;
     else if constexpr (F == K2_REG_TMA)
       return (void *)bg_reg_tma_kernel<N, 128>;
@@ -122,7 +153,9 @@ struct K2V {
       return (void *)bg_loop_kernel<N, 128>;
   }
   static size_t smem(int hist_bins) {
-    if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
+    if constexpr (pair)
+      return PairSmem<L, block>::bytes + EpiSmem<threads>::bytes(hist_bins);
+    else if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
       return rows_smem_per_thread<L>() * block + EpiSmem<block>::bytes(hist_bins);
     else if constexpr (F == K2_REG_TMA || F == K2_REG_TMA_HI)
       return RegStage<L, 128>::head + EpiSmem<128>::bytes(hist_bins);
@@ -131,7 +164,9 @@ struct K2V {
   }
   static cudaError_t launch(const ChunkParams &C, const ChunkBuf<R> &B, double *partials, int grid, size_t smem,
                             cudaStream_t s) {
-    if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
+    if constexpr (pair)
+      bg_pair_kernel<N, block><<<grid, threads, smem, s>>>(C, B, partials);
+    else if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
       bg_rows_kernel<N, block><<<grid, block, smem, s>>>(C, B, partials);
     else if constexpr (F == K2_REG_TMA)
       bg_reg_tma_kernel<N, 128><<<grid, 128, smem, s>>>(C, B, partials);
@@ -153,6 +188,8 @@ auto with_form(int f, Fn &&fn) {
   if constexpr (sizeof(R) == 8) {
     return fn(K2V<N, R, K2_LOOP>{});
   } else {
+    if (f == K2_PAIR32) return fn(K2V<N, R, K2_PAIR32>{});
+    if (f == K2_PAIR64) return fn(K2V<N, R, K2_PAIR64>{});
     if constexpr (N <= 7) {
       if (f == K2_REG_HI) return fn(K2V<N, R, K2_REG_HI>{});
       if (f == K2_REG_TMA_HI) return fn(K2V<N, R, K2_REG_TMA_HI>{});
@@ -177,27 +214,23 @@ int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, in
   pl->form = form;
   const int rc = with_form<N, R>(form, [&](auto K) {
     using KV = decltype(K);
-    pl->block = KV::block;
+    pl->block = KV::block;  // events per tile
     pl->smem = KV::smem(hist_bins);
-    if (pl->smem > 48 * 1024 &&
-        cudaFuncSetAttribute(KV::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem) != cudaSuccess)
-      return -1;
+    cudaError_t e = allow_max_smem(KV::fn());
+    if (e != cudaSuccess) return (int)e;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, KV::fn(), KV::block, pl->smem) != cudaSuccess ||
-        per_sm < 1)
-      return -1;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, KV::fn(), KV::threads, pl->smem)) != cudaSuccess)
+      return (int)e;
+    if (per_sm < 1) return kPlanNoResidentBlock;
     pl->per_sm = per_sm;
     return 0;
   });
   if (rc) return rc;
   if constexpr (sizeof(R) == 4) {
     pl->kin_smem = kin_tile_bytes<N>();
-    if (pl->kin_smem > 48 * 1024 &&
-        (cudaFuncSetAttribute((void *)kin_ds_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)pl->kin_smem) != cudaSuccess ||
-         cudaFuncSetAttribute((void *)kin_kernel<N, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)pl->kin_smem) != cudaSuccess))
-      return -1;
+    cudaError_t e = allow_max_smem((const void *)kin_ds_kernel<N>);
+    if (e == cudaSuccess) e = allow_max_smem((const void *)kin_kernel<N, float>);
+    if (e != cudaSuccess) return (int)e;
   } else {
     pl->kin_smem = 0;
   }

@@ -43,6 +43,8 @@ CASES = [
     (6, tess.TESS_FP32_DS, tess.TESS_K2_REG_TMA, 600_001),
     (8, tess.TESS_FP32_CURRENTS, tess.TESS_K2_REG_TMA, 400_003),
     (7, tess.TESS_FP32_DS, tess.TESS_K2_REG_TMA_HI, 500_009),
+    (10, tess.TESS_FP32_DS, tess.TESS_K2_PAIR32, 300_007),
+    (6, tess.TESS_FP32_CURRENTS, tess.TESS_K2_PAIR64, 600_011),
 ]
 
 
@@ -148,7 +150,7 @@ def test_overlap_stage_timing_and_batched(ctx):
 
 def test_select_variant_rejects_out_of_range(ctx):
     proc = tess.process(6)
-    for form, ov in ((7, 0), (-2, 0), (0, 4), (0, -2)):
+    for form, ov in ((99, 0), (-2, 0), (0, 4), (0, -2)):
         with pytest.raises(tess.TessError) as e:
             tess.tess_select_variant(ctx, proc, form, ov)
         assert e.value.code == tess.TESS_E_INVALID

@@ -245,6 +245,35 @@ def test_sampled_events_fp32_currents(ctx, orc, n, precision):
     assert st["median"] < 1e-5 and st["p99"] < 5e-2 and st["weighted"] < 1e-4
 
 
+FORMS_BY_N = {
+    4: ["REG", "REG_HI", "REG_TMA", "REG_TMA_HI", "PAIR32", "PAIR64"],
+    6: ["REG", "REG_HI", "REG_TMA", "REG_TMA_HI", "ROWS32", "ROWS64", "PAIR32", "PAIR64"],
+    8: ["REG", "REG_TMA", "ROWS32", "ROWS64", "PAIR32", "PAIR64"],
+    10: ["ROWS32", "ROWS64", "PAIR32", "PAIR64"],
+    12: ["ROWS32", "ROWS64", "PAIR32", "PAIR64"],
+}
+
+
+@pytest.mark.parametrize("n,form", [(n, f) for n, fs in FORMS_BY_N.items() for f in fs])
+def test_every_amplitude_variant_against_oracle(ctx, orc, n, form):
+    """Each amplitude-kernel variant, forced (serial schedule), on sampled
+    events against the oracle with the FP32 criteria; 1000 events span
+    several tiles of every variant and end in a ragged one."""
+    p = tess.process(n, precision=tess.TESS_FP32_DS, pt_min=30.0 if n >= 10 else 20.0)
+    code = getattr(tess, "TESS_K2_" + form)
+    tess.tess_select_variant(ctx, p, code, tess.TESS_SCHED_SERIAL)
+    try:
+        assert tess.tess_plan_info(ctx, p, 1000)["variant"] == code
+        N = 1000
+        g = gpu_generate(ctx, p, 13, 5, N)
+    finally:
+        tess.tess_select_variant(ctx, p)
+    st = {}
+    compare_events(orc, p, g, 13, 5, np.arange(N), st)
+    print(f"{form} n={n}: median {st['median']:.2e} p99 {st['p99']:.2e} weighted {st['weighted']:.2e}")
+    assert st["median"] < 1e-5 and st["p99"] < 5e-2 and st["weighted"] < 1e-4
+
+
 # ---------------------------------------------------------------- full-size configurations
 @pytest.mark.slow
 def test_full_gg2g_2e20_fp64(ctx, orc):
@@ -275,12 +304,16 @@ def test_full_gg2g_2e20_fp64(ctx, orc):
                                               (10, 1 << 26, 30.0, tess.TESS_FP32_CURRENTS),
                                               (10, 1 << 26, 30.0, tess.TESS_FP32_DS)])
 def test_full_size_sampled_parity(ctx, orc, n, N, pt, precision):
-    """Full-size runs in the benchmark's launch configuration; 1024 sampled
-    events are recomputed one by one by the oracle; sigma is checked against
-    the sum of the per-event weights."""
+    """Full-size runs in the benchmark's launch configuration (the amplitude
+    variant and chunk schedule chosen by the autotuner on a 2^22-event probe,
+    as bench.py does); 1024 sampled events are recomputed one by one by the
+    oracle; sigma is checked against the sum of the per-event weights."""
     p = tess.process(n, precision=precision, pt_min=pt, hist_bins=40, hist_observable=tess.TESS_OBS_HT,
                      hist_lo=200.0, hist_hi=3000.0)
     run = tess.Run(ctx, p, N, per_event=("weight", "me2", "pass", "ht", "ptlead", "rmin"))
+    acc = torch.zeros(tess.TESS_ACC_LEN, dtype=torch.float64, device="cuda")
+    tess.tess_autotune(ctx, p, min(N, 1 << 22), acc, run.workspace)
+    print("variant/schedule", tess.tess_plan_info(ctx, p, N))
     run.generate(1, 0)
     torch.cuda.synchronize()
     rng = np.random.default_rng(n)
