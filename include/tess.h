@@ -83,13 +83,19 @@ typedef struct tess_process {
   double hist_lo, hist_hi; /* histogram range [lo, hi), uniform bins          */
 } tess_process;
 
-/* Per-call device outputs (caller-owned; NULL = not requested, except acc).
+/* Per-call outputs (caller-owned; NULL = not requested, except acc).
  * Per-event arrays have n_events entries, indexed by event - first_event.
  *   weight  event weight in pb (0 for events failing the cuts)
  *   me2     helicity/colour estimator E of sum |A|^2 in GeV^(8-2n) (before
  *           couplings, luminosity and phase space), computed for every event
  *   pass    1 if the event passes the cuts (events are flagged, not dropped)
  *   ht, ptlead, rmin   observables (H_T, leading-jet pT, min Delta R)
+ * In tess_generate and tess_generate_batched the per-event arrays may be
+ * device memory or pinned host memory mapped into the device's address
+ * space (cudaHostAlloc, cudaHostRegister): the kernels then store into host
+ * memory directly (NVLink-C2C on Grace-Blackwell), with no separate copy;
+ * other host memory is rejected with TESS_E_INVALID.  acc, hist and the
+ * workspace are always device memory.
  * acc  [TESS_ACC_LEN] doubles, ACCUMULATED into (zero it before the first
  *      call): {sum w, sum w^2, n_pass, n_generated, compensation of sum w,
  *      compensation of sum w^2, n_nonfinite, n_stalled}; n_stalled counts

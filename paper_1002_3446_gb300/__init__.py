@@ -368,15 +368,24 @@ class Run:
     """Device buffers (torch) for one call of tess_generate plus its
     accumulators; ``per_event`` selects which per-event arrays exist."""
 
-    def __init__(self, ctx, proc, n_events, device="cuda", per_event=("weight", "me2", "pass", "ht", "ptlead", "rmin")):
+    def __init__(self, ctx, proc, n_events, device="cuda", per_event=("weight", "me2", "pass", "ht", "ptlead", "rmin"),
+                 host_per_event=False):
+        """host_per_event: the per-event arrays are pinned host memory, which
+        the kernels write directly (no device-to-host copy afterwards)."""
         import torch
         self.ctx, self.proc, self.n_events = ctx, proc, int(n_events)
         dev = torch.device(device)
         f64 = dict(dtype=torch.float64, device=dev)
+
+        def per_event_array(dtype):
+            if host_per_event:
+                return torch.empty(self.n_events, dtype=dtype).pin_memory()
+            return torch.empty(self.n_events, dtype=dtype, device=dev)
+
         self.t = {}
         for name in ("weight", "me2", "ht", "ptlead", "rmin"):
-            self.t[name] = torch.empty(self.n_events, **f64) if name in per_event else None
-        self.t["pass"] = torch.empty(self.n_events, dtype=torch.uint8, device=dev) if "pass" in per_event else None
+            self.t[name] = per_event_array(torch.float64) if name in per_event else None
+        self.t["pass"] = per_event_array(torch.uint8) if "pass" in per_event else None
         self.acc = torch.zeros(TESS_ACC_LEN, **f64)
         self.hist = torch.zeros(4 * (proc.hist_bins + 2), **f64) if proc.hist_bins > 0 else None
         ws = tess_workspace_size(ctx, proc, self.n_events)

@@ -251,6 +251,27 @@ int check_device_ptr(const void *p, int device, const char *name) {
   return TESS_OK;
 }
 
+// A per-event output array: device memory, or pinned host memory mapped into
+// the device's address space (cudaHostAlloc / cudaHostRegister), which the
+// kernels then store into directly (over NVLink-C2C on Grace-Blackwell).
+// *dev receives the pointer the kernels use.
+int output_ptr(void *p, int device, const char *name, void **dev) {
+  *dev = p;
+  if (!p) return TESS_OK;
+  cudaPointerAttributes a;
+  const cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(TESS_E_INVALID, "%s: not a CUDA pointer (%s)", name, cudaGetErrorName(e));
+  }
+  if (a.type == cudaMemoryTypeHost) {
+    if (!a.devicePointer) return fail(TESS_E_INVALID, "%s: pinned host memory not mapped for the device", name);
+    *dev = a.devicePointer;
+    return TESS_OK;
+  }
+  return check_device_ptr(p, device, name);
+}
+
 int grid_for(const tess_ctx *ctx, const tess_process *p, uint64_t n_events) {
   const bool sum = p->helicity_mode == TESS_HEL_SUM;
   const uint64_t ne = n_events ? n_events : 1;
@@ -514,13 +535,26 @@ int prepare(tess_ctx *ctx, const tess_process *proc, uint64_t seed, uint64_t fir
   if (!out || !out->acc) return fail(TESS_E_INVALID, "outputs and outputs->acc must not be NULL");
   if (proc->hist_bins > 0 && !out->hist) return fail(TESS_E_INVALID, "hist_bins > 0 needs outputs->hist");
   if (n_events > (UINT64_MAX - first_event)) return fail(TESS_E_INVALID, "event range overflows 64 bits");
-  const void *ptrs[] = {out->weight, out->me2, out->pass, out->ht, out->ptlead, out->rmin, out->acc, out->hist,
-                        workspace};
-  const char *names[] = {"weight", "me2", "pass", "ht", "ptlead", "rmin", "acc", "hist", "workspace"};
-  for (int i = 0; i < 9; ++i)
+  const void *ptrs[] = {out->acc, out->hist, workspace};
+  const char *names[] = {"acc", "hist", "workspace"};
+  for (int i = 0; i < 3; ++i)
     if ((rc = check_device_ptr(ptrs[i], ctx->device, names[i]))) return rc;
   if (((uintptr_t)workspace) % 256 != 0) return fail(TESS_E_WORKSPACE, "workspace must be 256-byte aligned");
-  fill_params(proc, seed, first_event, n_events, out, &pr->P);
+  tess_outputs o = *out;  // per-event arrays as the kernels address them
+  void *dev = nullptr;
+  if ((rc = output_ptr(out->weight, ctx->device, "weight", &dev))) return rc;
+  o.weight = (double *)dev;
+  if ((rc = output_ptr(out->me2, ctx->device, "me2", &dev))) return rc;
+  o.me2 = (double *)dev;
+  if ((rc = output_ptr(out->pass, ctx->device, "pass", &dev))) return rc;
+  o.pass = (uint8_t *)dev;
+  if ((rc = output_ptr(out->ht, ctx->device, "ht", &dev))) return rc;
+  o.ht = (double *)dev;
+  if ((rc = output_ptr(out->ptlead, ctx->device, "ptlead", &dev))) return rc;
+  o.ptlead = (double *)dev;
+  if ((rc = output_ptr(out->rmin, ctx->device, "rmin", &dev))) return rc;
+  o.rmin = (double *)dev;
+  fill_params(proc, seed, first_event, n_events, &o, &pr->P);
   pr->proc = proc;
   pr->workspace = workspace;
   pr->acc = out->acc;

@@ -67,36 +67,62 @@ struct PairView {
 // Sum over the splits i = a + i0, a + i0 + di, ... of X = [a..b] of the
 // three-vertex brackets (with the -S terms of the reorganised four-vertex
 // sum), plus 2 x the triples whose left part ends at one of those i; s
-// receives the split sum of J_l.J_r over the same splits.
+// receives the split sum of J_l.J_r over the same splits.  Table entries are
+// reached through pointers advanced incrementally (the triangular index of
+// [a..i] grows by 1 with i, that of [i+1..b] by L - i - 2, ...), so the
+// loops carry no index arithmetic beyond a few adds.
 template <int L, int NEV>
 __device__ __forceinline__ void pair_sums(const PairView<NEV> &V, int a, int b, int i0, int di, CV4<float> &acc,
                                           Cx<float> &s) {
+  constexpr int JS = 2 * NEV;  // float4 stride between table entries of one event
   const RV4<float> Pa = V.P(a), Pb = V.P(b + 1);
   CV4<float> acc1 = cv_zero<float>(), acc2 = cv_zero<float>(), trs = cv_zero<float>();
   s = cx<float>(0.f, 0.f);
+  auto ldJ = [](const float4 *q) {
+    const float4 u = q[0], v = q[NEV];
+    CV4<float> r;
+    r.c[0] = cx<float>(u.x, u.y);
+    r.c[1] = cx<float>(u.z, u.w);
+    r.c[2] = cx<float>(v.x, v.y);
+    r.c[3] = cx<float>(v.z, v.w);
+    return r;
+  };
+  const float4 *Jg = V.J4 + V.g;
+  const float2 *Sg = V.S2 + V.g;
+  const float4 *Pg = V.P4 + V.g;
+  int i = a + i0;
+  int xl = pair_tri<L>(a, i), xr = pair_tri<L>(i + 1, b);
 #pragma unroll 1
-  for (int i = a + i0; i < b; i += di) {
-    const int l = pair_tri<L>(a, i), r = pair_tri<L>(i + 1, b);
-    const CV4<float> Jl = V.J(l), Jr = V.J(r);
-    const RV4<float> Pi = V.P(i + 1);
+  for (; i < b; i += di) {
+    const CV4<float> Jl = ldJ(Jg + xl * JS), Jr = ldJ(Jg + xr * JS);
+    const float4 p4 = Pg[(i + 1) * NEV];
+    const RV4<float> Pi = {{p4.x, p4.y, p4.z, p4.w}};
     const RV4<float> Kl = rsub(Pi, Pa), Kr = rsub(Pb, Pi);
     const Cx<float> d = mdot(Jl, Jr);
     const Cx<float> jlkr = mdot(Jl, Kr);
     const Cx<float> krjl = mdot(Jr, Kl);
-    const Cx<float> Sl = V.S(l), Sr = V.S(r);  // zero for single legs
-    const Cx<float> cr = cx<float>(fmaf(2.f, jlkr.re, -Sl.re), fmaf(2.f, jlkr.im, -Sl.im));
-    const Cx<float> cl = cx<float>(fmaf(-2.f, krjl.re, -Sr.re), fmaf(-2.f, krjl.im, -Sr.im));
+    const float2 sl = Sg[xl * NEV], sr = Sg[xr * NEV];  // zero for single legs
+    const Cx<float> cr = cx<float>(fmaf(2.f, jlkr.re, -sl.x), fmaf(2.f, jlkr.im, -sl.y));
+    const Cx<float> cl = cx<float>(fmaf(-2.f, krjl.re, -sr.x), fmaf(-2.f, krjl.im, -sr.y));
     axpy(acc1, cr, Jr);
     axpy(acc2, cl, Jl);
     axpy(acc1, d, rsub(Kl, Kr));
     s.re += d.re;
     s.im += d.im;
-    if (i + 1 < b) {
-      // triples (J[a..i] . J[c+1..b]) J[i+1..c], i < c < b
-      const CV4<float> &JA = Jl;
+    // triples (J[a..i] . J[c+1..b]) J[i+1..c], i < c < b: [c+1..b] starts at
+    // [i+2..b] (index xr + L - i - 2) and steps by L - c - 2; [i+1..c] starts
+    // at [i+1..i+1] (index xr - (b - i - 1)) and steps by 1
+    int xc = xr + (L - i - 2), xm = xr - (b - i - 1);
 #pragma unroll 1
-      for (int c = i + 1; c < b; ++c) axpy(trs, mdot(JA, V.J(pair_tri<L>(c + 1, b))), V.J(pair_tri<L>(i + 1, c)));
+    for (int c = i + 1; c < b; ++c) {
+      axpy(trs, mdot(Jl, ldJ(Jg + xc * JS)), ldJ(Jg + xm * JS));
+      xc += L - c - 2;
+      xm += 1;
     }
+    // next split: [a..i+di] is di entries on; [i+di+1..b] is sum_{t=1..di} (L - i - t - 1) on
+#pragma unroll 1
+    for (int t = 1; t <= di; ++t) xr += L - i - t - 1;
+    xl += di;
   }
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
