@@ -320,8 +320,8 @@ def run_tess(args):
             "scaling": "weak",
             "vs_baseline": None,
             "dtype": {"fp32": "f32 currents and cuts; f64 Rambo rescale, polarisations, accumulation",
-                      "ds": ("f32 currents and cuts; double-single (2 x f32) Rambo rescale and polarisation "
-                             "Gram products; f64 accumulation"),
+                      "ds": ("f32 currents, cuts and polarisation basis; double-float (2 x f32) Rambo boost and "
+                             "rescale; f64 weights and accumulation"),
                       "fp64": "f64"}[wl["precision"]],
             "data": "synthetic (counter-based Philox draws, toy gluon PDF)",
             "config": {"workload": f"{args.workload}: gg->{n - 2} gluons, {N} events per GPU, seed 1, sqrt(S)=14 TeV, "

@@ -51,10 +51,11 @@ extern "C" {
                                 and rescale, the polarisation Gram products and
                                 the accumulation in native FP64                   */
 #define TESS_FP32_DS 2       /* as TESS_FP32_CURRENTS, but the Rambo boost/rescale
-                                and the Gram products in double-single (two-float,
-                                ~47-bit) arithmetic on the FP32 pipe instead of
-                                native FP64, which runs at 1/64 of the FP32 rate
-                                on GB300; accumulation stays FP64               */
+                                in double-float (two-float, ~44-bit) arithmetic
+                                on the FP32 pipe instead of native FP64, which
+                                runs at 1/64 of the FP32 rate on GB300, and the
+                                polarisation basis in FP32 from the rounded
+                                momenta; weights and accumulation stay FP64     */
 /* helicity_mode */
 #define TESS_HEL_SUM 0    /* exact sum over 2^n helicities and (n-1)! orderings (n <= 5) */
 #define TESS_HEL_SAMPLE 1 /* one helicity configuration and colour ordering per event,
