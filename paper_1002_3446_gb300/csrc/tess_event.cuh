@@ -45,21 +45,21 @@ struct EventResult {
 // Polarisation vectors eps_+ and eps_- of the physical direction of p
 // (helicity form; e1 = theta-hat, e2 = phi-hat; beam-axis legs take phi = 0):
 // eps_+ = -(e1 + i e2)/sqrt2, eps_- = (e1 - i e2)/sqrt2.
-template <typename R>
-__device__ __forceinline__ void polarisations(double px, double py, double pz, CV4<R> &ep, CV4<R> &em) {
-  const double pt2 = px * px + py * py;
-  const double pt = sqrt(pt2);
-  const double inv_p = 1.0 / sqrt(pt2 + pz * pz);
-  const double ct = pz * inv_p, st = pt * inv_p;
-  double cf = 1.0, sf = 0.0;
-  if (pt > 0.0) {
-    const double inv_pt = 1.0 / pt;
+template <typename R, typename T = double>
+__device__ __forceinline__ void polarisations(T px, T py, T pz, CV4<R> &ep, CV4<R> &em) {
+  const T pt2 = px * px + py * py;
+  const T pt = sqrt(pt2);
+  const T inv_p = T(1) / sqrt(pt2 + pz * pz);
+  const T ct = pz * inv_p, st = pt * inv_p;
+  T cf = T(1), sf = T(0);
+  if (pt > T(0)) {
+    const T inv_pt = T(1) / pt;
     cf = px * inv_pt;
     sf = py * inv_pt;
   }
-  const double r = 0.70710678118654752440;
-  const double e1[4] = {0.0, ct * cf, ct * sf, -st};
-  const double e2[4] = {0.0, -sf, cf, 0.0};
+  const T r = T(0.70710678118654752440);
+  const T e1[4] = {T(0), ct * cf, ct * sf, -st};
+  const T e2[4] = {T(0), -sf, cf, T(0)};
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     ep.c[m] = cx<R>(R(-e1[m] * r), R(-e2[m] * r));

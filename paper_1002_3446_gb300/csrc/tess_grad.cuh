@@ -221,29 +221,30 @@ struct BGAdjoint {
 
 // Gradient of the polarisation vector of direction p (3-vector, FP64) with
 // respect to p: g_p += Re sum conj(d eps / d p) g_eps for eps = eps_{+/-}.
-__device__ __forceinline__ void polvec_adjoint(const double (&p)[3], bool minus, const double (&ge_re)[4],
-                                               const double (&ge_im)[4], double (&gp)[3]) {
-  const double px = p[0], py = p[1], pz = p[2];
-  const double pt2 = px * px + py * py;
-  const double pt = sqrt(pt2), r = sqrt(pt2 + pz * pz);
-  if (!(pt > 0.0)) return;  // beam axis: the basis is fixed by convention
-  const double ct = pz / r, cf = px / pt, sf = py / pt;
-  const double s2 = 0.70710678118654752440;
+template <typename T>
+__device__ __forceinline__ void polvec_adjoint(const T (&p)[3], bool minus, const T (&ge_re)[4], const T (&ge_im)[4],
+                                               T (&gp)[3]) {
+  const T px = p[0], py = p[1], pz = p[2];
+  const T pt2 = px * px + py * py;
+  const T pt = sqrt(pt2), r = sqrt(pt2 + pz * pz);
+  if (!(pt > T(0))) return;  // beam axis: the basis is fixed by convention
+  const T ct = pz / r, cf = px / pt, sf = py / pt;
+  const T s2 = T(0.70710678118654752440);
   // Re eps = sgn e1 / sqrt2, Im eps = -e2 / sqrt2 with sgn = -1 (eps_+) or +1 (eps_-)
-  const double sg = minus ? 1.0 : -1.0;
-  const double G1x = sg * s2 * ge_re[1], G1y = sg * s2 * ge_re[2], G1z = sg * s2 * ge_re[3];
-  const double G2x = -s2 * ge_im[1], G2y = -s2 * ge_im[2];
+  const T sg = minus ? T(1) : T(-1);
+  const T G1x = sg * s2 * ge_re[1], G1y = sg * s2 * ge_re[2], G1z = sg * s2 * ge_re[3];
+  const T G2x = -s2 * ge_im[1], G2y = -s2 * ge_im[2];
   // e1 = (ct cf, ct sf, -st), e2 = (-sf, cf, 0)
-  const double g_ct = G1x * cf + G1y * sf;
-  const double g_cf = G1x * ct + G2y;
-  const double g_sf = G1y * ct - G2x;
-  const double g_st = -G1z;
-  const double r3 = r * r * r, pt3 = pt2 * pt;
-  gp[0] += g_ct * (-pz * px / r3) + g_st * (px / (pt * r) - pt * px / r3) + g_cf * (1.0 / pt - px * px / pt3) +
+  const T g_ct = G1x * cf + G1y * sf;
+  const T g_cf = G1x * ct + G2y;
+  const T g_sf = G1y * ct - G2x;
+  const T g_st = -G1z;
+  const T r3 = r * r * r, pt3 = pt2 * pt;
+  gp[0] += g_ct * (-pz * px / r3) + g_st * (px / (pt * r) - pt * px / r3) + g_cf * (T(1) / pt - px * px / pt3) +
            g_sf * (-px * py / pt3);
   gp[1] += g_ct * (-pz * py / r3) + g_st * (py / (pt * r) - pt * py / r3) + g_cf * (-px * py / pt3) +
-           g_sf * (1.0 / pt - py * py / pt3);
-  gp[2] += g_ct * (1.0 / r - pz * pz / r3) + g_st * (-pt * pz / r3);
+           g_sf * (T(1) / pt - py * py / pt3);
+  gp[2] += g_ct * (T(1) / r - pz * pz / r3) + g_st * (-pt * pz / r3);
 }
 
 }  // namespace tess
@@ -258,18 +259,25 @@ __global__ void __launch_bounds__(kBlock) grad_kernel(GradParams G) {
   const EventParams &P = G.P;
   const double *u = G.u + e * NU;
 
-  // ---- forward: x, Rambo (keeping its intermediates), cuts, alpha_s
-  const double x1 = exp(u[0] * P.lnxmin), x2 = exp(u[1] * P.lnxmin);
+  // ---- forward: x, Rambo (keeping its intermediates), cuts, alpha_s.
+  // Precision split of the FP32-current forms (as the kinematics kernel):
+  // x, the Rambo seeds, cuts, observables, alpha_s, PDF and the polarisation
+  // basis (and its adjoint) in T = R; the boost/rescale, its adjoint and the
+  // weight scalings in FP64.  For R = double everything is FP64.
+  using T = R;
+  const T lnx = (T)P.lnxmin;
+  const T tx1 = exp((T)u[0] * lnx), tx2 = exp((T)u[1] * lnx);
+  const double x1 = tx1, x2 = tx2;
   const double shat = x1 * x2 * P.S, rs = sqrt(shat);
   double q[M][4], cth[M], sth[M], cph[M], sph[M], q0v[M];
   double Q0 = 0, Q1 = 0, Q2 = 0, Q3 = 0;
 #pragma unroll
   for (int i = 0; i < M; ++i) {
-    const double c = 2.0 * u[2 + 4 * i] - 1.0;
-    const double s = sqrt(1.0 - c * c);
-    double sn, cs;
-    sincospi(2.0 * u[2 + 4 * i + 1], &sn, &cs);
-    const double q0 = -log(u[2 + 4 * i + 2] * u[2 + 4 * i + 3]);
+    const T c = T(2) * (T)u[2 + 4 * i] - T(1);
+    const T s = sqrt(T(1) - c * c);
+    T sn, cs;
+    sincospi(T(2) * (T)u[2 + 4 * i + 1], &sn, &cs);
+    const T q0 = -log((T)u[2 + 4 * i + 2] * (T)u[2 + 4 * i + 3]);
     cth[i] = c; sth[i] = s; cph[i] = cs; sph[i] = sn; q0v[i] = q0;
     q[i][0] = q0; q[i][1] = q0 * s * cs; q[i][2] = q0 * s * sn; q[i][3] = q0 * c;
     Q0 += q[i][0]; Q1 += q[i][1]; Q2 += q[i][2]; Q3 += q[i][3];
@@ -290,26 +298,27 @@ __global__ void __launch_bounds__(kBlock) grad_kernel(GradParams G) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) kk[2 + i][1 + j] = xs * (q[i][1 + j] + bv[j] * fq[i]);
   }
-  const double y = 0.5 * log(x1 / x2);
+  const T y = T(0.5) * lnx * ((T)u[0] - (T)u[1]);  // 0.5 ln(x1 / x2)
   int pass = 1;
-  double ht = 0.0, eta[M];
+  T tht = T(0), eta[M];
 #pragma unroll
   for (int i = 0; i < M; ++i) {
-    const double px = kk[2 + i][1], py = kk[2 + i][2], pz = kk[2 + i][3];
-    const double pt = sqrt(px * px + py * py), pa = sqrt(px * px + py * py + pz * pz);
-    eta[i] = 0.5 * log((pa + pz) / (pa - pz)) + y;
-    ht += pt;
-    pass &= (pt > P.pt_min) & (fabs(eta[i]) < P.eta_max);
+    const T px = (T)kk[2 + i][1], py = (T)kk[2 + i][2], pz = (T)kk[2 + i][3];
+    const T pt = sqrt(px * px + py * py), pa = sqrt(px * px + py * py + pz * pz);
+    eta[i] = T(0.5) * log((pa + pz) / (pa - pz)) + y;
+    tht += pt;
+    pass &= (pt > (T)P.pt_min) & (fabs(eta[i]) < (T)P.eta_max);
   }
 #pragma unroll
   for (int i = 0; i < M; ++i)
 #pragma unroll
     for (int j = i + 1; j < M; ++j) {
-      const double pxi = kk[2 + i][1], pyi = kk[2 + i][2], pxj = kk[2 + j][1], pyj = kk[2 + j][2];
-      const double dphi = atan2(fabs(pxi * pyj - pyi * pxj), pxi * pxj + pyi * pyj);
-      const double de = eta[i] - eta[j];
-      pass &= (de * de + dphi * dphi > P.dr2_min);
+      const T pxi = (T)kk[2 + i][1], pyi = (T)kk[2 + i][2], pxj = (T)kk[2 + j][1], pyj = (T)kk[2 + j][2];
+      const T dphi = atan2(fabs(pxi * pyj - pyi * pxj), pxi * pxj + pyi * pyj);
+      const T de = eta[i] - eta[j];
+      pass &= (de * de + dphi * dphi > (T)P.dr2_min);
     }
+  const double ht = tht;
 
   // ---- amplitude forward + adjoint (momenta in an exact power-of-two unit)
   int perm[N];
@@ -324,8 +333,8 @@ __global__ void __launch_bounds__(kBlock) grad_kernel(GradParams G) {
   CV4<R> e0;
   {
     CV4<R> ep, em;
-    const double sg = legp[0] < 2 ? -1.0 : 1.0;
-    polarisations<R>(sg * kp[0][1], sg * kp[0][2], sg * kp[0][3], ep, em);
+    const T sg = legp[0] < 2 ? T(-1) : T(1);
+    polarisations<R, T>(sg * (T)kp[0][1], sg * (T)kp[0][2], sg * (T)kp[0][3], ep, em);
     e0 = ((hel >> legp[0]) & 1u) ? em : ep;
   }
 #pragma unroll
@@ -334,8 +343,8 @@ __global__ void __launch_bounds__(kBlock) grad_kernel(GradParams G) {
 #pragma unroll
     for (int m = 0; m < 4; ++m) bg.K[X].v[m] = R(kp[a + 1][m] * c);
     CV4<R> ep, em;
-    const double sg = legp[a + 1] < 2 ? -1.0 : 1.0;
-    polarisations<R>(sg * kp[a + 1][1], sg * kp[a + 1][2], sg * kp[a + 1][3], ep, em);
+    const T sg = legp[a + 1] < 2 ? T(-1) : T(1);
+    polarisations<R, T>(sg * (T)kp[a + 1][1], sg * (T)kp[a + 1][2], sg * (T)kp[a + 1][3], ep, em);
     bg.J[X] = ((hel >> legp[a + 1]) & 1u) ? em : ep;
   }
   bg.forward();
@@ -368,14 +377,14 @@ __global__ void __launch_bounds__(kBlock) grad_kernel(GradParams G) {
       ge = bg.GJ[X];
     }
     const double sg = leg < 2 ? -1.0 : 1.0;
-    const double pphys[3] = {sg * kp[a][1], sg * kp[a][2], sg * kp[a][3]};
-    double gre[4], gim[4], gp[3] = {0, 0, 0};
+    const T pphys[3] = {T(sg * kp[a][1]), T(sg * kp[a][2]), T(sg * kp[a][3])};
+    T gre[4], gim[4], gp[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      gre[m] = (double)ge.c[m].re;
-      gim[m] = (double)ge.c[m].im;
+      gre[m] = (T)ge.c[m].re;
+      gim[m] = (T)ge.c[m].im;
     }
-    polvec_adjoint(pphys, (hel >> leg) & 1u, gre, gim, gp);
+    polvec_adjoint<T>(pphys, (hel >> leg) & 1u, gre, gim, gp);
     // f depends on k' = c k through the K sums (g4) and on the direction of k
     // through eps (gp, scale-free)
     const double scale = ufac * c;
@@ -392,15 +401,16 @@ __global__ void __launch_bounds__(kBlock) grad_kernel(GradParams G) {
   // ---- weight, and its gradients
   double w = 0.0, gw_lnmu = 0.0, wfac = 0.0, dwfac_dht = 0.0, as = 0.0;
   if (pass) {
-    const double mu = P.mu_r_factor * ht;
-    as = P.alphas_mz / (1.0 + P.alphas_mz * P.b0 * (log(mu * mu) - P.ln_mz2));
+    const T mu = (T)P.mu_r_factor * tht;
+    as = (T)P.alphas_mz / (T(1) + (T)P.alphas_mz * (T)P.b0 * (log(mu * mu) - (T)P.ln_mz2));
     const double g2 = 4.0 * 3.14159265358979323846 * as;
     double gp_ = 1.0, sp = 1.0;
 #pragma unroll
     for (int i = 0; i < N - 2; ++i) gp_ *= g2;
 #pragma unroll
     for (int i = 0; i < M - 2; ++i) sp *= shat;
-    const double f1 = 1.7 * pow(x1, -0.2) * pow(1.0 - x1, 5.0), f2 = 1.7 * pow(x2, -0.2) * pow(1.0 - x2, 5.0);
+    const double f1 = T(1.7) * pow(tx1, T(-0.2)) * pow(T(1) - tx1, T(5)),
+                 f2 = T(1.7) * pow(tx2, T(-0.2)) * pow(T(1) - tx2, T(5));
     wfac = P.wconst * (P.lnxmin * P.lnxmin * f1 * f2) / (2.0 * shat) * (P.phiconst * sp) * gp_;
     w = wfac * E;
     // d ln alpha_s / d ln mu = -2 b0 alpha_s (one loop)
