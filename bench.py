@@ -445,13 +445,14 @@ def plan_cap(tess, ctx, proc, n_events):
 
 
 def kernel_source_hash():
-    """sha256 over the CUDA sources of the library: a committed ncu figure is
-    used only while the kernels it was taken from are unchanged."""
+    """sha256 over the sources of the pipeline kernels (every device header
+    and the pipeline instantiation units): a committed ncu figure is used
+    only while the kernels it was taken from are unchanged."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1002_3446_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
+        if name.endswith(".cuh") or (name.startswith("tess_pipe_") and name.endswith(".cu")):
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()

@@ -168,11 +168,12 @@ int tess_stage_times(tess_ctx *ctx, double *ms /* [4] */, int *launches /* [4] *
  * event counts -- in one call.  Process i generates events
  * [first_events[i], first_events[i] + n_events[i]) of stream seeds[i] into
  * outs[i] (accumulating into its acc/hist, as tess_generate).  The per-process
- * pipelines are recorded as parallel branches of one CUDA graph, captured on
- * internal streams the first time an argument set is seen and replayed on
- * `stream` after that, so a batch is a single graph launch whose branches
- * overlap on the GPU (the tail of one multiplicity is filled with work of
- * another).  Capture happens inside this call; do not call it while `stream`
+ * pipelines are recorded one after another as a single chain of one CUDA
+ * graph (each pipeline's chunks are sized to stay resident in L2, so
+ * concurrent branches would evict each other's chunk buffers), captured on an
+ * internal stream the first time an argument set is seen and replayed on
+ * `stream` after that, so a batch is a single graph launch with no launch
+ * gaps.  Capture happens inside this call; do not call it while `stream`
  * is being captured.  workspace: tess_workspace_size_batched() bytes (the
  * per-process workspaces back to back).  Errors as tess_generate. */
 int tess_workspace_size_batched(const tess_ctx *ctx, int n_proc, const tess_process *procs,

@@ -143,9 +143,7 @@ struct tess_ctx {
   tess::OverlapRes ovl[kMaxBranches + 1];
   // batched generation: capture streams, fork/join events, cached graph
   cudaStream_t cap_stream = nullptr;
-  cudaStream_t branch[kMaxBranches] = {};
   cudaEvent_t fork_ev = nullptr;
-  cudaEvent_t join_ev[kMaxBranches] = {};
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<unsigned char> graph_key;
   // opt-in stage timing: event pairs recorded around each launch
@@ -455,10 +453,6 @@ void tess_destroy(tess_ctx *ctx) {
   if (!ctx) return;
   DeviceGuard g(ctx->device);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
-  for (int i = 0; i < kMaxBranches; ++i) {
-    if (ctx->branch[i]) cudaStreamDestroy(ctx->branch[i]);
-    if (ctx->join_ev[i]) cudaEventDestroy(ctx->join_ev[i]);
-  }
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
   for (auto &o : ctx->ovl) {
@@ -717,24 +711,19 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
     for (int i = 0; i < n_proc; ++i) {
       tess::OverlapRes *ov = nullptr;
       if (prs[i].pipeline && prs[i].pl.overlap && (rc = overlap_res(ctx, 1 + i, &ov))) return rc;
-      if (!ctx->branch[i]) {
-        if ((e = cudaStreamCreateWithFlags(&ctx->branch[i], cudaStreamNonBlocking)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&ctx->join_ev[i], cudaEventDisableTiming)) != cudaSuccess)
-          return cuda_fail(e, "stream/event creation");
-      }
     }
-    // one branch per process, forked from and joined back into the capture stream
+    // the processes one after another in a single chain: each pipeline's
+    // chunks are sized to stay resident in L2, so concurrent branches would
+    // evict each other's chunk buffers (measured slower than sequential
+    // launches); the graph removes the launch gaps, and a process with an
+    // overlapped schedule keeps its own second stream inside the chain
     cudaGraph_t graph = nullptr;
     if ((e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
       return cuda_fail(e, "cudaStreamBeginCapture");
-    e = cudaEventRecord(ctx->fork_ev, ctx->cap_stream);
     int lrc = TESS_OK;
-    for (int i = 0; i < n_proc && e == cudaSuccess && lrc == TESS_OK; ++i) {
-      e = cudaStreamWaitEvent(ctx->branch[i], ctx->fork_ev, 0);
+    for (int i = 0; i < n_proc && lrc == TESS_OK; ++i) {
       const tess::OverlapRes *ov = (prs[i].pipeline && prs[i].pl.overlap) ? &ctx->ovl[1 + i] : nullptr;
-      if (e == cudaSuccess) lrc = launch_prepared(prs[i], ctx->branch[i], nullptr, ov);
-      if (e == cudaSuccess && lrc == TESS_OK) e = cudaEventRecord(ctx->join_ev[i], ctx->branch[i]);
-      if (e == cudaSuccess && lrc == TESS_OK) e = cudaStreamWaitEvent(ctx->cap_stream, ctx->join_ev[i], 0);
+      lrc = launch_prepared(prs[i], ctx->cap_stream, nullptr, ov);
     }
     const cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &graph);
     if (lrc != TESS_OK) {
