@@ -3,6 +3,7 @@
 // mbarrier, and a wall-clock-bounded wait on that barrier.
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace tess {
@@ -44,6 +45,18 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
           smem_addr(dst)),
       "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Tiled tensor copy (TMA) of the box at coordinates (x, y) of the 2-D tensor
+// described by `map` into this CTA's shared memory (128-byte aligned),
+// completing on `bar`.  x times the element size must be a multiple of 16
+// bytes.  `map` is a __grid_constant__ kernel parameter.
+__device__ __forceinline__ void tensor2d_g2s(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_addr(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
       : "memory");
 }
 

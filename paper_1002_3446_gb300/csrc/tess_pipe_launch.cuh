@@ -3,6 +3,8 @@
 #pragma once
 #include <algorithm>
 
+#include <cudaTypedefs.h>
+
 #include "tess_pair.cuh"
 #include "tess_pipeline.cuh"
 
@@ -76,6 +78,30 @@ struct StageHook {
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Tensor map of a chunk buffer's amplitude inputs for the staged forms: a
+// 2-D float tensor of `rows` rows of `cap` events (row stride cap * 4 bytes,
+// a multiple of 512), box {32 events, all rows}.  cuTensorMapEncodeTiled is
+// reached through the runtime's driver entry point (no driver library link).
+inline cudaError_t encode_rows_map(CUtensorMap *map, const float *base, int rows, int cap) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)cap, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cap * sizeof(float)};
+  const cuuint32_t box[2] = {32u, (cuuint32_t)rows};
+  const cuuint32_t elem[2] = {1u, 1u};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)base, dims, strides, box, elem,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
 
 // Amplitude-kernel (K2) variants.  All are one thread per event; they differ
 // in where the current table lives and in the block shape:
@@ -158,20 +184,22 @@ struct K2V {
     else if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
       return rows_smem_per_thread<L>() * block + EpiSmem<block>::bytes(hist_bins);
     else if constexpr (F == K2_REG_TMA || F == K2_REG_TMA_HI)
-      return RegStage<L, 128>::head + EpiSmem<128>::bytes(hist_bins);
+      return RegStage<L, 128>::window + EpiSmem<128>::bytes(hist_bins);
     else
       return EpiSmem<128>::bytes(hist_bins);
   }
+  static constexpr bool staged = F == K2_REG_TMA || F == K2_REG_TMA_HI;
+  // map: tensor map of B.in (staged forms only)
   static cudaError_t launch(const ChunkParams &C, const ChunkBuf<R> &B, double *partials, int grid, size_t smem,
-                            cudaStream_t s) {
+                            cudaStream_t s, const CUtensorMap *map) {
     if constexpr (pair)
       bg_pair_kernel<N, block><<<grid, threads, smem, s>>>(C, B, partials);
     else if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
       bg_rows_kernel<N, block><<<grid, block, smem, s>>>(C, B, partials);
     else if constexpr (F == K2_REG_TMA)
-      bg_reg_tma_kernel<N, 128><<<grid, 128, smem, s>>>(C, B, partials);
+      bg_reg_tma_kernel<N, 128><<<grid, 128, smem, s>>>(C, B, partials, *map);
     else if constexpr (F == K2_REG_TMA_HI)
-      bg_reg_tma_kernel<N, 128, 3><<<grid, 128, smem, s>>>(C, B, partials);
+      bg_reg_tma_kernel<N, 128, 3><<<grid, 128, smem, s>>>(C, B, partials, *map);
     else if constexpr (F == K2_REG)
       bg_reg_kernel<N, float, 128><<<grid, 128, smem, s>>>(C, B, partials);
     else if constexpr (F == K2_REG_HI)
@@ -284,6 +312,17 @@ cudaError_t run_pipeline_t(const EventParams &P, const PipePlan &pl, char *ws, c
   }
   ChunkParams C;
   C.P = P;
+  CUtensorMap maps[2];
+  const CUtensorMap *mp[2] = {nullptr, nullptr};
+  if constexpr (sizeof(R) == 4) {
+    const bool staged = with_form<N, R>(pl.form, [](auto K) { return decltype(K)::staged; });
+    if (staged) {
+      for (int b = 0; b < (pl.overlap ? 2 : 1); ++b) {
+        if ((e = encode_rows_map(&maps[b], BB[b].in, InRows<N - 1>::rows, pl.cap)) != cudaSuccess) return e;
+        mp[b] = &maps[b];
+      }
+    }
+  }
   if (pl.overlap && ov) {
     // K1 of chunk c+1 (caller's stream) runs while K2 of chunk c (aux stream)
     // does; buffer c % 2 is reused only after K2 of chunk c-2 is done.
@@ -310,7 +349,8 @@ cudaError_t run_pipeline_t(const EventParams &P, const PipePlan &pl, char *ws, c
       if ((e = cudaEventRecord(ov->k1done[b], s)) != cudaSuccess) return e;
       if ((e = cudaStreamWaitEvent(a, ov->k1done[b], 0)) != cudaSuccess) return e;
       if (hook) (*hook)(STAGE_AMP, true, a);
-      e = with_form<N, R>(pl.form, [&](auto K) { return decltype(K)::launch(C, BB[b], partials, pl.grid, pl.smem, a); });
+      e = with_form<N, R>(pl.form,
+                          [&](auto K) { return decltype(K)::launch(C, BB[b], partials, pl.grid, pl.smem, a, mp[b]); });
       if (e != cudaSuccess) return e;
       if (hook) (*hook)(STAGE_AMP, false, a);
       if ((e = cudaEventRecord(ov->k2done[b], a)) != cudaSuccess) return e;
@@ -334,7 +374,8 @@ cudaError_t run_pipeline_t(const EventParams &P, const PipePlan &pl, char *ws, c
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (hook) (*hook)(STAGE_KIN, false, s);
     if (hook) (*hook)(STAGE_AMP, true, s);
-    e = with_form<N, R>(pl.form, [&](auto K) { return decltype(K)::launch(C, B, partials, pl.grid, pl.smem, s); });
+    e = with_form<N, R>(pl.form,
+                        [&](auto K) { return decltype(K)::launch(C, B, partials, pl.grid, pl.smem, s, mp[0]); });
     if (e != cudaSuccess) return e;
     if (hook) (*hook)(STAGE_AMP, false, s);
   }

@@ -833,8 +833,9 @@ __global__ void __launch_bounds__(NB, MINB) bg_reg_kernel(ChunkParams C, ChunkBu
 
 // K2, staged register form (FP32, n <= 8): as bg_reg_kernel, with each
 // warp's inputs (its 32 events' slice of the InRows rows of the chunk
-// buffer and of the event factors) brought into shared memory by bulk copies
-// (the TMA unit's linear form) one tile ahead.  Every warp owns two stages and
+// buffer and of the event factors) brought into shared memory by the TMA unit
+// one tile ahead: one tiled tensor copy of the box {32 events, all rows} and
+// four bulk copies of the event factors.  Every warp owns two stages and
 // their mbarriers (which count the copied bytes) and runs its own pipeline:
 // it issues the copies of its slice of tile t + gridDim.x, then waits for
 // tile t, so the next inputs arrive while this tile is computed, and warps
@@ -858,40 +859,45 @@ template <int L, int NB>
 struct RegStage {
   static constexpr int warps = NB / 32;
   static constexpr size_t head = (size_t)warps * 2 * WarpStage<L>::bytes + 128;  // stages, then mbarriers
+  static constexpr size_t window = head + 128;  // + alignment slack for the 128-byte stage base
   static_assert(warps * 2 * sizeof(uint64_t) <= 128, "mbarrier area");
 };
 
-// Copies of the 32 events starting at chunk index e0 into stage `st`.  The
-// chunk buffers hold cap events, cap a multiple of 128, so a whole slice of
-// a tile is always in bounds; every segment starts on a 16-byte boundary (cap
-// * 4 and e0 * 4 are multiples of 128) and is a multiple of 16 bytes long.
+// Copies of the 32 events starting at chunk index e0 into stage `st`: one
+// tiled tensor copy (TMA) of the box {32 events, all input rows} of the chunk
+// buffer (map: 2-D tensor [rows][cap] floats) and four bulk copies of the
+// event factors.  The chunk buffers hold cap events, cap a multiple of 128,
+// so a whole slice of a tile is in bounds; e0 * 4 bytes and the factor
+// offsets are multiples of 128 bytes.
 template <int L>
-__device__ __forceinline__ void issue_slice(const ChunkBuf<float> &B, size_t e0, char *st, uint64_t *bar) {
+__device__ __forceinline__ void issue_slice(const ChunkBuf<float> &B, const CUtensorMap *map, size_t e0, char *st,
+                                            uint64_t *bar) {
   using W = WarpStage<L>;
   const int lane = threadIdx.x & 31;
   fence_proxy_async();  // this warp's earlier reads of the stage precede the copies
   if (lane == 0) mbar_arrive_expect_tx(bar, W::tx);
   __syncwarp();
-  for (int r = lane; r < W::rows + 4; r += 32) {
-    if (r < W::rows)
-      bulk_g2s(st + (size_t)r * 32 * sizeof(float), B.in + (size_t)r * B.cap + e0, 32 * sizeof(float), bar);
-    else if (r == W::rows)
-      bulk_g2s(st + W::off_efac, B.efac + e0, 32 * sizeof(double), bar);
-    else if (r == W::rows + 1)
-      bulk_g2s(st + W::off_wfac, B.wfac + e0, 32 * sizeof(double), bar);
-    else if (r == W::rows + 2)
-      bulk_g2s(st + W::off_hval, B.hval + e0, 32 * sizeof(double), bar);
-    else
-      bulk_g2s(st + W::off_pass, B.pass + e0, 32, bar);
-  }
+  if (lane == 0)
+    tensor2d_g2s(st, map, (int)e0, 0, bar);
+  else if (lane == 1)
+    bulk_g2s(st + W::off_efac, B.efac + e0, 32 * sizeof(double), bar);
+  else if (lane == 2)
+    bulk_g2s(st + W::off_wfac, B.wfac + e0, 32 * sizeof(double), bar);
+  else if (lane == 3)
+    bulk_g2s(st + W::off_hval, B.hval + e0, 32 * sizeof(double), bar);
+  else if (lane == 4)
+    bulk_g2s(st + W::off_pass, B.pass + e0, 32, bar);
 }
 
 template <int N, int NB, int MINB = 1>
-__global__ void __launch_bounds__(NB, MINB) bg_reg_tma_kernel(ChunkParams C, ChunkBuf<float> B, double *partials) {
+__global__ void __launch_bounds__(NB, MINB)
+    bg_reg_tma_kernel(ChunkParams C, ChunkBuf<float> B, double *partials, const __grid_constant__ CUtensorMap map) {
   constexpr int L = N - 1;
   using W = WarpStage<L>;
   static_assert(NB == kBlock, "tiles must match the chunk-capacity granularity");
-  extern __shared__ __align__(128) char smem_stage[];
+  extern __shared__ __align__(128) char smem_stage_raw[];
+  // tensor copies land on 128-byte boundaries (the window is padded by 128 B)
+  char *const smem_stage = (char *)(((uintptr_t)smem_stage_raw + 127) & ~(uintptr_t)127);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   char *const my0 = smem_stage + (size_t)warp * 2 * W::bytes, *const my1 = my0 + W::bytes;
   uint64_t *const bar = (uint64_t *)(smem_stage + (size_t)RegStage<L, NB>::warps * 2 * W::bytes) + 2 * warp;
@@ -912,7 +918,7 @@ __global__ void __launch_bounds__(NB, MINB) bg_reg_tma_kernel(ChunkParams C, Chu
   if ((int)blockIdx.x < ntiles) {
     const size_t e0 = (size_t)blockIdx.x * NB + warp * 32;
     if (e0 < (size_t)C.count) {
-      issue_slice<L>(B, e0, my0, &bar[0]);
+      issue_slice<L>(B, &map, e0, my0, &bar[0]);
       pending = 1u;
     }
   }
@@ -923,7 +929,7 @@ __global__ void __launch_bounds__(NB, MINB) bg_reg_tma_kernel(ChunkParams C, Chu
     if (!dead && next < ntiles) {  // the other stage was read by this warp in the previous iteration
       const size_t e0n = (size_t)next * NB + warp * 32;
       if (e0n < (size_t)C.count) {
-        issue_slice<L>(B, e0n, sb ? my0 : my1, &bar[sb ^ 1]);
+        issue_slice<L>(B, &map, e0n, sb ? my0 : my1, &bar[sb ^ 1]);
         pending |= 1u << (sb ^ 1);
       }
     }
