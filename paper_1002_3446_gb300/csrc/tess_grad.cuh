@@ -251,20 +251,29 @@ __device__ __forceinline__ void polvec_adjoint(const T (&p)[3], bool minus, cons
 
 namespace tess {
 
-template <int N, typename R>
-__global__ void __launch_bounds__(kBlock) grad_kernel(GradParams G) {
-  constexpr int M = N - 2, L = N - 1, NU = 2 + 4 * M;
-  const uint64_t e = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
-  if (e >= G.n_events) return;
-  const EventParams &P = G.P;
-  const double *u = G.u + e * NU;
+// Kinematics of one event for the gradient kernels, with every intermediate
+// the reverse sweep needs (T: the FP32-split type, see grad_kinematics).
+template <int N, typename T>
+struct GradKin {
+  static constexpr int M = N - 2;
+  T tx1, tx2, tht;
+  double x1, x2, shat, rs, ht, c, Q0, Q1, Q2, Q3, Mq, gam, aa, xs;
+  double q[M][4], cth[M], sth[M], cph[M], sph[M], q0v[M], bv[3], kk[N][4], bq[M], fq[M], kp[N][4];
+  int legp[N];
+  int pass;
+};
 
-  // ---- forward: x, Rambo (keeping its intermediates), cuts, alpha_s.
-  // Precision split of the FP32-current forms (as the kinematics kernel):
-  // x, the Rambo seeds, cuts, observables, alpha_s, PDF and the polarisation
-  // basis (and its adjoint) in T = R; the boost/rescale, its adjoint and the
-  // weight scalings in FP64.  For R = double everything is FP64.
-  using T = R;
+// Forward kinematics of one event from its uniforms u (x1, x2, Rambo 4m) and
+// colour order: x, Rambo (keeping its intermediates), cuts, observables, the
+// colour-ordered momenta and the exact power-of-two momentum unit c of the
+// amplitude.  Precision split of the FP32-current forms (as the kinematics
+// kernel): x, the Rambo seeds, cuts, observables, alpha_s, PDF and the
+// polarisation basis in T; the boost/rescale and the weight scalings in FP64
+// (T = double: everything FP64).
+template <int N, typename T>
+__device__ __forceinline__ void grad_kinematics(const EventParams &P, const double *u, const uint8_t *order,
+                                                GradKin<N, T> &K) {
+  constexpr int M = N - 2;
   const T lnx = (T)P.lnxmin;
   const T tx1 = exp((T)u[0] * lnx), tx2 = exp((T)u[1] * lnx);
   const double x1 = tx1, x2 = tx2;
@@ -283,8 +292,9 @@ __global__ void __launch_bounds__(kBlock) grad_kernel(GradParams G) {
     Q0 += q[i][0]; Q1 += q[i][1]; Q2 += q[i][2]; Q3 += q[i][3];
   }
   const double Mq = sqrt(Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3);
-  const double bv[3] = {-Q1 / Mq, -Q2 / Mq, -Q3 / Mq};
-  const double gam = Q0 / Mq, aa = 1.0 / (1.0 + gam), xs = rs / Mq;
+  const double iMq = 1.0 / Mq;
+  const double bv[3] = {-Q1 * iMq, -Q2 * iMq, -Q3 * iMq};
+  const double gam = Q0 * iMq, aa = 1.0 / (1.0 + gam), xs = rs * iMq;
   double kk[N][4];
   const double h = 0.5 * rs;
   kk[0][0] = -h; kk[0][1] = 0.0; kk[0][2] = 0.0; kk[0][3] = -h;
@@ -320,38 +330,118 @@ __global__ void __launch_bounds__(kBlock) grad_kernel(GradParams G) {
     }
   const double ht = tht;
 
-  // ---- amplitude forward + adjoint (momenta in an exact power-of-two unit)
+  // ---- colour order and the momentum unit of the amplitude (exact power of two)
   int perm[N];
 #pragma unroll
-  for (int i = 0; i < N; ++i) perm[i] = G.order[e * N + i];
-  const uint32_t hel = G.hel[e];
+  for (int i = 0; i < N; ++i) perm[i] = order[i];
   double kp[N][4];
   int legp[N];
   gather_positions<N>(kk, perm, kp, legp);
   const double c = pow2_unit_inv(rs);
-  BGAdjoint<R, L> bg;
-  CV4<R> e0;
-  {
-    CV4<R> ep, em;
-    const T sg = legp[0] < 2 ? T(-1) : T(1);
-    polarisations<R, T>(sg * (T)kp[0][1], sg * (T)kp[0][2], sg * (T)kp[0][3], ep, em);
-    e0 = ((hel >> legp[0]) & 1u) ? em : ep;
-  }
+  K.tx1 = tx1;
+  K.tx2 = tx2;
+  K.tht = tht;
+  K.x1 = x1;
+  K.x2 = x2;
+  K.shat = shat;
+  K.rs = rs;
+  K.ht = ht;
+  K.c = c;
+  K.Q0 = Q0;
+  K.Q1 = Q1;
+  K.Q2 = Q2;
+  K.Q3 = Q3;
+  K.Mq = Mq;
+  K.gam = gam;
+  K.aa = aa;
+  K.xs = xs;
+  K.pass = pass;
 #pragma unroll
-  for (int a = 0; a < L; ++a) {
-    const int X = BGAdjoint<R, L>::tri(a, a);
+  for (int i = 0; i < M; ++i)
 #pragma unroll
-    for (int m = 0; m < 4; ++m) bg.K[X].v[m] = R(kp[a + 1][m] * c);
-    CV4<R> ep, em;
-    const T sg = legp[a + 1] < 2 ? T(-1) : T(1);
-    polarisations<R, T>(sg * (T)kp[a + 1][1], sg * (T)kp[a + 1][2], sg * (T)kp[a + 1][3], ep, em);
-    bg.J[X] = ((hel >> legp[a + 1]) & 1u) ? em : ep;
-  }
-  bg.forward();
-  const Cx<R> mamp = mdot(e0, bg.num);
-  CV4<R> ge0;
-  bg.adjoint(e0, cx<R>(R(2) * mamp.re, R(2) * mamp.im), ge0);
-  const double f = (double)mamp.re * (double)mamp.re + (double)mamp.im * (double)mamp.im;
+    for (int m = 0; m < 4; ++m) K.q[i][m] = q[i][m];
+#pragma unroll
+  for (int i = 0; i < M; ++i) K.cth[i] = cth[i];
+#pragma unroll
+  for (int i = 0; i < M; ++i) K.sth[i] = sth[i];
+#pragma unroll
+  for (int i = 0; i < M; ++i) K.cph[i] = cph[i];
+#pragma unroll
+  for (int i = 0; i < M; ++i) K.sph[i] = sph[i];
+#pragma unroll
+  for (int i = 0; i < M; ++i) K.q0v[i] = q0v[i];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) K.bv[i] = bv[i];
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) K.kk[i][m] = kk[i][m];
+#pragma unroll
+  for (int i = 0; i < M; ++i) K.bq[i] = bq[i];
+#pragma unroll
+  for (int i = 0; i < M; ++i) K.fq[i] = fq[i];
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) K.kp[i][m] = kp[i][m];
+#pragma unroll
+  for (int i = 0; i < N; ++i) K.legp[i] = legp[i];
+}
+
+// Amplitude inputs of colour position a: the momentum in the unit c and the
+// polarisation vector of its helicity label (position 0: eps only is used).
+template <int N, typename R, typename T>
+__device__ __forceinline__ void grad_amp_input(const GradKin<N, T> &K, uint32_t hel, int a, RV4<R> &k, CV4<R> &eps) {
+  CV4<R> ep, em;
+  const T sg = K.legp[a] < 2 ? T(-1) : T(1);
+  polarisations<R, T>(sg * (T)K.kp[a][1], sg * (T)K.kp[a][2], sg * (T)K.kp[a][3], ep, em);
+  eps = ((hel >> K.legp[a]) & 1u) ? em : ep;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) k.v[m] = R(K.kp[a][m] * K.c);
+}
+
+// Weights and gradients of one event from its kinematics and the amplitude
+// stage's result: f = |m|^2 and, through get(a, g4, ge) for every colour
+// position a, df/dk of the position's momentum in the unit c (g4; zero for
+// position 0, whose momentum the amplitude does not take) and df/d eps (ge,
+// convention g(z) = df/dRe z + i df/dIm z).  Writes w, dw/du, dw/dk,
+// dw/dlnmu of event e.
+template <int N, typename R, typename T, typename Get>
+__device__ __forceinline__ void grad_outputs(const GradParams &G, uint64_t e, const GradKin<N, T> &K, uint32_t hel,
+                                             double f, Get get) {
+  constexpr int M = N - 2, L = N - 1, NU = 2 + 4 * M;
+  const EventParams &P = G.P;
+  const double *u = G.u + e * NU;
+  const T tx1 = K.tx1;
+  const T tx2 = K.tx2;
+  const T tht = K.tht;
+  const double x1 = K.x1;
+  const double x2 = K.x2;
+  const double shat = K.shat;
+  const double rs = K.rs;
+  const double ht = K.ht;
+  const double c = K.c;
+  const double Q0 = K.Q0;
+  const double Q1 = K.Q1;
+  const double Q2 = K.Q2;
+  const double Q3 = K.Q3;
+  const double Mq = K.Mq;
+  const double gam = K.gam;
+  const double aa = K.aa;
+  const double xs = K.xs;
+  const int pass = K.pass;
+  const double(&q)[M][4] = K.q;
+  const double(&cth)[M] = K.cth;
+  const double(&sth)[M] = K.sth;
+  const double(&cph)[M] = K.cph;
+  const double(&sph)[M] = K.sph;
+  const double(&q0v)[M] = K.q0v;
+  const double(&bv)[3] = K.bv;
+  const double(&kk)[N][4] = K.kk;
+  const double(&bq)[M] = K.bq;
+  const double(&fq)[M] = K.fq;
+  const double(&kp)[N][4] = K.kp;
+  const int(&legp)[N] = K.legp;
   double ufac = P.efac;  // E = efac c^(2(N-4)) f
 #pragma unroll
   for (int i = 0; i < N - 4; ++i) ufac *= c * c;
@@ -368,14 +458,7 @@ __global__ void __launch_bounds__(kBlock) grad_kernel(GradParams G) {
     const int leg = legp[a];
     double g4[4] = {0, 0, 0, 0};
     CV4<R> ge;
-    if (a == 0) {
-      ge = ge0;
-    } else {
-      const int X = BGAdjoint<R, L>::tri(a - 1, a - 1);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) g4[m] = (double)bg.GK[X].v[m];
-      ge = bg.GJ[X];
-    }
+    get(a, g4, ge);
     const double sg = leg < 2 ? -1.0 : 1.0;
     const T pphys[3] = {T(sg * kp[a][1]), T(sg * kp[a][2]), T(sg * kp[a][3])};
     T gre[4], gim[4], gp[3] = {T(0), T(0), T(0)};
@@ -428,8 +511,9 @@ __global__ void __launch_bounds__(kBlock) grad_kernel(GradParams G) {
     for (int m = 0; m < 4; ++m) gt[i][m] = pass ? wfac * gk[i][m] : 0.0;
     if (pass && i >= 2) {
       const double px = kk[i][1], py = kk[i][2], pt = sqrt(px * px + py * py);
-      gt[i][1] += E * dwfac_dht * px / pt;
-      gt[i][2] += E * dwfac_dht * py / pt;
+      const double ept = E * dwfac_dht * (double)(T(1) / (T)pt);  // reciprocal in T
+      gt[i][1] += ept * px;
+      gt[i][2] += ept * py;
     }
   }
   if (G.dw_dk)
@@ -477,18 +561,19 @@ __global__ void __launch_bounds__(kBlock) grad_kernel(GradParams G) {
     }
   }
   ggam += gaa * (-aa * aa);
-  gM += gx * (-xs / Mq);
-  gQ[0] += ggam / Mq;
-  gM += ggam * (-gam / Mq);
+  const double iMq = 1.0 / Mq;
+  gM += gx * (-xs * iMq);
+  gQ[0] += ggam * iMq;
+  gM += ggam * (-gam * iMq);
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    gQ[1 + j] += -gb[j] / Mq;
-    gM += gb[j] * (-bv[j] / Mq);
+    gQ[1 + j] += -gb[j] * iMq;
+    gM += gb[j] * (-bv[j] * iMq);
   }
-  gQ[0] += gM * Q0 / Mq;
-  gQ[1] += gM * (-Q1 / Mq);
-  gQ[2] += gM * (-Q2 / Mq);
-  gQ[3] += gM * (-Q3 / Mq);
+  gQ[0] += gM * Q0 * iMq;
+  gQ[1] += gM * (-Q1 * iMq);
+  gQ[2] += gM * (-Q2 * iMq);
+  gQ[3] += gM * (-Q3 * iMq);
 #pragma unroll
   for (int i = 0; i < M; ++i) {
 #pragma unroll
@@ -496,13 +581,49 @@ __global__ void __launch_bounds__(kBlock) grad_kernel(GradParams G) {
     const double q0 = q0v[i], s = sth[i], cc = cth[i], cs = cph[i], sn = sph[i];
     const double gq0 = gq[i][0] + gq[i][1] * s * cs + gq[i][2] * s * sn + gq[i][3] * cc;
     const double gs = gq[i][1] * q0 * cs + gq[i][2] * q0 * sn;
-    const double gc = gq[i][3] * q0 + gs * (-cc / s);
+    const double gc = gq[i][3] * q0 + gs * (-cc * (double)(T(1) / (T)s));
     const double gphi = gq[i][1] * (-q0 * s * sn) + gq[i][2] * (q0 * s * cs);
     gu[2 + 4 * i + 0] = up * 2.0 * gc;
     gu[2 + 4 * i + 1] = up * 2.0 * 3.14159265358979323846 * gphi;
-    gu[2 + 4 * i + 2] = up * (-gq0 / u[2 + 4 * i + 2]);
-    gu[2 + 4 * i + 3] = up * (-gq0 / u[2 + 4 * i + 3]);
+    gu[2 + 4 * i + 2] = up * (-gq0 * (double)(T(1) / (T)u[2 + 4 * i + 2]));
+    gu[2 + 4 * i + 3] = up * (-gq0 * (double)(T(1) / (T)u[2 + 4 * i + 3]));
   }
+}
+
+template <int N, typename R>
+__global__ void __launch_bounds__(kBlock) grad_kernel(GradParams G) {
+  constexpr int M = N - 2, L = N - 1, NU = 2 + 4 * M;
+  const uint64_t e = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (e >= G.n_events) return;
+  GradKin<N, R> K;
+  grad_kinematics<N, R>(G.P, G.u + e * NU, G.order + e * N, K);
+  const uint32_t hel = G.hel[e];
+  BGAdjoint<R, L> bg;
+  CV4<R> e0;
+  {
+    RV4<R> k0;
+    grad_amp_input<N, R, R>(K, hel, 0, k0, e0);
+  }
+#pragma unroll
+  for (int a = 0; a < L; ++a) {
+    const int X = BGAdjoint<R, L>::tri(a, a);
+    grad_amp_input<N, R, R>(K, hel, a + 1, bg.K[X], bg.J[X]);
+  }
+  bg.forward();
+  const Cx<R> mamp = mdot(e0, bg.num);
+  CV4<R> ge0;
+  bg.adjoint(e0, cx<R>(R(2) * mamp.re, R(2) * mamp.im), ge0);
+  const double f = (double)mamp.re * (double)mamp.re + (double)mamp.im * (double)mamp.im;
+  grad_outputs<N, R, R>(G, e, K, hel, f, [&](int a, double(&g4)[4], CV4<R> &ge) {
+    if (a == 0) {
+      ge = ge0;
+    } else {
+      const int X = BGAdjoint<R, L>::tri(a - 1, a - 1);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) g4[m] = (double)bg.GK[X].v[m];
+      ge = bg.GJ[X];
+    }
+  });
 }
 
 // The generator's own draws for events [first, first + n): the x and Rambo

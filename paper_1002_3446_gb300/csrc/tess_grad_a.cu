@@ -1,41 +1,15 @@
 // Instantiations of the gradient and draws kernels, n = 4..8.
-#include "tess_grad.cuh"
+#include "tess_grad_pair.cuh"
 
 namespace tess {
 
 cudaError_t launch_grad_a(int n, bool fp64, const GradParams &G, cudaStream_t s) {
-  const unsigned blocks = (unsigned)((G.n_events + kBlock - 1) / kBlock);
   switch (n) {
-    case 4:
-      if (fp64)
-        grad_kernel<4, double><<<blocks, kBlock, 0, s>>>(G);
-      else
-        grad_kernel<4, float><<<blocks, kBlock, 0, s>>>(G);
-      return cudaGetLastError();
-    case 5:
-      if (fp64)
-        grad_kernel<5, double><<<blocks, kBlock, 0, s>>>(G);
-      else
-        grad_kernel<5, float><<<blocks, kBlock, 0, s>>>(G);
-      return cudaGetLastError();
-    case 6:
-      if (fp64)
-        grad_kernel<6, double><<<blocks, kBlock, 0, s>>>(G);
-      else
-        grad_kernel<6, float><<<blocks, kBlock, 0, s>>>(G);
-      return cudaGetLastError();
-    case 7:
-      if (fp64)
-        grad_kernel<7, double><<<blocks, kBlock, 0, s>>>(G);
-      else
-        grad_kernel<7, float><<<blocks, kBlock, 0, s>>>(G);
-      return cudaGetLastError();
-    case 8:
-      if (fp64)
-        grad_kernel<8, double><<<blocks, kBlock, 0, s>>>(G);
-      else
-        grad_kernel<8, float><<<blocks, kBlock, 0, s>>>(G);
-      return cudaGetLastError();
+    case 4: return launch_grad_n<4>(fp64, G, s);
+    case 5: return launch_grad_n<5>(fp64, G, s);
+    case 6: return launch_grad_n<6>(fp64, G, s);
+    case 7: return launch_grad_n<7>(fp64, G, s);
+    case 8: return launch_grad_n<8>(fp64, G, s);
     default: return cudaErrorInvalidValue;
   }
 }

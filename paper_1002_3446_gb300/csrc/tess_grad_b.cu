@@ -1,23 +1,12 @@
 // Instantiations of the gradient and draws kernels, n = 9..10.
-#include "tess_grad.cuh"
+#include "tess_grad_pair.cuh"
 
 namespace tess {
 
 cudaError_t launch_grad_b(int n, bool fp64, const GradParams &G, cudaStream_t s) {
-  const unsigned blocks = (unsigned)((G.n_events + kBlock - 1) / kBlock);
   switch (n) {
-    case 9:
-      if (fp64)
-        grad_kernel<9, double><<<blocks, kBlock, 0, s>>>(G);
-      else
-        grad_kernel<9, float><<<blocks, kBlock, 0, s>>>(G);
-      return cudaGetLastError();
-    case 10:
-      if (fp64)
-        grad_kernel<10, double><<<blocks, kBlock, 0, s>>>(G);
-      else
-        grad_kernel<10, float><<<blocks, kBlock, 0, s>>>(G);
-      return cudaGetLastError();
+    case 9: return launch_grad_n<9>(fp64, G, s);
+    case 10: return launch_grad_n<10>(fp64, G, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1,23 +1,12 @@
 // Instantiations of the gradient and draws kernels, n = 11..12.
-#include "tess_grad.cuh"
+#include "tess_grad_pair.cuh"
 
 namespace tess {
 
 cudaError_t launch_grad_c(int n, bool fp64, const GradParams &G, cudaStream_t s) {
-  const unsigned blocks = (unsigned)((G.n_events + kBlock - 1) / kBlock);
   switch (n) {
-    case 11:
-      if (fp64)
-        grad_kernel<11, double><<<blocks, kBlock, 0, s>>>(G);
-      else
-        grad_kernel<11, float><<<blocks, kBlock, 0, s>>>(G);
-      return cudaGetLastError();
-    case 12:
-      if (fp64)
-        grad_kernel<12, double><<<blocks, kBlock, 0, s>>>(G);
-      else
-        grad_kernel<12, float><<<blocks, kBlock, 0, s>>>(G);
-      return cudaGetLastError();
+    case 11: return launch_grad_n<11>(fp64, G, s);
+    case 12: return launch_grad_n<12>(fp64, G, s);
     default: return cudaErrorInvalidValue;
   }
 }

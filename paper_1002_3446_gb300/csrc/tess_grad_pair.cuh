@@ -1,0 +1,392 @@
+// Event weights and gradients, FP32 current forms: two threads per event
+// sharing the event's Berends-Giele table in shared memory (the lane-pair
+// layout of tess_pair.cuh), with the reverse sweep in pull form.
+//
+// The reverse sweep of the recursion (Sec. 3) is usually written in push
+// form: each set X, in decreasing length, adds its contributions into the
+// gradient accumulators of its parts (left, right, and the three parts of
+// every four-vertex triple).  Two lanes sharing an event would then write the
+// same accumulators.  Here every set Y instead gathers its own gradient from
+// all of its parents X (longer sets, already final): as the left part of X =
+// [c..b], as the right part of X = [a..d], as the first or last part of a
+// triple of those X, and as the middle part of a triple of X = [a..b] with
+// a < c, d < b.  Every term is the same as in the push form; only who adds it
+// changes, so the lanes split the sets of one length (lane j: sets starting
+// at c = j, j + 2, ...) with no shared accumulator, one barrier per length.
+// Momentum gradients go through the prefix sums P (K[c..d] = P[d+1] - P[c]):
+// each set adds its K-gradient to P[d+1] and subtracts it from P[c] in the
+// lane's own prefix-gradient row; the rows are added in a fixed order at the
+// end.  Kinematics, polarisations and the output stage are those of the
+// thread-per-event kernel (grad_kinematics, grad_amp_input, grad_outputs),
+// run by lane 0; the kinematics are recomputed after the sweep instead of
+// being kept live across it.
+#pragma once
+#include "tess_grad.cuh"
+#include "tess_pair.cuh"
+
+namespace tess {
+
+template <int L, int NEV>
+struct GradPairSmem {
+  static constexpr int T = L * (L + 1) / 2;
+  static constexpr size_t j_off = 0;                                               // float4 [2 T][NEV] currents
+  static constexpr size_t g_off = j_off + (size_t)2 * T * NEV * sizeof(float4);    // float4 [2 T][NEV] adjoints
+  static constexpr size_t p_off = g_off + (size_t)2 * T * NEV * sizeof(float4);    // float4 [L + 1][NEV]
+  static constexpr size_t gp_off = p_off + (size_t)(L + 1) * NEV * sizeof(float4);  // float4 [2][L + 1][NEV]
+  static constexpr size_t e_off = gp_off + (size_t)2 * (L + 1) * NEV * sizeof(float4);  // float4 [2][NEV]
+  static constexpr size_t s_off = e_off + (size_t)2 * NEV * sizeof(float4);        // float2 [T][NEV]
+  static constexpr size_t gs_off = s_off + (size_t)T * NEV * sizeof(float2);       // float2 [T][NEV]
+  static constexpr size_t bytes = gs_off + (size_t)T * NEV * sizeof(float2);
+};
+
+template <int NEV>
+__device__ __forceinline__ CV4<float> ld_cv4(const float4 *base, int X, int g) {
+  const float4 u = base[(2 * X) * NEV + g], v = base[(2 * X + 1) * NEV + g];
+  CV4<float> r;
+  r.c[0] = cx<float>(u.x, u.y);
+  r.c[1] = cx<float>(u.z, u.w);
+  r.c[2] = cx<float>(v.x, v.y);
+  r.c[3] = cx<float>(v.z, v.w);
+  return r;
+}
+
+template <int NEV>
+__device__ __forceinline__ void st_cv4(float4 *base, int X, int g, const CV4<float> &r) {
+  base[(2 * X) * NEV + g] = make_float4(r.c[0].re, r.c[0].im, r.c[1].re, r.c[1].im);
+  base[(2 * X + 1) * NEV + g] = make_float4(r.c[2].re, r.c[2].im, r.c[3].re, r.c[3].im);
+}
+
+__device__ __forceinline__ RV4<float> rv4(const float4 p) {
+  RV4<float> r = {{p.x, p.y, p.z, p.w}};
+  return r;
+}
+
+// Minkowski metric sign of component m
+__device__ __forceinline__ float eta_of(int m) { return m == 0 ? 1.f : -1.f; }
+
+// sum_m conj(v^m) G^m
+__device__ __forceinline__ Cx<float> conj_dot4(const CV4<float> &v, const CV4<float> &G) {
+  float re = 0.f, im = 0.f;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    re = fmaf(v.c[m].re, G.c[m].re, fmaf(v.c[m].im, G.c[m].im, re));
+    im = fmaf(v.c[m].re, G.c[m].im, fmaf(-v.c[m].im, G.c[m].re, im));
+  }
+  return cx<float>(re, im);
+}
+
+// g += conj(z) G
+__device__ __forceinline__ void add_conj(CV4<float> &g, const Cx<float> &z, const CV4<float> &G) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    g.c[m].re = fmaf(z.re, G.c[m].re, fmaf(z.im, G.c[m].im, g.c[m].re));
+    g.c[m].im = fmaf(z.re, G.c[m].im, fmaf(-z.im, G.c[m].re, g.c[m].im));
+  }
+}
+
+// g^m += eta_m conj(v^m) z
+__device__ __forceinline__ void add_eta_conj(CV4<float> &g, const CV4<float> &v, const Cx<float> &z) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const float e = eta_of(m);
+    g.c[m].re = fmaf(e, v.c[m].re * z.re + v.c[m].im * z.im, g.c[m].re);
+    g.c[m].im = fmaf(e, v.c[m].re * z.im - v.c[m].im * z.re, g.c[m].im);
+  }
+}
+
+// Gathers the gradient of set Y = [c..d] (L legs, lane-pair tables): GJ =
+// df/dJ_Y, GS = df/dS_Y, GK = df/dK_Y, from all parents of Y.
+template <int L, int NEV>
+__device__ void pull_set(const float4 *J4, const float4 *G4, const float4 *P4, const float2 *S2, const float2 *gS2,
+                         int g, int c, int d, CV4<float> &GJ, Cx<float> &GS, RV4<float> &GK) {
+  GJ = cv_zero<float>();
+  GS = cx<float>(0.f, 0.f);
+  GK.v[0] = GK.v[1] = GK.v[2] = GK.v[3] = 0.f;
+  const RV4<float> Pc = rv4(P4[c * NEV + g]), Pd1 = rv4(P4[(d + 1) * NEV + g]);
+  const RV4<float> KY = rsub(Pd1, Pc);
+  const CV4<float> JY = ld_cv4<NEV>(J4, pair_tri<L>(c, d), g);
+  // Y as the left part of X = [c..b] (split after d), and as the first part
+  // A of the triples of X with A = Y
+#pragma unroll 1
+  for (int b = d + 1; b < L; ++b) {
+    const int X = pair_tri<L>(c, b), r = pair_tri<L>(d + 1, b);
+    const CV4<float> GX = ld_cv4<NEV>(G4, X, g), Jr = ld_cv4<NEV>(J4, r, g);
+    const float2 gsx = gS2[X * NEV + g], sr = S2[r * NEV + g];
+    const RV4<float> Kr = rsub(rv4(P4[(b + 1) * NEV + g]), Pd1);
+    const Cx<float> dd = mdot(JY, Jr);
+    const Cx<float> krjl = mdot(Jr, KY);
+    const Cx<float> cl = cx<float>(fmaf(-2.f, krjl.re, -sr.x), fmaf(-2.f, krjl.im, -sr.y));
+    const Cx<float> gcr = conj_dot4(Jr, GX), gcl = conj_dot4(JY, GX);
+    add_conj(GJ, cl, GX);
+    Cx<float> gd = cx<float>(gsx.x, gsx.y);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const float dk = KY.v[m] - Kr.v[m];
+      gd.re = fmaf(dk, GX.c[m].re, gd.re);
+      gd.im = fmaf(dk, GX.c[m].im, gd.im);
+      GK.v[m] += dd.re * GX.c[m].re + dd.im * GX.c[m].im;  // Re(conj(d) G), as K_l
+    }
+    GS.re -= gcr.re;  // cr = 2 J_l.K_r - S_l
+    GS.im -= gcr.im;
+    const Cx<float> gjlkr = cx<float>(2.f * gcr.re, 2.f * gcr.im);
+    const Cx<float> gkrjl = cx<float>(-2.f * gcl.re, -2.f * gcl.im);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const float e = eta_of(m);
+      GJ.c[m].re = fmaf(e * Kr.v[m], gjlkr.re, GJ.c[m].re);  // from J_l.K_r
+      GJ.c[m].im = fmaf(e * Kr.v[m], gjlkr.im, GJ.c[m].im);
+      GK.v[m] += e * (Jr.c[m].re * gkrjl.re + Jr.c[m].im * gkrjl.im);  // from J_r.K_l
+    }
+    add_eta_conj(GJ, Jr, gd);  // from d = J_l.J_r
+    // triples (Y, [d+1..j], [j+1..b])
+#pragma unroll 1
+    for (int j = d + 1; j < b; ++j) {
+      const CV4<float> JB = ld_cv4<NEV>(J4, pair_tri<L>(d + 1, j), g);
+      const CV4<float> JC = ld_cv4<NEV>(J4, pair_tri<L>(j + 1, b), g);
+      const Cx<float> gt0 = conj_dot4(JB, GX);
+      add_eta_conj(GJ, JC, cx<float>(2.f * gt0.re, 2.f * gt0.im));
+    }
+  }
+  // Y as the right part of X = [a..d] (split before c), and as the last part
+  // C of the triples of X with C = Y
+#pragma unroll 1
+  for (int a = 0; a < c; ++a) {
+    const int X = pair_tri<L>(a, d), l = pair_tri<L>(a, c - 1);
+    const CV4<float> GX = ld_cv4<NEV>(G4, X, g), Jl = ld_cv4<NEV>(J4, l, g);
+    const float2 gsx = gS2[X * NEV + g], sl = S2[l * NEV + g];
+    const RV4<float> Kl = rsub(Pc, rv4(P4[a * NEV + g]));
+    const Cx<float> dd = mdot(Jl, JY);
+    const Cx<float> jlkr = mdot(Jl, KY);
+    const Cx<float> cr = cx<float>(fmaf(2.f, jlkr.re, -sl.x), fmaf(2.f, jlkr.im, -sl.y));
+    const Cx<float> gcr = conj_dot4(JY, GX), gcl = conj_dot4(Jl, GX);
+    add_conj(GJ, cr, GX);
+    Cx<float> gd = cx<float>(gsx.x, gsx.y);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const float dk = Kl.v[m] - KY.v[m];
+      gd.re = fmaf(dk, GX.c[m].re, gd.re);
+      gd.im = fmaf(dk, GX.c[m].im, gd.im);
+      GK.v[m] -= dd.re * GX.c[m].re + dd.im * GX.c[m].im;  // as K_r
+    }
+    GS.re -= gcl.re;  // cl = -2 J_r.K_l - S_r
+    GS.im -= gcl.im;
+    const Cx<float> gjlkr = cx<float>(2.f * gcr.re, 2.f * gcr.im);
+    const Cx<float> gkrjl = cx<float>(-2.f * gcl.re, -2.f * gcl.im);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const float e = eta_of(m);
+      GK.v[m] += e * (Jl.c[m].re * gjlkr.re + Jl.c[m].im * gjlkr.im);  // from J_l.K_r
+      GJ.c[m].re = fmaf(e * Kl.v[m], gkrjl.re, GJ.c[m].re);            // from J_r.K_l
+      GJ.c[m].im = fmaf(e * Kl.v[m], gkrjl.im, GJ.c[m].im);
+    }
+    add_eta_conj(GJ, Jl, gd);
+    // triples ([a..i], [i+1..c-1], Y)
+#pragma unroll 1
+    for (int i = a; i + 1 < c; ++i) {
+      const CV4<float> JA = ld_cv4<NEV>(J4, pair_tri<L>(a, i), g);
+      const CV4<float> JB = ld_cv4<NEV>(J4, pair_tri<L>(i + 1, c - 1), g);
+      const Cx<float> gt0 = conj_dot4(JB, GX);
+      add_eta_conj(GJ, JA, cx<float>(2.f * gt0.re, 2.f * gt0.im));
+    }
+    // Y as the middle part of X = [a..b], b > d: ([a..c-1], Y, [d+1..b])
+#pragma unroll 1
+    for (int b = d + 1; b < L; ++b) {
+      const CV4<float> GXb = ld_cv4<NEV>(G4, pair_tri<L>(a, b), g);
+      const Cx<float> t = mdot(Jl, ld_cv4<NEV>(J4, pair_tri<L>(d + 1, b), g));
+      add_conj(GJ, cx<float>(2.f * t.re, 2.f * t.im), GXb);
+    }
+  }
+}
+
+template <int N, int NEV>
+__global__ void __launch_bounds__(2 * NEV) grad_pair_kernel(GradParams G) {
+  constexpr int M = N - 2, L = N - 1, NU = 2 + 4 * M;
+  using PS = GradPairSmem<L, NEV>;
+  extern __shared__ __align__(16) char smem_gp[];
+  float4 *J4 = (float4 *)(smem_gp + PS::j_off), *G4 = (float4 *)(smem_gp + PS::g_off);
+  float4 *P4 = (float4 *)(smem_gp + PS::p_off), *E4 = (float4 *)(smem_gp + PS::e_off);
+  float2 *S2 = (float2 *)(smem_gp + PS::s_off), *gS2 = (float2 *)(smem_gp + PS::gs_off);
+  const int lane = threadIdx.x / NEV, g = threadIdx.x % NEV;
+  float4 *GP4 = (float4 *)(smem_gp + PS::gp_off) + (size_t)lane * (L + 1) * NEV;
+  const uint64_t e = (uint64_t)blockIdx.x * NEV + g;
+  const bool live = e < G.n_events;
+  uint32_t hel = 0;
+
+  // ---- amplitude inputs (lane 0): prefix momenta, single-leg currents, eps_0
+  if (live && lane == 0) {
+    GradKin<N, float> K;
+    grad_kinematics<N, float>(G.P, G.u + e * NU, G.order + e * N, K);
+    hel = G.hel[e];
+    RV4<float> k;
+    CV4<float> eps;
+    grad_amp_input<N, float, float>(K, hel, 0, k, eps);
+    E4[g] = make_float4(eps.c[0].re, eps.c[0].im, eps.c[1].re, eps.c[1].im);
+    E4[NEV + g] = make_float4(eps.c[2].re, eps.c[2].im, eps.c[3].re, eps.c[3].im);
+    RV4<float> p = {{0.f, 0.f, 0.f, 0.f}};
+    P4[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int a = 0; a < L; ++a) {
+      grad_amp_input<N, float, float>(K, hel, a + 1, k, eps);
+      p = radd(p, k);
+      P4[(a + 1) * NEV + g] = make_float4(p.v[0], p.v[1], p.v[2], p.v[3]);
+      const int X = pair_tri<L>(a, a);
+      st_cv4<NEV>(J4, X, g, eps);
+      S2[X * NEV + g] = make_float2(0.f, 0.f);
+    }
+  }
+#pragma unroll 1
+  for (int i = 0; i <= L; ++i) GP4[i * NEV + g] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+
+  // ---- forward recursion (as bg_pair_kernel)
+  PairView<NEV> V;
+  V.J4 = J4;
+  V.P4 = P4;
+  V.E4 = E4;
+  V.S2 = S2;
+  V.g = g;
+#pragma unroll 1
+  for (int len = 2; len < L; ++len) {
+    if (live) {
+#pragma unroll 1
+      for (int a = lane; a + len - 1 < L; a += 2) {
+        const int b = a + len - 1;
+        CV4<float> acc;
+        Cx<float> s;
+        pair_sums<L, NEV>(V, a, b, 0, 1, acc, s);
+        const RV4<float> Kab = rsub(V.P(b + 1), V.P(a));
+        const float inv = 1.f / mdot(Kab, Kab);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          acc.c[m].re *= inv;
+          acc.c[m].im *= inv;
+        }
+        const int X = pair_tri<L>(a, b);
+        V.setJ(X, acc);
+        S2[X * NEV + g] = make_float2(s.re, s.im);
+      }
+    }
+    __syncthreads();
+  }
+  const int top = pair_tri<L>(0, L - 1);
+  CV4<float> num = cv_zero<float>();
+  if (live) {
+    Cx<float> s;
+    pair_sums<L, NEV>(V, 0, L - 1, lane, 2, num, s);
+    if (lane == 1) V.setJ(top, num);  // the top current is never propagated: its slot is scratch
+  }
+  __syncthreads();
+
+  // ---- m = eps_0 . num, f = |m|^2, adjoint seeds (lane 0)
+  double f = 0.0;
+  CV4<float> ge0 = cv_zero<float>();
+  if (live && lane == 0) {
+    const CV4<float> other = V.J(top);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      num.c[m].re += other.c[m].re;
+      num.c[m].im += other.c[m].im;
+    }
+    const float4 u0 = E4[g], v0 = E4[NEV + g];
+    CV4<float> e0;
+    e0.c[0] = cx<float>(u0.x, u0.y);
+    e0.c[1] = cx<float>(u0.z, u0.w);
+    e0.c[2] = cx<float>(v0.x, v0.y);
+    e0.c[3] = cx<float>(v0.z, v0.w);
+    const Cx<float> mamp = mdot(e0, num);
+    f = (double)mamp.re * (double)mamp.re + (double)mamp.im * (double)mamp.im;
+    const Cx<float> gm = cx<float>(2.f * mamp.re, 2.f * mamp.im);  // g(m) for f = |m|^2
+    CV4<float> gtop = cv_zero<float>();
+    add_eta_conj(ge0, num, gm);
+    add_eta_conj(gtop, e0, gm);
+    st_cv4<NEV>(G4, top, g, gtop);
+    gS2[top * NEV + g] = make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+
+  // ---- reverse sweep in pull form, longest sets first
+#pragma unroll 1
+  for (int len = L - 1; len >= 1; --len) {
+    if (live) {
+#pragma unroll 1
+      for (int c = lane; c + len - 1 < L; c += 2) {
+        const int d = c + len - 1, Y = pair_tri<L>(c, d);
+        CV4<float> GJ;
+        Cx<float> GS;
+        RV4<float> GK;
+        pull_set<L, NEV>(J4, G4, P4, S2, gS2, g, c, d, GJ, GS, GK);
+        if (len >= 2) {  // J_Y = acc_Y / K_Y^2: store G_Y = df/dacc_Y, K-gradient of 1/K^2
+          const RV4<float> KY = rsub(rv4(P4[(d + 1) * NEV + g]), rv4(P4[c * NEV + g]));
+          const float inv = 1.f / mdot(KY, KY);
+          const Cx<float> cj = conj_dot4(V.J(Y), GJ);
+          const float gk2 = -2.f * cj.re * inv;
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            GK.v[m] = fmaf(gk2 * eta_of(m), KY.v[m], GK.v[m]);
+            GJ.c[m].re *= inv;
+            GJ.c[m].im *= inv;
+          }
+          gS2[Y * NEV + g] = make_float2(GS.re, GS.im);
+        }
+        st_cv4<NEV>(G4, Y, g, GJ);  // G_Y, or df/deps for a single leg
+        float4 hi = GP4[(d + 1) * NEV + g], lo = GP4[c * NEV + g];
+        GP4[(d + 1) * NEV + g] = make_float4(hi.x + GK.v[0], hi.y + GK.v[1], hi.z + GK.v[2], hi.w + GK.v[3]);
+        GP4[c * NEV + g] = make_float4(lo.x - GK.v[0], lo.y - GK.v[1], lo.z - GK.v[2], lo.w - GK.v[3]);
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- outputs (lane 0): momentum gradients from the prefix rows, eps
+  // gradients of the single legs, kinematics recomputed for the adjoint
+  if (live && lane == 0) {
+    const float4 *GPo = (const float4 *)(smem_gp + PS::gp_off) + (size_t)(L + 1) * NEV;  // lane 1's row
+    RV4<float> gkp[L];  // df/dk of BG leg t = sum_{i > t} GP[i]
+    RV4<float> acc = {{0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int t = L - 1; t >= 0; --t) {
+      const float4 a0 = GP4[(t + 1) * NEV + g], a1 = GPo[(t + 1) * NEV + g];
+      acc.v[0] += a0.x + a1.x;
+      acc.v[1] += a0.y + a1.y;
+      acc.v[2] += a0.z + a1.z;
+      acc.v[3] += a0.w + a1.w;
+      gkp[t] = acc;
+    }
+    GradKin<N, float> K;
+    grad_kinematics<N, float>(G.P, G.u + e * NU, G.order + e * N, K);
+    grad_outputs<N, float, float>(G, e, K, hel, f, [&](int a, double(&g4)[4], CV4<float> &ge) {
+      if (a == 0) {
+        ge = ge0;
+      } else {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) g4[m] = (double)gkp[a - 1].v[m];
+        ge = ld_cv4<NEV>(G4, pair_tri<L>(a - 1, a - 1), g);
+      }
+    });
+  }
+}
+
+// Gradient kernel launch for n: FP64 thread per event; the FP32 forms lane
+// pairs up to n = 8 (above, the table's shared memory leaves one block of two
+// warps per SM and the thread-per-event kernel measures faster).
+template <int N>
+cudaError_t launch_grad_n(bool fp64, const GradParams &G, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((G.n_events + kBlock - 1) / kBlock);
+  if (fp64) {
+    grad_kernel<N, double><<<blocks, kBlock, 0, s>>>(G);
+    return cudaGetLastError();
+  }
+  if constexpr (N > 8) {
+    grad_kernel<N, float><<<blocks, kBlock, 0, s>>>(G);
+    return cudaGetLastError();
+  } else {
+    constexpr int NEV = 32;
+    const cudaError_t e = allow_max_smem((const void *)grad_pair_kernel<N, NEV>);
+    if (e != cudaSuccess) return e;
+    grad_pair_kernel<N, NEV>
+        <<<(unsigned)((G.n_events + NEV - 1) / NEV), 2 * NEV, GradPairSmem<N - 1, NEV>::bytes, s>>>(G);
+    return cudaGetLastError();
+  }
+}
+
+}  // namespace tess

@@ -52,20 +52,6 @@ constexpr size_t kChunkTargetBytes = 64ull << 20;  // stays resident in the 129 
 // call, or this code when no block of the variant fits on an SM
 constexpr int kPlanNoResidentBlock = -2;
 
-// Lets `fn` launch with up to the device's opt-in maximum of shared memory
-// per block (dynamic + static).  Always the same value for a kernel, so plans
-// of different sizes for one kernel (batched processes, histograms) never
-// lower each other's limit.
-inline cudaError_t allow_max_smem(const void *fn) {
-  int dev = 0, optin = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  cudaFuncAttributes fa;
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
-  return e;
-}
 
 // Optional host hook around each launch (stage timing); kinds below.
 enum StageKind { STAGE_KIN = 0, STAGE_AMP = 1, STAGE_FINAL = 2, STAGE_FUSED = 3, STAGE_NKINDS = 4 };
