@@ -24,14 +24,14 @@ struct EventParams {
   double hist_lo, hist_inv_width;
   int hist_bins;       // 0: no histogram
   int hist_obs;
-  // double-single kinematics: S split into two floats, and the weight
+  // double-float kinematics: S split into two floats, and the weight
   // constant wconst (ln x_min)^2 phiconst / 2
   float S_hi, S_lo;
   double wk;
   uint32_t rk[20];     // Philox round keys of `seed`
   // single-precision copies of the constants the FP32 kinematics read
   float f_lnxmin, f_pt_min, f_eta_max, f_dr2_min, f_alphas_mz, f_asb0, f_ln_mz2, f_mu_r_factor;
-  int kin_ds;          // 1: double-single kinematics kernel
+  int kin_ds;          // 1: double-float kinematics kernel
   // outputs (device; may be null)
   double *weight, *me2, *ht, *ptlead, *rmin;
   uint8_t *pass;

@@ -42,12 +42,6 @@ __device__ __forceinline__ double2 uniform_pair(uint64_t seed, uint64_t ev, uint
   return make_double2(unit_from_words(w.x, w.y), unit_from_words(w.z, w.w));
 }
 
-// The raw Philox block `blk` of event `ev`.
-__device__ __forceinline__ uint4 philox_block(uint64_t seed, uint64_t ev, uint32_t blk) {
-  return philox4x32_10(make_uint4((uint32_t)ev, (uint32_t)(ev >> 32), blk, 0u),
-                       make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-}
-
 // Philox4x32-10 with the ten round keys given (rk[2r], rk[2r+1] = key of
 // round r); the same function of (counter, key) as philox4x32_10.  Kernels
 // take the round keys from their launch constants, so the key schedule is
@@ -223,11 +217,11 @@ __device__ __forceinline__ RV4<R> radd(const RV4<R> &a, const RV4<R> &b) {
 namespace tess {
 
 // ---------------------------------------------------------------------------
-// Double-single ("two-float") arithmetic: a value is hi + lo with |lo| <=
+// Double-float ("two-float") arithmetic: a value is hi + lo with |lo| <=
 // ulp(hi)/2, about 47-48 significant bits, evaluated on the FP32 pipe.  Built
 // from the error-free transformations two-sum (Knuth) and two-product (one
 // FMA); reciprocal and reciprocal square root take one Newton step in
-// double-single from the FP32 estimate.  Rounding a normalised value to FP32
+// double-float from the FP32 estimate.  Rounding a normalised value to FP32
 // gives hi.
 // ---------------------------------------------------------------------------
 struct DS {
@@ -235,13 +229,6 @@ struct DS {
 };
 
 __device__ __forceinline__ DS ds(float x) { return DS{x, 0.f}; }
-
-__device__ __forceinline__ DS ds_from_double(double x) {
-  const float h = (float)x;
-  return DS{h, (float)(x - (double)h)};
-}
-
-__device__ __forceinline__ double ds_to_double(DS a) { return (double)a.hi + (double)a.lo; }
 
 __device__ __forceinline__ DS ds_fast_two_sum(float a, float b) {  // |a| >= |b|
   const float s = a + b;
@@ -278,9 +265,6 @@ __device__ __forceinline__ DS ds_mul(DS a, float b) {
   const float e = fmaf(a.lo, b, fmaf(a.hi, b, -p));
   return ds_fast_two_sum(p, e);
 }
-
-// a*b + c
-__device__ __forceinline__ DS ds_fma(DS a, DS b, DS c) { return ds_add(ds_mul(a, b), c); }
 
 // 1/a: y0 = rcp(hi), y = y0 + y0 (1 - a y0)
 __device__ __forceinline__ DS ds_rcp(DS a) {

@@ -477,7 +477,7 @@ __device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<fl
 }
 
 // Polarisation basis in FP32 from the FP32-rounded momentum components (each
-// within half an ulp of the double-single value, so every product here has
+// within half an ulp of the double-float value, so every product here has
 // FP32 relative accuracy: no cancellation occurs); E = |p|.
 __device__ __forceinline__ void pol_basis_rounded(float E, float px, float py, float pz, float (&e1)[3],
                                                   float (&e2)[2]) {
@@ -498,11 +498,12 @@ __device__ __forceinline__ void pol_basis_rounded(float E, float px, float py, f
   e2[1] = cf;
 }
 
-// K1, double-single form: as kin_fp32, with the steps that need more than
-// FP32 -- Rambo's boost and rescale, the polarisation Gram products -- in
-// double-single arithmetic on the FP32 pipe instead of native FP64 (1/64 of
-// the FP32 rate on this GPU).  The weight factor is assembled in FP32 with
-// its power-of-two scale kept as an exact exponent.
+// K1, double-float form: as kin_fp32, with the step that needs more than
+// FP32 -- Rambo's boost and rescale -- in double-float (two-float)
+// arithmetic on the FP32 pipe instead of native FP64 (1/64 of the FP32 rate
+// on this GPU), and the polarisation basis in FP32 from the rounded momenta.
+// The weight factor is assembled in FP32 with its power-of-two scale kept as
+// an exact exponent.
 template <int N>
 __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<float> &B, int e, float *tile) {
   constexpr int M = N - 2;
