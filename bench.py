@@ -444,15 +444,20 @@ def plan_cap(tess, ctx, proc, n_events):
     return -(-n_events // max(info["chunks"], 1))
 
 
+PIPELINE_SOURCES = ("tess_async.cuh", "tess_bg.cuh", "tess_event.cuh", "tess_kernels.cuh", "tess_math.cuh",
+                    "tess_pair.cuh", "tess_pipe_launch.cuh", "tess_pipeline.cuh")
+
+
 def kernel_source_hash():
-    """sha256 over the sources of the pipeline kernels (every device header
-    and the pipeline instantiation units): a committed ncu figure is used
-    only while the kernels it was taken from are unchanged."""
+    """sha256 over the sources of the generation pipeline's kernels (the
+    pipeline instantiation units and every header they include): a committed
+    ncu figure is used only while the kernels it was taken from are
+    unchanged."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1002_3446_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith(".cuh") or (name.startswith("tess_pipe_") and name.endswith(".cu")):
+        if name in PIPELINE_SOURCES or (name.startswith("tess_pipe_") and name.endswith(".cu")):
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()
