@@ -267,14 +267,22 @@ int tess_plan_info(const tess_ctx *ctx, const tess_process *proc, uint64_t n_eve
  *   dw_dlnmu  [n_events]              w.r.t. ln mu_R (one-loop running)
  * all multiplied by dL_dw[e] when dL_dw is given (a vector-Jacobian product).
  * The cuts are a step function: events failing them have w = 0 and zero
- * gradients.  Kinematics and their adjoints are FP64; the Berends-Giele
- * forward pass and its adjoint are FP64 for TESS_FP64 and FP32 otherwise.
- * Any output pointer may be NULL. */
+ * gradients.  TESS_FP64: every step FP64, one kernel.  FP32 forms: the
+ * kinematics' precision split of tess_generate (FP32 seeds, cuts,
+ * observables, PDF, alpha_s, polarisation basis; FP64 boost/rescale and its
+ * adjoint, weight scalings) and an FP32 Berends-Giele forward pass and
+ * reverse sweep, run as three kernels per chunk of events (kinematics ->
+ * amplitude inputs; two threads per event for the recursion and its adjoint;
+ * kinematics again -> outputs) through `workspace`:
+ * tess_gradients_workspace_size(proc, n_events) bytes, device, 256-byte
+ * aligned (0 bytes, NULL allowed, for TESS_FP64).  TESS_E_WORKSPACE if it is
+ * missing or too small.  Any output pointer may be NULL. */
 int tess_draws(tess_ctx *ctx, int n, uint64_t seed, uint64_t first_event, uint64_t n_events, double *u,
                uint32_t *hel, uint8_t *order, void *stream);
+int tess_gradients_workspace_size(const tess_ctx *ctx, const tess_process *proc, uint64_t n_events, size_t *bytes);
 int tess_gradients(tess_ctx *ctx, const tess_process *proc, uint64_t n_events, const double *u, const uint32_t *hel,
                    const uint8_t *order, const double *dL_dw, double *w, double *dw_du, double *dw_dk,
-                   double *dw_dlnmu, void *stream);
+                   double *dw_dlnmu, void *workspace, size_t workspace_bytes, void *stream);
 
 /* Colour-ordered matrix elements for caller-given kinematics (the
  * matrix-element stage alone, Eq. (BG-recursion) and the amplitude

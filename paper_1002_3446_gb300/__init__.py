@@ -40,7 +40,7 @@ EXPORTED = ["tess_version", "tess_last_error", "tess_init", "tess_destroy", "tes
             "tess_me2", "tess_result", "tess_weights", "tess_histograms", "tess_generate_noalloc",
             "tess_kernel_launches", "tess_workspace_size_batched", "tess_generate_batched", "tess_autotune",
             "tess_stage_timing", "tess_stage_times", "tess_draws", "tess_gradients", "tess_select_variant",
-            "tess_plan_info"]
+            "tess_plan_info", "tess_gradients_workspace_size"]
 
 
 class TessError(RuntimeError):
@@ -103,7 +103,9 @@ def _load():
         lib.tess_select_variant.argtypes = [vp, P(tess_process), i32, i32]
         lib.tess_plan_info.argtypes = [vp, P(tess_process), u64, P(ctypes.c_int)]
         lib.tess_draws.argtypes = [vp, i32, u64, u64, u64, vp, vp, vp, vp]
-        lib.tess_gradients.argtypes = [vp, P(tess_process), u64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.tess_gradients.argtypes = [vp, P(tess_process), u64, vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t,
+                                       vp]
+        lib.tess_gradients_workspace_size.argtypes = [vp, P(tess_process), u64, P(ctypes.c_size_t)]
         lib.tess_stage_times.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int)]
         lib.tess_generate.argtypes = [vp, P(tess_process), u64, u64, u64, P(tess_outputs), vp, ctypes.c_size_t, vp]
         lib.tess_me2.argtypes = [vp, i32, i32, u64, vp, vp, vp, vp, vp]
@@ -243,9 +245,17 @@ def tess_draws(ctx, n, seed, first_event, n_events, stream=None):
     return u, hel, order
 
 
-def tess_gradients(ctx, proc, u, hel, order, dL_dw=None, want=("w", "dw_du", "dw_dk", "dw_dlnmu"), stream=None):
+def tess_gradients_workspace_size(ctx, proc, n_events):
+    b = ctypes.c_size_t()
+    _check(_load().tess_gradients_workspace_size(ctx, ctypes.byref(proc), int(n_events), ctypes.byref(b)))
+    return b.value
+
+
+def tess_gradients(ctx, proc, u, hel, order, dL_dw=None, want=("w", "dw_du", "dw_dk", "dw_dlnmu"), stream=None,
+                   workspace=None):
     """Event weights and their gradients (see include/tess.h); returns a dict of
-    device tensors for the requested outputs."""
+    device tensors for the requested outputs.  workspace: a device tensor of
+    at least tess_gradients_workspace_size bytes (allocated here if None)."""
     import torch
     E = u.shape[0]
     n = proc.n_gluons
@@ -254,9 +264,13 @@ def tess_gradients(ctx, proc, u, hel, order, dL_dw=None, want=("w", "dw_du", "dw
            "dw_du": torch.empty((E, n_uniforms(n)), **f64) if "dw_du" in want else None,
            "dw_dk": torch.empty((E, n, 4), **f64) if "dw_dk" in want else None,
            "dw_dlnmu": torch.empty(E, **f64) if "dw_dlnmu" in want else None}
+    if workspace is None:
+        need = tess_gradients_workspace_size(ctx, proc, E)
+        workspace = torch.empty((need + 7) // 8, **f64) if need else None
+    nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check(_load().tess_gradients(ctx, ctypes.byref(proc), int(E), _ptr(u.contiguous()), _ptr(hel), _ptr(order),
                                   _ptr(dL_dw), _ptr(out["w"]), _ptr(out["dw_du"]), _ptr(out["dw_dk"]),
-                                  _ptr(out["dw_dlnmu"]), _stream(stream)))
+                                  _ptr(out["dw_dlnmu"]), _ptr(workspace), nbytes, _stream(stream)))
     return {k: v for k, v in out.items() if v is not None}
 
 

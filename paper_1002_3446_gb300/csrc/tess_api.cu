@@ -23,9 +23,12 @@ cudaError_t launch_me2_f64(int n, uint64_t n_events, const double *k, const uint
                            double *me2, cudaStream_t s);
 cudaError_t launch_me2_f32(int n, uint64_t n_events, const double *k, const uint8_t *order, const uint32_t *hel,
                            double *me2, cudaStream_t s);
-cudaError_t launch_grad_a(int n, bool fp64, const GradParams &G, cudaStream_t s);
-cudaError_t launch_grad_b(int n, bool fp64, const GradParams &G, cudaStream_t s);
-cudaError_t launch_grad_c(int n, bool fp64, const GradParams &G, cudaStream_t s);
+cudaError_t launch_grad_a(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s);
+cudaError_t launch_grad_b(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s);
+cudaError_t launch_grad_c(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s);
+size_t grad_workspace_a(int n, uint64_t n_events);
+size_t grad_workspace_b(int n, uint64_t n_events);
+size_t grad_workspace_c(int n, uint64_t n_events);
 cudaError_t launch_draws_a(int n, const EventParams &P, double *u, uint32_t *hel, uint8_t *order, cudaStream_t s);
 cudaError_t launch_draws_b(int n, const EventParams &P, double *u, uint32_t *hel, uint8_t *order, cudaStream_t s);
 cudaError_t launch_draws_c(int n, const EventParams &P, double *u, uint32_t *hel, uint8_t *order, cudaStream_t s);
@@ -901,9 +904,23 @@ int tess_draws(tess_ctx *ctx, int n, uint64_t seed, uint64_t first_event, uint64
   return ok();
 }
 
+int tess_gradients_workspace_size(const tess_ctx *ctx, const tess_process *proc, uint64_t n_events, size_t *bytes) {
+  if (!ctx || !bytes) return fail(TESS_E_INVALID, "ctx and bytes must not be NULL");
+  int rc = check_process(proc);
+  if (rc) return rc;
+  const int n = proc->n_gluons;
+  if (proc->precision == TESS_FP64) {
+    *bytes = 0;
+  } else {
+    *bytes = n <= 8 ? tess::grad_workspace_a(n, n_events)
+                    : (n <= 10 ? tess::grad_workspace_b(n, n_events) : tess::grad_workspace_c(n, n_events));
+  }
+  return ok();
+}
+
 int tess_gradients(tess_ctx *ctx, const tess_process *proc, uint64_t n_events, const double *u, const uint32_t *hel,
                    const uint8_t *order, const double *dL_dw, double *w, double *dw_du, double *dw_dk,
-                   double *dw_dlnmu, void *stream) {
+                   double *dw_dlnmu, void *workspace, size_t workspace_bytes, void *stream) {
   if (!ctx) return fail(TESS_E_INVALID, "ctx is NULL");
   int rc = check_process(proc);
   if (rc) return rc;
@@ -934,9 +951,19 @@ int tess_gradients(tess_ctx *ctx, const tess_process *proc, uint64_t n_events, c
   G.n_events = n_events;
   const int n = proc->n_gluons;
   const bool fp64 = proc->precision == TESS_FP64;
+  size_t need = 0;
+  if ((rc = tess_gradients_workspace_size(ctx, proc, n_events, &need))) return rc;
+  if (need) {
+    if (!workspace || workspace_bytes < need)
+      return fail(TESS_E_WORKSPACE, "gradient workspace of %zu bytes needed, %zu given", need,
+                  workspace ? workspace_bytes : 0);
+    if ((rc = check_device_ptr(workspace, ctx->device, "workspace"))) return rc;
+    if (((uintptr_t)workspace) % 256 != 0) return fail(TESS_E_WORKSPACE, "workspace must be 256-byte aligned");
+  }
   cudaStream_t s = (cudaStream_t)stream;
-  const cudaError_t e = n <= 8 ? tess::launch_grad_a(n, fp64, G, s)
-                               : (n <= 10 ? tess::launch_grad_b(n, fp64, G, s) : tess::launch_grad_c(n, fp64, G, s));
+  const cudaError_t e = n <= 8 ? tess::launch_grad_a(n, fp64, G, workspace, s)
+                               : (n <= 10 ? tess::launch_grad_b(n, fp64, G, workspace, s)
+                                          : tess::launch_grad_c(n, fp64, G, workspace, s));
   if (e != cudaSuccess) return cuda_fail(e, "gradient kernel launch");
   return ok();
 }

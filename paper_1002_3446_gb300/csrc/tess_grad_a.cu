@@ -3,14 +3,25 @@
 
 namespace tess {
 
-cudaError_t launch_grad_a(int n, bool fp64, const GradParams &G, cudaStream_t s) {
+cudaError_t launch_grad_a(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s) {
   switch (n) {
-    case 4: return launch_grad_n<4>(fp64, G, s);
-    case 5: return launch_grad_n<5>(fp64, G, s);
-    case 6: return launch_grad_n<6>(fp64, G, s);
-    case 7: return launch_grad_n<7>(fp64, G, s);
-    case 8: return launch_grad_n<8>(fp64, G, s);
+    case 4: return launch_grad_n<4>(fp64, G, ws, s);
+    case 5: return launch_grad_n<5>(fp64, G, ws, s);
+    case 6: return launch_grad_n<6>(fp64, G, ws, s);
+    case 7: return launch_grad_n<7>(fp64, G, ws, s);
+    case 8: return launch_grad_n<8>(fp64, G, ws, s);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+size_t grad_workspace_a(int n, uint64_t n_events) {
+  switch (n) {
+    case 4: return grad_workspace_bytes<4>(n_events);
+    case 5: return grad_workspace_bytes<5>(n_events);
+    case 6: return grad_workspace_bytes<6>(n_events);
+    case 7: return grad_workspace_bytes<7>(n_events);
+    case 8: return grad_workspace_bytes<8>(n_events);
+    default: return 0;
   }
 }
 

@@ -3,11 +3,19 @@
 
 namespace tess {
 
-cudaError_t launch_grad_b(int n, bool fp64, const GradParams &G, cudaStream_t s) {
+cudaError_t launch_grad_b(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s) {
   switch (n) {
-    case 9: return launch_grad_n<9>(fp64, G, s);
-    case 10: return launch_grad_n<10>(fp64, G, s);
+    case 9: return launch_grad_n<9>(fp64, G, ws, s);
+    case 10: return launch_grad_n<10>(fp64, G, ws, s);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+size_t grad_workspace_b(int n, uint64_t n_events) {
+  switch (n) {
+    case 9: return grad_workspace_bytes<9>(n_events);
+    case 10: return grad_workspace_bytes<10>(n_events);
+    default: return 0;
   }
 }
 

@@ -3,11 +3,19 @@
 
 namespace tess {
 
-cudaError_t launch_grad_c(int n, bool fp64, const GradParams &G, cudaStream_t s) {
+cudaError_t launch_grad_c(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s) {
   switch (n) {
-    case 11: return launch_grad_n<11>(fp64, G, s);
-    case 12: return launch_grad_n<12>(fp64, G, s);
+    case 11: return launch_grad_n<11>(fp64, G, ws, s);
+    case 12: return launch_grad_n<12>(fp64, G, ws, s);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+size_t grad_workspace_c(int n, uint64_t n_events) {
+  switch (n) {
+    case 11: return grad_workspace_bytes<11>(n_events);
+    case 12: return grad_workspace_bytes<12>(n_events);
+    default: return 0;
   }
 }
 

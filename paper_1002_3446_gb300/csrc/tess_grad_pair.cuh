@@ -21,6 +21,8 @@
 // run by lane 0; the kinematics are recomputed after the sweep instead of
 // being kept live across it.
 #pragma once
+#include <algorithm>
+
 #include "tess_grad.cuh"
 #include "tess_pair.cuh"
 
@@ -198,47 +200,97 @@ __device__ void pull_set(const float4 *J4, const float4 *G4, const float4 *P4, c
   }
 }
 
-template <int N, int NEV>
-__global__ void __launch_bounds__(2 * NEV) grad_pair_kernel(GradParams G) {
-  constexpr int M = N - 2, L = N - 1, NU = 2 + 4 * M;
-  using PS = GradPairSmem<L, NEV>;
-  extern __shared__ __align__(16) char smem_gp[];
-  float4 *J4 = (float4 *)(smem_gp + PS::j_off), *G4 = (float4 *)(smem_gp + PS::g_off);
-  float4 *P4 = (float4 *)(smem_gp + PS::p_off), *E4 = (float4 *)(smem_gp + PS::e_off);
-  float2 *S2 = (float2 *)(smem_gp + PS::s_off), *gS2 = (float2 *)(smem_gp + PS::gs_off);
-  const int lane = threadIdx.x / NEV, g = threadIdx.x % NEV;
-  float4 *GP4 = (float4 *)(smem_gp + PS::gp_off) + (size_t)lane * (L + 1) * NEV;
-  const uint64_t e = (uint64_t)blockIdx.x * NEV + g;
-  const bool live = e < G.n_events;
-  uint32_t hel = 0;
+// ---------------------------------------------------------------------------
+// Split gradient pipeline (FP32 forms), per chunk of events sized for L2:
+//   G1 grad_in_kernel   thread per event: kinematics -> amplitude inputs
+//                       (rows as InRows: momenta in the unit c and the five
+//                       nonzero eps components per colour position)
+//   G2 grad_amp_kernel  lane pairs: recursion, |m|^2 and the pull-form
+//                       reverse sweep -> df/dk and df/deps per position
+//   G3 grad_out_kernel  thread per event: kinematics again -> weights and
+//                       gradients (grad_outputs)
+// so that the table-bound middle stage keeps both lanes busy and the
+// kinematics run at full occupancy.  The eps gradients keep the five
+// components the polarisation adjoint reads (Re x, y, z; Im x, y).
+// ---------------------------------------------------------------------------
+struct GradChunk {
+  float *in;  // [InRows<L>::rows][cap]
+  float *gr;  // [InRows<L>::rows][cap]: df/dk (4) and df/deps (5) per position 1..L, then df/deps_0
+  double *f;  // [cap] |m|^2
+  int cap;
+};
 
-  // ---- amplitude inputs (lane 0): prefix momenta, single-leg currents, eps_0
-  if (live && lane == 0) {
-    GradKin<N, float> K;
-    grad_kinematics<N, float>(G.P, G.u + e * NU, G.order + e * N, K);
-    hel = G.hel[e];
+template <int N>
+__global__ void __launch_bounds__(kBlock) grad_in_kernel(GradParams G, uint64_t first, int count, GradChunk B) {
+  constexpr int M = N - 2, L = N - 1, NU = 2 + 4 * M;
+  const int e = blockIdx.x * kBlock + threadIdx.x;
+  if (e >= count) return;
+  const uint64_t ev = first + (uint64_t)e;
+  GradKin<N, float> K;
+  grad_kinematics<N, float>(G.P, G.u + ev * NU, G.order + ev * N, K);
+  const uint32_t hel = G.hel[ev];
+  const size_t cap = (size_t)B.cap;
+#pragma unroll
+  for (int a = 0; a <= L; ++a) {
     RV4<float> k;
     CV4<float> eps;
-    grad_amp_input<N, float, float>(K, hel, 0, k, eps);
-    E4[g] = make_float4(eps.c[0].re, eps.c[0].im, eps.c[1].re, eps.c[1].im);
-    E4[NEV + g] = make_float4(eps.c[2].re, eps.c[2].im, eps.c[3].re, eps.c[3].im);
-    RV4<float> p = {{0.f, 0.f, 0.f, 0.f}};
-    P4[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+    grad_amp_input<N, float, float>(K, hel, a, k, eps);
+    float *o = B.in + (size_t)(a == 0 ? InRows<L>::eps0 : InRows<L>::eps(a - 1)) * cap + e;
+    if (a > 0) {
+      float *ok = B.in + (size_t)InRows<L>::k(a - 1) * cap + e;
 #pragma unroll
-    for (int a = 0; a < L; ++a) {
-      grad_amp_input<N, float, float>(K, hel, a + 1, k, eps);
-      p = radd(p, k);
-      P4[(a + 1) * NEV + g] = make_float4(p.v[0], p.v[1], p.v[2], p.v[3]);
-      const int X = pair_tri<L>(a, a);
-      st_cv4<NEV>(J4, X, g, eps);
-      S2[X * NEV + g] = make_float2(0.f, 0.f);
+      for (int m = 0; m < 4; ++m) ok[m * cap] = k.v[m];
+    }
+    o[0] = eps.c[1].re;
+    o[cap] = eps.c[2].re;
+    o[2 * cap] = eps.c[3].re;
+    o[3 * cap] = eps.c[1].im;
+    o[4 * cap] = eps.c[2].im;
+  }
+}
+
+template <int N, int NEV>
+__global__ void __launch_bounds__(2 * NEV) grad_amp_kernel(int count, GradChunk B) {
+  constexpr int L = N - 1;
+  using PS = GradPairSmem<L, NEV>;
+  extern __shared__ __align__(16) char smem_ga[];
+  float4 *J4 = (float4 *)(smem_ga + PS::j_off), *G4 = (float4 *)(smem_ga + PS::g_off);
+  float4 *P4 = (float4 *)(smem_ga + PS::p_off), *E4 = (float4 *)(smem_ga + PS::e_off);
+  float2 *S2 = (float2 *)(smem_ga + PS::s_off), *gS2 = (float2 *)(smem_ga + PS::gs_off);
+  const int lane = threadIdx.x / NEV, g = threadIdx.x % NEV;
+  float4 *GP4 = (float4 *)(smem_ga + PS::gp_off) + (size_t)lane * (L + 1) * NEV;
+  const int e = blockIdx.x * NEV + g;
+  const bool live = e < count;
+  const size_t cap = (size_t)B.cap;
+  if (live) {
+    if (lane == 0) {  // momenta -> prefix sums, eps_0
+      RV4<float> p = {{0.f, 0.f, 0.f, 0.f}};
+      P4[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+      for (int a = 0; a < L; ++a) {
+        RV4<float> k;
+        load_k(B.in + (size_t)InRows<L>::k(a) * cap + e, cap, k);
+        p = radd(p, k);
+        P4[(a + 1) * NEV + g] = make_float4(p.v[0], p.v[1], p.v[2], p.v[3]);
+      }
+      CV4<float> e0;
+      load_eps(B.in + (size_t)InRows<L>::eps0 * cap + e, cap, e0);
+      E4[g] = make_float4(e0.c[0].re, e0.c[0].im, e0.c[1].re, e0.c[1].im);
+      E4[NEV + g] = make_float4(e0.c[2].re, e0.c[2].im, e0.c[3].re, e0.c[3].im);
+    } else {  // single-leg currents
+#pragma unroll 1
+      for (int a = 0; a < L; ++a) {
+        CV4<float> ea;
+        load_eps(B.in + (size_t)InRows<L>::eps(a) * cap + e, cap, ea);
+        const int X = pair_tri<L>(a, a);
+        st_cv4<NEV>(J4, X, g, ea);
+        S2[X * NEV + g] = make_float2(0.f, 0.f);
+      }
     }
   }
 #pragma unroll 1
   for (int i = 0; i <= L; ++i) GP4[i * NEV + g] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
-
-  // ---- forward recursion (as bg_pair_kernel)
   PairView<NEV> V;
   V.J4 = J4;
   V.P4 = P4;
@@ -273,13 +325,9 @@ __global__ void __launch_bounds__(2 * NEV) grad_pair_kernel(GradParams G) {
   if (live) {
     Cx<float> s;
     pair_sums<L, NEV>(V, 0, L - 1, lane, 2, num, s);
-    if (lane == 1) V.setJ(top, num);  // the top current is never propagated: its slot is scratch
+    if (lane == 1) V.setJ(top, num);  // the top current's slot is scratch
   }
   __syncthreads();
-
-  // ---- m = eps_0 . num, f = |m|^2, adjoint seeds (lane 0)
-  double f = 0.0;
-  CV4<float> ge0 = cv_zero<float>();
   if (live && lane == 0) {
     const CV4<float> other = V.J(top);
 #pragma unroll
@@ -294,17 +342,21 @@ __global__ void __launch_bounds__(2 * NEV) grad_pair_kernel(GradParams G) {
     e0.c[2] = cx<float>(v0.x, v0.y);
     e0.c[3] = cx<float>(v0.z, v0.w);
     const Cx<float> mamp = mdot(e0, num);
-    f = (double)mamp.re * (double)mamp.re + (double)mamp.im * (double)mamp.im;
-    const Cx<float> gm = cx<float>(2.f * mamp.re, 2.f * mamp.im);  // g(m) for f = |m|^2
-    CV4<float> gtop = cv_zero<float>();
+    B.f[e] = (double)mamp.re * (double)mamp.re + (double)mamp.im * (double)mamp.im;
+    const Cx<float> gm = cx<float>(2.f * mamp.re, 2.f * mamp.im);
+    CV4<float> ge0 = cv_zero<float>(), gtop = cv_zero<float>();
     add_eta_conj(ge0, num, gm);
     add_eta_conj(gtop, e0, gm);
     st_cv4<NEV>(G4, top, g, gtop);
     gS2[top * NEV + g] = make_float2(0.f, 0.f);
+    float *o = B.gr + (size_t)InRows<L>::eps0 * cap + e;
+    o[0] = ge0.c[1].re;
+    o[cap] = ge0.c[2].re;
+    o[2 * cap] = ge0.c[3].re;
+    o[3 * cap] = ge0.c[1].im;
+    o[4 * cap] = ge0.c[2].im;
   }
   __syncthreads();
-
-  // ---- reverse sweep in pull form, longest sets first
 #pragma unroll 1
   for (int len = L - 1; len >= 1; --len) {
     if (live) {
@@ -315,7 +367,7 @@ __global__ void __launch_bounds__(2 * NEV) grad_pair_kernel(GradParams G) {
         Cx<float> GS;
         RV4<float> GK;
         pull_set<L, NEV>(J4, G4, P4, S2, gS2, g, c, d, GJ, GS, GK);
-        if (len >= 2) {  // J_Y = acc_Y / K_Y^2: store G_Y = df/dacc_Y, K-gradient of 1/K^2
+        if (len >= 2) {
           const RV4<float> KY = rsub(rv4(P4[(d + 1) * NEV + g]), rv4(P4[c * NEV + g]));
           const float inv = 1.f / mdot(KY, KY);
           const Cx<float> cj = conj_dot4(V.J(Y), GJ);
@@ -327,8 +379,15 @@ __global__ void __launch_bounds__(2 * NEV) grad_pair_kernel(GradParams G) {
             GJ.c[m].im *= inv;
           }
           gS2[Y * NEV + g] = make_float2(GS.re, GS.im);
+          st_cv4<NEV>(G4, Y, g, GJ);
+        } else {  // a single leg: df/deps of position c + 1
+          float *o = B.gr + (size_t)InRows<L>::eps(c) * cap + e;
+          o[0] = GJ.c[1].re;
+          o[cap] = GJ.c[2].re;
+          o[2 * cap] = GJ.c[3].re;
+          o[3 * cap] = GJ.c[1].im;
+          o[4 * cap] = GJ.c[2].im;
         }
-        st_cv4<NEV>(G4, Y, g, GJ);  // G_Y, or df/deps for a single leg
         float4 hi = GP4[(d + 1) * NEV + g], lo = GP4[c * NEV + g];
         GP4[(d + 1) * NEV + g] = make_float4(hi.x + GK.v[0], hi.y + GK.v[1], hi.z + GK.v[2], hi.w + GK.v[3]);
         GP4[c * NEV + g] = make_float4(lo.x - GK.v[0], lo.y - GK.v[1], lo.z - GK.v[2], lo.w - GK.v[3]);
@@ -336,57 +395,95 @@ __global__ void __launch_bounds__(2 * NEV) grad_pair_kernel(GradParams G) {
     }
     __syncthreads();
   }
-
-  // ---- outputs (lane 0): momentum gradients from the prefix rows, eps
-  // gradients of the single legs, kinematics recomputed for the adjoint
-  if (live && lane == 0) {
-    const float4 *GPo = (const float4 *)(smem_gp + PS::gp_off) + (size_t)(L + 1) * NEV;  // lane 1's row
-    RV4<float> gkp[L];  // df/dk of BG leg t = sum_{i > t} GP[i]
+  if (live && lane == 0) {  // df/dk of BG leg t = sum over i > t of both lanes' prefix rows
+    const float4 *GPo = (const float4 *)(smem_ga + PS::gp_off) + (size_t)(L + 1) * NEV;
     RV4<float> acc = {{0.f, 0.f, 0.f, 0.f}};
-#pragma unroll
+#pragma unroll 1
     for (int t = L - 1; t >= 0; --t) {
       const float4 a0 = GP4[(t + 1) * NEV + g], a1 = GPo[(t + 1) * NEV + g];
       acc.v[0] += a0.x + a1.x;
       acc.v[1] += a0.y + a1.y;
       acc.v[2] += a0.z + a1.z;
       acc.v[3] += a0.w + a1.w;
-      gkp[t] = acc;
-    }
-    GradKin<N, float> K;
-    grad_kinematics<N, float>(G.P, G.u + e * NU, G.order + e * N, K);
-    grad_outputs<N, float, float>(G, e, K, hel, f, [&](int a, double(&g4)[4], CV4<float> &ge) {
-      if (a == 0) {
-        ge = ge0;
-      } else {
+      float *ok = B.gr + (size_t)InRows<L>::k(t) * cap + e;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) g4[m] = (double)gkp[a - 1].v[m];
-        ge = ld_cv4<NEV>(G4, pair_tri<L>(a - 1, a - 1), g);
-      }
-    });
+      for (int m = 0; m < 4; ++m) ok[m * cap] = acc.v[m];
+    }
   }
 }
 
-// Gradient kernel launch for n: FP64 thread per event; the FP32 forms lane
-// pairs up to n = 8 (above, the table's shared memory leaves one block of two
-// warps per SM and the thread-per-event kernel measures faster).
 template <int N>
-cudaError_t launch_grad_n(bool fp64, const GradParams &G, cudaStream_t s) {
-  const unsigned blocks = (unsigned)((G.n_events + kBlock - 1) / kBlock);
+__global__ void __launch_bounds__(kBlock) grad_out_kernel(GradParams G, uint64_t first, int count, GradChunk B) {
+  constexpr int M = N - 2, L = N - 1, NU = 2 + 4 * M;
+  const int e = blockIdx.x * kBlock + threadIdx.x;
+  if (e >= count) return;
+  const uint64_t ev = first + (uint64_t)e;
+  GradKin<N, float> K;
+  grad_kinematics<N, float>(G.P, G.u + ev * NU, G.order + ev * N, K);
+  const uint32_t hel = G.hel[ev];
+  const size_t cap = (size_t)B.cap;
+  grad_outputs<N, float, float>(G, ev, K, hel, B.f[e], [&](int a, double(&g4)[4], CV4<float> &ge) {
+    const float *o = B.gr + (size_t)(a == 0 ? InRows<L>::eps0 : InRows<L>::eps(a - 1)) * cap + e;
+    ge = cv_zero<float>();
+    ge.c[1].re = o[0];
+    ge.c[2].re = o[cap];
+    ge.c[3].re = o[2 * cap];
+    ge.c[1].im = o[3 * cap];
+    ge.c[2].im = o[4 * cap];
+    if (a > 0) {
+      const float *ok = B.gr + (size_t)InRows<L>::k(a - 1) * cap + e;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) g4[m] = (double)ok[m * cap];
+    }
+  });
+}
+
+// Events per chunk of the split pipeline and its workspace (two row buffers
+// and |m|^2), sized like the generator's chunks to stay resident in L2.
+template <int N>
+__host__ inline int grad_chunk_cap(uint64_t n_events) {
+  constexpr int L = N - 1;
+  const size_t per_event = (size_t)2 * InRows<L>::rows * sizeof(float) + sizeof(double);
+  const uint64_t target = std::max<uint64_t>(128, ((64ull << 20) / per_event) / 128 * 128);
+  const uint64_t want = (std::max<uint64_t>(n_events, 1) + 127) / 128 * 128;
+  return (int)std::min(target, want);
+}
+
+template <int N>
+__host__ inline size_t grad_workspace_bytes(uint64_t n_events) {
+  constexpr int L = N - 1;
+  const size_t cap = (size_t)grad_chunk_cap<N>(n_events);
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  return 2 * al((size_t)InRows<L>::rows * cap * sizeof(float)) + al(cap * sizeof(double));
+}
+
+// Gradient launch for n: FP64 one kernel, thread per event (push form, tables
+// in local memory); FP32 forms the split pipeline over chunks of the
+// caller's workspace (grad_workspace_bytes).
+template <int N>
+cudaError_t launch_grad_n(bool fp64, const GradParams &G, void *ws, cudaStream_t s) {
   if (fp64) {
-    grad_kernel<N, double><<<blocks, kBlock, 0, s>>>(G);
+    grad_kernel<N, double><<<(unsigned)((G.n_events + kBlock - 1) / kBlock), kBlock, 0, s>>>(G);
     return cudaGetLastError();
   }
-  if constexpr (N > 8) {
-    grad_kernel<N, float><<<blocks, kBlock, 0, s>>>(G);
-    return cudaGetLastError();
-  } else {
-    constexpr int NEV = 32;
-    const cudaError_t e = allow_max_smem((const void *)grad_pair_kernel<N, NEV>);
-    if (e != cudaSuccess) return e;
-    grad_pair_kernel<N, NEV>
-        <<<(unsigned)((G.n_events + NEV - 1) / NEV), 2 * NEV, GradPairSmem<N - 1, NEV>::bytes, s>>>(G);
-    return cudaGetLastError();
+  constexpr int L = N - 1, NEV = 32;
+  const int cap = grad_chunk_cap<N>(G.n_events);
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  GradChunk B;
+  B.cap = cap;
+  B.in = (float *)ws;
+  B.gr = (float *)((char *)ws + al((size_t)InRows<L>::rows * cap * sizeof(float)));
+  B.f = (double *)((char *)B.gr + al((size_t)InRows<L>::rows * cap * sizeof(float)));
+  cudaError_t e = allow_max_smem((const void *)grad_amp_kernel<N, NEV>);
+  if (e != cudaSuccess) return e;
+  for (uint64_t off = 0; off < G.n_events; off += (uint64_t)cap) {
+    const int count = (int)std::min<uint64_t>((uint64_t)cap, G.n_events - off);
+    grad_in_kernel<N><<<(unsigned)((count + kBlock - 1) / kBlock), kBlock, 0, s>>>(G, off, count, B);
+    grad_amp_kernel<N, NEV><<<(unsigned)((count + NEV - 1) / NEV), 2 * NEV, GradPairSmem<L, NEV>::bytes, s>>>(count, B);
+    grad_out_kernel<N><<<(unsigned)((count + kBlock - 1) / kBlock), kBlock, 0, s>>>(G, off, count, B);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  return cudaSuccess;
 }
 
 }  // namespace tess

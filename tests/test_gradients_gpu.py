@@ -149,3 +149,41 @@ def test_autograd_function(ctx):
     assert torch.allclose(uu.grad, g["dw_du"], rtol=0, atol=0)
     assert torch.isclose(lx.grad, g["dw_dlnmu"].sum(), rtol=1e-12)
     assert torch.equal(w.detach(), tess.tess_gradients(ctx, proc, u, hel, order, want=("w",))["w"])
+
+
+@pytest.mark.parametrize("n", [6, 8])
+def test_chunk_boundaries_do_not_change_results(ctx, n):
+    """The FP32 forms run in chunks of the workspace; each event's arithmetic
+    is the same wherever its chunk starts, so results are bit-identical to a
+    call on a slice of the same draws.  E spans several chunks (ragged last)."""
+    E = 300_017
+    u, hel, order = tess.tess_draws(ctx, n, 13, 0, E)
+    proc = tess.process(n, precision=tess.TESS_FP32_CURRENTS)
+    full = tess.tess_gradients(ctx, proc, u, hel, order)
+    need = tess.tess_gradients_workspace_size(ctx, proc, E)
+    assert need > 0 and need < 80 << 20  # chunked, not sized for every event
+    for lo in (0, 65_000, 121_000, 190_000, E - 700):
+        hi = min(lo + 2_000, E)
+        part = tess.tess_gradients(ctx, proc, u[lo:hi].contiguous(), hel[lo:hi].contiguous(),
+                                   order[lo:hi].contiguous())
+        for key in ("w", "dw_du", "dw_dk", "dw_dlnmu"):
+            assert torch.equal(full[key][lo:hi], part[key]), (lo, key)
+
+
+def test_gradient_workspace_checks(ctx):
+    n, E = 7, 5000
+    u, hel, order = tess.tess_draws(ctx, n, 2, 0, E)
+    proc = tess.process(n, precision=tess.TESS_FP32_CURRENTS)
+    need = tess.tess_gradients_workspace_size(ctx, proc, E)
+    small = torch.empty(need // 8 - 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(tess.TessError) as e:
+        tess.tess_gradients(ctx, proc, u, hel, order, workspace=small)
+    assert e.value.code == tess.TESS_E_WORKSPACE
+    big = torch.empty(need // 8 + 64, dtype=torch.float64, device="cuda")
+    with pytest.raises(tess.TessError) as e:
+        tess.tess_gradients(ctx, proc, u, hel, order, workspace=big[1:])  # 8-byte offset
+    assert e.value.code == tess.TESS_E_WORKSPACE
+    a = tess.tess_gradients(ctx, proc, u, hel, order, workspace=big)
+    b = tess.tess_gradients(ctx, proc, u, hel, order)
+    assert all(torch.equal(a[k], b[k]) for k in a)
+    assert tess.tess_gradients_workspace_size(ctx, tess.process(n, precision=tess.TESS_FP64), E) == 0
