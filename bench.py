@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--events", type=int, default=0, help="override events per GPU (small cases for profiling)")
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-multiplicity batched measurement")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
+    ap.add_argument("--grad-only", action="store_true",
+                    help="time only the gradient path (gg -> 6 gluons; --events overrides 2^22) and print its line")
     ap.add_argument("--no-autotune", action="store_true", help="time the built-in default amplitude variant")
     ap.add_argument("--variant", default="", help="FORM,SCHEDULE: use this amplitude variant and chunk schedule "
                                                  "instead of autotuning (reproducible profiling)")
@@ -416,10 +418,10 @@ def bench_batched(torch, tess, ctx, flush, steps):
     return res
 
 
-def bench_gradients(torch, tess, ctx, steps):
+def bench_gradients(torch, tess, ctx, steps, E=1 << 22):
     """gg -> 6 gluons (n = 8), 2^22 events: weights and d w/d u, d w/d k,
-    d w/d ln mu_R (FP32 forward + adjoint amplitude, FP64 kinematics)."""
-    n, E = 8, 1 << 22
+    d w/d ln mu_R (FP32 forward + adjoint amplitude, FP64 boost)."""
+    n = 8
     u, hel, order = tess.tess_draws(ctx, n, 1, 0, E)
     proc = tess.process(n, precision=tess.TESS_FP32_CURRENTS)
     f = lambda: tess.tess_gradients(ctx, proc, u, hel, order)
@@ -538,9 +540,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_grad_only(args):
+    import torch
+    import paper_1002_3446_gb300 as tess
+    torch.cuda.set_device(0)
+    ctx = tess.tess_init(0)
+    for _ in range(max(0, args.warmup - 1)):  # bench_gradients runs one untimed call itself
+        bench_gradients(torch, tess, ctx, 1, args.events or (1 << 22))
+    r = bench_gradients(torch, tess, ctx, args.steps, args.events or (1 << 22))
+    print(json.dumps({"metric": "gg -> 6 gluons gradient events/s", "impl": "tess", **r}), flush=True)
+    tess.tess_destroy(ctx)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.grad_only:
+        run_grad_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_tess(args)

@@ -24,6 +24,7 @@
 #include <algorithm>
 
 #include "tess_grad.cuh"
+#include "tess_grad_f32.cuh"
 #include "tess_pair.cuh"
 
 namespace tess {
@@ -226,15 +227,15 @@ __global__ void __launch_bounds__(kBlock) grad_in_kernel(GradParams G, uint64_t 
   const int e = blockIdx.x * kBlock + threadIdx.x;
   if (e >= count) return;
   const uint64_t ev = first + (uint64_t)e;
-  GradKin<N, float> K;
-  grad_kinematics<N, float>(G.P, G.u + ev * NU, G.order + ev * N, K);
+  GradKinF<N> K;
+  grad_kin_f32<N>(G.P, G.u + ev * NU, G.order + ev * N, K);
   const uint32_t hel = G.hel[ev];
   const size_t cap = (size_t)B.cap;
 #pragma unroll
   for (int a = 0; a <= L; ++a) {
     RV4<float> k;
     CV4<float> eps;
-    grad_amp_input<N, float, float>(K, hel, a, k, eps);
+    grad_amp_input_f32<N>(K, hel, a, k, eps);
     float *o = B.in + (size_t)(a == 0 ? InRows<L>::eps0 : InRows<L>::eps(a - 1)) * cap + e;
     if (a > 0) {
       float *ok = B.in + (size_t)InRows<L>::k(a - 1) * cap + e;
@@ -418,11 +419,11 @@ __global__ void __launch_bounds__(kBlock) grad_out_kernel(GradParams G, uint64_t
   const int e = blockIdx.x * kBlock + threadIdx.x;
   if (e >= count) return;
   const uint64_t ev = first + (uint64_t)e;
-  GradKin<N, float> K;
-  grad_kinematics<N, float>(G.P, G.u + ev * NU, G.order + ev * N, K);
+  GradKinF<N> K;
+  grad_kin_f32<N>(G.P, G.u + ev * NU, G.order + ev * N, K);
   const uint32_t hel = G.hel[ev];
   const size_t cap = (size_t)B.cap;
-  grad_outputs<N, float, float>(G, ev, K, hel, B.f[e], [&](int a, double(&g4)[4], CV4<float> &ge) {
+  grad_outputs_f32<N>(G, ev, K, hel, B.f[e], [&](int a, float(&g4)[4], CV4<float> &ge) {
     const float *o = B.gr + (size_t)(a == 0 ? InRows<L>::eps0 : InRows<L>::eps(a - 1)) * cap + e;
     ge = cv_zero<float>();
     ge.c[1].re = o[0];
@@ -433,7 +434,7 @@ __global__ void __launch_bounds__(kBlock) grad_out_kernel(GradParams G, uint64_t
     if (a > 0) {
       const float *ok = B.gr + (size_t)InRows<L>::k(a - 1) * cap + e;
 #pragma unroll
-      for (int m = 0; m < 4; ++m) g4[m] = (double)ok[m * cap];
+      for (int m = 0; m < 4; ++m) g4[m] = ok[m * cap];
     }
   });
 }
