@@ -268,12 +268,14 @@ int tess_plan_info(const tess_ctx *ctx, const tess_process *proc, uint64_t n_eve
  * all multiplied by dL_dw[e] when dL_dw is given (a vector-Jacobian product).
  * The cuts are a step function: events failing them have w = 0 and zero
  * gradients.  TESS_FP64: every step FP64, one kernel.  FP32 forms: the
- * kinematics' precision split of tess_generate (FP32 seeds, cuts,
- * observables, PDF, alpha_s, polarisation basis; FP64 boost/rescale and its
- * adjoint, weight scalings) and an FP32 Berends-Giele forward pass and
- * reverse sweep, run as three kernels per chunk of events (kinematics ->
- * amplitude inputs; two threads per event for the recursion and its adjoint;
- * kinematics again -> outputs) through `workspace`:
+ * kinematics of TESS_FP32_DS (FP32 seeds, cuts, observables, PDF, alpha_s,
+ * polarisation basis; double-float boost/rescale rounded to FP32), an FP32
+ * Berends-Giele forward pass and reverse sweep and an FP32 kinematics
+ * adjoint (weights and the final scalings in FP64), run as three kernels per
+ * chunk of events (kinematics -> amplitude inputs; 2 to 8 threads per event
+ * for the recursion and its adjoint; kinematics again -> outputs, on a second
+ * stream of the context beside the next chunk; the call is ordered on
+ * `stream` as usual) through `workspace`:
  * tess_gradients_workspace_size(proc, n_events) bytes, device, 256-byte
  * aligned (0 bytes, NULL allowed, for TESS_FP64).  TESS_E_WORKSPACE if it is
  * missing or too small.  Any output pointer may be NULL. */

@@ -63,7 +63,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
-    if jobs or not os.path.exists(LIB):
+    if jobs or _stale(LIB, objs):  # also after a failed link left an older library
         tmp = LIB + f".{os.getpid()}.tmp"
         run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
         os.replace(tmp, LIB)

@@ -23,9 +23,12 @@ cudaError_t launch_me2_f64(int n, uint64_t n_events, const double *k, const uint
                            double *me2, cudaStream_t s);
 cudaError_t launch_me2_f32(int n, uint64_t n_events, const double *k, const uint8_t *order, const uint32_t *hel,
                            double *me2, cudaStream_t s);
-cudaError_t launch_grad_a(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s);
-cudaError_t launch_grad_b(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s);
-cudaError_t launch_grad_c(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s);
+cudaError_t launch_grad_a(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s,
+                           const GradStreams &gs);
+cudaError_t launch_grad_b(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s,
+                           const GradStreams &gs);
+cudaError_t launch_grad_c(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s,
+                           const GradStreams &gs);
 size_t grad_workspace_a(int n, uint64_t n_events);
 size_t grad_workspace_b(int n, uint64_t n_events);
 size_t grad_workspace_c(int n, uint64_t n_events);
@@ -134,6 +137,7 @@ __global__ void __launch_bounds__(kFinThreads) finalize_cols_kernel(const double
 }  // namespace tess
 
 constexpr int kMaxBranches = 16;
+constexpr int kGradSlot = kMaxBranches + 1;
 
 struct tess_ctx {
   int device = 0;
@@ -142,8 +146,9 @@ struct tess_ctx {
   // -1 = built-in default
   int form[2][TESS_MAX_N + 1];
   int sched[2][TESS_MAX_N + 1];
-  // streams/events of the overlapped pipeline: [0] plain calls, [1 + i] batch branch i
-  tess::OverlapRes ovl[kMaxBranches + 1];
+  // streams/events of the overlapped pipelines: [0] plain calls, [1 + i] batch
+  // branch i, [kGradSlot] the gradient pipeline
+  tess::OverlapRes ovl[kMaxBranches + 2];
   // batched generation: capture streams, fork/join events, cached graph
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t fork_ev = nullptr;
@@ -961,9 +966,21 @@ int tess_gradients(tess_ctx *ctx, const tess_process *proc, uint64_t n_events, c
     if (((uintptr_t)workspace) % 256 != 0) return fail(TESS_E_WORKSPACE, "workspace must be 256-byte aligned");
   }
   cudaStream_t s = (cudaStream_t)stream;
-  const cudaError_t e = n <= 8 ? tess::launch_grad_a(n, fp64, G, workspace, s)
-                               : (n <= 10 ? tess::launch_grad_b(n, fp64, G, workspace, s)
-                                          : tess::launch_grad_c(n, fp64, G, workspace, s));
+  tess::GradStreams gs;
+  if (!fp64) {
+    tess::OverlapRes *ov = nullptr;
+    if ((rc = overlap_res(ctx, kGradSlot, &ov))) return rc;
+    gs.aux = ov->aux;
+    gs.fork = ov->fork;
+    gs.join = ov->join;
+    for (int b = 0; b < 2; ++b) {
+      gs.g2done[b] = ov->k1done[b];
+      gs.g3done[b] = ov->k2done[b];
+    }
+  }
+  const cudaError_t e = n <= 8 ? tess::launch_grad_a(n, fp64, G, workspace, s, gs)
+                               : (n <= 10 ? tess::launch_grad_b(n, fp64, G, workspace, s, gs)
+                                          : tess::launch_grad_c(n, fp64, G, workspace, s, gs));
   if (e != cudaSuccess) return cuda_fail(e, "gradient kernel launch");
   return ok();
 }

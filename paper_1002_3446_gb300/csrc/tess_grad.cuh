@@ -27,6 +27,14 @@ struct GradParams {
   uint64_t n_events;
 };
 
+// Streams and events of the overlapped split pipeline of the FP32 forms
+// (aux == nullptr: all stages on the caller's stream).
+struct GradStreams {
+  cudaStream_t aux = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t g2done[2] = {nullptr, nullptr}, g3done[2] = {nullptr, nullptr};
+};
+
 // Berends-Giele forward pass and adjoint of f = |m|^2 for one ordering.
 // Inputs in colour-position order: k[a], eps[a] (a = 0..L-1), e0.  Outputs
 // the gradients g_k[a] (real), g_eps[a], g_e0 in the convention

@@ -3,13 +3,14 @@
 
 namespace tess {
 
-cudaError_t launch_grad_a(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s) {
+cudaError_t launch_grad_a(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s,
+                           const GradStreams &gs) {
   switch (n) {
-    case 4: return launch_grad_n<4>(fp64, G, ws, s);
-    case 5: return launch_grad_n<5>(fp64, G, ws, s);
-    case 6: return launch_grad_n<6>(fp64, G, ws, s);
-    case 7: return launch_grad_n<7>(fp64, G, ws, s);
-    case 8: return launch_grad_n<8>(fp64, G, ws, s);
+    case 4: return launch_grad_n<4>(fp64, G, ws, s, gs);
+    case 5: return launch_grad_n<5>(fp64, G, ws, s, gs);
+    case 6: return launch_grad_n<6>(fp64, G, ws, s, gs);
+    case 7: return launch_grad_n<7>(fp64, G, ws, s, gs);
+    case 8: return launch_grad_n<8>(fp64, G, ws, s, gs);
     default: return cudaErrorInvalidValue;
   }
 }

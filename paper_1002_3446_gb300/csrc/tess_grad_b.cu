@@ -3,10 +3,11 @@
 
 namespace tess {
 
-cudaError_t launch_grad_b(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s) {
+cudaError_t launch_grad_b(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s,
+                           const GradStreams &gs) {
   switch (n) {
-    case 9: return launch_grad_n<9>(fp64, G, ws, s);
-    case 10: return launch_grad_n<10>(fp64, G, ws, s);
+    case 9: return launch_grad_n<9>(fp64, G, ws, s, gs);
+    case 10: return launch_grad_n<10>(fp64, G, ws, s, gs);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -3,10 +3,11 @@
 
 namespace tess {
 
-cudaError_t launch_grad_c(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s) {
+cudaError_t launch_grad_c(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s,
+                           const GradStreams &gs) {
   switch (n) {
-    case 11: return launch_grad_n<11>(fp64, G, ws, s);
-    case 12: return launch_grad_n<12>(fp64, G, ws, s);
+    case 11: return launch_grad_n<11>(fp64, G, ws, s, gs);
+    case 12: return launch_grad_n<12>(fp64, G, ws, s, gs);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -18,12 +18,19 @@
 
 namespace tess {
 
+// Rare paths of the conversions below, kept out of line: the compiler cannot
+// turn a call into a predicated select, so the FP64 instructions in them are
+// issued only when taken.
+static __device__ __noinline__ float f32_of_f64_native(double x) { return (float)x; }
+static __device__ __noinline__ double f64_of_f32_native(float x, int k) { return ldexp((double)x, k); }
+static __device__ __noinline__ double f64_times_f32_native(double a, float x) { return a * (double)x; }
+
 // binary64 -> binary32, round to nearest even, in integer operations; exact
 // for results in the normal binary32 range (the native conversion otherwise).
 __device__ __forceinline__ float f32_of_f64(double x) {
   const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
   const int e = (int)((hi >> 20) & 0x7ffu) - 896;  // rebiased for binary32
-  if (e < 1 || e > 254) return (float)x;
+  if (e < 1 || e > 254) return f32_of_f64_native(x);
   const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);  // leading 23 mantissa bits
   const uint32_t rest = lo & 0x1fffffffu;                   // the 29 dropped bits
   const uint32_t up = (rest > 0x10000000u) | ((rest == 0x10000000u) & (m & 1u));
@@ -39,7 +46,7 @@ __device__ __forceinline__ double f64_of_f32_scaled(float x, int k) {
   if ((b & 0x7fffffffu) == 0u) return __hiloint2double((int)s, 0);
   const int e = (int)((b >> 23) & 0xffu);
   const int E = e + 896 + k;
-  if (e == 0 || e == 255 || E < 1 || E > 2046) return ldexp((double)x, k);
+  if (e == 0 || e == 255 || E < 1 || E > 2046) return f64_of_f32_native(x, k);
   return __hiloint2double((int)(s | ((uint32_t)E << 20) | ((b & 0x7fffffu) >> 3)), (int)(b << 29));
 }
 
@@ -58,7 +65,7 @@ struct ScaledOut {
     m = fast ? f32_of_f64(__hiloint2double((int)((hi & 0x800fffffu) | (1023u << 20)), __double2loint(a_))) : 0.f;
   }
   __device__ __forceinline__ double operator()(float x) const {
-    return fast ? f64_of_f32_scaled(m * x, k) : a * (double)x;
+    return fast ? f64_of_f32_scaled(m * x, k) : f64_times_f32_native(a, x);
   }
 };
 

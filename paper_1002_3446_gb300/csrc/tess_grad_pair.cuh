@@ -1,25 +1,24 @@
-// Event weights and gradients, FP32 current forms: two threads per event
-// sharing the event's Berends-Giele table in shared memory (the lane-pair
-// layout of tess_pair.cuh), with the reverse sweep in pull form.
+// Event weights and gradients, FP32 current forms: LN threads ("lanes") per
+// event sharing the event's Berends-Giele table in shared memory (the layout
+// of the lane-pair amplitude form, tess_pair.cuh), with the reverse sweep in
+// pull form.
 //
 // The reverse sweep of the recursion (Sec. 3) is usually written in push
 // form: each set X, in decreasing length, adds its contributions into the
 // gradient accumulators of its parts (left, right, and the three parts of
-// every four-vertex triple).  Two lanes sharing an event would then write the
+// every four-vertex triple).  Lanes sharing an event would then write the
 // same accumulators.  Here every set Y instead gathers its own gradient from
 // all of its parents X (longer sets, already final): as the left part of X =
 // [c..b], as the right part of X = [a..d], as the first or last part of a
 // triple of those X, and as the middle part of a triple of X = [a..b] with
 // a < c, d < b.  Every term is the same as in the push form; only who adds it
 // changes, so the lanes split the sets of one length (lane j: sets starting
-// at c = j, j + 2, ...) with no shared accumulator, one barrier per length.
+// at c = j, j + LN, ...) with no shared accumulator, one barrier per length.
 // Momentum gradients go through the prefix sums P (K[c..d] = P[d+1] - P[c]):
 // each set adds its K-gradient to P[d+1] and subtracts it from P[c] in the
 // lane's own prefix-gradient row; the rows are added in a fixed order at the
-// end.  Kinematics, polarisations and the output stage are those of the
-// thread-per-event kernel (grad_kinematics, grad_amp_input, grad_outputs),
-// run by lane 0; the kinematics are recomputed after the sweep instead of
-// being kept live across it.
+// end.  Kinematics, polarisations and the output stage run thread per event
+// in kernels of their own (the split pipeline below).
 #pragma once
 #include <algorithm>
 
@@ -29,14 +28,14 @@
 
 namespace tess {
 
-template <int L, int NEV>
+template <int L, int NEV, int LN>
 struct GradPairSmem {
   static constexpr int T = L * (L + 1) / 2;
   static constexpr size_t j_off = 0;                                               // float4 [2 T][NEV] currents
   static constexpr size_t g_off = j_off + (size_t)2 * T * NEV * sizeof(float4);    // float4 [2 T][NEV] adjoints
   static constexpr size_t p_off = g_off + (size_t)2 * T * NEV * sizeof(float4);    // float4 [L + 1][NEV]
-  static constexpr size_t gp_off = p_off + (size_t)(L + 1) * NEV * sizeof(float4);  // float4 [2][L + 1][NEV]
-  static constexpr size_t e_off = gp_off + (size_t)2 * (L + 1) * NEV * sizeof(float4);  // float4 [2][NEV]
+  static constexpr size_t gp_off = p_off + (size_t)(L + 1) * NEV * sizeof(float4);  // float4 [LN][L + 1][NEV]
+  static constexpr size_t e_off = gp_off + (size_t)LN * (L + 1) * NEV * sizeof(float4);  // float4 [2][NEV]
   static constexpr size_t s_off = e_off + (size_t)2 * NEV * sizeof(float4);        // float2 [T][NEV]
   static constexpr size_t gs_off = s_off + (size_t)T * NEV * sizeof(float2);       // float2 [T][NEV]
   static constexpr size_t bytes = gs_off + (size_t)T * NEV * sizeof(float2);
@@ -97,7 +96,7 @@ __device__ __forceinline__ void add_eta_conj(CV4<float> &g, const CV4<float> &v,
   }
 }
 
-// Gathers the gradient of set Y = [c..d] (L legs, lane-pair tables): GJ =
+// Gathers the gradient of set Y = [c..d] (L legs, shared tables): GJ =
 // df/dJ_Y, GS = df/dS_Y, GK = df/dK_Y, from all parents of Y.
 template <int L, int NEV>
 __device__ void pull_set(const float4 *J4, const float4 *G4, const float4 *P4, const float2 *S2, const float2 *gS2,
@@ -206,11 +205,11 @@ __device__ void pull_set(const float4 *J4, const float4 *G4, const float4 *P4, c
 //   G1 grad_in_kernel   thread per event: kinematics -> amplitude inputs
 //                       (rows as InRows: momenta in the unit c and the five
 //                       nonzero eps components per colour position)
-//   G2 grad_amp_kernel  lane pairs: recursion, |m|^2 and the pull-form
+//   G2 grad_amp_kernel  LN lanes per event: recursion, |m|^2 and the pull-form
 //                       reverse sweep -> df/dk and df/deps per position
 //   G3 grad_out_kernel  thread per event: kinematics again -> weights and
-//                       gradients (grad_outputs)
-// so that the table-bound middle stage keeps both lanes busy and the
+//                       gradients (grad_outputs_f32)
+// so that the table-bound middle stage keeps all its lanes busy and the
 // kinematics run at full occupancy.  The eps gradients keep the five
 // components the polarisation adjoint reads (Re x, y, z; Im x, y).
 // ---------------------------------------------------------------------------
@@ -250,10 +249,11 @@ __global__ void __launch_bounds__(kBlock) grad_in_kernel(GradParams G, uint64_t 
   }
 }
 
-template <int N, int NEV>
-__global__ void __launch_bounds__(2 * NEV) grad_amp_kernel(int count, GradChunk B) {
+template <int N, int NEV, int LN>
+__global__ void __launch_bounds__(LN * NEV) grad_amp_kernel(int count, GradChunk B) {
   constexpr int L = N - 1;
-  using PS = GradPairSmem<L, NEV>;
+  using PS = GradPairSmem<L, NEV, LN>;
+  static_assert(LN >= 2 && LN - 1 <= PS::T, "the lanes' partial top sums use adjoint-table slots 0 .. LN-2");
   extern __shared__ __align__(16) char smem_ga[];
   float4 *J4 = (float4 *)(smem_ga + PS::j_off), *G4 = (float4 *)(smem_ga + PS::g_off);
   float4 *P4 = (float4 *)(smem_ga + PS::p_off), *E4 = (float4 *)(smem_ga + PS::e_off);
@@ -278,9 +278,9 @@ __global__ void __launch_bounds__(2 * NEV) grad_amp_kernel(int count, GradChunk 
       load_eps(B.in + (size_t)InRows<L>::eps0 * cap + e, cap, e0);
       E4[g] = make_float4(e0.c[0].re, e0.c[0].im, e0.c[1].re, e0.c[1].im);
       E4[NEV + g] = make_float4(e0.c[2].re, e0.c[2].im, e0.c[3].re, e0.c[3].im);
-    } else {  // single-leg currents
+    } else {  // single-leg currents, shared by the other lanes
 #pragma unroll 1
-      for (int a = 0; a < L; ++a) {
+      for (int a = lane - 1; a < L; a += LN - 1) {
         CV4<float> ea;
         load_eps(B.in + (size_t)InRows<L>::eps(a) * cap + e, cap, ea);
         const int X = pair_tri<L>(a, a);
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(2 * NEV) grad_amp_kernel(int count, GradChunk 
   for (int len = 2; len < L; ++len) {
     if (live) {
 #pragma unroll 1
-      for (int a = lane; a + len - 1 < L; a += 2) {
+      for (int a = lane; a + len - 1 < L; a += LN) {
         const int b = a + len - 1;
         CV4<float> acc;
         Cx<float> s;
@@ -325,16 +325,20 @@ __global__ void __launch_bounds__(2 * NEV) grad_amp_kernel(int count, GradChunk 
   CV4<float> num = cv_zero<float>();
   if (live) {
     Cx<float> s;
-    pair_sums<L, NEV>(V, 0, L - 1, lane, 2, num, s);
-    if (lane == 1) V.setJ(top, num);  // the top current's slot is scratch
+    pair_sums<L, NEV>(V, 0, L - 1, lane, LN, num, s);
+    // the adjoint table is free until the sweep: scratch for the partial sums
+    if (lane > 0) st_cv4<NEV>(G4, lane - 1, g, num);
   }
   __syncthreads();
   if (live && lane == 0) {
-    const CV4<float> other = V.J(top);
+#pragma unroll 1
+    for (int j = 1; j < LN; ++j) {
+      const CV4<float> other = ld_cv4<NEV>(G4, j - 1, g);
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      num.c[m].re += other.c[m].re;
-      num.c[m].im += other.c[m].im;
+      for (int m = 0; m < 4; ++m) {
+        num.c[m].re += other.c[m].re;
+        num.c[m].im += other.c[m].im;
+      }
     }
     const float4 u0 = E4[g], v0 = E4[NEV + g];
     CV4<float> e0;
@@ -362,7 +366,7 @@ __global__ void __launch_bounds__(2 * NEV) grad_amp_kernel(int count, GradChunk 
   for (int len = L - 1; len >= 1; --len) {
     if (live) {
 #pragma unroll 1
-      for (int c = lane; c + len - 1 < L; c += 2) {
+      for (int c = lane; c + len - 1 < L; c += LN) {
         const int d = c + len - 1, Y = pair_tri<L>(c, d);
         CV4<float> GJ;
         Cx<float> GS;
@@ -396,16 +400,19 @@ __global__ void __launch_bounds__(2 * NEV) grad_amp_kernel(int count, GradChunk 
     }
     __syncthreads();
   }
-  if (live && lane == 0) {  // df/dk of BG leg t = sum over i > t of both lanes' prefix rows
-    const float4 *GPo = (const float4 *)(smem_ga + PS::gp_off) + (size_t)(L + 1) * NEV;
+  if (live && lane == 0) {  // df/dk of BG leg t = sum over i > t of every lane's prefix rows
+    const float4 *GPa = (const float4 *)(smem_ga + PS::gp_off);
     RV4<float> acc = {{0.f, 0.f, 0.f, 0.f}};
 #pragma unroll 1
     for (int t = L - 1; t >= 0; --t) {
-      const float4 a0 = GP4[(t + 1) * NEV + g], a1 = GPo[(t + 1) * NEV + g];
-      acc.v[0] += a0.x + a1.x;
-      acc.v[1] += a0.y + a1.y;
-      acc.v[2] += a0.z + a1.z;
-      acc.v[3] += a0.w + a1.w;
+#pragma unroll
+      for (int j = 0; j < LN; ++j) {
+        const float4 a0 = GPa[((size_t)j * (L + 1) + t + 1) * NEV + g];
+        acc.v[0] += a0.x;
+        acc.v[1] += a0.y;
+        acc.v[2] += a0.z;
+        acc.v[3] += a0.w;
+      }
       float *ok = B.gr + (size_t)InRows<L>::k(t) * cap + e;
 #pragma unroll
       for (int m = 0; m < 4; ++m) ok[m * cap] = acc.v[m];
@@ -439,51 +446,94 @@ __global__ void __launch_bounds__(kBlock) grad_out_kernel(GradParams G, uint64_t
   });
 }
 
-// Events per chunk of the split pipeline and its workspace (two row buffers
-// and |m|^2), sized like the generator's chunks to stay resident in L2.
+// Lanes per event of the amplitude stage (measured at 2^20 events: n <= 5
+// two, n = 6, 7 four, n >= 8 eight; more lanes split the sets of a length
+// finer and raise the warps per SM for the same table).
+template <int N>
+__host__ __device__ constexpr int grad_lanes() {
+  return N <= 5 ? 2 : (N <= 7 ? 4 : 8);
+}
+
+// Events per chunk of the split pipeline: two chunk buffers (input rows,
+// gradient rows, |m|^2) of about 32 MB each, together resident in L2 like
+// the generator's chunks.
 template <int N>
 __host__ inline int grad_chunk_cap(uint64_t n_events) {
   constexpr int L = N - 1;
   const size_t per_event = (size_t)2 * InRows<L>::rows * sizeof(float) + sizeof(double);
-  const uint64_t target = std::max<uint64_t>(128, ((64ull << 20) / per_event) / 128 * 128);
+  const uint64_t target = std::max<uint64_t>(128, ((32ull << 20) / per_event) / 128 * 128);
   const uint64_t want = (std::max<uint64_t>(n_events, 1) + 127) / 128 * 128;
   return (int)std::min(target, want);
 }
 
 template <int N>
-__host__ inline size_t grad_workspace_bytes(uint64_t n_events) {
+__host__ inline size_t grad_buffer_bytes(int cap) {
   constexpr int L = N - 1;
-  const size_t cap = (size_t)grad_chunk_cap<N>(n_events);
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  return 2 * al((size_t)InRows<L>::rows * cap * sizeof(float)) + al(cap * sizeof(double));
+  return 2 * al((size_t)InRows<L>::rows * cap * sizeof(float)) + al((size_t)cap * sizeof(double));
+}
+
+// One chunk buffer when a single chunk holds every event, else two.
+template <int N>
+__host__ inline size_t grad_workspace_bytes(uint64_t n_events) {
+  const int cap = grad_chunk_cap<N>(n_events);
+  return (n_events > (uint64_t)cap ? 2 : 1) * grad_buffer_bytes<N>(cap);
 }
 
 // Gradient launch for n: FP64 one kernel, thread per event (push form, tables
 // in local memory); FP32 forms the split pipeline over chunks of the
-// caller's workspace (grad_workspace_bytes).
+// caller's workspace (grad_workspace_bytes).  With two buffers and an aux
+// stream, G3 of chunk c (aux stream) runs beside G1/G2 of chunk c+1 (caller's
+// stream): the amplitude stage is held to few warps per SM by its shared
+// tables, and the output stage fills the issue slots it leaves.  Buffer c % 2
+// is rewritten by G2 of chunk c only after G3 of chunk c-2 has read it.
 template <int N>
-cudaError_t launch_grad_n(bool fp64, const GradParams &G, void *ws, cudaStream_t s) {
+cudaError_t launch_grad_n(bool fp64, const GradParams &G, void *ws, cudaStream_t s, const GradStreams &gs) {
   if (fp64) {
     grad_kernel<N, double><<<(unsigned)((G.n_events + kBlock - 1) / kBlock), kBlock, 0, s>>>(G);
     return cudaGetLastError();
   }
-  constexpr int L = N - 1, NEV = 32;
+  constexpr int L = N - 1, NEV = 32, LN = grad_lanes<N>();
   const int cap = grad_chunk_cap<N>(G.n_events);
+  const size_t bb = grad_buffer_bytes<N>(cap);
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  GradChunk B;
-  B.cap = cap;
-  B.in = (float *)ws;
-  B.gr = (float *)((char *)ws + al((size_t)InRows<L>::rows * cap * sizeof(float)));
-  B.f = (double *)((char *)B.gr + al((size_t)InRows<L>::rows * cap * sizeof(float)));
-  cudaError_t e = allow_max_smem((const void *)grad_amp_kernel<N, NEV>);
-  if (e != cudaSuccess) return e;
-  for (uint64_t off = 0; off < G.n_events; off += (uint64_t)cap) {
-    const int count = (int)std::min<uint64_t>((uint64_t)cap, G.n_events - off);
-    grad_in_kernel<N><<<(unsigned)((count + kBlock - 1) / kBlock), kBlock, 0, s>>>(G, off, count, B);
-    grad_amp_kernel<N, NEV><<<(unsigned)((count + NEV - 1) / NEV), 2 * NEV, GradPairSmem<L, NEV>::bytes, s>>>(count, B);
-    grad_out_kernel<N><<<(unsigned)((count + kBlock - 1) / kBlock), kBlock, 0, s>>>(G, off, count, B);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int nbuf = G.n_events > (uint64_t)cap ? 2 : 1;
+  GradChunk BB[2];
+  for (int b = 0; b < nbuf; ++b) {
+    char *base = (char *)ws + b * bb;
+    BB[b].cap = cap;
+    BB[b].in = (float *)base;
+    BB[b].gr = (float *)(base + al((size_t)InRows<L>::rows * cap * sizeof(float)));
+    BB[b].f = (double *)((char *)BB[b].gr + al((size_t)InRows<L>::rows * cap * sizeof(float)));
   }
+  cudaError_t e = allow_max_smem((const void *)grad_amp_kernel<N, NEV, LN>);
+  if (e != cudaSuccess) return e;
+  const bool ovl = nbuf == 2 && gs.aux != nullptr;
+  if (ovl && ((e = cudaEventRecord(gs.fork, s)) != cudaSuccess || (e = cudaStreamWaitEvent(gs.aux, gs.fork, 0)) != cudaSuccess))
+    return e;
+  int c = 0;
+  for (uint64_t off = 0; off < G.n_events; off += (uint64_t)cap, ++c) {
+    const int b = ovl ? (c & 1) : 0;
+    const GradChunk &B = BB[b];
+    const int count = (int)std::min<uint64_t>((uint64_t)cap, G.n_events - off);
+    const unsigned tb = (unsigned)((count + kBlock - 1) / kBlock);
+    grad_in_kernel<N><<<tb, kBlock, 0, s>>>(G, off, count, B);
+    if (ovl && c >= 2 && (e = cudaStreamWaitEvent(s, gs.g3done[b], 0)) != cudaSuccess) return e;
+    grad_amp_kernel<N, NEV, LN>
+        <<<(unsigned)((count + NEV - 1) / NEV), LN * NEV, GradPairSmem<L, NEV, LN>::bytes, s>>>(count, B);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ovl) {
+      if ((e = cudaEventRecord(gs.g2done[b], s)) != cudaSuccess || (e = cudaStreamWaitEvent(gs.aux, gs.g2done[b], 0)) != cudaSuccess)
+        return e;
+      grad_out_kernel<N><<<tb, kBlock, 0, gs.aux>>>(G, off, count, B);
+      if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaEventRecord(gs.g3done[b], gs.aux)) != cudaSuccess) return e;
+    } else {
+      grad_out_kernel<N><<<tb, kBlock, 0, s>>>(G, off, count, B);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  }
+  if (ovl && ((e = cudaEventRecord(gs.join, gs.aux)) != cudaSuccess || (e = cudaStreamWaitEvent(s, gs.join, 0)) != cudaSuccess))
+    return e;
   return cudaSuccess;
 }
 
