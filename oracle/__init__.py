@@ -79,6 +79,8 @@ def lib():
             h.orc_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32]
             h.orc_uniform.restype = ctypes.c_double
             h.orc_n_uniforms.argtypes = [ctypes.c_int]
+            h.orc_n_uniforms_mode.argtypes = [ctypes.c_int, ctypes.c_int]
+            h.orc_polvec_real.argtypes = [_D, ctypes.c_double, _D]
             h.orc_xg.argtypes = [ctypes.c_double]
             h.orc_xg.restype = ctypes.c_double
             h.orc_rambo.argtypes = [ctypes.c_int, ctypes.c_double, _D, _D]
@@ -118,8 +120,8 @@ def uniform(seed, ev, j):
     return lib().orc_uniform(seed, ev, j)
 
 
-def n_uniforms(n):
-    return lib().orc_n_uniforms(n)
+def n_uniforms(n, hel_mode=1):
+    return lib().orc_n_uniforms_mode(n, hel_mode)
 
 
 def xg(x):
@@ -153,6 +155,14 @@ def polvec(p, h):
     p = np.ascontiguousarray(p, dtype=np.float64)
     e = np.zeros(8)
     lib().orc_polvec(_dp(p), int(h), _dp(e))
+    return e[0::2] + 1j * e[1::2]
+
+
+def polvec_real(p, phi):
+    """Random-polarisation vector cos(phi) e1 + sin(phi) e2 of momentum p (real)."""
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    e = np.zeros(8)
+    lib().orc_polvec_real(_dp(p), float(phi), _dp(e))
     return e[0::2] + 1j * e[1::2]
 
 
@@ -191,7 +201,7 @@ def event(proc, seed, ev):
 def event_u(proc, u):
     """Event from caller-given uniforms (layout as the counter-based draws)."""
     u = np.ascontiguousarray(u, dtype=np.float64)
-    assert u.size >= n_uniforms(proc.n)
+    assert u.size >= n_uniforms(proc.n, proc.hel_mode)
     rec = np.zeros(14 + proc.n + 4 * proc.n)
     if lib().orc_event_record_u(ctypes.byref(proc), _dp(u), _dp(rec)):
         raise ValueError("oracle rejected the process")
@@ -229,8 +239,11 @@ def ulp_sensitivity(proc, seed, ev, trials=6):
 
 
 def uniforms(proc_or_n, seed, ev):
-    n = proc_or_n if isinstance(proc_or_n, int) else proc_or_n.n
-    return np.array([uniform(seed, ev, j) for j in range(n_uniforms(n))])
+    if isinstance(proc_or_n, int):
+        n, mode = proc_or_n, 1
+    else:
+        n, mode = proc_or_n.n, proc_or_n.hel_mode
+    return np.array([uniform(seed, ev, j) for j in range(n_uniforms(n, mode))])
 
 
 def generate(proc, seed, first, n_events, threads=None, per_event=True, hist=True):

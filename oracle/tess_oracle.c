@@ -42,7 +42,8 @@
 typedef struct {
   int n;               /* total gluons 4..12                              */
   int hel_mode;        /* 0: exact sum over helicities and orderings;     */
-                       /* 1: one helicity + ordering sampled per event    */
+                       /* 1: one helicity + ordering sampled per event;   */
+                       /* 2: random real polarisations + sampled ordering */
   double sqrt_s;       /* hadronic centre-of-mass energy, GeV             */
   double pt_min;       /* jet cuts, Sec. 4: pT > pt_min (GeV)             */
   double eta_max;      /*            |eta| < eta_max                      */
@@ -111,8 +112,11 @@ double orc_uniform(uint64_t seed, uint64_t ev, uint32_t j) {
  *   u[0], u[1]            x1, x2
  *   u[2 .. 2+4m)          Rambo, four per final-state gluon
  *   u[2+4m]               helicity word: top n bits of u
- *   u[3+4m .. 3+4m+n-2)   colour ordering (Fisher-Yates on {2..n})          */
+ *   u[3+4m .. 3+4m+n-2)   colour ordering (Fisher-Yates on {2..n})
+ * and, in the random-polarisation mode only,
+ *   u[1+4m+n .. 1+5m+2n)  polarisation angle of leg i = 0..n-1: phi = 2 pi u */
 int orc_n_uniforms(int n) { return 2 + 4 * (n - 2) + 1 + (n - 2); }
+int orc_n_uniforms_mode(int n, int hel_mode) { return orc_n_uniforms(n) + (hel_mode == 2 ? n : 0); }
 
 /* ========================================================================
  * 2. Parton luminosity.  Sec. 3, cross-section formula: the integrand has
@@ -242,6 +246,32 @@ void orc_polvec(const double *p, int h, double *eps) {
     double complex e = (h == 0) ? -(e1[mu] + I * e2[mu]) * r : (e1[mu] - I * e2[mu]) * r;
     eps[2 * mu] = creal(e);
     eps[2 * mu + 1] = cimag(e);
+  }
+}
+
+/* Random real polarisation, Sec. 3 (the paper's own choice): a random unit
+ * vector orthogonal to the gluon momentum, eps = cos(phi) e1 + sin(phi) e2
+ * with e1, e2 the transverse basis above and phi uniform in [0, 2 pi).
+ * The currents are then real.  Since the amplitude is linear in each eps and
+ * E[cos^2] = E[sin^2] = 1/2, E[cos sin] = 0 for independent angles,
+ * E_phi |m(eps(phi))|^2 = 2^-n sum over the basis {e1, e2}^n of |m|^2, and
+ * by completeness (eps_+, eps_- and e1, e2 span the same transverse plane,
+ * related by a unitary map) that basis sum equals the helicity sum: 2^n
+ * |m(eps(phi))|^2 estimates sum_h |m_h|^2 without bias.
+ * Output as orc_polvec: 4 complex (imaginary parts zero) = 8 doubles.      */
+void orc_polvec_real(const double *p, double phi, double *eps) {
+  const double px = p[1], py = p[2], pz = p[3];
+  const double pt = sqrt(px * px + py * py);
+  const double pabs = sqrt(px * px + py * py + pz * pz);
+  const double ct = pz / pabs, st = pt / pabs;
+  const double cf = pt > 0.0 ? px / pt : 1.0;
+  const double sf = pt > 0.0 ? py / pt : 0.0;
+  const double e1[4] = {0.0, ct * cf, ct * sf, -st};
+  const double e2[4] = {0.0, -sf, cf, 0.0};
+  const double c = cos(phi), s = sin(phi);
+  for (int mu = 0; mu < 4; ++mu) {
+    eps[2 * mu] = c * e1[mu] + s * e2[mu];
+    eps[2 * mu + 1] = 0.0;
   }
 }
 
@@ -408,6 +438,8 @@ void orc_amp(int n, const int *order, const double *k, const double *eps, int fo
  *    hel_mode 1: E = 2^n (n-1)! |A_D(1, sigma; h)|^2 for one sampled
  *    (sigma, h) -- the unbiased estimator of the same sum; with the
  *    final-state symmetry 1/(n-2)! this is the paper's (n-1)|m|^2.
+ *    hel_mode 2: the same with random real polarisations in place of the
+ *    sampled helicities (orc_polvec_real), Sec. 3's own choice.
  * ====================================================================== */
 typedef struct {
   double x1, x2, shat, y, alphas, ht, ptlead, rmin, me2, weight, pdf, phi;
@@ -473,6 +505,17 @@ static double amp2_dixon(int n, const int *order, const orc_event_out *o, int he
   return (a[0] * a[0] + a[1] * a[1]) / pow(2.0, n - 2);
 }
 
+/* |A_D|^2 with the random real polarisations of the event's angle draws */
+static double amp2_dixon_real(int n, const int *order, const orc_event_out *o, const double *uphi) {
+  double eps[ORC_MAXN * 8], pp[4], a[2];
+  for (int i = 0; i < n; ++i) {
+    physical_momentum(o, i, pp);
+    orc_polvec_real(pp, 2.0 * M_PI * uphi[i], eps + 8 * i);
+  }
+  orc_amp(n, order, &o->k[0][0], eps, 0, a);
+  return (a[0] * a[0] + a[1] * a[1]) / pow(2.0, n - 2);
+}
+
 /* next permutation of v[0..len) in lexicographic order; 0 at the end */
 static int next_perm(int *v, int len) {
   int i = len - 2;
@@ -497,9 +540,13 @@ static int event_from_uniforms(const orc_process *pr, const double *u, orc_event
       for (int h = 0; h < (1 << n); ++h) E += amp2_dixon(n, order, o, h);
     } while (next_perm(order + 1, n - 1));
   } else {
+    /* sampled ordering; one sampled helicity configuration (mode 1) or
+     * random real polarisations (mode 2): both 2^n (n-1)! |A_D|^2 */
     double fact = 1.0;
     for (int i = 2; i <= n - 1; ++i) fact *= i;
-    E = (double)(1 << n) * fact * amp2_dixon(n, o->perm, o, o->hel_bits);
+    const double a2 = pr->hel_mode == 2 ? amp2_dixon_real(n, o->perm, o, u + orc_n_uniforms(n))
+                                        : amp2_dixon(n, o->perm, o, o->hel_bits);
+    E = (double)(1 << n) * fact * a2;
   }
   o->me2 = E;
   double w = 0.0;
@@ -518,8 +565,8 @@ static int event_from_uniforms(const orc_process *pr, const double *u, orc_event
 
 int orc_event(const orc_process *pr, uint64_t seed, uint64_t ev, orc_event_out *o) {
   if (pr->n < 4 || pr->n > ORC_MAXN) return -1;
-  double u[64];
-  const int nu = orc_n_uniforms(pr->n);
+  double u[80];
+  const int nu = orc_n_uniforms_mode(pr->n, pr->hel_mode);
   for (int j = 0; j < nu; ++j) u[j] = orc_uniform(seed, ev, (uint32_t)j);
   return event_from_uniforms(pr, u, o);
 }
@@ -668,7 +715,7 @@ int orc_event_record(const orc_process *pr, uint64_t seed, uint64_t ev, double *
   return 0;
 }
 
-/* The same record for caller-given uniforms u[0 .. orc_n_uniforms(n)). */
+/* The same record for caller-given uniforms u[0 .. orc_n_uniforms_mode(n, mode)). */
 int orc_event_record_u(const orc_process *pr, const double *u, double *rec) {
   orc_event_out o;
   const int rc = event_from_uniforms(pr, u, &o);
