@@ -273,6 +273,9 @@ def run_tess(args):
                          "achieved_tflops": tess.bg_flops(n) * n64 / (statistics.mean(ms) * 1e-3) / 1e12,
                          "peak_tflops": FP64_PEAK_TFLOPS}
         del r64
+    if wl["hel"] == "sample" and wl["precision"] in ("fp32", "ds") and rank == 0:
+        extra["random_polarisation"] = bench_random_pol(torch, tess, ctx, wl, N, seed, first, flush,
+                                                        max(2, args.steps // 2), not args.no_autotune)
     if not args.no_batched and rank == 0:
         extra["batched_mixed"] = bench_batched(torch, tess, ctx, flush, max(2, args.steps // 2))
     if not args.no_grad and rank == 0:
@@ -415,6 +418,44 @@ def bench_batched(torch, tess, ctx, flush, steps):
     ms = timed(plain)
     res["plain_9_launches_autotuned"] = {"value": total / (ms * 1e-3), "ms": ms}
     res["unit"] = "events/s"
+    return res
+
+
+def bench_random_pol(torch, tess, ctx, wl, N, seed, first, flush, steps, autotune):
+    """The same workload with the paper's random real polarisations
+    (TESS_POL_RANDOM) instead of sampled helicities: real currents, so the
+    real-current amplitude forms apply; FLOPs from bg_flops_real."""
+    p = make_proc(tess, wl)
+    p.helicity_mode = tess.TESS_POL_RANDOM
+    r = tess.Run(ctx, p, N, per_event=("weight", "me2", "pass"))
+    if autotune:
+        tess.tess_autotune(ctx, p, min(N, 1 << 22), torch.zeros(tess.TESS_ACC_LEN, dtype=torch.float64,
+                                                                 device="cuda"), r.workspace)
+    ms = time_steps(torch, r, seed, first, steps, 2, flush)
+    info = tess.tess_plan_info(ctx, p, N)
+    serial_of = {tess.TESS_SCHED_OVERLAP: tess.TESS_SCHED_SERIAL,
+                 tess.TESS_SCHED_OVERLAP_TILES: tess.TESS_SCHED_SERIAL_TILES}
+    if info["schedule"] in serial_of:
+        tess.tess_select_variant(ctx, p, info["variant"], serial_of[info["schedule"]])
+    tess.tess_stage_timing(ctx, 1)
+    tess.tess_stage_times(ctx)
+    for _ in range(steps):
+        flush.fill_(1.0)
+        r.reset()
+        r.generate(seed, first)
+    st = tess.tess_stage_times(ctx)
+    tess.tess_stage_timing(ctx, 0)
+    tess.tess_select_variant(ctx, p, info["variant"], info["schedule"])
+    amp_ms, amp_n = st["amplitude"]
+    cap = plan_cap(tess, ctx, p, N)
+    res = {"value": N / (statistics.mean(ms) * 1e-3), "unit": "events/s", "ms_per_step": statistics.mean(ms),
+           "sigma_pb": r.result()[:2], "variant_schedule": [info["variant"], info["schedule"]]}
+    if amp_n:
+        launch_ms = amp_ms / amp_n
+        res["amplitude_kernel"] = {"tflops": tess.bg_flops_real(wl["n"]) * cap / (launch_ms * 1e-3) / 1e12,
+                                   "peak_tflops": FP32_PEAK_TFLOPS, "flops_per_event": tess.bg_flops_real(wl["n"]),
+                                   "ms_per_launch": launch_ms}
+    del r
     return res
 
 

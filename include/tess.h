@@ -60,6 +60,13 @@ extern "C" {
 #define TESS_HEL_SUM 0    /* exact sum over 2^n helicities and (n-1)! orderings (n <= 5) */
 #define TESS_HEL_SAMPLE 1 /* one helicity configuration and colour ordering per event,
                              sampled uniformly; estimator 2^n (n-1)! |A|^2          */
+#define TESS_POL_RANDOM 2 /* the paper's choice (Sec. 3): every polarisation vector a
+                             random unit vector orthogonal to the gluon momentum,
+                             eps = cos(phi) e1 + sin(phi) e2 with phi = 2 pi u from n
+                             more draws per event (after the colour-ordering draws),
+                             so the currents are real; one sampled colour ordering;
+                             estimator 2^n (n-1)! |A|^2 (unbiased for the helicity
+                             sum).  Not for tess_gradients or tess_generate_noalloc. */
 /* hist_observable */
 #define TESS_OBS_PTLEAD 0
 #define TESS_OBS_HT 1
@@ -70,7 +77,7 @@ extern "C" {
 typedef struct tess_process {
   int32_t n_gluons;        /* total gluons, TESS_MIN_N..TESS_MAX_N            */
   int32_t precision;       /* TESS_FP64, TESS_FP32_CURRENTS or TESS_FP32_DS   */
-  int32_t helicity_mode;   /* TESS_HEL_SUM or TESS_HEL_SAMPLE                 */
+  int32_t helicity_mode;   /* TESS_HEL_SUM, TESS_HEL_SAMPLE or TESS_POL_RANDOM */
   int32_t hist_observable; /* TESS_OBS_*                                      */
   int32_t hist_bins;       /* 0 = no histogram, else 1..TESS_MAX_BINS         */
   int32_t nf;              /* flavours in the one-loop running of alpha_s     */
@@ -186,8 +193,10 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
  * Times every amplitude-kernel variant built for (precision, n) of proc on
  * probe_events sampled events (one warm-up, median of three timed runs, with
  * proc's histogram settings) and makes the fastest the context's choice for
- * later calls with that (precision, n); the choice is keyed by (precision, n)
- * only, so tune with the histogram settings the calls will use.  Choose
+ * later calls with that (precision, polarisation kind, n) -- the kinds being
+ * helicity vectors (TESS_HEL_SAMPLE) and random real vectors
+ * (TESS_POL_RANDOM); the choice ignores the histogram settings, so tune with
+ * the ones the calls will use.  Choose
  * probe_events to span several chunks (a few million events) so that the
  * overlapped schedules can show their gain.  Variants (all one thread per
  * event): TESS_K2_REG (current table in registers), TESS_K2_ROWS32 /
@@ -196,8 +205,9 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
  * (register form compiled for more resident blocks), TESS_K2_REG_TMA (inputs
  * staged in shared memory by bulk copies), TESS_K2_REG_TMA_HI (the same for
  * more resident blocks), TESS_K2_PAIR32 / TESS_K2_PAIR64 (two threads per
- * event sharing its current table in shared memory) -- each under every chunk
- * schedule
+ * event sharing its current table in shared memory), and for TESS_POL_RANDOM
+ * only TESS_K2_REAL / TESS_K2_REAL_HI (real currents in registers) -- each
+ * under every chunk schedule
  * TESS_SCHED_* below.  acc_scratch: device, TESS_ACC_LEN doubles (not
  * written: the timed runs stop before folding their sums); workspace:
  * tess_workspace_size(proc, probe_events) bytes -- that size already covers
@@ -230,6 +240,8 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
 #define TESS_K2_REG_TMA_HI 6 /* the staged form compiled for 3 resident blocks per SM (FP32, n <= 7) */
 #define TESS_K2_PAIR32 7     /* two threads per event, table in shared memory, 32 events per block (FP32) */
 #define TESS_K2_PAIR64 8     /* the same with 64 events per block (FP32) */
+#define TESS_K2_REAL 9       /* real currents in registers (FP32, TESS_POL_RANDOM only, n <= 9) */
+#define TESS_K2_REAL_HI 10   /* the real form compiled for more resident blocks (FP32, TESS_POL_RANDOM, n <= 8) */
 #define TESS_SCHED_SERIAL 0
 #define TESS_SCHED_OVERLAP 1
 #define TESS_SCHED_OVERLAP_TILES 2
@@ -237,8 +249,9 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
 int tess_autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events, double *acc_scratch,
                   void *workspace, size_t workspace_bytes, void *stream, int *form_out);
 
-/* Sets the variant for (precision, n) of proc without timing: form one of
- * TESS_K2_* (-1: built-in default; a form not built for (precision, n) falls
+/* Sets the variant for (precision, polarisation kind, n) of proc without
+ * timing: form one of TESS_K2_* (-1: built-in default; a form not built for
+ * (precision, n) or, for the real-current forms, for helicity vectors falls
  * back to the default), schedule one of TESS_SCHED_* (-1: default, serial).
  * Takes effect for later calls; TESS_E_INVALID for values out of range.  A
  * workspace sized by tess_workspace_size covers every choice. */

@@ -215,17 +215,21 @@ def event_u(proc, u):
 
 def ulp_sensitivity(proc, seed, ev, trials=6):
     """Largest relative change of the oracle's |A|^2 and weight for event ev
-    when each x and Rambo uniform moves by at most one ulp: the difference a
+    when each x, Rambo (and polarisation-angle) uniform moves by at most one
+    ulp: the difference a
     one-ulp discrepancy in a transcendental function can cause downstream.
     Events near a zero of the amplitude have large values."""
     rng = np.random.default_rng(ev & 0xFFFFFFFF)
     u = uniforms(proc, seed, ev)
     base = event_u(proc, u)
     m = proc.n - 2
+    js = list(range(2 + 4 * m))
+    if proc.hel_mode == 2:  # and the polarisation angles
+        js += list(range(n_uniforms(proc.n, 1), n_uniforms(proc.n, 2)))
     worst = 0.0
     for _ in range(trials):
         up = u.copy()
-        for j in range(2 + 4 * m):
+        for j in js:
             r = rng.integers(3)
             if r:
                 up[j] = np.nextafter(up[j], 0.0 if r == 1 else 1.0)

@@ -29,10 +29,10 @@ TESS_E_NUMERICAL = -5
 TESS_MIN_N, TESS_MAX_N, TESS_MAX_BINS, TESS_ACC_LEN = 4, 12, 1024, 8
 TESS_NOALLOC_SCRATCH_BYTES, TESS_NOALLOC_MAX_BINS = 1 << 20, 254
 TESS_FP64, TESS_FP32_CURRENTS, TESS_FP32_DS = 0, 1, 2
-TESS_HEL_SUM, TESS_HEL_SAMPLE = 0, 1
+TESS_HEL_SUM, TESS_HEL_SAMPLE, TESS_POL_RANDOM = 0, 1, 2
 TESS_OBS_PTLEAD, TESS_OBS_HT, TESS_OBS_RMIN = 0, 1, 2
 TESS_K2_REG, TESS_K2_ROWS32, TESS_K2_ROWS64, TESS_K2_LOOP, TESS_K2_REG_HI, TESS_K2_REG_TMA = 0, 1, 2, 3, 4, 5
-TESS_K2_REG_TMA_HI, TESS_K2_PAIR32, TESS_K2_PAIR64 = 6, 7, 8
+TESS_K2_REG_TMA_HI, TESS_K2_PAIR32, TESS_K2_PAIR64, TESS_K2_REAL, TESS_K2_REAL_HI = 6, 7, 8, 9, 10
 TESS_SCHED_SERIAL, TESS_SCHED_OVERLAP, TESS_SCHED_OVERLAP_TILES, TESS_SCHED_SERIAL_TILES = 0, 1, 2, 3
 
 # Every symbol include/tess.h declares (checked by the ABI tests).
@@ -438,6 +438,23 @@ def bg_flops(n):
             total += 62 * ((ln - 1) * (ln - 2) // 2)
             total += 20 + (16 if ln < L else 0)
     return total + 30
+
+
+def bg_flops_real(n):
+    """The same count for the real-current recursion (random real
+    polarisations, tess_bg.cuh bg_amplitude_real): per split 52 (+1 for each
+    S term of a multi-leg side), per four-vertex triple 15, per set 12 plus 12
+    when propagated, and the final contraction 7."""
+    L = n - 1
+    total = 0
+    for ln in range(2, L + 1):
+        for a in range(0, L - ln + 1):
+            b = a + ln - 1
+            for i in range(a, b):
+                total += 52 + (1 if i > a else 0) + (1 if b > i + 1 else 0)
+            total += 15 * ((ln - 1) * (ln - 2) // 2)
+            total += 12 + (12 if ln < L else 0)
+    return total + 7
 
 
 def splits_and_triples(n):

@@ -36,13 +36,13 @@ cudaError_t launch_draws_a(int n, const EventParams &P, double *u, uint32_t *hel
 cudaError_t launch_draws_b(int n, const EventParams &P, double *u, uint32_t *hel, uint8_t *order, cudaStream_t s);
 cudaError_t launch_draws_c(int n, const EventParams &P, double *u, uint32_t *hel, uint8_t *order, cudaStream_t s);
 int plan_pipeline_f64(int n, int sm_count, uint64_t n_events, int hist_bins, int form, int sched,
-                      PipePlan *pl);
+                      bool real_eps, PipePlan *pl);
 int plan_pipeline_f32a(int n, int sm_count, uint64_t n_events, int hist_bins, int form, int sched,
-                      PipePlan *pl);
+                      bool real_eps, PipePlan *pl);
 int plan_pipeline_f32b(int n, int sm_count, uint64_t n_events, int hist_bins, int form, int sched,
-                      PipePlan *pl);
+                      bool real_eps, PipePlan *pl);
 int plan_pipeline_f32c(int n, int sm_count, uint64_t n_events, int hist_bins, int form, int sched,
-                      PipePlan *pl);
+                      bool real_eps, PipePlan *pl);
 cudaError_t run_pipeline_f64(int n, const EventParams &P, const PipePlan &pl, char *ws, cudaStream_t s,
                              const StageHook *hook, const OverlapRes *ov);
 cudaError_t run_pipeline_f32a(int n, const EventParams &P, const PipePlan &pl, char *ws, cudaStream_t s,
@@ -142,10 +142,10 @@ constexpr int kGradSlot = kMaxBranches + 1;
 struct tess_ctx {
   int device = 0;
   int sm_count = 1;
-  // tuned amplitude-kernel variant and chunk schedule per (precision, n);
-  // -1 = built-in default
-  int form[2][TESS_MAX_N + 1];
-  int sched[2][TESS_MAX_N + 1];
+  // tuned amplitude-kernel variant and chunk schedule per (precision,
+  // polarisation kind, n) -- see variant_slot; -1 = built-in default
+  int form[4][TESS_MAX_N + 1];
+  int sched[4][TESS_MAX_N + 1];
   // streams/events of the overlapped pipelines: [0] plain calls, [1 + i] batch
   // branch i, [kGradSlot] the gradient pipeline
   tess::OverlapRes ovl[kMaxBranches + 2];
@@ -216,8 +216,9 @@ int check_process(const tess_process *p) {
   if (p->precision != TESS_FP64 && p->precision != TESS_FP32_CURRENTS && p->precision != TESS_FP32_DS)
     return fail(TESS_E_INVALID, "precision = %d is not TESS_FP64, TESS_FP32_CURRENTS or TESS_FP32_DS",
                 p->precision);
-  if (p->helicity_mode != TESS_HEL_SUM && p->helicity_mode != TESS_HEL_SAMPLE)
-    return fail(TESS_E_INVALID, "helicity_mode = %d is not TESS_HEL_SUM or TESS_HEL_SAMPLE", p->helicity_mode);
+  if (p->helicity_mode != TESS_HEL_SUM && p->helicity_mode != TESS_HEL_SAMPLE && p->helicity_mode != TESS_POL_RANDOM)
+    return fail(TESS_E_INVALID, "helicity_mode = %d is not TESS_HEL_SUM, TESS_HEL_SAMPLE or TESS_POL_RANDOM",
+                p->helicity_mode);
   if (p->helicity_mode == TESS_HEL_SUM && p->n_gluons > 5)
     return fail(TESS_E_UNSUPPORTED, "TESS_HEL_SUM is built for n <= 5 (n = %d)", p->n_gluons);
   if (!finite_pos(p->sqrt_s)) return fail(TESS_E_INVALID, "sqrt_s must be finite and > 0");
@@ -293,20 +294,28 @@ double factorial(int k) {
 
 // Sampled helicity/ordering runs the two-kernel pipeline; the exact sum runs
 // the fused kernel.
-bool uses_pipeline(const tess_process *p) { return p->helicity_mode == TESS_HEL_SAMPLE; }
+bool uses_pipeline(const tess_process *p) { return p->helicity_mode != TESS_HEL_SUM; }
+
+// Variant-table row of a process: precision (FP64 / FP32) x polarisation
+// kind (complex helicity vectors / random real vectors, which admit the
+// real-current amplitude forms).
+int variant_slot(const tess_process *p) {
+  return (p->precision == TESS_FP64 ? 0 : 1) + (p->helicity_mode == TESS_POL_RANDOM ? 2 : 0);
+}
 
 int plan_with_form(const tess_ctx *ctx, const tess_process *p, uint64_t n_events, int form, int sched,
                    tess::PipePlan *pl) {
   const int n = p->n_gluons;
+  const bool real = p->helicity_mode == TESS_POL_RANDOM;
   int rc;
   if (p->precision == TESS_FP64)
-    rc = tess::plan_pipeline_f64(n, ctx->sm_count, n_events, p->hist_bins, form, sched, pl);
+    rc = tess::plan_pipeline_f64(n, ctx->sm_count, n_events, p->hist_bins, form, sched, real, pl);
   else if (n <= 7)
-    rc = tess::plan_pipeline_f32a(n, ctx->sm_count, n_events, p->hist_bins, form, sched, pl);
+    rc = tess::plan_pipeline_f32a(n, ctx->sm_count, n_events, p->hist_bins, form, sched, real, pl);
   else if (n <= 10)
-    rc = tess::plan_pipeline_f32b(n, ctx->sm_count, n_events, p->hist_bins, form, sched, pl);
+    rc = tess::plan_pipeline_f32b(n, ctx->sm_count, n_events, p->hist_bins, form, sched, real, pl);
   else
-    rc = tess::plan_pipeline_f32c(n, ctx->sm_count, n_events, p->hist_bins, form, sched, pl);
+    rc = tess::plan_pipeline_f32c(n, ctx->sm_count, n_events, p->hist_bins, form, sched, real, pl);
   if (rc)
     return fail(TESS_E_CUDA, "could not size the pipeline kernels (n %d, amplitude variant %d, schedule %d: %s)", n,
                 form, sched,
@@ -315,7 +324,7 @@ int plan_with_form(const tess_ctx *ctx, const tess_process *p, uint64_t n_events
 }
 
 int pipeline_plan(const tess_ctx *ctx, const tess_process *p, uint64_t n_events, tess::PipePlan *pl) {
-  const int pi = p->precision == TESS_FP64 ? 0 : 1;
+  const int pi = variant_slot(p);
   return plan_with_form(ctx, p, n_events, ctx->form[pi][p->n_gluons], ctx->sched[pi][p->n_gluons], pl);
 }
 
@@ -413,6 +422,7 @@ void fill_params(const tess_process *proc, uint64_t seed, uint64_t first_event, 
   P.ptlead = out->ptlead;
   P.rmin = out->rmin;
   P.kin_ds = proc->precision == TESS_FP32_DS;
+  P.pol_random = proc->helicity_mode == TESS_POL_RANDOM;
   P.S_hi = (float)P.S;
   P.S_lo = (float)(P.S - (double)P.S_hi);
   P.wk = P.wconst * P.lnxmin * P.lnxmin * P.phiconst * 0.5;
@@ -766,7 +776,7 @@ int tess_select_variant(tess_ctx *ctx, const tess_process *proc, int form, int s
   if (rc) return rc;
   if (form < -1 || form >= tess::K2_NFORMS) return fail(TESS_E_INVALID, "form out of range");
   if (schedule < -1 || schedule >= tess::SCHED_N) return fail(TESS_E_INVALID, "schedule out of range");
-  const int pi = proc->precision == TESS_FP64 ? 0 : 1;
+  const int pi = variant_slot(proc);
   ctx->form[pi][proc->n_gluons] = form;
   ctx->sched[pi][proc->n_gluons] = schedule;
   return ok();
@@ -805,7 +815,7 @@ int tess_autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events
   int rc = check_process(proc);
   if (rc) return rc;
   if (probe_events == 0) return fail(TESS_E_INVALID, "probe_events must be > 0");
-  const int pi = proc->precision == TESS_FP64 ? 0 : 1;
+  const int pi = variant_slot(proc);
   const int n = proc->n_gluons;
   if (!uses_pipeline(proc)) {  // the exact-sum mode has a single kernel
     *form_out = -1;
@@ -1125,6 +1135,8 @@ extern "C" int tess_generate_noalloc(tess_ctx *ctx, const tess_process *proc, ui
   if (!ctx) return fail(TESS_E_INVALID, "ctx is NULL");
   int rc = check_process(proc);
   if (rc) return rc;
+  if (proc->helicity_mode == TESS_POL_RANDOM)
+    return fail(TESS_E_UNSUPPORTED, "tess_generate_noalloc is built for TESS_HEL_SUM and TESS_HEL_SAMPLE");
   if (proc->hist_bins > TESS_NOALLOC_MAX_BINS)
     return fail(TESS_E_INVALID, "tess_generate_noalloc supports at most %d histogram bins (%d requested)",
                 TESS_NOALLOC_MAX_BINS, proc->hist_bins);

@@ -99,6 +99,69 @@ __device__ __forceinline__ Cx<R> bg_amplitude(const RV4<R> (&k)[L], const CV4<R>
   return mdot(e0, num);
 }
 
+// The same recursion with real polarisation vectors (Sec. 3's random real
+// polarisations): every current is then a real four-vector, so each complex
+// multiply-add of the helicity form becomes one real FMA.  Same splits, same
+// reorganised four-vertex sum, same operation order per component.
+template <typename R>
+__device__ __forceinline__ void raxpy(RV4<R> &acc, R s, const RV4<R> &v) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) acc.v[m] = fma(s, v.v[m], acc.v[m]);
+}
+
+template <typename R, int L>
+__device__ __forceinline__ R bg_amplitude_real(const RV4<R> (&k)[L], const RV4<R> (&e)[L], const RV4<R> &e0) {
+  RV4<R> J[L][L], K[L][L];
+  R S[L][L];
+#pragma unroll
+  for (int a = 0; a < L; ++a) {
+    J[a][a] = e[a];
+    K[a][a] = k[a];
+  }
+  RV4<R> num = {{R(0), R(0), R(0), R(0)}};
+#pragma unroll
+  for (int len = 2; len <= L; ++len) {
+#pragma unroll
+    for (int a = 0; a + len - 1 < L; ++a) {
+      const int b = a + len - 1;
+      K[a][b] = radd(K[a][b - 1], k[b]);
+      RV4<R> acc = {{R(0), R(0), R(0), R(0)}}, tri = {{R(0), R(0), R(0), R(0)}};
+      R sum = R(0);
+#pragma unroll
+      for (int i = a; i < b; ++i) {
+        // split l = [a..i], r = [i+1..b]
+        const RV4<R> &Jl = J[a][i];
+        const RV4<R> &Jr = J[i + 1][b];
+        const R d = mdot(Jl, Jr);
+        R cr = R(2) * mdot(Jl, K[i + 1][b]);
+        R cl = R(-2) * mdot(Jr, K[a][i]);
+        if (i > a) cr -= S[a][i];
+        if (b > i + 1) cl -= S[i + 1][b];
+        raxpy(acc, cr, Jr);
+        raxpy(acc, cl, Jl);
+        raxpy(acc, d, rsub(K[a][i], K[i + 1][b]));
+        sum += d;
+      }
+#pragma unroll
+      for (int i = a; i + 1 < b; ++i) {
+#pragma unroll
+        for (int j = i + 1; j < b; ++j) raxpy(tri, mdot(J[a][i], J[j + 1][b]), J[i + 1][j]);
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m) acc.v[m] = fma(R(2), tri.v[m], acc.v[m]);
+      if (len < L) {
+        const R inv = R(1) / mdot(K[a][b], K[a][b]);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) J[a][b].v[m] = acc.v[m] * inv;
+        S[a][b] = sum;
+      } else {
+        num = acc;
+      }
+    }
+  }
+  return mdot(e0, num);
+}
+
 // ---------------------------------------------------------------------------
 // Loop form of the same recursion for large tables (FP64, and FP32 with
 // n >= 8): runtime loops over lengths, sets and splits, the table in

@@ -104,6 +104,9 @@ inline cudaError_t encode_rows_map(CUtensorMap *map, const float *base, int rows
 //   K2_PAIR32  two threads per event, table in shared memory, 32 events
 //              per block (64 threads)                            FP32, any n
 //   K2_PAIR64  the same with 64 events per block (128 threads)   FP32, any n
+//   K2_REAL    register form with real currents, 128 threads; random real
+//              polarisations only (TESS_POL_RANDOM)               FP32, n <= 9
+//   K2_REAL_HI the real form compiled for more resident blocks   FP32, n <= 8
 enum K2Form {
   K2_REG = 0,
   K2_ROWS32 = 1,
@@ -114,15 +117,21 @@ enum K2Form {
   K2_REG_TMA_HI = 6,
   K2_PAIR32 = 7,
   K2_PAIR64 = 8,
-  K2_NFORMS = 9
+  K2_REAL = 9,
+  K2_REAL_HI = 10,
+  K2_NFORMS = 11
 };
 
+// real_eps: the call's polarisation vectors are real (random polarisations),
+// which the real-current forms require; every other form takes either kind.
 template <int N, typename R>
-constexpr bool k2_valid(int f) {
+constexpr bool k2_valid(int f, bool real_eps) {
   if constexpr (sizeof(R) == 8) {
     return f == K2_LOOP;
   } else {
     switch (f) {
+      case K2_REAL: return real_eps && N <= 9;
+      case K2_REAL_HI: return real_eps && N <= 8;
       case K2_REG:
       case K2_REG_TMA: return N <= 8;
       case K2_REG_HI:
@@ -148,8 +157,13 @@ struct K2V {
   static constexpr bool pair = F == K2_PAIR32 || F == K2_PAIR64;
   static constexpr int threads = pair ? 2 * block : block;  // block = events per tile
   static constexpr int hi_blocks = N >= 6 ? 3 : 4;
+  static constexpr int real_hi_blocks = N >= 8 ? 3 : 4;
   static void *fn() {
-    if constexpr (pair)
+    if constexpr (F == K2_REAL)
+      return (void *)bg_real_kernel<N, 128>;
+    else if constexpr (F == K2_REAL_HI)
+      return (void *)bg_real_kernel<N, 128, real_hi_blocks>;
+    else if constexpr (pair)
       return (void *)bg_pair_kernel<N, block>;
     else if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
       return (void *)bg_rows_kernel<N, block>;
@@ -178,7 +192,11 @@ struct K2V {
   // map: tensor map of B.in (staged forms only)
   static cudaError_t launch(const ChunkParams &C, const ChunkBuf<R> &B, double *partials, int grid, size_t smem,
                             cudaStream_t s, const CUtensorMap *map) {
-    if constexpr (pair)
+    if constexpr (F == K2_REAL)
+      bg_real_kernel<N, 128><<<grid, 128, smem, s>>>(C, B, partials);
+    else if constexpr (F == K2_REAL_HI)
+      bg_real_kernel<N, 128, real_hi_blocks><<<grid, 128, smem, s>>>(C, B, partials);
+    else if constexpr (pair)
       bg_pair_kernel<N, block><<<grid, threads, smem, s>>>(C, B, partials);
     else if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
       bg_rows_kernel<N, block><<<grid, block, smem, s>>>(C, B, partials);
@@ -204,6 +222,12 @@ auto with_form(int f, Fn &&fn) {
   } else {
     if (f == K2_PAIR32) return fn(K2V<N, R, K2_PAIR32>{});
     if (f == K2_PAIR64) return fn(K2V<N, R, K2_PAIR64>{});
+    if constexpr (N <= 9) {
+      if (f == K2_REAL) return fn(K2V<N, R, K2_REAL>{});
+    }
+    if constexpr (N <= 8) {
+      if (f == K2_REAL_HI) return fn(K2V<N, R, K2_REAL_HI>{});
+    }
     if constexpr (N <= 7) {
       if (f == K2_REG_HI) return fn(K2V<N, R, K2_REG_HI>{});
       if (f == K2_REG_TMA_HI) return fn(K2V<N, R, K2_REG_TMA_HI>{});
@@ -222,9 +246,10 @@ auto with_form(int f, Fn &&fn) {
 }
 
 template <int N, typename R>
-int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, int sched, PipePlan *pl) {
+int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, int sched, bool real_eps,
+                    PipePlan *pl) {
   constexpr int L = N - 1;
-  if (!k2_valid<N, R>(form)) form = k2_default<N, R>();
+  if (!k2_valid<N, R>(form, real_eps)) form = k2_default<N, R>();
   pl->form = form;
   const int rc = with_form<N, R>(form, [&](auto K) {
     using KV = decltype(K);
@@ -242,8 +267,10 @@ int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, in
   if (rc) return rc;
   if constexpr (sizeof(R) == 4) {
     pl->kin_smem = kin_tile_bytes<N>();
-    cudaError_t e = allow_max_smem((const void *)kin_ds_kernel<N>);
-    if (e == cudaSuccess) e = allow_max_smem((const void *)kin_kernel<N, float>);
+    cudaError_t e = allow_max_smem((const void *)kin_ds_kernel<N, false>);
+    if (e == cudaSuccess) e = allow_max_smem((const void *)kin_ds_kernel<N, true>);
+    if (e == cudaSuccess) e = allow_max_smem((const void *)kin_kernel<N, float, false>);
+    if (e == cudaSuccess) e = allow_max_smem((const void *)kin_kernel<N, float, true>);
     if (e != cudaSuccess) return (int)e;
   } else {
     pl->kin_smem = 0;
@@ -322,15 +349,7 @@ cudaError_t run_pipeline_t(const EventParams &P, const PipePlan &pl, char *ws, c
       C.count = (int)std::min<uint64_t>((uint64_t)pl.cap, P.n_events - off);
       if (c >= 2 && (e = cudaStreamWaitEvent(s, ov->k2done[b], 0)) != cudaSuccess) return e;
       if (hook) (*hook)(STAGE_KIN, true, s);
-      if constexpr (sizeof(R) == 4) {
-        if (P.kin_ds)
-          kin_ds_kernel<N><<<(C.count + kBlock - 1) / kBlock, kBlock, pl.kin_smem, s>>>(C, BB[b]);
-        else
-          kin_kernel<N, R><<<(C.count + kBlock - 1) / kBlock, kBlock, pl.kin_smem, s>>>(C, BB[b]);
-      } else {
-        kin_kernel<N, R><<<(C.count + kBlock - 1) / kBlock, kBlock, pl.kin_smem, s>>>(C, BB[b]);
-      }
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = launch_kin<N, R>(C, BB[b], pl.kin_smem, s)) != cudaSuccess) return e;
       if (hook) (*hook)(STAGE_KIN, false, s);
       if ((e = cudaEventRecord(ov->k1done[b], s)) != cudaSuccess) return e;
       if ((e = cudaStreamWaitEvent(a, ov->k1done[b], 0)) != cudaSuccess) return e;
@@ -349,15 +368,7 @@ cudaError_t run_pipeline_t(const EventParams &P, const PipePlan &pl, char *ws, c
     C.chunk_first = off;
     C.count = (int)std::min<uint64_t>((uint64_t)pl.cap, P.n_events - off);
     if (hook) (*hook)(STAGE_KIN, true, s);
-    if constexpr (sizeof(R) == 4) {
-      if (P.kin_ds)
-        kin_ds_kernel<N><<<(C.count + kBlock - 1) / kBlock, kBlock, pl.kin_smem, s>>>(C, B);
-      else
-        kin_kernel<N, R><<<(C.count + kBlock - 1) / kBlock, kBlock, pl.kin_smem, s>>>(C, B);
-    } else {
-      kin_kernel<N, R><<<(C.count + kBlock - 1) / kBlock, kBlock, pl.kin_smem, s>>>(C, B);
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_kin<N, R>(C, B, pl.kin_smem, s)) != cudaSuccess) return e;
     if (hook) (*hook)(STAGE_KIN, false, s);
     if (hook) (*hook)(STAGE_AMP, true, s);
     e = with_form<N, R>(pl.form,

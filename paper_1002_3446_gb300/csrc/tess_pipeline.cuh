@@ -112,8 +112,33 @@ __device__ __forceinline__ R r_unit(double u) {
   return v < R(1) ? v : R(1) - R(1) / R(1 << 24);
 }
 
+// Random real polarisations (Sec. 3): cos and sin of the angle phi = 2 pi u of
+// every leg, from the draws after the colour-ordering draws (positions
+// 2 + 4m + 1 + (n - 2) + l of the event's draw layout).
+template <int N, typename T>
+__device__ __forceinline__ void polarisation_angles(const EventParams &P, uint64_t ev, T (&cphi)[N], T (&sphi)[N]) {
+  constexpr uint32_t j0 = 2 + 4 * (N - 2) + 1 + (N - 2);
+#pragma unroll
+  for (uint32_t b = j0 >> 1; b <= (j0 + N - 1) >> 1; ++b) {
+    const uint4 w = event_block(P, ev, b);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int l = (int)(2 * b + h) - (int)j0;
+      if (l >= 0 && l < N) {
+        if constexpr (sizeof(T) == 4) {
+          const float u = h ? unit_f32(w.z, w.w) : unit_f32(w.x, w.y);
+          sincospif(2.f * u, &sphi[l], &cphi[l]);
+        } else {
+          const double u = h ? unit_from_words(w.z, w.w) : unit_from_words(w.x, w.y);
+          sincospi(2.0 * u, &sphi[l], &cphi[l]);
+        }
+      }
+    }
+  }
+}
+
 // K1, FP64 form: every step in double precision.
-template <int N, typename R>
+template <int N, typename R, bool RP>
 __device__ __forceinline__ void kin_generic(const ChunkParams &C, const ChunkBuf<R> &B, int e) {
   constexpr int M = N - 2, L = N - 1;
   const EventParams &P = C.P;
@@ -231,9 +256,12 @@ __device__ __forceinline__ void kin_generic(const ChunkParams &C, const ChunkBuf
   B.pass[e] = (uint8_t)pass;
   if (B.hval) B.hval[e] = P.hist_obs == 0 ? ptlead : (P.hist_obs == 1 ? ht : rmin);
 
-  // ---- colour ordering, helicities, polarisations (FP64 construction)
+  // ---- colour ordering, then sampled helicities or random real
+  // polarisations (FP64 construction)
   int perm[N];
   const uint32_t hel = sample_config<N>(P, ev, perm);
+  double cphi[N], sphi[N];
+  if constexpr (RP) polarisation_angles<N, double>(P, ev, cphi, sphi);
   double kp[N][4];
   int legp[N];
   gather_positions<N>(kk, perm, kp, legp);
@@ -243,7 +271,6 @@ __device__ __forceinline__ void kin_generic(const ChunkParams &C, const ChunkBuf
     const double sg = legp[a] < 2 ? -1.0 : 1.0;
     CV4<double> ep, em;
     polarisations<double>(sg * kp[a][1], sg * kp[a][2], sg * kp[a][3], ep, em);
-    const bool minus = (hel >> legp[a]) & 1u;
     using IR = InRows<L>;
     R *o = B.in + (size_t)(a == 0 ? IR::eps0 : IR::eps(a - 1)) * cap + e;
     if (a > 0) {
@@ -251,12 +278,29 @@ __device__ __forceinline__ void kin_generic(const ChunkParams &C, const ChunkBuf
 #pragma unroll
       for (int m = 0; m < 4; ++m) ok[(size_t)m * cap] = R(kp[a][m] * inv_rs);
     }
-    const CV4<double> &z = minus ? em : ep;
-    o[0] = R(z.c[1].re);
-    o[(size_t)cap] = R(z.c[2].re);
-    o[(size_t)2 * cap] = R(z.c[3].re);
-    o[(size_t)3 * cap] = R(z.c[1].im);
-    o[(size_t)4 * cap] = R(z.c[2].im);
+    if constexpr (RP) {
+      // eps_+ = -(e1 + i e2)/sqrt2, so cos e1 + sin e2 = -sqrt2 (cos Re + sin Im) eps_+
+      double cl = 0.0, sl = 0.0;
+#pragma unroll
+      for (int l = 0; l < N; ++l)
+        if (legp[a] == l) {
+          cl = cphi[l];
+          sl = sphi[l];
+        }
+      const double r = -1.41421356237309504880;
+#pragma unroll
+      for (int m = 1; m < 4; ++m) o[(size_t)(m - 1) * cap] = R(r * (cl * ep.c[m].re + sl * ep.c[m].im));
+      o[(size_t)3 * cap] = R(0);
+      o[(size_t)4 * cap] = R(0);
+    } else {
+      const bool minus = (hel >> legp[a]) & 1u;
+      const CV4<double> &z = minus ? em : ep;
+      o[0] = R(z.c[1].re);
+      o[(size_t)cap] = R(z.c[2].re);
+      o[(size_t)2 * cap] = R(z.c[3].re);
+      o[(size_t)3 * cap] = R(z.c[1].im);
+      o[(size_t)4 * cap] = R(z.c[2].im);
+    }
   }
 }
 
@@ -321,6 +365,45 @@ __device__ __forceinline__ void scatter_ordered(const EventParams &P, uint64_t e
   }
 }
 
+// As scatter_ordered, with the random real polarisation eps = cos(phi) e1 +
+// sin(phi) e2 of every leg (imaginary rows zero); the colour ordering comes
+// from the same draws.
+template <int N>
+__device__ __forceinline__ void scatter_ordered_real(const EventParams &P, uint64_t ev, float *tile,
+                                                     const float (&lk)[N][4], const float (&le1)[N][3],
+                                                     const float (&le2)[N][2]) {
+  constexpr int L = N - 1;
+  uint64_t posw;
+  sample_positions<N>(P, ev, &posw);
+  float cphi[N], sphi[N];
+  polarisation_angles<N, float>(P, ev, cphi, sphi);
+  float *col = tile + threadIdx.x;
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    const int p = (int)((posw >> (4 * l)) & 15ull);  // colour position of leg l
+    float *o = col + (p == 0 ? InRows<L>::eps0 : InRows<L>::eps(p - 1)) * kBlock;
+    if (p > 0) {
+      float *ok = col + InRows<L>::k(p - 1) * kBlock;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) ok[q * kBlock] = lk[l][q];
+    }
+    o[0] = fmaf(cphi[l], le1[l][0], sphi[l] * le2[l][0]);
+    o[1 * kBlock] = fmaf(cphi[l], le1[l][1], sphi[l] * le2[l][1]);
+    o[2 * kBlock] = cphi[l] * le1[l][2];
+    o[3 * kBlock] = 0.f;
+    o[4 * kBlock] = 0.f;
+  }
+}
+
+template <int N, bool RP>
+__device__ __forceinline__ void scatter_legs(const EventParams &P, uint64_t ev, float *tile, const float (&lk)[N][4],
+                                             const float (&le1)[N][3], const float (&le2)[N][2]) {
+  if constexpr (RP)
+    scatter_ordered_real<N>(P, ev, tile, lk, le1, le2);
+  else
+    scatter_ordered<N>(P, ev, tile, lk, le1, le2);
+}
+
 // Rows of the block's tile -> chunk buffer, one bulk copy per row issued by
 // warp 0.  The chunk buffers hold cap events, cap a multiple of kBlock, so a
 // whole tile is in bounds (columns of threads without an event carry no data
@@ -343,7 +426,7 @@ __device__ __forceinline__ void store_tile(const ChunkBuf<float> &B, const float
 // and rescale (conservation and masslessness), the polarisation Gram
 // products, the weight factor.  Helicity labels and colour ordering are
 // exact integer functions of the draws (identical in both forms).
-template <int N>
+template <int N, bool RP>
 __device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<float> &B, int e, float *tile) {
   constexpr int M = N - 2;
   const EventParams &P = C.P;
@@ -473,7 +556,7 @@ __device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<fl
     pol_basis_f32(pk[i][0], pk[i][1], pk[i][2], pk[i][3], le1[2 + i], le2[2 + i]);
   }
 
-  scatter_ordered<N>(P, ev, tile, lk, le1, le2);
+  scatter_legs<N, RP>(P, ev, tile, lk, le1, le2);
 }
 
 // Polarisation basis in FP32 from the FP32-rounded momentum components (each
@@ -504,7 +587,7 @@ __device__ __forceinline__ void pol_basis_rounded(float E, float px, float py, f
 // on this GPU), and the polarisation basis in FP32 from the rounded momenta.
 // The weight factor is assembled in FP32 with its power-of-two scale kept as
 // an exact exponent.
-template <int N>
+template <int N, bool RP>
 __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<float> &B, int e, float *tile) {
   constexpr int M = N - 2;
   const EventParams &P = C.P;
@@ -659,30 +742,51 @@ __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<floa
     for (int m = 0; m < 4; ++m) lk[2 + i][m] = pk[i][m] * sc;
     pol_basis_rounded(pk[i][0], pk[i][1], pk[i][2], pk[i][3], le1[2 + i], le2[2 + i]);
   }
-  scatter_ordered<N>(P, ev, tile, lk, le1, le2);
+  scatter_legs<N, RP>(P, ev, tile, lk, le1, le2);
 }
 
 // K1 kernels.  The FP32 forms take kin_tile_bytes<N>() of dynamic shared
 // memory for the block's output tile.
-template <int N, typename R>
+template <int N, typename R, bool RP = false>
 __global__ void __launch_bounds__(kBlock) kin_kernel(ChunkParams C, ChunkBuf<R> B) {
   const int e = blockIdx.x * kBlock + threadIdx.x;
   if constexpr (sizeof(R) == 4) {
     extern __shared__ __align__(128) float kin_tile[];
-    if (e < C.count) kin_fp32<N>(C, B, e, kin_tile);
+    if (e < C.count) kin_fp32<N, RP>(C, B, e, kin_tile);
     store_tile<N>(B, kin_tile);
   } else {
     if (e >= C.count) return;
-    kin_generic<N, R>(C, B, e);
+    kin_generic<N, R, RP>(C, B, e);
   }
 }
 
-template <int N>
+template <int N, bool RP = false>
 __global__ void __launch_bounds__(kBlock) kin_ds_kernel(ChunkParams C, ChunkBuf<float> B) {
   extern __shared__ __align__(128) float kin_tile[];
   const int e = blockIdx.x * kBlock + threadIdx.x;
-  if (e < C.count) kin_ds<N>(C, B, e, kin_tile);
+  if (e < C.count) kin_ds<N, RP>(C, B, e, kin_tile);
   store_tile<N>(B, kin_tile);
+}
+
+// The kinematics kernel of a call: double-float or plain form, sampled
+// helicities or random real polarisations.
+template <int N, typename R>
+__host__ inline cudaError_t launch_kin(const ChunkParams &C, const ChunkBuf<R> &B, int kin_smem, cudaStream_t s) {
+  const unsigned grid = (unsigned)((C.count + kBlock - 1) / kBlock);
+  if constexpr (sizeof(R) == 4) {
+    if (C.P.kin_ds) {
+      if (C.P.pol_random)
+        kin_ds_kernel<N, true><<<grid, kBlock, kin_smem, s>>>(C, B);
+      else
+        kin_ds_kernel<N, false><<<grid, kBlock, kin_smem, s>>>(C, B);
+      return cudaGetLastError();
+    }
+  }
+  if (C.P.pol_random)
+    kin_kernel<N, R, true><<<grid, kBlock, kin_smem, s>>>(C, B);
+  else
+    kin_kernel<N, R, false><<<grid, kBlock, kin_smem, s>>>(C, B);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -826,6 +930,50 @@ __global__ void __launch_bounds__(NB, MINB) bg_reg_kernel(ChunkParams C, ChunkBu
       load_eps(B.in + (size_t)InRows<L>::eps0 * B.cap + e, (size_t)B.cap, e0);
       const Cx<R> amp = bg_amplitude<R, L>(k, ev, e0);
       finish_event<NB, R>(C, B, e, amp2_of(amp), A, w, bin);
+    }
+    epi_tile<NB>(S, nb2, w, bin);
+  }
+  epi_flush<NB>(S, nb2, A, partials, C.P.hist_bins);
+}
+
+// K2, real-current register form (FP32, random real polarisations, n <= 9):
+// as bg_reg_kernel with the real recursion; reads the momentum rows and the
+// three real polarisation rows of every position (the imaginary rows, zero,
+// are not read).
+template <int N, int NB, int MINB = 1>
+__global__ void __launch_bounds__(NB, MINB) bg_real_kernel(ChunkParams C, ChunkBuf<float> B, double *partials) {
+  constexpr int L = N - 1;
+  extern __shared__ __align__(16) char smem_raw[];
+  const int nb2 = C.P.hist_bins > 0 ? C.P.hist_bins + 2 : 0;
+  EpiSmem<NB> S(smem_raw, nb2);
+  for (int i = threadIdx.x; i < 2 * nb2; i += NB) S.hw[i] = 0.0;
+  Accum<NB> A;
+  const int ntiles = (C.count + NB - 1) / NB;
+  const size_t cap = (size_t)B.cap;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int e = tile * NB + threadIdx.x;
+    double w = 0.0;
+    int bin = -1;
+    if (e < C.count) {
+      RV4<float> k[L], ev[L], e0;
+#pragma unroll
+      for (int a = 0; a < L; ++a) {
+        load_k(B.in + (size_t)InRows<L>::k(a) * cap + e, cap, k[a]);
+        const float *p = B.in + (size_t)InRows<L>::eps(a) * cap + e;
+        ev[a].v[0] = 0.f;
+        ev[a].v[1] = p[0];
+        ev[a].v[2] = p[cap];
+        ev[a].v[3] = p[2 * cap];
+      }
+      {
+        const float *p = B.in + (size_t)InRows<L>::eps0 * cap + e;
+        e0.v[0] = 0.f;
+        e0.v[1] = p[0];
+        e0.v[2] = p[cap];
+        e0.v[3] = p[2 * cap];
+      }
+      const float amp = bg_amplitude_real<float, L>(k, ev, e0);
+      finish_event<NB, float>(C, B, e, amp2_of(Cx<float>{amp, 0.f}), A, w, bin);
     }
     epi_tile<NB>(S, nb2, w, bin);
   }

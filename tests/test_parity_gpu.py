@@ -19,10 +19,10 @@ oracle's inputs; nothing is derived from the CUDA path):
     are rounding noise: both sides must be below 1e-20 (FP64) / 1e-6 (FP32)
     of the event's MHV scale |A(legs 1, 2 with the odd label)|^2.
   Observables: relative 1e-10 (Rambo's final boost amplifies rounding for
-    two nearly collinear seeds); 1e-4 in the FP32 form, whose Rambo seeds,
-    cuts and observables are FP32 (the FP64 boost amplifies the seeds'
-    rounding by up to ~gamma^2; flags may then differ within 1e-4 of a
-    threshold).  Cross sections and histogram bins:
+    two nearly collinear seeds); in the FP32 forms, whose Rambo seeds, cuts
+    and observables are FP32, 1e-4 or 8 ulp(FP32) x gamma^2 of the event's
+    boost if larger (the boost amplifies the seeds' rounding by up to
+    ~gamma^2; flags may then differ within that distance of a threshold).  Cross sections and histogram bins:
     relative 1e-10 plus an absolute 1e-12 of the total.
   A pass flag may differ only when a cut quantity lies within 1e-9 of its
     threshold.
@@ -108,6 +108,22 @@ def ulp_sensitivity(orc, op, seed, ev):
     return orc.ulp_sensitivity(op, seed, ev)
 
 
+def rambo_gamma(orc, op, seed, ev):
+    """Lorentz factor gamma = Q0/M of Rambo's final boost for event ev (from
+    its seed momenta): the boost amplifies the FP32 seeds' relative rounding
+    by up to ~gamma^2, which sets the FP32 forms' observable tolerance."""
+    u = orc.uniforms(op, seed, ev)
+    m = op.n - 2
+    Q = np.zeros(4)
+    for i in range(m):
+        a1, a2, b1, b2 = u[2 + 4 * i: 6 + 4 * i]
+        c = 2 * a1 - 1
+        s = math.sqrt(max(1 - c * c, 0.0))
+        q0 = -math.log(b1 * b2)
+        Q += q0 * np.array([1.0, s * math.cos(2 * math.pi * a2), s * math.sin(2 * math.pi * a2), c])
+    return Q[0] / math.sqrt(max(Q[0] ** 2 - Q[1] ** 2 - Q[2] ** 2 - Q[3] ** 2, 1e-300))
+
+
 def compare_events(orc, p, g, seed, first, idx, stats=None):
     """Per-event comparison of GPU outputs at positions idx with the oracle."""
     op = orc_proc(orc, p)
@@ -122,10 +138,13 @@ def compare_events(orc, p, g, seed, first, idx, stats=None):
     for i in idx:
         ev = first + int(i)
         r = orc.event(op, seed, ev)
+        etol = otol
+        if fp32:  # FP32 seeds through the boost: a few ulp times gamma^2
+            etol = max(otol, 8 * 2.0**-24 * rambo_gamma(orc, op, seed, ev) ** 2)
         for key in ("ht", "ptlead", "rmin"):
-            assert np.isclose(g[key][i], r[key], rtol=otol, atol=0), (key, i, g[key][i], r[key])
+            assert np.isclose(g[key][i], r[key], rtol=etol, atol=0), (key, i, g[key][i], r[key], etol)
         if bool(g["pass"][i]) != r["pass"]:
-            assert near_cut(orc, p, r["k"], r["y"], otol), f"pass flag differs away from a cut boundary (event {i})"
+            assert near_cut(orc, p, r["k"], r["y"], etol), f"pass flag differs away from a cut boundary (event {i})"
             flips += 1
             continue
         if p.helicity_mode == tess.TESS_HEL_SAMPLE and vanishing(r["hel_bits"], n):
@@ -245,6 +264,52 @@ def test_sampled_events_fp32_currents(ctx, orc, n, precision):
     assert st["median"] < 1e-5 and st["p99"] < 5e-2 and st["weighted"] < 1e-4
 
 
+@pytest.mark.parametrize("n", [4, 5, 6, 8, 10, 12])
+def test_random_polarisation_fp64(ctx, orc, n):
+    """Random real polarisations (Sec. 3) against the oracle's mode 2, FP64."""
+    p = tess.process(n, precision=tess.TESS_FP64, helicity_mode=tess.TESS_POL_RANDOM,
+                     pt_min=30.0 if n >= 10 else 20.0, hist_bins=20, hist_observable=tess.TESS_OBS_PTLEAD,
+                     hist_lo=20.0, hist_hi=1020.0)
+    N = 2 * 128 + 29 if n >= 10 else 4 * 128 + 29
+    first = (1 << 33) + 11
+    g = gpu_generate(ctx, p, 4, first, N)
+    st = {}
+    compare_events(orc, p, g, 4, first, np.arange(N), st)
+    print(f"random polarisation FP64 n={n}: {st}")
+    r = orc.generate(orc_proc(orc, p), 4, first, N)
+    assert np.isclose(g["acc"][0] + g["acc"][4], r["acc"][0], rtol=1e-10)
+    assert g["acc"][2] == r["acc"][2]
+    assert np.allclose(g["hist_w"], r["hist_w"], rtol=1e-10, atol=1e-12 * r["hist_w"].sum())
+
+
+@pytest.mark.parametrize("n", [4, 6, 8, 10, 12])
+@pytest.mark.parametrize("precision", [tess.TESS_FP32_CURRENTS, tess.TESS_FP32_DS])
+def test_random_polarisation_fp32(ctx, orc, n, precision):
+    p = tess.process(n, precision=precision, helicity_mode=tess.TESS_POL_RANDOM, pt_min=30.0 if n >= 10 else 20.0)
+    N = 4 * 128 + 17
+    g = gpu_generate(ctx, p, 8, 5, N)
+    st = {}
+    compare_events(orc, p, g, 8, 5, np.arange(N), st)
+    print(f"random polarisation FP32 precision={precision} n={n}: median {st['median']:.2e} p99 {st['p99']:.2e} "
+          f"weighted {st['weighted']:.2e} flips {st['flips']}")
+    assert st["median"] < 1e-5 and st["p99"] < 5e-2 and st["weighted"] < 1e-4
+
+
+def test_random_polarisation_sigma_matches_helicity_sampling(ctx):
+    """Both estimators are unbiased for the same cross section (n = 6,
+    2^22 events each, disjoint from any other test's draws)."""
+    res = []
+    for mode in (tess.TESS_HEL_SAMPLE, tess.TESS_POL_RANDOM):
+        p = tess.process(6, precision=tess.TESS_FP32_DS, helicity_mode=mode)
+        run = tess.Run(ctx, p, 1 << 22)
+        run.generate(31, 0)
+        res.append(run.result())
+    (s1, e1), (s2, e2) = res[0][:2], res[1][:2]
+    print(f"sigma: sampled helicities {s1:.5e} +- {e1:.1e}, random polarisations {s2:.5e} +- {e2:.1e}")
+    assert abs(s1 - s2) < 4 * math.hypot(e1, e2)
+    assert res[0][2] == res[1][2]  # the same kinematics pass the same cuts
+
+
 FORMS_BY_N = {
     4: ["REG", "REG_HI", "REG_TMA", "REG_TMA_HI", "PAIR32", "PAIR64"],
     6: ["REG", "REG_HI", "REG_TMA", "REG_TMA_HI", "ROWS32", "ROWS64", "PAIR32", "PAIR64"],
@@ -272,6 +337,55 @@ def test_every_amplitude_variant_against_oracle(ctx, orc, n, form):
     compare_events(orc, p, g, 13, 5, np.arange(N), st)
     print(f"{form} n={n}: median {st['median']:.2e} p99 {st['p99']:.2e} weighted {st['weighted']:.2e}")
     assert st["median"] < 1e-5 and st["p99"] < 5e-2 and st["weighted"] < 1e-4
+
+
+REAL_FORMS_BY_N = {
+    4: ["REAL", "REAL_HI", "REG", "PAIR32"],
+    6: ["REAL", "REAL_HI", "REG_HI", "ROWS32", "PAIR64"],
+    8: ["REAL", "REAL_HI", "ROWS64", "PAIR32"],
+    9: ["REAL", "ROWS32", "PAIR32"],
+    10: ["ROWS32", "PAIR64"],
+}
+
+
+@pytest.mark.parametrize("n,form", [(n, f) for n, fs in REAL_FORMS_BY_N.items() for f in fs])
+def test_random_polarisation_variants_against_oracle(ctx, orc, n, form):
+    """Random real polarisations through each amplitude variant that takes
+    them: the real-current forms and (imaginary parts zero) the complex
+    ones, against the oracle's mode 2 with the FP32 criteria."""
+    p = tess.process(n, precision=tess.TESS_FP32_DS, helicity_mode=tess.TESS_POL_RANDOM,
+                     pt_min=30.0 if n >= 10 else 20.0)
+    code = getattr(tess, "TESS_K2_" + form)
+    tess.tess_select_variant(ctx, p, code, tess.TESS_SCHED_SERIAL)
+    try:
+        assert tess.tess_plan_info(ctx, p, 1000)["variant"] == code
+        N = 1000
+        g = gpu_generate(ctx, p, 17, 3, N)
+    finally:
+        tess.tess_select_variant(ctx, p)
+    st = {}
+    compare_events(orc, p, g, 17, 3, np.arange(N), st)
+    print(f"random polarisation {form} n={n}: median {st['median']:.2e} p99 {st['p99']:.2e} "
+          f"weighted {st['weighted']:.2e}")
+    assert st["median"] < 1e-5 and st["p99"] < 5e-2 and st["weighted"] < 1e-4
+
+
+def test_real_forms_refused_for_helicity_vectors(ctx):
+    """The real-current forms need real polarisations: with sampled helicities
+    the plan falls back to a complex form, and the two polarisation kinds
+    keep separate variant choices."""
+    ph = tess.process(6, precision=tess.TESS_FP32_DS)
+    pr = tess.process(6, precision=tess.TESS_FP32_DS, helicity_mode=tess.TESS_POL_RANDOM)
+    try:
+        tess.tess_select_variant(ctx, ph, tess.TESS_K2_REAL, tess.TESS_SCHED_SERIAL)
+        assert tess.tess_plan_info(ctx, ph, 10000)["variant"] not in (tess.TESS_K2_REAL, tess.TESS_K2_REAL_HI)
+        tess.tess_select_variant(ctx, pr, tess.TESS_K2_REAL_HI, tess.TESS_SCHED_SERIAL)
+        assert tess.tess_plan_info(ctx, pr, 10000)["variant"] == tess.TESS_K2_REAL_HI
+        tess.tess_select_variant(ctx, ph, tess.TESS_K2_REG, tess.TESS_SCHED_SERIAL)
+        assert tess.tess_plan_info(ctx, pr, 10000)["variant"] == tess.TESS_K2_REAL_HI
+    finally:
+        tess.tess_select_variant(ctx, ph)
+        tess.tess_select_variant(ctx, pr)
 
 
 # ---------------------------------------------------------------- full-size configurations
