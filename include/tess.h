@@ -242,6 +242,7 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
 #define TESS_K2_PAIR64 8     /* the same with 64 events per block (FP32) */
 #define TESS_K2_REAL 9       /* real currents in registers (FP32, TESS_POL_RANDOM only, n <= 9) */
 #define TESS_K2_REAL_HI 10   /* the real form compiled for more resident blocks (FP32, TESS_POL_RANDOM, n <= 8) */
+#define TESS_K2_ROWS_REAL 11 /* row form with real currents, 64 threads (FP32, TESS_POL_RANDOM, n >= 8) */
 #define TESS_SCHED_SERIAL 0
 #define TESS_SCHED_OVERLAP 1
 #define TESS_SCHED_OVERLAP_TILES 2

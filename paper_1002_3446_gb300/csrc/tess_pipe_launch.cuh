@@ -107,6 +107,8 @@ inline cudaError_t encode_rows_map(CUtensorMap *map, const float *base, int rows
 //   K2_REAL    register form with real currents, 128 threads; random real
 //              polarisations only (TESS_POL_RANDOM)               FP32, n <= 9
 //   K2_REAL_HI the real form compiled for more resident blocks   FP32, n <= 8
+//   K2_ROWS_REAL  row form with real currents, 64 threads; random real
+//              polarisations only                                 FP32, n >= 8
 enum K2Form {
   K2_REG = 0,
   K2_ROWS32 = 1,
@@ -119,7 +121,8 @@ enum K2Form {
   K2_PAIR64 = 8,
   K2_REAL = 9,
   K2_REAL_HI = 10,
-  K2_NFORMS = 11
+  K2_ROWS_REAL = 11,
+  K2_NFORMS = 12
 };
 
 // real_eps: the call's polarisation vectors are real (random polarisations),
@@ -132,6 +135,7 @@ constexpr bool k2_valid(int f, bool real_eps) {
     switch (f) {
       case K2_REAL: return real_eps && N <= 9;
       case K2_REAL_HI: return real_eps && N <= 8;
+      case K2_ROWS_REAL: return real_eps && N >= 8;
       case K2_REG:
       case K2_REG_TMA: return N <= 8;
       case K2_REG_HI:
@@ -153,19 +157,25 @@ constexpr int k2_default() {
 template <int N, typename R, int F>
 struct K2V {
   static constexpr int L = N - 1;
-  static constexpr int block = (F == K2_ROWS32 || F == K2_PAIR32) ? 32 : ((F == K2_ROWS64 || F == K2_PAIR64) ? 64 : 128);
+  static constexpr int block =
+      (F == K2_ROWS32 || F == K2_PAIR32)
+          ? 32
+          : ((F == K2_ROWS64 || F == K2_PAIR64 || F == K2_ROWS_REAL) ? 64 : 128);
+  static constexpr bool rows = F == K2_ROWS32 || F == K2_ROWS64;
   static constexpr bool pair = F == K2_PAIR32 || F == K2_PAIR64;
   static constexpr int threads = pair ? 2 * block : block;  // block = events per tile
   static constexpr int hi_blocks = N >= 6 ? 3 : 4;
   static constexpr int real_hi_blocks = N >= 8 ? 3 : 4;
   static void *fn() {
-    if constexpr (F == K2_REAL)
+    if constexpr (F == K2_ROWS_REAL)
+      return (void *)bg_rows_real_kernel<N, block>;
+    else if constexpr (F == K2_REAL)
       return (void *)bg_real_kernel<N, 128>;
     else if constexpr (F == K2_REAL_HI)
       return (void *)bg_real_kernel<N, 128, real_hi_blocks>;
     else if constexpr (pair)
       return (void *)bg_pair_kernel<N, block>;
-    else if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
+    else if constexpr (rows)
       return (void *)bg_rows_kernel<N, block>;
     else if constexpr (F == K2_REG_TMA)
       return (void *)bg_reg_tma_kernel<N, 128>;
@@ -179,9 +189,11 @@ struct K2V {
       return (void *)bg_loop_kernel<N, 128>;
   }
   static size_t smem(int hist_bins) {
-    if constexpr (pair)
+    if constexpr (F == K2_ROWS_REAL)
+      return ((rows_real_smem_per_thread<L>() * block + 15) & ~(size_t)15) + EpiSmem<block>::bytes(hist_bins);
+    else if constexpr (pair)
       return PairSmem<L, block>::bytes + EpiSmem<threads>::bytes(hist_bins);
-    else if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
+    else if constexpr (rows)
       return rows_smem_per_thread<L>() * block + EpiSmem<block>::bytes(hist_bins);
     else if constexpr (F == K2_REG_TMA || F == K2_REG_TMA_HI)
       return RegStage<L, 128>::window + EpiSmem<128>::bytes(hist_bins);
@@ -192,13 +204,15 @@ struct K2V {
   // map: tensor map of B.in (staged forms only)
   static cudaError_t launch(const ChunkParams &C, const ChunkBuf<R> &B, double *partials, int grid, size_t smem,
                             cudaStream_t s, const CUtensorMap *map) {
-    if constexpr (F == K2_REAL)
+    if constexpr (F == K2_ROWS_REAL)
+      bg_rows_real_kernel<N, block><<<grid, block, smem, s>>>(C, B, partials);
+    else if constexpr (F == K2_REAL)
       bg_real_kernel<N, 128><<<grid, 128, smem, s>>>(C, B, partials);
     else if constexpr (F == K2_REAL_HI)
       bg_real_kernel<N, 128, real_hi_blocks><<<grid, 128, smem, s>>>(C, B, partials);
     else if constexpr (pair)
       bg_pair_kernel<N, block><<<grid, threads, smem, s>>>(C, B, partials);
-    else if constexpr (F == K2_ROWS32 || F == K2_ROWS64)
+    else if constexpr (rows)
       bg_rows_kernel<N, block><<<grid, block, smem, s>>>(C, B, partials);
     else if constexpr (F == K2_REG_TMA)
       bg_reg_tma_kernel<N, 128><<<grid, 128, smem, s>>>(C, B, partials, *map);
@@ -235,6 +249,9 @@ auto with_form(int f, Fn &&fn) {
     if constexpr (N <= 8) {
       if (f == K2_REG) return fn(K2V<N, R, K2_REG>{});
       if (f == K2_REG_TMA) return fn(K2V<N, R, K2_REG_TMA>{});
+    }
+    if constexpr (N >= 8) {
+      if (f == K2_ROWS_REAL) return fn(K2V<N, R, K2_ROWS_REAL>{});
     }
     if constexpr (N >= 6) {
       if (f == K2_ROWS64) return fn(K2V<N, R, K2_ROWS64>{});

@@ -1273,6 +1273,126 @@ __device__ __forceinline__ Cx<float> bg_rows(const float4 *K4, const CV4<float> 
   return amp;
 }
 
+// Row form with real currents (random real polarisations): the same schedule
+// as bg_rows, with the real recursion of bg_amplitude_real; the table holds
+// one float4 per current and one float per split sum.
+template <int L, int NB>
+__device__ __forceinline__ float bg_rows_real(const float4 *K4, const RV4<float> &eps_pos0, const RV4<float> &e0,
+                                              float4 *J4, float *S1) {
+  float amp = 0.f;
+  auto kleg = [&](int leg) {
+    const float4 v = K4[leg * NB + threadIdx.x];
+    RV4<float> r = {{v.x, v.y, v.z, v.w}};
+    return r;
+  };
+  auto ldj = [&](int t) {
+    const float4 v = J4[t * NB + threadIdx.x];
+    RV4<float> r = {{v.x, v.y, v.z, v.w}};
+    return r;
+  };
+#pragma unroll 1
+  for (int a = L - 1; a >= 0; --a) {
+    const int len = L - a;
+    RV4<float> row[L], krow[L];
+    float srow[L];
+    row[0] = (a == 0) ? eps_pos0 : ldj(t1<L>(a, a));
+    srow[0] = 0.f;
+    krow[0] = kleg(a);
+#pragma unroll
+    for (int d = 1; d < L; ++d) {
+      if (d >= len) break;
+      const int b = a + d;
+      krow[d] = radd(krow[d - 1], kleg(b));
+      RV4<float> acc = {{0.f, 0.f, 0.f, 0.f}}, tri = {{0.f, 0.f, 0.f, 0.f}};
+      float sum = 0.f;
+      RV4<float> kr = {{0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+      for (int dp = d - 1; dp >= 0; --dp) {
+        const int r0 = a + dp + 1;  // right part [r0..b]
+        kr = radd(kr, kleg(r0));
+        const RV4<float> Jr = ldj(t1<L>(r0, b));
+        const RV4<float> &Jl = row[dp];
+        const float d0 = mdot(Jl, Jr);
+        const float cr = 2.f * mdot(Jl, kr) - srow[dp];
+        float cl = -2.f * mdot(Jr, krow[dp]);
+        if (dp + 1 < d) cl -= S1[t1<L>(r0, b) * NB + threadIdx.x];
+        raxpy(acc, cr, Jr);
+        raxpy(acc, cl, Jl);
+        raxpy(acc, d0, rsub(krow[dp], kr));
+        sum += d0;
+#pragma unroll
+        for (int dpp = 0; dpp < dp; ++dpp) raxpy(tri, mdot(row[dpp], Jr), ldj(t1<L>(a + dpp + 1, a + dp)));
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m) acc.v[m] = fmaf(2.f, tri.v[m], acc.v[m]);
+      if (a == 0 && d == L - 1) {
+        amp = mdot(e0, acc);
+      } else {
+        const float inv = 1.f / mdot(krow[d], krow[d]);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) row[d].v[m] = acc.v[m] * inv;
+        srow[d] = sum;
+        if (a > 0) {
+          J4[t1<L>(a, b) * NB + threadIdx.x] = make_float4(row[d].v[0], row[d].v[1], row[d].v[2], row[d].v[3]);
+          S1[t1<L>(a, b) * NB + threadIdx.x] = sum;
+        }
+      }
+    }
+  }
+  return amp;
+}
+
+template <int L>
+__host__ __device__ constexpr size_t rows_real_smem_per_thread() {
+  return (size_t)(L * (L - 1) / 2) * (sizeof(float4) + sizeof(float)) + (size_t)L * sizeof(float4);
+}
+
+template <int N, int NB>
+__global__ void __launch_bounds__(NB) bg_rows_real_kernel(ChunkParams C, ChunkBuf<float> B, double *partials) {
+  constexpr int L = N - 1, T1 = L * (L - 1) / 2;
+  extern __shared__ __align__(16) char smem_raw[];
+  float4 *J4 = (float4 *)smem_raw;
+  float4 *K4 = J4 + T1 * NB;
+  float *S1 = (float *)(K4 + L * NB);
+  const int nb2 = C.P.hist_bins > 0 ? C.P.hist_bins + 2 : 0;
+  // epilogue scratch after the table, 16-byte aligned
+  EpiSmem<NB> S((char *)smem_raw + ((rows_real_smem_per_thread<L>() * NB + 15) & ~(size_t)15), nb2);
+  for (int i = threadIdx.x; i < 2 * nb2; i += NB) S.hw[i] = 0.0;
+  Accum<NB> A;
+  const int ntiles = (C.count + NB - 1) / NB;
+  const size_t cap = (size_t)B.cap;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int e = tile * NB + threadIdx.x;
+    double w = 0.0;
+    int bin = -1;
+    if (e < C.count) {
+      RV4<float> eps0pos, e0;
+#pragma unroll
+      for (int a = 0; a < L; ++a) {
+        const float *base = B.in + (size_t)InRows<L>::k(a) * cap + e;
+        K4[a * NB + threadIdx.x] = make_float4(base[0], base[cap], base[2 * cap], base[3 * cap]);
+        const float *pe = B.in + (size_t)InRows<L>::eps(a) * cap + e;
+        const RV4<float> ea = {{0.f, pe[0], pe[cap], pe[2 * cap]}};
+        if (a == 0)
+          eps0pos = ea;
+        else
+          J4[t1<L>(a, a) * NB + threadIdx.x] = make_float4(0.f, ea.v[1], ea.v[2], ea.v[3]);
+      }
+      {
+        const float *pe = B.in + (size_t)InRows<L>::eps0 * cap + e;
+        e0.v[0] = 0.f;
+        e0.v[1] = pe[0];
+        e0.v[2] = pe[cap];
+        e0.v[3] = pe[2 * cap];
+      }
+      const float amp = bg_rows_real<L, NB>(K4, eps0pos, e0, J4, S1);
+      finish_event<NB, float>(C, B, e, amp2_of(Cx<float>{amp, 0.f}), A, w, bin);
+    }
+    epi_tile<NB>(S, nb2, w, bin);
+  }
+  epi_flush<NB>(S, nb2, A, partials, C.P.hist_bins);
+}
+
 template <int L>
 __host__ __device__ constexpr size_t rows_smem_per_thread() {
   return (size_t)(L * (L - 1) / 2) * (2 * sizeof(float4) + sizeof(float2)) + (size_t)L * sizeof(float4);

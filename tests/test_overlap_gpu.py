@@ -44,6 +44,7 @@ CASES = [
     (8, tess.TESS_FP32_CURRENTS, tess.TESS_K2_REG_TMA, 400_003),
     (7, tess.TESS_FP32_DS, tess.TESS_K2_REG_TMA_HI, 500_009),
     (10, tess.TESS_FP32_DS, tess.TESS_K2_PAIR32, 300_007),
+    (9, tess.TESS_FP32_CURRENTS, tess.TESS_K2_ROWS64, 600_003),
     (6, tess.TESS_FP32_CURRENTS, tess.TESS_K2_PAIR64, 600_011),
 ]
 

@@ -342,9 +342,10 @@ def test_every_amplitude_variant_against_oracle(ctx, orc, n, form):
 REAL_FORMS_BY_N = {
     4: ["REAL", "REAL_HI", "REG", "PAIR32"],
     6: ["REAL", "REAL_HI", "REG_HI", "ROWS32", "PAIR64"],
-    8: ["REAL", "REAL_HI", "ROWS64", "PAIR32"],
-    9: ["REAL", "ROWS32", "PAIR32"],
-    10: ["ROWS32", "PAIR64"],
+    8: ["REAL", "REAL_HI", "ROWS_REAL", "ROWS64", "PAIR32"],
+    9: ["REAL", "ROWS_REAL", "ROWS32", "PAIR32"],
+    10: ["ROWS_REAL", "ROWS32", "PAIR64"],
+    12: ["ROWS_REAL", "PAIR32"],
 }
 
 
