@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--grad-only", action="store_true",
                     help="time only the gradient path (gg -> 6 gluons; --events overrides 2^22) and print its line")
     ap.add_argument("--no-autotune", action="store_true", help="time the built-in default amplitude variant")
+    ap.add_argument("--no-random-pol", action="store_true", help="skip the random-polarisation measurement")
+    ap.add_argument("--pol", default="helicity", choices=["helicity", "random"],
+                    help="sampled helicities (default) or the paper's random real polarisations (TESS_POL_RANDOM)")
     ap.add_argument("--variant", default="", help="FORM,SCHEDULE: use this amplitude variant and chunk schedule "
                                                  "instead of autotuning (reproducible profiling)")
     return ap.parse_args()
@@ -123,10 +126,11 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ tess arm
-def make_proc(tess, wl, precision=None):
+def make_proc(tess, wl, precision=None, random_pol=False):
     prec = precision or wl["precision"]
+    mode = tess.TESS_HEL_SUM if wl["hel"] == "sum" else (tess.TESS_POL_RANDOM if random_pol else tess.TESS_HEL_SAMPLE)
     kw = dict(precision={"fp32": tess.TESS_FP32_CURRENTS, "ds": tess.TESS_FP32_DS, "fp64": tess.TESS_FP64}[prec],
-              helicity_mode=tess.TESS_HEL_SUM if wl["hel"] == "sum" else tess.TESS_HEL_SAMPLE, pt_min=wl["pt_min"])
+              helicity_mode=mode, pt_min=wl["pt_min"])
     if wl["hist"]:
         obs, nb, lo, hi = wl["hist"]
         kw.update(hist_observable=obs, hist_bins=nb, hist_lo=lo, hist_hi=hi)
@@ -167,8 +171,10 @@ def run_tess(args):
     if args.events:
         wl["n_events"] = args.events
     n, N = wl["n"], wl["n_events"]
+    rp = args.pol == "random" and wl["hel"] == "sample"
+    flops_per_event = tess.bg_flops_real(n) if rp else tess.bg_flops(n)
     ctx = tess.tess_init(local)
-    proc = make_proc(tess, wl)
+    proc = make_proc(tess, wl, random_pol=rp)
     run = tess.Run(ctx, proc, N, per_event=("weight", "me2", "pass"))
     variant = None
     if args.variant:
@@ -256,7 +262,7 @@ def run_tess(args):
     # ---- FP64 plain form of the same workload, and the per-n sweep
     extra = {}
     if wl["precision"] == "ds" and rank == 0:
-        p32 = make_proc(tess, wl, "fp32")
+        p32 = make_proc(tess, wl, "fp32", random_pol=rp)
         r32 = tess.Run(ctx, p32, N, per_event=("weight", "me2", "pass"))
         ms = time_steps(torch, r32, seed, first, max(2, args.steps // 2), 2, flush)
         extra["fp32_native_fp64_steps"] = {
@@ -264,7 +270,7 @@ def run_tess(args):
             "note": "TESS_FP32_CURRENTS: Rambo boost/rescale and polarisation Gram products in native FP64"}
         del r32
     if not args.no_fp64 and wl["precision"] in ("fp32", "ds") and rank == 0:
-        p64 = make_proc(tess, wl, "fp64")
+        p64 = make_proc(tess, wl, "fp64", random_pol=rp)
         n64 = N >> 3
         r64 = tess.Run(ctx, p64, n64, per_event=("weight", "me2", "pass"))
         ms = time_steps(torch, r64, seed, first, max(1, args.steps // 2), 1, flush)
@@ -273,7 +279,8 @@ def run_tess(args):
                          "achieved_tflops": tess.bg_flops(n) * n64 / (statistics.mean(ms) * 1e-3) / 1e12,
                          "peak_tflops": FP64_PEAK_TFLOPS}
         del r64
-    if wl["hel"] == "sample" and wl["precision"] in ("fp32", "ds") and rank == 0:
+    if not rp and not args.no_random_pol and wl["hel"] == "sample" and wl["precision"] in ("fp32", "ds") \
+            and rank == 0:
         extra["random_polarisation"] = bench_random_pol(torch, tess, ctx, wl, N, seed, first, flush,
                                                         max(2, args.steps // 2), not args.no_autotune)
     if not args.no_batched and rank == 0:
@@ -303,16 +310,17 @@ def run_tess(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl, budget_s=12.0)
+        cpu = cpu_baseline(wl, budget_s=12.0, random_pol=rp)
 
     if rank == 0:
         amp_ms, amp_launches = stages["amplitude"]
         if amp_launches == 0:  # exact-sum mode: one fused kernel
             amp_ms, amp_launches = stages["fused"]
         amp_ms_step = amp_ms / args.steps
-        achieved = tess.bg_flops(n) * N / (amp_ms_step * 1e-3) / 1e12
+        achieved = flops_per_event * N / (amp_ms_step * 1e-3) / 1e12
         tot = sum(v[0] for v in stages.values()) or 1.0
-        traffic = read_traffic(args.workload, plan["variant"], min(N, plan_cap(tess, ctx, proc, N)))
+        traffic = read_traffic(args.workload + ("_rp" if rp else ""), plan["variant"],
+                               min(N, plan_cap(tess, ctx, proc, N)))
         line = {
             "metric": f"events/s (gg->{n - 2}g, {n}-point, {'FP64' if wl['precision'] == 'fp64' else 'FP32 currents'})",
             "value": value,
@@ -330,7 +338,9 @@ def run_tess(args):
                       "fp64": "f64"}[wl["precision"]],
             "data": "synthetic (counter-based Philox draws, toy gluon PDF)",
             "config": {"workload": f"{args.workload}: gg->{n - 2} gluons, {N} events per GPU, seed 1, sqrt(S)=14 TeV, "
-                                   f"pT>{wl['pt_min']:g} |eta|<2.5 dR>0.4, helicity+ordering sampled",
+                                   f"pT>{wl['pt_min']:g} |eta|<2.5 dR>0.4, "
+                                   + ("random real polarisations + ordering sampled" if rp
+                                      else "helicity+ordering sampled"),
                        "events_per_gpu": N, "n_gluons": n, "l2": "flushed between timed steps (256 MB write)"},
             "roofline": {"bound": "alu", "kernel": "Berends-Giele amplitude kernel", "achieved": achieved,
                          "peak": FP64_PEAK_TFLOPS if wl["precision"] == "fp64" else FP32_PEAK_TFLOPS,
@@ -339,7 +349,7 @@ def run_tess(args):
                          "traffic": traffic,
                          "peak_source": ("152 SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts and clock); "
                                          "an FMA probe measured 78.2 FP32 / 1.25 FP64 TFLOP/s"),
-                         "flops_per_event": tess.bg_flops(n), "ms_per_step": amp_ms_step,
+                         "flops_per_event": flops_per_event, "ms_per_step": amp_ms_step,
                          "variant": variant,
                          "plan": plan,
                          "launches_per_step": amp_launches // args.steps,
@@ -525,10 +535,10 @@ def read_traffic(workload, variant, events_per_launch):
 
 
 # ------------------------------------------------------------------ oracle (CPU) arm
-def cpu_baseline(wl, budget_s=12.0, events=None):
+def cpu_baseline(wl, budget_s=12.0, events=None, random_pol=False):
     import oracle
     threads = os.cpu_count() or 1
-    prec_hel = 0 if wl["hel"] == "sum" else 1
+    prec_hel = 0 if wl["hel"] == "sum" else (2 if random_pol else 1)
     kw = dict(hel_mode=prec_hel, pt_min=wl["pt_min"])
     if wl["hist"]:
         obs, nb, lo, hi = wl["hist"]
