@@ -56,6 +56,9 @@ def parse():
                     help="time only the gradient path (gg -> 6 gluons; --events overrides 2^22) and print its line")
     ap.add_argument("--no-autotune", action="store_true", help="time the built-in default amplitude variant")
     ap.add_argument("--no-random-pol", action="store_true", help="skip the random-polarisation measurement")
+    ap.add_argument("--no-cut-first", action="store_true", help="skip the cut-first measurements")
+    ap.add_argument("--cut-first", action="store_true",
+                    help="the whole line with TESS_FLAG_CUT_FIRST (amplitudes only for events passing the cuts)")
     ap.add_argument("--pol", default="helicity", choices=["helicity", "random"],
                     help="sampled helicities (default) or the paper's random real polarisations (TESS_POL_RANDOM)")
     ap.add_argument("--variant", default="", help="FORM,SCHEDULE: use this amplitude variant and chunk schedule "
@@ -175,6 +178,9 @@ def run_tess(args):
     flops_per_event = tess.bg_flops_real(n) if rp else tess.bg_flops(n)
     ctx = tess.tess_init(local)
     proc = make_proc(tess, wl, random_pol=rp)
+    cf = args.cut_first and wl["hel"] == "sample" and wl["precision"] in ("fp32", "ds")
+    if cf:
+        proc.flags = tess.TESS_FLAG_CUT_FIRST
     run = tess.Run(ctx, proc, N, per_event=("weight", "me2", "pass"))
     variant = None
     if args.variant:
@@ -214,6 +220,7 @@ def run_tess(args):
     value = ws * N / (ms_per_step * 1e-3)
     sigma = run.result()
     acc = run.acc.clone()
+    n_pass_local = int(acc[2].item())  # passing events of this rank's last step
 
     # ---- per-stage device time (library-recorded CUDA events on the launch stream).
     # Under an overlapped schedule the two kernels share the SMs, so the stages
@@ -279,10 +286,18 @@ def run_tess(args):
                          "achieved_tflops": tess.bg_flops(n) * n64 / (statistics.mean(ms) * 1e-3) / 1e12,
                          "peak_tflops": FP64_PEAK_TFLOPS}
         del r64
-    if not rp and not args.no_random_pol and wl["hel"] == "sample" and wl["precision"] in ("fp32", "ds") \
+    if not rp and not cf and not args.no_random_pol and wl["hel"] == "sample" and wl["precision"] in ("fp32", "ds") \
             and rank == 0:
         extra["random_polarisation"] = bench_random_pol(torch, tess, ctx, wl, N, seed, first, flush,
                                                         max(2, args.steps // 2), not args.no_autotune)
+    if not rp and not cf and not args.no_cut_first and wl["hel"] == "sample" and wl["precision"] in ("fp32", "ds") \
+            and rank == 0:
+        extra["cut_first"] = bench_random_pol(torch, tess, ctx, wl, N, seed, first, flush, max(2, args.steps // 2),
+                                              not args.no_autotune, random_pol=False,
+                                              flags=tess.TESS_FLAG_CUT_FIRST)
+        extra["cut_first_random_polarisation"] = bench_random_pol(
+            torch, tess, ctx, wl, N, seed, first, flush, max(2, args.steps // 2), not args.no_autotune,
+            random_pol=True, flags=tess.TESS_FLAG_CUT_FIRST)
     if not args.no_batched and rank == 0:
         extra["batched_mixed"] = bench_batched(torch, tess, ctx, flush, max(2, args.steps // 2))
     if not args.no_grad and rank == 0:
@@ -317,9 +332,10 @@ def run_tess(args):
         if amp_launches == 0:  # exact-sum mode: one fused kernel
             amp_ms, amp_launches = stages["fused"]
         amp_ms_step = amp_ms / args.steps
-        achieved = flops_per_event * N / (amp_ms_step * 1e-3) / 1e12
+        evaluated = n_pass_local if cf else N  # amplitudes computed per step (cut-first: passing events)
+        achieved = flops_per_event * evaluated / (amp_ms_step * 1e-3) / 1e12
         tot = sum(v[0] for v in stages.values()) or 1.0
-        traffic = read_traffic(args.workload + ("_rp" if rp else ""), plan["variant"],
+        traffic = read_traffic(args.workload + ("_rp" if rp else "") + ("_cf" if cf else ""), plan["variant"],
                                min(N, plan_cap(tess, ctx, proc, N)))
         line = {
             "metric": f"events/s (gg->{n - 2}g, {n}-point, {'FP64' if wl['precision'] == 'fp64' else 'FP32 currents'})",
@@ -340,7 +356,8 @@ def run_tess(args):
             "config": {"workload": f"{args.workload}: gg->{n - 2} gluons, {N} events per GPU, seed 1, sqrt(S)=14 TeV, "
                                    f"pT>{wl['pt_min']:g} |eta|<2.5 dR>0.4, "
                                    + ("random real polarisations + ordering sampled" if rp
-                                      else "helicity+ordering sampled"),
+                                      else "helicity+ordering sampled")
+                                   + (", cut-first (amplitudes only for events passing the cuts)" if cf else ""),
                        "events_per_gpu": N, "n_gluons": n, "l2": "flushed between timed steps (256 MB write)"},
             "roofline": {"bound": "alu", "kernel": "Berends-Giele amplitude kernel", "achieved": achieved,
                          "peak": FP64_PEAK_TFLOPS if wl["precision"] == "fp64" else FP32_PEAK_TFLOPS,
@@ -431,12 +448,15 @@ def bench_batched(torch, tess, ctx, flush, steps):
     return res
 
 
-def bench_random_pol(torch, tess, ctx, wl, N, seed, first, flush, steps, autotune):
+def bench_random_pol(torch, tess, ctx, wl, N, seed, first, flush, steps, autotune, random_pol=True, flags=0):
     """The same workload with the paper's random real polarisations
-    (TESS_POL_RANDOM) instead of sampled helicities: real currents, so the
-    real-current amplitude forms apply; FLOPs from bg_flops_real."""
-    p = make_proc(tess, wl)
-    p.helicity_mode = tess.TESS_POL_RANDOM
+    (TESS_POL_RANDOM) instead of sampled helicities -- real currents, so the
+    real-current amplitude forms apply; FLOPs from bg_flops_real -- and/or
+    with process flags (TESS_FLAG_CUT_FIRST: amplitudes only for the events
+    that pass the cuts; the amplitude kernel's FLOP rate then counts the
+    evaluated events)."""
+    p = make_proc(tess, wl, random_pol=random_pol)
+    p.flags = flags
     r = tess.Run(ctx, p, N, per_event=("weight", "me2", "pass"))
     if autotune:
         tess.tess_autotune(ctx, p, min(N, 1 << 22), torch.zeros(tess.TESS_ACC_LEN, dtype=torch.float64,
@@ -457,14 +477,17 @@ def bench_random_pol(torch, tess, ctx, wl, N, seed, first, flush, steps, autotun
     tess.tess_stage_timing(ctx, 0)
     tess.tess_select_variant(ctx, p, info["variant"], info["schedule"])
     amp_ms, amp_n = st["amplitude"]
-    cap = plan_cap(tess, ctx, p, N)
+    res_ = r.result()
+    fl = tess.bg_flops_real(wl["n"]) if random_pol else tess.bg_flops(wl["n"])
+    evaluated = res_[2] if flags & tess.TESS_FLAG_CUT_FIRST else N  # amplitudes computed per step
     res = {"value": N / (statistics.mean(ms) * 1e-3), "unit": "events/s", "ms_per_step": statistics.mean(ms),
-           "sigma_pb": r.result()[:2], "variant_schedule": [info["variant"], info["schedule"]]}
+           "sigma_pb": res_[:2], "variant_schedule": [info["variant"], info["schedule"]],
+           "amplitudes_per_step": evaluated}
     if amp_n:
-        launch_ms = amp_ms / amp_n
-        res["amplitude_kernel"] = {"tflops": tess.bg_flops_real(wl["n"]) * cap / (launch_ms * 1e-3) / 1e12,
-                                   "peak_tflops": FP32_PEAK_TFLOPS, "flops_per_event": tess.bg_flops_real(wl["n"]),
-                                   "ms_per_launch": launch_ms}
+        amp_step_ms = amp_ms / steps
+        res["amplitude_kernel"] = {"tflops": fl * evaluated / (amp_step_ms * 1e-3) / 1e12,
+                                   "peak_tflops": FP32_PEAK_TFLOPS, "flops_per_event": fl,
+                                   "ms_per_step": amp_step_ms}
     del r
     return res
 

@@ -67,6 +67,14 @@ extern "C" {
                              so the currents are real; one sampled colour ordering;
                              estimator 2^n (n-1)! |A|^2 (unbiased for the helicity
                              sum).  Not for tess_gradients or tess_generate_noalloc. */
+/* flags */
+#define TESS_FLAG_CUT_FIRST 1 /* cut-first generation (FP32 forms, sampled modes): the kinematics
+                                 kernel compacts the events that pass the cuts, and the amplitude
+                                 kernel evaluates only those (Sec. 3 notes that events failing the
+                                 cuts need no matrix element).  Failing events get weight 0 and
+                                 me2 0 (not evaluated); every other output is as without the flag.
+                                 Not for TESS_FP64, TESS_HEL_SUM, tess_gradients or
+                                 tess_generate_noalloc. */
 /* hist_observable */
 #define TESS_OBS_PTLEAD 0
 #define TESS_OBS_HT 1
@@ -89,6 +97,8 @@ typedef struct tess_process {
   double mz;               /* M_Z (> 0)                                       */
   double mu_r_factor;      /* mu_R = mu_r_factor * H_T (> 0)                  */
   double hist_lo, hist_hi; /* histogram range [lo, hi), uniform bins          */
+  int32_t flags;           /* 0 or TESS_FLAG_CUT_FIRST                        */
+  int32_t reserved;        /* 0                                               */
 } tess_process;
 
 /* Per-call outputs (caller-owned; NULL = not requested, except acc).

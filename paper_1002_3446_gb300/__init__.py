@@ -30,6 +30,7 @@ TESS_MIN_N, TESS_MAX_N, TESS_MAX_BINS, TESS_ACC_LEN = 4, 12, 1024, 8
 TESS_NOALLOC_SCRATCH_BYTES, TESS_NOALLOC_MAX_BINS = 1 << 20, 254
 TESS_FP64, TESS_FP32_CURRENTS, TESS_FP32_DS = 0, 1, 2
 TESS_HEL_SUM, TESS_HEL_SAMPLE, TESS_POL_RANDOM = 0, 1, 2
+TESS_FLAG_CUT_FIRST = 1
 TESS_OBS_PTLEAD, TESS_OBS_HT, TESS_OBS_RMIN = 0, 1, 2
 TESS_K2_REG, TESS_K2_ROWS32, TESS_K2_ROWS64, TESS_K2_LOOP, TESS_K2_REG_HI, TESS_K2_REG_TMA = 0, 1, 2, 3, 4, 5
 TESS_K2_REG_TMA_HI, TESS_K2_PAIR32, TESS_K2_PAIR64, TESS_K2_REAL, TESS_K2_REAL_HI = 6, 7, 8, 9, 10
@@ -67,6 +68,8 @@ class tess_process(ctypes.Structure):
         ("mu_r_factor", ctypes.c_double),
         ("hist_lo", ctypes.c_double),
         ("hist_hi", ctypes.c_double),
+        ("flags", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -362,11 +365,11 @@ def tess_histograms(ctx, proc, hist, stream=None):
 # ----------------------------------------------------------------- helpers
 def process(n, precision=TESS_FP64, helicity_mode=TESS_HEL_SAMPLE, sqrt_s=14000.0, pt_min=20.0, eta_max=2.5,
             dr_min=0.4, alphas_mz=0.118, mz=91.19, nf=5, mu_r_factor=0.5, hist_observable=TESS_OBS_PTLEAD,
-            hist_bins=0, hist_lo=20.0, hist_hi=1020.0):
+            hist_bins=0, hist_lo=20.0, hist_hi=1020.0, flags=0):
     return tess_process(n_gluons=n, precision=precision, helicity_mode=helicity_mode,
                         hist_observable=hist_observable, hist_bins=hist_bins, nf=nf, sqrt_s=sqrt_s, pt_min=pt_min,
                         eta_max=eta_max, dr_min=dr_min, alphas_mz=alphas_mz, mz=mz, mu_r_factor=mu_r_factor,
-                        hist_lo=hist_lo, hist_hi=hist_hi)
+                        hist_lo=hist_lo, hist_hi=hist_hi, flags=flags, reserved=0)
 
 
 # Workloads of the numerical study (Sec. 4), 14 TeV, toy gluon density.

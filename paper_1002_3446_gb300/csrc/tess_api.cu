@@ -36,13 +36,13 @@ cudaError_t launch_draws_a(int n, const EventParams &P, double *u, uint32_t *hel
 cudaError_t launch_draws_b(int n, const EventParams &P, double *u, uint32_t *hel, uint8_t *order, cudaStream_t s);
 cudaError_t launch_draws_c(int n, const EventParams &P, double *u, uint32_t *hel, uint8_t *order, cudaStream_t s);
 int plan_pipeline_f64(int n, int sm_count, uint64_t n_events, int hist_bins, int form, int sched,
-                      bool real_eps, PipePlan *pl);
+                      unsigned caps, PipePlan *pl);
 int plan_pipeline_f32a(int n, int sm_count, uint64_t n_events, int hist_bins, int form, int sched,
-                      bool real_eps, PipePlan *pl);
+                      unsigned caps, PipePlan *pl);
 int plan_pipeline_f32b(int n, int sm_count, uint64_t n_events, int hist_bins, int form, int sched,
-                      bool real_eps, PipePlan *pl);
+                      unsigned caps, PipePlan *pl);
 int plan_pipeline_f32c(int n, int sm_count, uint64_t n_events, int hist_bins, int form, int sched,
-                      bool real_eps, PipePlan *pl);
+                      unsigned caps, PipePlan *pl);
 cudaError_t run_pipeline_f64(int n, const EventParams &P, const PipePlan &pl, char *ws, cudaStream_t s,
                              const StageHook *hook, const OverlapRes *ov);
 cudaError_t run_pipeline_f32a(int n, const EventParams &P, const PipePlan &pl, char *ws, cudaStream_t s,
@@ -143,9 +143,9 @@ struct tess_ctx {
   int device = 0;
   int sm_count = 1;
   // tuned amplitude-kernel variant and chunk schedule per (precision,
-  // polarisation kind, n) -- see variant_slot; -1 = built-in default
-  int form[4][TESS_MAX_N + 1];
-  int sched[4][TESS_MAX_N + 1];
+  // polarisation kind, cut-first, n) -- see variant_slot; -1 = built-in default
+  int form[8][TESS_MAX_N + 1];
+  int sched[8][TESS_MAX_N + 1];
   // streams/events of the overlapped pipelines: [0] plain calls, [1 + i] batch
   // branch i, [kGradSlot] the gradient pipeline
   tess::OverlapRes ovl[kMaxBranches + 2];
@@ -221,6 +221,11 @@ int check_process(const tess_process *p) {
                 p->helicity_mode);
   if (p->helicity_mode == TESS_HEL_SUM && p->n_gluons > 5)
     return fail(TESS_E_UNSUPPORTED, "TESS_HEL_SUM is built for n <= 5 (n = %d)", p->n_gluons);
+  if ((p->flags & ~TESS_FLAG_CUT_FIRST) != 0 || p->reserved != 0)
+    return fail(TESS_E_INVALID, "flags = %d / reserved = %d: only TESS_FLAG_CUT_FIRST is defined", p->flags,
+                p->reserved);
+  if ((p->flags & TESS_FLAG_CUT_FIRST) && (p->precision == TESS_FP64 || p->helicity_mode == TESS_HEL_SUM))
+    return fail(TESS_E_UNSUPPORTED, "TESS_FLAG_CUT_FIRST is built for the FP32 forms with sampled events");
   if (!finite_pos(p->sqrt_s)) return fail(TESS_E_INVALID, "sqrt_s must be finite and > 0");
   if (!finite_pos(p->pt_min)) return fail(TESS_E_INVALID, "pt_min must be finite and > 0");
   if (!finite_pos(p->eta_max)) return fail(TESS_E_INVALID, "eta_max must be finite and > 0");
@@ -298,24 +303,26 @@ bool uses_pipeline(const tess_process *p) { return p->helicity_mode != TESS_HEL_
 
 // Variant-table row of a process: precision (FP64 / FP32) x polarisation
 // kind (complex helicity vectors / random real vectors, which admit the
-// real-current amplitude forms).
+// real-current amplitude forms) x cut-first (which the staged forms lack).
 int variant_slot(const tess_process *p) {
-  return (p->precision == TESS_FP64 ? 0 : 1) + (p->helicity_mode == TESS_POL_RANDOM ? 2 : 0);
+  return (p->precision == TESS_FP64 ? 0 : 1) + (p->helicity_mode == TESS_POL_RANDOM ? 2 : 0) +
+         ((p->flags & TESS_FLAG_CUT_FIRST) ? 4 : 0);
 }
 
 int plan_with_form(const tess_ctx *ctx, const tess_process *p, uint64_t n_events, int form, int sched,
                    tess::PipePlan *pl) {
   const int n = p->n_gluons;
-  const bool real = p->helicity_mode == TESS_POL_RANDOM;
+  const unsigned caps = (p->helicity_mode == TESS_POL_RANDOM ? tess::CAP_REAL_EPS : 0u) |
+                        ((p->flags & TESS_FLAG_CUT_FIRST) ? tess::CAP_CUT_FIRST : 0u);
   int rc;
   if (p->precision == TESS_FP64)
-    rc = tess::plan_pipeline_f64(n, ctx->sm_count, n_events, p->hist_bins, form, sched, real, pl);
+    rc = tess::plan_pipeline_f64(n, ctx->sm_count, n_events, p->hist_bins, form, sched, caps, pl);
   else if (n <= 7)
-    rc = tess::plan_pipeline_f32a(n, ctx->sm_count, n_events, p->hist_bins, form, sched, real, pl);
+    rc = tess::plan_pipeline_f32a(n, ctx->sm_count, n_events, p->hist_bins, form, sched, caps, pl);
   else if (n <= 10)
-    rc = tess::plan_pipeline_f32b(n, ctx->sm_count, n_events, p->hist_bins, form, sched, real, pl);
+    rc = tess::plan_pipeline_f32b(n, ctx->sm_count, n_events, p->hist_bins, form, sched, caps, pl);
   else
-    rc = tess::plan_pipeline_f32c(n, ctx->sm_count, n_events, p->hist_bins, form, sched, real, pl);
+    rc = tess::plan_pipeline_f32c(n, ctx->sm_count, n_events, p->hist_bins, form, sched, caps, pl);
   if (rc)
     return fail(TESS_E_CUDA, "could not size the pipeline kernels (n %d, amplitude variant %d, schedule %d: %s)", n,
                 form, sched,
@@ -423,6 +430,7 @@ void fill_params(const tess_process *proc, uint64_t seed, uint64_t first_event, 
   P.rmin = out->rmin;
   P.kin_ds = proc->precision == TESS_FP32_DS;
   P.pol_random = proc->helicity_mode == TESS_POL_RANDOM;
+  P.cut_first = (proc->flags & TESS_FLAG_CUT_FIRST) != 0;
   P.S_hi = (float)P.S;
   P.S_lo = (float)(P.S - (double)P.S_hi);
   P.wk = P.wconst * P.lnxmin * P.lnxmin * P.phiconst * 0.5;
@@ -939,8 +947,9 @@ int tess_gradients(tess_ctx *ctx, const tess_process *proc, uint64_t n_events, c
   if (!ctx) return fail(TESS_E_INVALID, "ctx is NULL");
   int rc = check_process(proc);
   if (rc) return rc;
-  if (proc->helicity_mode != TESS_HEL_SAMPLE)
-    return fail(TESS_E_UNSUPPORTED, "gradients are built for sampled helicity and ordering (TESS_HEL_SAMPLE)");
+  if (proc->helicity_mode != TESS_HEL_SAMPLE || proc->flags != 0)
+    return fail(TESS_E_UNSUPPORTED,
+                "gradients are built for sampled helicity and ordering (TESS_HEL_SAMPLE, no TESS_FLAG_CUT_FIRST)");
   if (n_events == 0) return ok();
   if (!u || !hel || !order) return fail(TESS_E_INVALID, "u, hel and order must not be NULL");
   if (n_events > (uint64_t)INT32_MAX * 128ull) return fail(TESS_E_INVALID, "n_events too large for one call");
@@ -1135,8 +1144,9 @@ extern "C" int tess_generate_noalloc(tess_ctx *ctx, const tess_process *proc, ui
   if (!ctx) return fail(TESS_E_INVALID, "ctx is NULL");
   int rc = check_process(proc);
   if (rc) return rc;
-  if (proc->helicity_mode == TESS_POL_RANDOM)
-    return fail(TESS_E_UNSUPPORTED, "tess_generate_noalloc is built for TESS_HEL_SUM and TESS_HEL_SAMPLE");
+  if (proc->helicity_mode == TESS_POL_RANDOM || proc->flags != 0)
+    return fail(TESS_E_UNSUPPORTED,
+                "tess_generate_noalloc is built for TESS_HEL_SUM and TESS_HEL_SAMPLE without TESS_FLAG_CUT_FIRST");
   if (proc->hist_bins > TESS_NOALLOC_MAX_BINS)
     return fail(TESS_E_INVALID, "tess_generate_noalloc supports at most %d histogram bins (%d requested)",
                 TESS_NOALLOC_MAX_BINS, proc->hist_bins);

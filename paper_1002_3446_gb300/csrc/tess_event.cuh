@@ -33,6 +33,7 @@ struct EventParams {
   float f_lnxmin, f_pt_min, f_eta_max, f_dr2_min, f_alphas_mz, f_asb0, f_ln_mz2, f_mu_r_factor;
   int kin_ds;          // 1: double-float kinematics kernel
   int pol_random;      // 1: random real polarisations instead of sampled helicities
+  int cut_first;       // 1: amplitudes only for events passing the cuts (compacted)
   // outputs (device; may be null)
   double *weight, *me2, *ht, *ptlead, *rmin;
   uint8_t *pass;

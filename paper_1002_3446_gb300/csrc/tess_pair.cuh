@@ -147,10 +147,12 @@ __global__ void __launch_bounds__(2 * NEV) bg_pair_kernel(ChunkParams C, ChunkBu
   EpiSmem<NB> ES(smem_pair + PS::bytes, nb2);
   for (int i = threadIdx.x; i < 2 * nb2; i += NB) ES.hw[i] = 0.0;
   Accum<NB> A;
-  const int ntiles = (C.count + NEV - 1) / NEV;
+  const int count = k2_count(C, B);
+  const int ntiles = (count + NEV - 1) / NEV;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int e = tile * NEV + V.g;
-    const bool live = e < C.count;
+    const int j = tile * NEV + V.g;
+    const bool live = j < count;
+    const int e = live ? k2_col(C, B, j) : 0;
     if (live) {
       if (lane == 0) {  // momenta -> prefix sums, and eps of position 0
         RV4<float> p = {{0.f, 0.f, 0.f, 0.f}};

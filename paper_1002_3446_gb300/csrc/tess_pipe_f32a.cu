@@ -4,12 +4,12 @@
 namespace tess {
 
 int plan_pipeline_f32a(int n, int sm_count, uint64_t n_events, int hist_bins, int form, int sched,
-                          bool real_eps, PipePlan *pl) {
+                          unsigned caps, PipePlan *pl) {
   switch (n) {
-    case 4: return plan_pipeline_t<4, float>(sm_count, n_events, hist_bins, form, sched, real_eps, pl);
-    case 5: return plan_pipeline_t<5, float>(sm_count, n_events, hist_bins, form, sched, real_eps, pl);
-    case 6: return plan_pipeline_t<6, float>(sm_count, n_events, hist_bins, form, sched, real_eps, pl);
-    case 7: return plan_pipeline_t<7, float>(sm_count, n_events, hist_bins, form, sched, real_eps, pl);
+    case 4: return plan_pipeline_t<4, float>(sm_count, n_events, hist_bins, form, sched, caps, pl);
+    case 5: return plan_pipeline_t<5, float>(sm_count, n_events, hist_bins, form, sched, caps, pl);
+    case 6: return plan_pipeline_t<6, float>(sm_count, n_events, hist_bins, form, sched, caps, pl);
+    case 7: return plan_pipeline_t<7, float>(sm_count, n_events, hist_bins, form, sched, caps, pl);
     default: return -1;
   }
 }

@@ -4,11 +4,11 @@
 namespace tess {
 
 int plan_pipeline_f32b(int n, int sm_count, uint64_t n_events, int hist_bins, int form, int sched,
-                          bool real_eps, PipePlan *pl) {
+                          unsigned caps, PipePlan *pl) {
   switch (n) {
-    case 8: return plan_pipeline_t<8, float>(sm_count, n_events, hist_bins, form, sched, real_eps, pl);
-    case 9: return plan_pipeline_t<9, float>(sm_count, n_events, hist_bins, form, sched, real_eps, pl);
-    case 10: return plan_pipeline_t<10, float>(sm_count, n_events, hist_bins, form, sched, real_eps, pl);
+    case 8: return plan_pipeline_t<8, float>(sm_count, n_events, hist_bins, form, sched, caps, pl);
+    case 9: return plan_pipeline_t<9, float>(sm_count, n_events, hist_bins, form, sched, caps, pl);
+    case 10: return plan_pipeline_t<10, float>(sm_count, n_events, hist_bins, form, sched, caps, pl);
     default: return -1;
   }
 }

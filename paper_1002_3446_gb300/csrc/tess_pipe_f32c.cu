@@ -4,10 +4,10 @@
 namespace tess {
 
 int plan_pipeline_f32c(int n, int sm_count, uint64_t n_events, int hist_bins, int form, int sched,
-                          bool real_eps, PipePlan *pl) {
+                          unsigned caps, PipePlan *pl) {
   switch (n) {
-    case 11: return plan_pipeline_t<11, float>(sm_count, n_events, hist_bins, form, sched, real_eps, pl);
-    case 12: return plan_pipeline_t<12, float>(sm_count, n_events, hist_bins, form, sched, real_eps, pl);
+    case 11: return plan_pipeline_t<11, float>(sm_count, n_events, hist_bins, form, sched, caps, pl);
+    case 12: return plan_pipeline_t<12, float>(sm_count, n_events, hist_bins, form, sched, caps, pl);
     default: return -1;
   }
 }

@@ -4,17 +4,17 @@
 namespace tess {
 
 int plan_pipeline_f64(int n, int sm_count, uint64_t n_events, int hist_bins, int form, int sched,
-                          bool real_eps, PipePlan *pl) {
+                          unsigned caps, PipePlan *pl) {
   switch (n) {
-    case 4: return plan_pipeline_t<4, double>(sm_count, n_events, hist_bins, form, sched, real_eps, pl);
-    case 5: return plan_pipeline_t<5, double>(sm_count, n_events, hist_bins, form, sched, real_eps, pl);
-    case 6: return plan_pipeline_t<6, double>(sm_count, n_events, hist_bins, form, sched, real_eps, pl);
-    case 7: return plan_pipeline_t<7, double>(sm_count, n_events, hist_bins, form, sched, real_eps, pl);
-    case 8: return plan_pipeline_t<8, double>(sm_count, n_events, hist_bins, form, sched, real_eps, pl);
-    case 9: return plan_pipeline_t<9, double>(sm_count, n_events, hist_bins, form, sched, real_eps, pl);
-    case 10: return plan_pipeline_t<10, double>(sm_count, n_events, hist_bins, form, sched, real_eps, pl);
-    case 11: return plan_pipeline_t<11, double>(sm_count, n_events, hist_bins, form, sched, real_eps, pl);
-    case 12: return plan_pipeline_t<12, double>(sm_count, n_events, hist_bins, form, sched, real_eps, pl);
+    case 4: return plan_pipeline_t<4, double>(sm_count, n_events, hist_bins, form, sched, caps, pl);
+    case 5: return plan_pipeline_t<5, double>(sm_count, n_events, hist_bins, form, sched, caps, pl);
+    case 6: return plan_pipeline_t<6, double>(sm_count, n_events, hist_bins, form, sched, caps, pl);
+    case 7: return plan_pipeline_t<7, double>(sm_count, n_events, hist_bins, form, sched, caps, pl);
+    case 8: return plan_pipeline_t<8, double>(sm_count, n_events, hist_bins, form, sched, caps, pl);
+    case 9: return plan_pipeline_t<9, double>(sm_count, n_events, hist_bins, form, sched, caps, pl);
+    case 10: return plan_pipeline_t<10, double>(sm_count, n_events, hist_bins, form, sched, caps, pl);
+    case 11: return plan_pipeline_t<11, double>(sm_count, n_events, hist_bins, form, sched, caps, pl);
+    case 12: return plan_pipeline_t<12, double>(sm_count, n_events, hist_bins, form, sched, caps, pl);
     default: return -1;
   }
 }

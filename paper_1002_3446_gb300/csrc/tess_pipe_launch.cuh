@@ -19,6 +19,7 @@ struct PipePlan {
   int cap = 128;     // events per chunk
   int chunks = 1;
   size_t off_in = 0, off_efac = 0, off_wfac = 0, off_hval = 0, off_pass = 0;
+  size_t off_col = 0, off_orig = 0, off_tcount = 0, off_dcount = 0;  // cut-first only
   size_t kin_smem = 0;   // K1 dynamic shared memory (FP32 forms: the output tile)
   size_t buf_bytes = 0;  // one chunk buffer
   int sched = 0;         // Schedule
@@ -125,21 +126,26 @@ enum K2Form {
   K2_NFORMS = 12
 };
 
-// real_eps: the call's polarisation vectors are real (random polarisations),
-// which the real-current forms require; every other form takes either kind.
+// What a call offers the amplitude kernel: CAP_REAL_EPS, its polarisation
+// vectors are real (random polarisations), which the real-current forms
+// require; CAP_CUT_FIRST, its events are compacted (an index list), which the
+// staged forms do not read.
+constexpr unsigned CAP_REAL_EPS = 1u, CAP_CUT_FIRST = 2u;
+
 template <int N, typename R>
-constexpr bool k2_valid(int f, bool real_eps) {
+constexpr bool k2_valid(int f, unsigned caps) {
+  const bool real_eps = (caps & CAP_REAL_EPS) != 0, cut_first = (caps & CAP_CUT_FIRST) != 0;
   if constexpr (sizeof(R) == 8) {
-    return f == K2_LOOP;
+    return f == K2_LOOP && !cut_first;
   } else {
     switch (f) {
       case K2_REAL: return real_eps && N <= 9;
       case K2_REAL_HI: return real_eps && N <= 8;
       case K2_ROWS_REAL: return real_eps && N >= 8;
-      case K2_REG:
-      case K2_REG_TMA: return N <= 8;
-      case K2_REG_HI:
-      case K2_REG_TMA_HI: return N <= 7;
+      case K2_REG_TMA: return N <= 8 && !cut_first;
+      case K2_REG_TMA_HI: return N <= 7 && !cut_first;
+      case K2_REG: return N <= 8;
+      case K2_REG_HI: return N <= 7;
       case K2_ROWS32:
       case K2_ROWS64: return N >= 6;
       case K2_PAIR32:
@@ -263,10 +269,10 @@ auto with_form(int f, Fn &&fn) {
 }
 
 template <int N, typename R>
-int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, int sched, bool real_eps,
+int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, int sched, unsigned caps,
                     PipePlan *pl) {
   constexpr int L = N - 1;
-  if (!k2_valid<N, R>(form, real_eps)) form = k2_default<N, R>();
+  if (!k2_valid<N, R>(form, caps)) form = k2_default<N, R>();
   pl->form = form;
   const int rc = with_form<N, R>(form, [&](auto K) {
     using KV = decltype(K);
@@ -284,16 +290,22 @@ int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, in
   if (rc) return rc;
   if constexpr (sizeof(R) == 4) {
     pl->kin_smem = kin_tile_bytes<N>();
-    cudaError_t e = allow_max_smem((const void *)kin_ds_kernel<N, false>);
-    if (e == cudaSuccess) e = allow_max_smem((const void *)kin_ds_kernel<N, true>);
-    if (e == cudaSuccess) e = allow_max_smem((const void *)kin_kernel<N, float, false>);
-    if (e == cudaSuccess) e = allow_max_smem((const void *)kin_kernel<N, float, true>);
+    const void *kin_fns[] = {
+        (const void *)kin_ds_kernel<N, false, false>, (const void *)kin_ds_kernel<N, true, false>,
+        (const void *)kin_ds_kernel<N, false, true>,  (const void *)kin_ds_kernel<N, true, true>,
+        (const void *)kin_kernel<N, float, false, false>, (const void *)kin_kernel<N, float, true, false>,
+        (const void *)kin_kernel<N, float, false, true>,  (const void *)kin_kernel<N, float, true, true>};
+    cudaError_t e = cudaSuccess;
+    for (const void *fn : kin_fns)
+      if (e == cudaSuccess) e = allow_max_smem(fn);
     if (e != cudaSuccess) return (int)e;
   } else {
     pl->kin_smem = 0;
   }
   const int per_sm = pl->per_sm;
-  const uint64_t per_event = (uint64_t)InRows<L>::rows * sizeof(R) + 3 * sizeof(double) + 1;
+  const bool cut_first = (caps & CAP_CUT_FIRST) != 0;
+  const uint64_t per_event =
+      (uint64_t)InRows<L>::rows * sizeof(R) + 3 * sizeof(double) + 1 + (cut_first ? 2 * sizeof(int) : 0);
   const uint64_t target = std::max<uint64_t>(128, (kChunkTargetBytes / per_event) / 128 * 128);
   const uint64_t want = (std::max<uint64_t>(n_events, 1) + 127) / 128 * 128;
   pl->cap = (int)std::min(target, want);
@@ -319,6 +331,16 @@ int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, in
   off = align256(off + (size_t)pl->cap * sizeof(double));
   pl->off_pass = off;
   off = align256(off + (size_t)pl->cap);
+  if (cut_first) {  // compaction: column and source index per event, count per K1 tile, total
+    pl->off_col = off;
+    off = align256(off + (size_t)pl->cap * sizeof(int));
+    pl->off_orig = off;
+    off = align256(off + (size_t)pl->cap * sizeof(int));
+    pl->off_tcount = off;
+    off = align256(off + (size_t)(pl->cap / kBlock + 1) * sizeof(int));
+    pl->off_dcount = off;
+    off = align256(off + sizeof(int));
+  }
   pl->buf_bytes = off - pl->off_in;
   pl->bytes = pl->overlap ? off + pl->buf_bytes : off;  // second chunk buffer
   return 0;
@@ -339,6 +361,12 @@ cudaError_t run_pipeline_t(const EventParams &P, const PipePlan &pl, char *ws, c
     BB[b].hval = (double *)(base + pl.off_hval);
     BB[b].pass = (uint8_t *)(base + pl.off_pass);
     BB[b].cap = pl.cap;
+    if (P.cut_first) {
+      BB[b].col = (int *)(base + pl.off_col);
+      BB[b].orig = (int *)(base + pl.off_orig);
+      BB[b].tcount = (int *)(base + pl.off_tcount);
+      BB[b].dcount = (int *)(base + pl.off_dcount);
+    }
   }
   ChunkParams C;
   C.P = P;

@@ -29,6 +29,13 @@ struct ChunkBuf {
   double *hval;   // [cap] histogram observable
   uint8_t *pass;  // [cap] pass flag
   int cap;
+  // cut-first generation only (else null): the kinematics kernel puts the
+  // events that pass the cuts in the first columns of its tile (in event
+  // order) and counts them per tile; the index kernel lists their columns.
+  int *col = nullptr;     // [cap] column of the j-th kept event of the chunk
+  int *orig = nullptr;    // [cap] chunk index of the event in a kept column
+  int *tcount = nullptr;  // [cap / kBlock] kept events per kinematics tile
+  int *dcount = nullptr;  // [1] kept events of the chunk
 };
 
 struct ChunkParams {
@@ -339,13 +346,13 @@ constexpr size_t kin_tile_bytes() {
 }
 
 template <int N>
-__device__ __forceinline__ void scatter_ordered(const EventParams &P, uint64_t ev, float *tile,
+__device__ __forceinline__ void scatter_ordered(const EventParams &P, uint64_t ev, float *tile, int slot,
                                                 const float (&lk)[N][4], const float (&le1)[N][3],
                                                 const float (&le2)[N][2]) {
   constexpr int L = N - 1;
   uint64_t posw;
   const uint32_t hel = sample_positions<N>(P, ev, &posw);
-  float *col = tile + threadIdx.x;
+  float *col = tile + slot;
   const float r2 = 0.70710678118654752440f;
 #pragma unroll
   for (int l = 0; l < N; ++l) {
@@ -369,7 +376,7 @@ __device__ __forceinline__ void scatter_ordered(const EventParams &P, uint64_t e
 // sin(phi) e2 of every leg (imaginary rows zero); the colour ordering comes
 // from the same draws.
 template <int N>
-__device__ __forceinline__ void scatter_ordered_real(const EventParams &P, uint64_t ev, float *tile,
+__device__ __forceinline__ void scatter_ordered_real(const EventParams &P, uint64_t ev, float *tile, int slot,
                                                      const float (&lk)[N][4], const float (&le1)[N][3],
                                                      const float (&le2)[N][2]) {
   constexpr int L = N - 1;
@@ -377,7 +384,7 @@ __device__ __forceinline__ void scatter_ordered_real(const EventParams &P, uint6
   sample_positions<N>(P, ev, &posw);
   float cphi[N], sphi[N];
   polarisation_angles<N, float>(P, ev, cphi, sphi);
-  float *col = tile + threadIdx.x;
+  float *col = tile + slot;
 #pragma unroll
   for (int l = 0; l < N; ++l) {
     const int p = (int)((posw >> (4 * l)) & 15ull);  // colour position of leg l
@@ -396,12 +403,46 @@ __device__ __forceinline__ void scatter_ordered_real(const EventParams &P, uint6
 }
 
 template <int N, bool RP>
-__device__ __forceinline__ void scatter_legs(const EventParams &P, uint64_t ev, float *tile, const float (&lk)[N][4],
-                                             const float (&le1)[N][3], const float (&le2)[N][2]) {
+__device__ __forceinline__ void scatter_legs(const EventParams &P, uint64_t ev, float *tile, int slot,
+                                             const float (&lk)[N][4], const float (&le1)[N][3],
+                                             const float (&le2)[N][2]) {
   if constexpr (RP)
-    scatter_ordered_real<N>(P, ev, tile, lk, le1, le2);
+    scatter_ordered_real<N>(P, ev, tile, slot, lk, le1, le2);
   else
-    scatter_ordered<N>(P, ev, tile, lk, le1, le2);
+    scatter_ordered<N>(P, ev, tile, slot, lk, le1, le2);
+}
+
+// Cut-first compaction point of the kinematics kernels (CF): the block's
+// events that pass the cuts take the first columns of its tile, in event
+// order; returns this event's column (-1 when it is not kept, i.e. it fails
+// the cuts or lies past the chunk) and records the block's count.  Failing
+// events get their weight and |m|^2 outputs (0) here, since no amplitude
+// kernel sees them.  Every thread of the block must call it.
+template <bool CF>
+__device__ __forceinline__ int cut_first_slot(const EventParams &P, const ChunkBuf<float> &B, bool live, int pass,
+                                              uint64_t idx) {
+  if constexpr (!CF) {
+    return (int)threadIdx.x;
+  } else {
+    __shared__ int wsum[kBlock / 32];
+    const bool keep = live && pass;
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) wsum[w] = __popc(m);
+    __syncthreads();
+    int base = 0, tot = 0;
+#pragma unroll
+    for (int i = 0; i < kBlock / 32; ++i) {
+      base += i < w ? wsum[i] : 0;
+      tot += wsum[i];
+    }
+    if (threadIdx.x == 0) B.tcount[blockIdx.x] = tot;
+    if (live && !pass) {
+      if (P.weight) P.weight[idx] = 0.0;
+      if (P.me2) P.me2[idx] = 0.0;
+    }
+    return keep ? base + __popc(m & ((1u << lane) - 1u)) : -1;
+  }
 }
 
 // Rows of the block's tile -> chunk buffer, one bulk copy per row issued by
@@ -426,8 +467,9 @@ __device__ __forceinline__ void store_tile(const ChunkBuf<float> &B, const float
 // and rescale (conservation and masslessness), the polarisation Gram
 // products, the weight factor.  Helicity labels and colour ordering are
 // exact integer functions of the draws (identical in both forms).
-template <int N, bool RP>
-__device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<float> &B, int e, float *tile) {
+template <int N, bool RP, bool CF>
+__device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<float> &B, int e, float *tile,
+                                     bool live) {
   constexpr int M = N - 2;
   const EventParams &P = C.P;
   const uint64_t idx = C.chunk_first + (uint64_t)e;
@@ -509,10 +551,16 @@ __device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<fl
     }
   }
   const double ht = (double)sum, ptlead = (double)lead, rmin = (double)sqrtf(dr2min);
-  if (P.ht) P.ht[idx] = ht;
-  if (P.ptlead) P.ptlead[idx] = ptlead;
-  if (P.rmin) P.rmin[idx] = rmin;
-  if (P.pass) P.pass[idx] = (uint8_t)pass;
+  if (live) {
+    if (P.ht) P.ht[idx] = ht;
+    if (P.ptlead) P.ptlead[idx] = ptlead;
+    if (P.rmin) P.rmin[idx] = rmin;
+    if (P.pass) P.pass[idx] = (uint8_t)pass;
+  }
+  const int slot = cut_first_slot<CF>(P, B, live, pass, idx);
+  if (slot < 0) return;
+  const int ec = CF ? (int)blockIdx.x * kBlock + slot : e;  // chunk column of the event's factors
+  if constexpr (CF) B.orig[ec] = e;
 
   double wf = 0.0;
   if (pass) {
@@ -535,10 +583,10 @@ __device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<fl
   const double u2 = inv_rs * inv_rs;
 #pragma unroll
   for (int i = 0; i < N - 4; ++i) ef *= u2;
-  B.efac[e] = ef;
-  B.wfac[e] = wf;
-  B.pass[e] = (uint8_t)pass;
-  if (B.hval) B.hval[e] = P.hist_obs == 0 ? ptlead : (P.hist_obs == 1 ? ht : rmin);
+  B.efac[ec] = ef;
+  B.wfac[ec] = wf;
+  B.pass[ec] = (uint8_t)pass;
+  if (B.hval) B.hval[ec] = P.hist_obs == 0 ? ptlead : (P.hist_obs == 1 ? ht : rmin);
 
   // per-leg FP32 data: momentum in units of the power-of-two scale, and the
   // polarisation basis (e1 spatial, e2 transverse); beam-axis legs are exact
@@ -556,7 +604,7 @@ __device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<fl
     pol_basis_f32(pk[i][0], pk[i][1], pk[i][2], pk[i][3], le1[2 + i], le2[2 + i]);
   }
 
-  scatter_legs<N, RP>(P, ev, tile, lk, le1, le2);
+  scatter_legs<N, RP>(P, ev, tile, slot, lk, le1, le2);
 }
 
 // Polarisation basis in FP32 from the FP32-rounded momentum components (each
@@ -587,8 +635,9 @@ __device__ __forceinline__ void pol_basis_rounded(float E, float px, float py, f
 // on this GPU), and the polarisation basis in FP32 from the rounded momenta.
 // The weight factor is assembled in FP32 with its power-of-two scale kept as
 // an exact exponent.
-template <int N, bool RP>
-__device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<float> &B, int e, float *tile) {
+template <int N, bool RP, bool CF>
+__device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<float> &B, int e, float *tile,
+                                     bool live) {
   constexpr int M = N - 2;
   const EventParams &P = C.P;
   const uint64_t idx = C.chunk_first + (uint64_t)e;
@@ -695,10 +744,16 @@ __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<floa
     }
   }
   const float rmin = sqrtf(dr2min);
-  if (P.ht) P.ht[idx] = (double)sum;
-  if (P.ptlead) P.ptlead[idx] = (double)lead;
-  if (P.rmin) P.rmin[idx] = (double)rmin;
-  if (P.pass) P.pass[idx] = (uint8_t)pass;
+  if (live) {
+    if (P.ht) P.ht[idx] = (double)sum;
+    if (P.ptlead) P.ptlead[idx] = (double)lead;
+    if (P.rmin) P.rmin[idx] = (double)rmin;
+    if (P.pass) P.pass[idx] = (uint8_t)pass;
+  }
+  const int slot = cut_first_slot<CF>(P, B, live, pass, idx);
+  if (slot < 0) return;
+  const int ec = CF ? (int)blockIdx.x * kBlock + slot : e;  // chunk column of the event's factors
+  if constexpr (CF) B.orig[ec] = e;
 
   // momentum unit 2^-ex near 1/sqrt(s_hat); s' = s_hat 2^-2ex in [1/4, 1)
   int ex;
@@ -725,10 +780,10 @@ __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<floa
     }
     if (F > 0.f) wf = scale_pow2(P.wk * (double)F, 2 * ex * (M - 3));
   }
-  B.efac[e] = scale_pow2(P.efac, -2 * ex * (N - 4));
-  B.wfac[e] = wf;
-  B.pass[e] = (uint8_t)pass;
-  if (B.hval) B.hval[e] = (double)(P.hist_obs == 0 ? lead : (P.hist_obs == 1 ? sum : rmin));
+  B.efac[ec] = scale_pow2(P.efac, -2 * ex * (N - 4));
+  B.wfac[ec] = wf;
+  B.pass[ec] = (uint8_t)pass;
+  if (B.hval) B.hval[ec] = (double)(P.hist_obs == 0 ? lead : (P.hist_obs == 1 ? sum : rmin));
 
   float lk[N][4], le1[N][3], le2[N][2];
   const float hs = 0.5f * rs.hi * sc;
@@ -742,17 +797,23 @@ __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<floa
     for (int m = 0; m < 4; ++m) lk[2 + i][m] = pk[i][m] * sc;
     pol_basis_rounded(pk[i][0], pk[i][1], pk[i][2], pk[i][3], le1[2 + i], le2[2 + i]);
   }
-  scatter_legs<N, RP>(P, ev, tile, lk, le1, le2);
+  scatter_legs<N, RP>(P, ev, tile, slot, lk, le1, le2);
 }
 
 // K1 kernels.  The FP32 forms take kin_tile_bytes<N>() of dynamic shared
 // memory for the block's output tile.
-template <int N, typename R, bool RP = false>
+// CF (cut-first): every thread of a block runs the kinematics (threads past
+// the chunk on its last event, writing nothing) so that all reach the
+// compaction point.
+template <int N, typename R, bool RP = false, bool CF = false>
 __global__ void __launch_bounds__(kBlock) kin_kernel(ChunkParams C, ChunkBuf<R> B) {
   const int e = blockIdx.x * kBlock + threadIdx.x;
   if constexpr (sizeof(R) == 4) {
     extern __shared__ __align__(128) float kin_tile[];
-    if (e < C.count) kin_fp32<N, RP>(C, B, e, kin_tile);
+    if (CF)
+      kin_fp32<N, RP, CF>(C, B, min(e, C.count - 1), kin_tile, e < C.count);
+    else if (e < C.count)
+      kin_fp32<N, RP, CF>(C, B, e, kin_tile, true);
     store_tile<N>(B, kin_tile);
   } else {
     if (e >= C.count) return;
@@ -760,12 +821,43 @@ __global__ void __launch_bounds__(kBlock) kin_kernel(ChunkParams C, ChunkBuf<R> 
   }
 }
 
-template <int N, bool RP = false>
+template <int N, bool RP = false, bool CF = false>
 __global__ void __launch_bounds__(kBlock) kin_ds_kernel(ChunkParams C, ChunkBuf<float> B) {
   extern __shared__ __align__(128) float kin_tile[];
   const int e = blockIdx.x * kBlock + threadIdx.x;
-  if (e < C.count) kin_ds<N, RP>(C, B, e, kin_tile);
+  if (CF)
+    kin_ds<N, RP, CF>(C, B, min(e, C.count - 1), kin_tile, e < C.count);
+  else if (e < C.count)
+    kin_ds<N, RP, CF>(C, B, e, kin_tile, true);
   store_tile<N>(B, kin_tile);
+}
+
+// Cut-first: exclusive scan of the kinematics tiles' kept counts and the
+// list of kept columns of the chunk (kept index j -> column), in event
+// order; one block.
+template <int NT>
+__global__ void __launch_bounds__(NT) cut_first_index_kernel(const int *tcount, int ntiles, int *col, int *dcount) {
+  __shared__ int part[NT];
+  const int t = threadIdx.x;
+  const int per = (ntiles + NT - 1) / NT;
+  const int t0 = min(t * per, ntiles), t1 = min(t0 + per, ntiles);
+  int sum = 0;
+  for (int i = t0; i < t1; ++i) sum += tcount[i];
+  part[t] = sum;
+  __syncthreads();
+  for (int d = 1; d < NT; d <<= 1) {
+    const int v = t >= d ? part[t - d] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int off = part[t] - sum;
+  for (int i = t0; i < t1; ++i) {
+    const int c = tcount[i];
+    for (int q = 0; q < c; ++q) col[off + q] = i * kBlock + q;
+    off += c;
+  }
+  if (t == NT - 1) *dcount = part[NT - 1];
 }
 
 // The kinematics kernel of a call: double-float or plain form, sampled
@@ -774,19 +866,35 @@ template <int N, typename R>
 __host__ inline cudaError_t launch_kin(const ChunkParams &C, const ChunkBuf<R> &B, int kin_smem, cudaStream_t s) {
   const unsigned grid = (unsigned)((C.count + kBlock - 1) / kBlock);
   if constexpr (sizeof(R) == 4) {
+    const int v = (C.P.pol_random ? 1 : 0) + (C.P.cut_first ? 2 : 0);
     if (C.P.kin_ds) {
-      if (C.P.pol_random)
-        kin_ds_kernel<N, true><<<grid, kBlock, kin_smem, s>>>(C, B);
-      else
-        kin_ds_kernel<N, false><<<grid, kBlock, kin_smem, s>>>(C, B);
-      return cudaGetLastError();
+      switch (v) {
+        case 0: kin_ds_kernel<N, false, false><<<grid, kBlock, kin_smem, s>>>(C, B); break;
+        case 1: kin_ds_kernel<N, true, false><<<grid, kBlock, kin_smem, s>>>(C, B); break;
+        case 2: kin_ds_kernel<N, false, true><<<grid, kBlock, kin_smem, s>>>(C, B); break;
+        default: kin_ds_kernel<N, true, true><<<grid, kBlock, kin_smem, s>>>(C, B); break;
+      }
+    } else {
+      switch (v) {
+        case 0: kin_kernel<N, R, false, false><<<grid, kBlock, kin_smem, s>>>(C, B); break;
+        case 1: kin_kernel<N, R, true, false><<<grid, kBlock, kin_smem, s>>>(C, B); break;
+        case 2: kin_kernel<N, R, false, true><<<grid, kBlock, kin_smem, s>>>(C, B); break;
+        default: kin_kernel<N, R, true, true><<<grid, kBlock, kin_smem, s>>>(C, B); break;
+      }
     }
+    if (C.P.cut_first) {
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      cut_first_index_kernel<1024><<<1, 1024, 0, s>>>(B.tcount, (int)grid, B.col, B.dcount);
+    }
+    return cudaGetLastError();
+  } else {
+    if (C.P.pol_random)
+      kin_kernel<N, R, true><<<grid, kBlock, kin_smem, s>>>(C, B);
+    else
+      kin_kernel<N, R, false><<<grid, kBlock, kin_smem, s>>>(C, B);
+    return cudaGetLastError();
   }
-  if (C.P.pol_random)
-    kin_kernel<N, R, true><<<grid, kBlock, kin_smem, s>>>(C, B);
-  else
-    kin_kernel<N, R, false><<<grid, kBlock, kin_smem, s>>>(C, B);
-  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -836,10 +944,26 @@ __device__ __forceinline__ void finish_values(const ChunkParams &C, int e, doubl
   bin_out = (P.hist_bins > 0 && ok) ? hist_bin(*hval, P.hist_lo, P.hist_inv_width, P.hist_bins) : -1;
 }
 
+// Events the amplitude kernel evaluates in a chunk, and the chunk column of
+// the j-th: every event in order, or under cut-first the kept ones (their
+// count and columns from the index kernel).
+template <typename R>
+__device__ __forceinline__ int k2_count(const ChunkParams &C, const ChunkBuf<R> &B) {
+  return C.P.cut_first ? *B.dcount : C.count;
+}
+
+template <typename R>
+__device__ __forceinline__ int k2_col(const ChunkParams &C, const ChunkBuf<R> &B, int j) {
+  return C.P.cut_first ? B.col[j] : j;
+}
+
+// Epilogue of the event in chunk column e (factors at e; per-event outputs
+// at its chunk index, e itself unless cut-first moved it).
 template <int NB, typename R>
 __device__ __forceinline__ void finish_event(const ChunkParams &C, const ChunkBuf<R> &B, int e, double amp2,
                                              Accum<NB> &A, double &w_out, int &bin_out) {
-  finish_values<NB>(C, e, B.efac[e], B.wfac[e], B.pass[e], B.hval + e, amp2, A, w_out, bin_out);
+  const int o = C.P.cut_first ? B.orig[e] : e;
+  finish_values<NB>(C, o, B.efac[e], B.wfac[e], B.pass[e], B.hval + e, amp2, A, w_out, bin_out);
 }
 
 // Shared-memory scratch of the epilogue: histogram accumulators and a tile's
@@ -914,12 +1038,14 @@ __global__ void __launch_bounds__(NB, MINB) bg_reg_kernel(ChunkParams C, ChunkBu
   EpiSmem<NB> S(smem_raw, nb2);
   for (int i = threadIdx.x; i < 2 * nb2; i += NB) S.hw[i] = 0.0;
   Accum<NB> A;
-  const int ntiles = (C.count + NB - 1) / NB;
+  const int count = k2_count(C, B);
+  const int ntiles = (count + NB - 1) / NB;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int e = tile * NB + threadIdx.x;
+    const int j = tile * NB + threadIdx.x;
     double w = 0.0;
     int bin = -1;
-    if (e < C.count) {
+    if (j < count) {
+      const int e = k2_col(C, B, j);
       RV4<R> k[L];
       CV4<R> ev[L], e0;
 #pragma unroll
@@ -948,13 +1074,15 @@ __global__ void __launch_bounds__(NB, MINB) bg_real_kernel(ChunkParams C, ChunkB
   EpiSmem<NB> S(smem_raw, nb2);
   for (int i = threadIdx.x; i < 2 * nb2; i += NB) S.hw[i] = 0.0;
   Accum<NB> A;
-  const int ntiles = (C.count + NB - 1) / NB;
+  const int count = k2_count(C, B);
+  const int ntiles = (count + NB - 1) / NB;
   const size_t cap = (size_t)B.cap;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int e = tile * NB + threadIdx.x;
+    const int j = tile * NB + threadIdx.x;
     double w = 0.0;
     int bin = -1;
-    if (e < C.count) {
+    if (j < count) {
+      const int e = k2_col(C, B, j);
       RV4<float> k[L], ev[L], e0;
 #pragma unroll
       for (int a = 0; a < L; ++a) {
@@ -1134,12 +1262,14 @@ __global__ void __launch_bounds__(NB) bg_loop_kernel(ChunkParams C, ChunkBuf<dou
   EpiSmem<NB> S(smem_raw, nb2);
   for (int i = threadIdx.x; i < 2 * nb2; i += NB) S.hw[i] = 0.0;
   Accum<NB> A;
-  const int ntiles = (C.count + NB - 1) / NB;
+  const int count = k2_count(C, B);
+  const int ntiles = (count + NB - 1) / NB;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int e = tile * NB + threadIdx.x;
+    const int j = tile * NB + threadIdx.x;
     double w = 0.0;
     int bin = -1;
-    if (e < C.count) {
+    if (j < count) {
+      const int e = k2_col(C, B, j);
       BGLoop<double, L> bg;
 #pragma unroll 1
       for (int a = 0; a < L; ++a) {
@@ -1359,13 +1489,15 @@ __global__ void __launch_bounds__(NB) bg_rows_real_kernel(ChunkParams C, ChunkBu
   EpiSmem<NB> S((char *)smem_raw + ((rows_real_smem_per_thread<L>() * NB + 15) & ~(size_t)15), nb2);
   for (int i = threadIdx.x; i < 2 * nb2; i += NB) S.hw[i] = 0.0;
   Accum<NB> A;
-  const int ntiles = (C.count + NB - 1) / NB;
+  const int count = k2_count(C, B);
+  const int ntiles = (count + NB - 1) / NB;
   const size_t cap = (size_t)B.cap;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int e = tile * NB + threadIdx.x;
+    const int j = tile * NB + threadIdx.x;
     double w = 0.0;
     int bin = -1;
-    if (e < C.count) {
+    if (j < count) {
+      const int e = k2_col(C, B, j);
       RV4<float> eps0pos, e0;
 #pragma unroll
       for (int a = 0; a < L; ++a) {
@@ -1409,12 +1541,14 @@ __global__ void __launch_bounds__(NB) bg_rows_kernel(ChunkParams C, ChunkBuf<flo
   EpiSmem<NB> S((char *)(S2 + T1 * NB), nb2);
   for (int i = threadIdx.x; i < 2 * nb2; i += NB) S.hw[i] = 0.0;
   Accum<NB> A;
-  const int ntiles = (C.count + NB - 1) / NB;
+  const int count = k2_count(C, B);
+  const int ntiles = (count + NB - 1) / NB;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int e = tile * NB + threadIdx.x;
+    const int j = tile * NB + threadIdx.x;
     double w = 0.0;
     int bin = -1;
-    if (e < C.count) {
+    if (j < count) {
+      const int e = k2_col(C, B, j);
       CV4<float> eps0pos, e0;
 #pragma unroll
       for (int a = 0; a < L; ++a) {
