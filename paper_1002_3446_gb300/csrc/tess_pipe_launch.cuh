@@ -19,7 +19,7 @@ struct PipePlan {
   int cap = 128;     // events per chunk
   int chunks = 1;
   size_t off_in = 0, off_efac = 0, off_wfac = 0, off_hval = 0, off_pass = 0;
-  size_t off_col = 0, off_orig = 0, off_tcount = 0, off_dcount = 0;  // cut-first only
+  size_t off_col = 0, off_orig = 0, off_tcount = 0, off_toff = 0, off_dcount = 0;  // cut-first only
   size_t kin_smem = 0;   // K1 dynamic shared memory (FP32 forms: the output tile)
   size_t buf_bytes = 0;  // one chunk buffer
   int sched = 0;         // Schedule
@@ -338,6 +338,8 @@ int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, in
     off = align256(off + (size_t)pl->cap * sizeof(int));
     pl->off_tcount = off;
     off = align256(off + (size_t)(pl->cap / kBlock + 1) * sizeof(int));
+    pl->off_toff = off;
+    off = align256(off + (size_t)(pl->cap / kBlock + 1) * sizeof(int));
     pl->off_dcount = off;
     off = align256(off + sizeof(int));
   }
@@ -365,6 +367,7 @@ cudaError_t run_pipeline_t(const EventParams &P, const PipePlan &pl, char *ws, c
       BB[b].col = (int *)(base + pl.off_col);
       BB[b].orig = (int *)(base + pl.off_orig);
       BB[b].tcount = (int *)(base + pl.off_tcount);
+      BB[b].toff = (int *)(base + pl.off_toff);
       BB[b].dcount = (int *)(base + pl.off_dcount);
     }
   }

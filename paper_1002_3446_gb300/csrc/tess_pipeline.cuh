@@ -35,6 +35,7 @@ struct ChunkBuf {
   int *col = nullptr;     // [cap] column of the j-th kept event of the chunk
   int *orig = nullptr;    // [cap] chunk index of the event in a kept column
   int *tcount = nullptr;  // [cap / kBlock] kept events per kinematics tile
+  int *toff = nullptr;    // [cap / kBlock] kept events before the tile
   int *dcount = nullptr;  // [1] kept events of the chunk
 };
 
@@ -142,6 +143,59 @@ __device__ __forceinline__ void polarisation_angles(const EventParams &P, uint64
       }
     }
   }
+}
+
+// Cuts and observables of the FP32 kinematics forms from the rounded
+// momenta pk (E, px, py, pz of the final-state gluons) and the partonic
+// rapidity y: pT, eta (lab), H_T, leading pT, and the pT / |eta| cuts.
+// Every operation's rounding is written out (no contraction left to the
+// compiler), so the kernels' instantiations (cut-first or not) give
+// bit-identical observables.
+template <int M>
+__device__ __forceinline__ void cuts_observables(const EventParams &P, const float (&pk)[M][4], float y, float (&px)[M],
+                                                 float (&py)[M], float (&pt)[M], float (&eta)[M], int &pass, float &sum,
+                                                 float &lead) {
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    px[i] = pk[i][1];
+    py[i] = pk[i][2];
+    const float pz = pk[i][3];
+    const float pt2 = __fmaf_rn(px[i], px[i], __fmul_rn(py[i], py[i]));
+    const float pabs = sqrtf(__fmaf_rn(pz, pz, pt2));
+    pt[i] = sqrtf(pt2);
+    eta[i] = __fadd_rn(__fmul_rn(0.5f, logf(__fdiv_rn(__fadd_rn(pabs, pz), __fsub_rn(pabs, pz)))), y);
+    sum = __fadd_rn(sum, pt[i]);
+    lead = fmaxf(lead, pt[i]);
+    pass &= (pt[i] > P.f_pt_min) & (fabsf(eta[i]) < P.f_eta_max);
+  }
+}
+
+// Delta R of every pair (the Delta R cut); returns the smallest Delta R^2.
+template <int M>
+__device__ __forceinline__ float pair_cuts(const EventParams &P, const float (&px)[M], const float (&py)[M],
+                                           const float (&eta)[M], int &pass) {
+  float dr2min = 1e30f;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+#pragma unroll
+    for (int j = i + 1; j < M; ++j) {
+      const float cross = __fmaf_rn(px[i], py[j], -__fmul_rn(py[i], px[j]));
+      const float dot = __fmaf_rn(px[i], px[j], __fmul_rn(py[i], py[j]));
+      const float dphi = atan2f(fabsf(cross), dot);
+      const float de = __fsub_rn(eta[i], eta[j]);
+      const float dr2 = __fmaf_rn(de, de, __fmul_rn(dphi, dphi));
+      dr2min = fminf(dr2min, dr2);
+      pass &= (dr2 > P.f_dr2_min);
+    }
+  }
+  return dr2min;
+}
+
+// One-loop alpha_s at mu_R = mu_r_factor H_T, FP32, roundings written out.
+__device__ __forceinline__ float alphas_f32(const EventParams &P, float ht) {
+  const float mu = __fmul_rn(P.f_mu_r_factor, ht);
+  const float l = __fsub_rn(logf(__fmul_rn(mu, mu)), P.f_ln_mz2);
+  return __fdiv_rn(P.f_alphas_mz, __fmaf_rn(P.f_asb0, l, 1.f));
 }
 
 // K1, FP64 form: every step in double precision.
@@ -420,7 +474,7 @@ __device__ __forceinline__ void scatter_legs(const EventParams &P, uint64_t ev, 
 // kernel sees them.  Every thread of the block must call it.
 template <bool CF>
 __device__ __forceinline__ int cut_first_slot(const EventParams &P, const ChunkBuf<float> &B, bool live, int pass,
-                                              uint64_t idx) {
+                                              uint64_t idx, int *kept = nullptr) {
   if constexpr (!CF) {
     return (int)threadIdx.x;
   } else {
@@ -437,6 +491,7 @@ __device__ __forceinline__ int cut_first_slot(const EventParams &P, const ChunkB
       tot += wsum[i];
     }
     if (threadIdx.x == 0) B.tcount[blockIdx.x] = tot;
+    if (kept) *kept = tot;
     if (live && !pass) {
       if (P.weight) P.weight[idx] = 0.0;
       if (P.me2) P.me2[idx] = 0.0;
@@ -521,35 +576,16 @@ __device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<fl
   }
 
   // cuts and observables in FP32
-  const float y = 0.5f * logf(x1 / x2);
-  float eta[M], pt[M], px[M], py[M];
+  const float y = __fmul_rn(0.5f, logf(__fdiv_rn(x1, x2)));
+  float eta[M], pt[M], px[M], py[M], pkf[M][4];
+#pragma unroll
+  for (int i = 0; i < M; ++i)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) pkf[i][m] = (float)pk[i][m];
   int pass = 1;
   float sum = 0.f, lead = 0.f;
-#pragma unroll
-  for (int i = 0; i < M; ++i) {
-    px[i] = (float)pk[i][1];
-    py[i] = (float)pk[i][2];
-    const float pz = (float)pk[i][3];
-    const float pt2 = px[i] * px[i] + py[i] * py[i];
-    const float pabs = sqrtf(pt2 + pz * pz);
-    pt[i] = sqrtf(pt2);
-    eta[i] = 0.5f * logf((pabs + pz) / (pabs - pz)) + y;
-    sum += pt[i];
-    lead = fmaxf(lead, pt[i]);
-    pass &= (pt[i] > P.f_pt_min) & (fabsf(eta[i]) < P.f_eta_max);
-  }
-  float dr2min = 1e30f;
-#pragma unroll
-  for (int i = 0; i < M; ++i) {
-#pragma unroll
-    for (int j = i + 1; j < M; ++j) {
-      const float dphi = atan2f(fabsf(px[i] * py[j] - py[i] * px[j]), px[i] * px[j] + py[i] * py[j]);
-      const float de = eta[i] - eta[j];
-      const float dr2 = de * de + dphi * dphi;
-      dr2min = fminf(dr2min, dr2);
-      pass &= (dr2 > P.f_dr2_min);
-    }
-  }
+  cuts_observables<M>(P, pkf, y, px, py, pt, eta, pass, sum, lead);
+  const float dr2min = pair_cuts<M>(P, px, py, eta, pass);
   const double ht = (double)sum, ptlead = (double)lead, rmin = (double)sqrtf(dr2min);
   if (live) {
     if (P.ht) P.ht[idx] = ht;
@@ -564,8 +600,7 @@ __device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<fl
 
   double wf = 0.0;
   if (pass) {
-    const float mu = P.f_mu_r_factor * sum;
-    const float as = P.f_alphas_mz / (1.f + P.f_asb0 * (logf(mu * mu) - P.f_ln_mz2));
+    const float as = alphas_f32(P, sum);
     const double g2 = 4.0 * 3.14159265358979323846 * (double)as;
     double gp = 1.0;
 #pragma unroll
@@ -635,6 +670,66 @@ __device__ __forceinline__ void pol_basis_rounded(float E, float px, float py, f
 // on this GPU), and the polarisation basis in FP32 from the rounded momenta.
 // The weight factor is assembled in FP32 with its power-of-two scale kept as
 // an exact exponent.
+// Second half of the double-float kinematics of one event (weight factor,
+// momenta in the power-of-two unit, polarisation basis, scatter into tile
+// column `slot`), from the first half's results.
+template <int N, bool RP, bool CF>
+__device__ __forceinline__ void kin_ds_back(const ChunkParams &C, const ChunkBuf<float> &B, float *tile, int slot,
+                                            int e, uint64_t ev, float rs_hi, float shat_hi, float sum, float lead,
+                                            float rmin, float x1, float x2, float ux1, float ux2, int pass,
+                                            const float (&pk)[N - 2][4]) {
+  constexpr int M = N - 2;
+  const EventParams &P = C.P;
+  const float lnxmin = P.f_lnxmin;
+  const int ec = CF ? (int)blockIdx.x * kBlock + slot : e;  // chunk column of the event's factors
+  if constexpr (CF) B.orig[ec] = e;
+
+  // momentum unit 2^-ex near 1/sqrt(s_hat); s' = s_hat 2^-2ex in [1/4, 1)
+  int ex;
+  frexpf(rs_hi, &ex);
+  const float sc = ldexpf(1.f, -ex);
+  const float sp = __fmul_rn(__fmul_rn(shat_hi, sc), sc);
+  double wf = 0.0;
+  if (pass) {
+    const float as = alphas_f32(P, sum);
+    const float g2 = __fmul_rn(4.f * 3.14159265358979323846f, as);
+    // f(x1) f(x2) with f(x) = 1.7 x^-0.2 (1 - x)^5: (x1 x2)^-0.2 from ln x1 + ln x2
+    const float t1 = __fsub_rn(1.f, x1), t2 = __fsub_rn(1.f, x2);
+    const float t1s = __fmul_rn(t1, t1), t2s = __fmul_rn(t2, t2);
+    const float p1 = __fmul_rn(__fmul_rn(t1s, t1s), t1), p2 = __fmul_rn(__fmul_rn(t2s, t2s), t2);
+    float F = __fmul_rn(__fmul_rn(__fmul_rn(2.89f, expf(__fmul_rn(__fmul_rn(-0.2f, lnxmin), __fadd_rn(ux1, ux2)))), p1),
+                        p2);
+#pragma unroll
+    for (int i = 0; i < N - 2; ++i) F = __fmul_rn(F, g2);
+    // s_hat^(m-3) = s'^(m-3) 2^(2 ex (m-3))
+    if (M >= 3) {
+#pragma unroll
+      for (int i = 0; i < M - 3; ++i) F = __fmul_rn(F, sp);
+    } else {
+      F = __fdiv_rn(F, sp);
+    }
+    if (F > 0.f) wf = scale_pow2(P.wk * (double)F, 2 * ex * (M - 3));
+  }
+  B.efac[ec] = scale_pow2(P.efac, -2 * ex * (N - 4));
+  B.wfac[ec] = wf;
+  B.pass[ec] = (uint8_t)pass;
+  if (B.hval) B.hval[ec] = (double)(P.hist_obs == 0 ? lead : (P.hist_obs == 1 ? sum : rmin));
+
+  float lk[N][4], le1[N][3], le2[N][2];
+  const float hs = 0.5f * rs_hi * sc;
+  lk[0][0] = -hs; lk[0][1] = 0.f; lk[0][2] = 0.f; lk[0][3] = -hs;
+  lk[1][0] = -hs; lk[1][1] = 0.f; lk[1][2] = 0.f; lk[1][3] = hs;
+  le1[0][0] = 1.f; le1[0][1] = 0.f; le1[0][2] = 0.f; le2[0][0] = 0.f; le2[0][1] = 1.f;   // physical +z
+  le1[1][0] = -1.f; le1[1][1] = 0.f; le1[1][2] = 0.f; le2[1][0] = 0.f; le2[1][1] = 1.f;  // physical -z
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) lk[2 + i][m] = pk[i][m] * sc;
+    pol_basis_rounded(pk[i][0], pk[i][1], pk[i][2], pk[i][3], le1[2 + i], le2[2 + i]);
+  }
+  scatter_legs<N, RP>(P, ev, tile, slot, lk, le1, le2);
+}
+
 template <int N, bool RP, bool CF>
 __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<float> &B, int e, float *tile,
                                      bool live) {
@@ -714,35 +809,12 @@ __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<floa
 
   // cuts and observables in FP32 from the rounded momenta; the partonic
   // rapidity 0.5 ln(x1 / x2) from the logarithms drawn above
-  const float y = 0.5f * lnxmin * (ux1 - ux2);
+  const float y = __fmul_rn(__fmul_rn(0.5f, lnxmin), __fsub_rn(ux1, ux2));
   float eta[M], pt[M], px[M], py[M];
   int pass = 1;
   float sum = 0.f, lead = 0.f;
-#pragma unroll
-  for (int i = 0; i < M; ++i) {
-    px[i] = pk[i][1];
-    py[i] = pk[i][2];
-    const float pz = pk[i][3];
-    const float pt2 = px[i] * px[i] + py[i] * py[i];
-    const float pabs = sqrtf(pt2 + pz * pz);
-    pt[i] = sqrtf(pt2);
-    eta[i] = 0.5f * logf((pabs + pz) / (pabs - pz)) + y;
-    sum += pt[i];
-    lead = fmaxf(lead, pt[i]);
-    pass &= (pt[i] > P.f_pt_min) & (fabsf(eta[i]) < P.f_eta_max);
-  }
-  float dr2min = 1e30f;
-#pragma unroll
-  for (int i = 0; i < M; ++i) {
-#pragma unroll
-    for (int j = i + 1; j < M; ++j) {
-      const float dphi = atan2f(fabsf(px[i] * py[j] - py[i] * px[j]), px[i] * px[j] + py[i] * py[j]);
-      const float de = eta[i] - eta[j];
-      const float dr2 = de * de + dphi * dphi;
-      dr2min = fminf(dr2min, dr2);
-      pass &= (dr2 > P.f_dr2_min);
-    }
-  }
+  cuts_observables<M>(P, pk, y, px, py, pt, eta, pass, sum, lead);
+  float dr2min = pair_cuts<M>(P, px, py, eta, pass);
   const float rmin = sqrtf(dr2min);
   if (live) {
     if (P.ht) P.ht[idx] = (double)sum;
@@ -750,54 +822,42 @@ __device__ __forceinline__ void kin_ds(const ChunkParams &C, const ChunkBuf<floa
     if (P.rmin) P.rmin[idx] = (double)rmin;
     if (P.pass) P.pass[idx] = (uint8_t)pass;
   }
-  const int slot = cut_first_slot<CF>(P, B, live, pass, idx);
-  if (slot < 0) return;
-  const int ec = CF ? (int)blockIdx.x * kBlock + slot : e;  // chunk column of the event's factors
-  if constexpr (CF) B.orig[ec] = e;
-
-  // momentum unit 2^-ex near 1/sqrt(s_hat); s' = s_hat 2^-2ex in [1/4, 1)
-  int ex;
-  frexpf(rs.hi, &ex);
-  const float sc = ldexpf(1.f, -ex);
-  const float sp = shat.hi * sc * sc;
-  double wf = 0.0;
-  if (pass) {
-    const float mu = P.f_mu_r_factor * sum;
-    const float as = P.f_alphas_mz / (1.f + P.f_asb0 * (logf(mu * mu) - P.f_ln_mz2));
-    const float g2 = 4.f * 3.14159265358979323846f * as;
-    // f(x1) f(x2) with f(x) = 1.7 x^-0.2 (1 - x)^5: (x1 x2)^-0.2 from ln x1 + ln x2
-    const float t1 = 1.f - x1, t2 = 1.f - x2;
-    const float t1s = t1 * t1, t2s = t2 * t2;
-    float F = 2.89f * expf(-0.2f * lnxmin * (ux1 + ux2)) * (t1s * t1s * t1) * (t2s * t2s * t2);
+  if constexpr (!CF) {
+    kin_ds_back<N, RP, CF>(C, B, tile, (int)threadIdx.x, e, ev, rs.hi, shat.hi, sum, lead, rmin, x1, x2, ux1, ux2,
+                           pass, pk);
+  } else {
+    // the block's kept events are finished by its first threads, one each,
+    // with their first-half results staged in shared memory
+    constexpr int NS = 4 * M + 12;
+    __shared__ uint32_t st[NS][kBlock];
+    int kept = 0;
+    int slot = cut_first_slot<CF>(P, B, live, pass, idx, &kept);
+    if (slot >= 0) {
+      const float v[12] = {rs.hi, shat.hi, sum, lead, rmin, x1, x2, ux1, ux2, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int i = 0; i < N - 2; ++i) F *= g2;
-    // s_hat^(m-3) = s'^(m-3) 2^(2 ex (m-3))
-    if (M >= 3) {
+      for (int q = 0; q < 9; ++q) st[q][slot] = __float_as_uint(v[q]);
+      st[9][slot] = (uint32_t)e;
+      st[10][slot] = (uint32_t)ev;
+      st[11][slot] = (uint32_t)(ev >> 32);
 #pragma unroll
-      for (int i = 0; i < M - 3; ++i) F *= sp;
-    } else {
-      F /= sp;
+      for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) st[12 + 4 * i + m][slot] = __float_as_uint(pk[i][m]);
     }
-    if (F > 0.f) wf = scale_pow2(P.wk * (double)F, 2 * ex * (M - 3));
-  }
-  B.efac[ec] = scale_pow2(P.efac, -2 * ex * (N - 4));
-  B.wfac[ec] = wf;
-  B.pass[ec] = (uint8_t)pass;
-  if (B.hval) B.hval[ec] = (double)(P.hist_obs == 0 ? lead : (P.hist_obs == 1 ? sum : rmin));
-
-  float lk[N][4], le1[N][3], le2[N][2];
-  const float hs = 0.5f * rs.hi * sc;
-  lk[0][0] = -hs; lk[0][1] = 0.f; lk[0][2] = 0.f; lk[0][3] = -hs;
-  lk[1][0] = -hs; lk[1][1] = 0.f; lk[1][2] = 0.f; lk[1][3] = hs;
-  le1[0][0] = 1.f; le1[0][1] = 0.f; le1[0][2] = 0.f; le2[0][0] = 0.f; le2[0][1] = 1.f;   // physical +z
-  le1[1][0] = -1.f; le1[1][1] = 0.f; le1[1][2] = 0.f; le2[1][0] = 0.f; le2[1][1] = 1.f;  // physical -z
+    __syncthreads();
+    slot = (int)threadIdx.x;
+    if (slot >= kept) return;
+    float q[9], pq[M][4];
 #pragma unroll
-  for (int i = 0; i < M; ++i) {
+    for (int i = 0; i < 9; ++i) q[i] = __uint_as_float(st[i][slot]);
 #pragma unroll
-    for (int m = 0; m < 4; ++m) lk[2 + i][m] = pk[i][m] * sc;
-    pol_basis_rounded(pk[i][0], pk[i][1], pk[i][2], pk[i][3], le1[2 + i], le2[2 + i]);
+    for (int i = 0; i < M; ++i)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) pq[i][m] = __uint_as_float(st[12 + 4 * i + m][slot]);
+    const int eo = (int)st[9][slot];
+    const uint64_t evo = (uint64_t)st[10][slot] | ((uint64_t)st[11][slot] << 32);
+    kin_ds_back<N, RP, CF>(C, B, tile, slot, eo, evo, q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], q[8], 1, pq);
   }
-  scatter_legs<N, RP>(P, ev, tile, slot, lk, le1, le2);
 }
 
 // K1 kernels.  The FP32 forms take kin_tile_bytes<N>() of dynamic shared
@@ -832,11 +892,10 @@ __global__ void __launch_bounds__(kBlock) kin_ds_kernel(ChunkParams C, ChunkBuf<
   store_tile<N>(B, kin_tile);
 }
 
-// Cut-first: exclusive scan of the kinematics tiles' kept counts and the
-// list of kept columns of the chunk (kept index j -> column), in event
-// order; one block.
+// Cut-first: exclusive scan of the kinematics tiles' kept counts (one
+// block) into per-tile offsets and the chunk's kept total ...
 template <int NT>
-__global__ void __launch_bounds__(NT) cut_first_index_kernel(const int *tcount, int ntiles, int *col, int *dcount) {
+__global__ void __launch_bounds__(NT) cut_first_scan_kernel(const int *tcount, int ntiles, int *toff, int *dcount) {
   __shared__ int part[NT];
   const int t = threadIdx.x;
   const int per = (ntiles + NT - 1) / NT;
@@ -853,11 +912,18 @@ __global__ void __launch_bounds__(NT) cut_first_index_kernel(const int *tcount, 
   }
   int off = part[t] - sum;
   for (int i = t0; i < t1; ++i) {
-    const int c = tcount[i];
-    for (int q = 0; q < c; ++q) col[off + q] = i * kBlock + q;
-    off += c;
+    toff[i] = off;
+    off += tcount[i];
   }
   if (t == NT - 1) *dcount = part[NT - 1];
+}
+
+// ... then the list of kept columns in event order (kept index j -> column),
+// one block per kinematics tile.
+template <int NB>
+__global__ void __launch_bounds__(NB) cut_first_fill_kernel(const int *tcount, const int *toff, int *col) {
+  const int t = blockIdx.x;
+  if ((int)threadIdx.x < tcount[t]) col[toff[t] + threadIdx.x] = t * NB + threadIdx.x;
 }
 
 // The kinematics kernel of a call: double-float or plain form, sampled
@@ -885,7 +951,9 @@ __host__ inline cudaError_t launch_kin(const ChunkParams &C, const ChunkBuf<R> &
     if (C.P.cut_first) {
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
-      cut_first_index_kernel<1024><<<1, 1024, 0, s>>>(B.tcount, (int)grid, B.col, B.dcount);
+      cut_first_scan_kernel<1024><<<1, 1024, 0, s>>>(B.tcount, (int)grid, B.toff, B.dcount);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      cut_first_fill_kernel<kBlock><<<grid, kBlock, 0, s>>>(B.tcount, B.toff, B.col);
     }
     return cudaGetLastError();
   } else {
