@@ -325,6 +325,15 @@ int tess_gradients(tess_ctx *ctx, const tess_process *proc, uint64_t n_events, c
 int tess_me2(tess_ctx *ctx, int n, int precision, uint64_t n_events, const double *k, const uint8_t *order,
              const uint32_t *hel, double *me2, void *stream);
 
+/* Gauge check of Sec. 4 (a precision diagnostic), same arguments as tess_me2:
+ * ratio[e] = |k^ . Num|^2 / |eps . Num|^2 for the leg order_e[0] contracted
+ * last, Num the un-propagated current of the other legs and k^ that leg's
+ * momentum divided by its energy.  Current conservation makes the
+ * numerator vanish exactly, so the ratio measures the rounding of the
+ * evaluation (FP32 currents vs FP64). */
+int tess_gauge_ratio(tess_ctx *ctx, int n, int precision, uint64_t n_events, const double *k, const uint8_t *order,
+                     const uint32_t *hel, double *ratio, void *stream);
+
 /* Cross section from a device acc (synchronises the stream):
  * host out[4] = {sigma_pb, mc_error_pb, n_pass, n_generated}.
  * Returns TESS_E_CUDA (after filling out) if acc counts stalled blocks,

@@ -42,7 +42,7 @@ EXPORTED = ["tess_version", "tess_last_error", "tess_init", "tess_destroy", "tes
             "tess_me2", "tess_result", "tess_weights", "tess_histograms", "tess_generate_noalloc",
             "tess_kernel_launches", "tess_workspace_size_batched", "tess_generate_batched", "tess_autotune",
             "tess_stage_timing", "tess_stage_times", "tess_draws", "tess_gradients", "tess_select_variant",
-            "tess_plan_info", "tess_gradients_workspace_size"]
+            "tess_plan_info", "tess_gradients_workspace_size", "tess_gauge_ratio"]
 
 
 class TessError(RuntimeError):
@@ -113,6 +113,7 @@ def _load():
         lib.tess_stage_times.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int)]
         lib.tess_generate.argtypes = [vp, P(tess_process), u64, u64, u64, P(tess_outputs), vp, ctypes.c_size_t, vp]
         lib.tess_me2.argtypes = [vp, i32, i32, u64, vp, vp, vp, vp, vp]
+        lib.tess_gauge_ratio.argtypes = [vp, i32, i32, u64, vp, vp, vp, vp, vp]
         lib.tess_generate_noalloc.argtypes = [vp, P(tess_process), u64, u64, u64, P(tess_outputs), vp]
         lib.tess_result.argtypes = [vp, vp, P(ctypes.c_double), vp]
         lib.tess_weights.argtypes = [vp, P(tess_outputs), u64, vp, vp, vp, vp]
@@ -336,6 +337,11 @@ def tess_generate_noalloc(ctx, proc, seed, first_event, n_events, outputs, strea
 def tess_me2(ctx, n, precision, k, order, hel, me2, stream=None):
     _check(_load().tess_me2(ctx, int(n), int(precision), int(me2.numel()), _ptr(k), _ptr(order), _ptr(hel),
                             _ptr(me2), _stream(stream)))
+
+
+def tess_gauge_ratio(ctx, n, precision, k, order, hel, ratio, stream=None):
+    _check(_load().tess_gauge_ratio(ctx, int(n), int(precision), int(ratio.numel()), _ptr(k), _ptr(order), _ptr(hel),
+                                    _ptr(ratio), _stream(stream)))
 
 
 def tess_result(ctx, acc, stream=None, allow_nonfinite=False):

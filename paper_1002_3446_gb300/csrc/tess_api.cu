@@ -20,9 +20,9 @@ cudaError_t launch_generate_f32(int n, bool sum, const EventParams &P, double *p
 int grid_generate_f64(int n, bool sum, int sm_count, uint64_t n_events, int hist_bins);
 int grid_generate_f32(int n, bool sum, int sm_count, uint64_t n_events, int hist_bins);
 cudaError_t launch_me2_f64(int n, uint64_t n_events, const double *k, const uint8_t *order, const uint32_t *hel,
-                           double *me2, cudaStream_t s);
+                           double *me2, cudaStream_t s, bool gauge = false);
 cudaError_t launch_me2_f32(int n, uint64_t n_events, const double *k, const uint8_t *order, const uint32_t *hel,
-                           double *me2, cudaStream_t s);
+                           double *me2, cudaStream_t s, bool gauge = false);
 cudaError_t launch_grad_a(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s,
                            const GradStreams &gs);
 cudaError_t launch_grad_b(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s,
@@ -1004,8 +1004,9 @@ int tess_gradients(tess_ctx *ctx, const tess_process *proc, uint64_t n_events, c
   return ok();
 }
 
-int tess_me2(tess_ctx *ctx, int n, int precision, uint64_t n_events, const double *k, const uint8_t *order,
-             const uint32_t *hel, double *me2, void *stream) {
+namespace {
+int me2_or_gauge(tess_ctx *ctx, int n, int precision, uint64_t n_events, const double *k, const uint8_t *order,
+                 const uint32_t *hel, double *me2, void *stream, bool gauge) {
   if (!ctx) return fail(TESS_E_INVALID, "ctx is NULL");
   if (n < TESS_MIN_N || n > TESS_MAX_N) return fail(TESS_E_UNSUPPORTED, "n = %d outside %d..%d", n, TESS_MIN_N, TESS_MAX_N);
   if (precision != TESS_FP64 && precision != TESS_FP32_CURRENTS && precision != TESS_FP32_DS)
@@ -1020,10 +1021,21 @@ int tess_me2(tess_ctx *ctx, int n, int precision, uint64_t n_events, const doubl
       (rc = check_device_ptr(hel, ctx->device, "hel")) || (rc = check_device_ptr(me2, ctx->device, "me2")))
     return rc;
   cudaStream_t s = (cudaStream_t)stream;
-  const cudaError_t e = precision == TESS_FP64 ? tess::launch_me2_f64(n, n_events, k, order, hel, me2, s)
-                                               : tess::launch_me2_f32(n, n_events, k, order, hel, me2, s);
-  if (e != cudaSuccess) return cuda_fail(e, "me2 kernel launch");
+  const cudaError_t e = precision == TESS_FP64 ? tess::launch_me2_f64(n, n_events, k, order, hel, me2, s, gauge)
+                                               : tess::launch_me2_f32(n, n_events, k, order, hel, me2, s, gauge);
+  if (e != cudaSuccess) return cuda_fail(e, gauge ? "gauge kernel launch" : "me2 kernel launch");
   return ok();
+}
+}  // namespace
+
+int tess_me2(tess_ctx *ctx, int n, int precision, uint64_t n_events, const double *k, const uint8_t *order,
+             const uint32_t *hel, double *me2, void *stream) {
+  return me2_or_gauge(ctx, n, precision, n_events, k, order, hel, me2, stream, false);
+}
+
+int tess_gauge_ratio(tess_ctx *ctx, int n, int precision, uint64_t n_events, const double *k, const uint8_t *order,
+                     const uint32_t *hel, double *ratio, void *stream) {
+  return me2_or_gauge(ctx, n, precision, n_events, k, order, hel, ratio, stream, true);
 }
 
 int tess_result(tess_ctx *ctx, const double *acc, double *out, void *stream) {

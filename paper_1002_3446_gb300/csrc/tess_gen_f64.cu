@@ -49,17 +49,17 @@ int grid_generate_f64(int n, bool sum, int sm_count, uint64_t n_events, int hist
 }
 
 cudaError_t launch_me2_f64(int n, uint64_t n_events, const double *k, const uint8_t *order, const uint32_t *hel,
-                              double *me2, cudaStream_t s) {
+                              double *me2, cudaStream_t s, bool gauge) {
   switch (n) {
-    case 4: return launch_me2_t<4, double>(n_events, k, order, hel, me2, s);
-    case 5: return launch_me2_t<5, double>(n_events, k, order, hel, me2, s);
-    case 6: return launch_me2_t<6, double>(n_events, k, order, hel, me2, s);
-    case 7: return launch_me2_t<7, double>(n_events, k, order, hel, me2, s);
-    case 8: return launch_me2_t<8, double>(n_events, k, order, hel, me2, s);
-    case 9: return launch_me2_t<9, double>(n_events, k, order, hel, me2, s);
-    case 10: return launch_me2_t<10, double>(n_events, k, order, hel, me2, s);
-    case 11: return launch_me2_t<11, double>(n_events, k, order, hel, me2, s);
-    case 12: return launch_me2_t<12, double>(n_events, k, order, hel, me2, s);
+    case 4: return launch_me2_t<4, double>(n_events, k, order, hel, me2, s, gauge);
+    case 5: return launch_me2_t<5, double>(n_events, k, order, hel, me2, s, gauge);
+    case 6: return launch_me2_t<6, double>(n_events, k, order, hel, me2, s, gauge);
+    case 7: return launch_me2_t<7, double>(n_events, k, order, hel, me2, s, gauge);
+    case 8: return launch_me2_t<8, double>(n_events, k, order, hel, me2, s, gauge);
+    case 9: return launch_me2_t<9, double>(n_events, k, order, hel, me2, s, gauge);
+    case 10: return launch_me2_t<10, double>(n_events, k, order, hel, me2, s, gauge);
+    case 11: return launch_me2_t<11, double>(n_events, k, order, hel, me2, s, gauge);
+    case 12: return launch_me2_t<12, double>(n_events, k, order, hel, me2, s, gauge);
     default: return cudaErrorInvalidValue;
   }
 }
