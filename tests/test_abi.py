@@ -52,8 +52,9 @@ def test_struct_layout_matches_c():
 #include <stddef.h>
 #include "tess.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(tess_process), offsetof(tess_process, sqrt_s),
-         offsetof(tess_process, hist_hi), sizeof(tess_outputs), offsetof(tess_outputs, hist));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(tess_process), offsetof(tess_process, sqrt_s),
+         offsetof(tess_process, hist_hi), sizeof(tess_outputs), offsetof(tess_outputs, hist),
+         offsetof(tess_process, flags));
   return 0;
 }
 """
@@ -64,7 +65,8 @@ int main(void) {
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         vals = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     P, O = tess.tess_process, tess.tess_outputs
-    assert vals == [ctypes.sizeof(P), P.sqrt_s.offset, P.hist_hi.offset, ctypes.sizeof(O), O.hist.offset]
+    assert vals == [ctypes.sizeof(P), P.sqrt_s.offset, P.hist_hi.offset, ctypes.sizeof(O), O.hist.offset,
+                    P.flags.offset]
 
 
 def test_version_and_error_strings():
