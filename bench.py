@@ -338,7 +338,7 @@ def run_tess(args):
         traffic = read_traffic(args.workload + ("_rp" if rp else "") + ("_cf" if cf else ""), plan["variant"],
                                min(N, plan_cap(tess, ctx, proc, N)))
         line = {
-            "metric": f"events/s (gg->{n - 2}g, {n}-point, {'FP64' if wl['precision'] == 'fp64' else 'FP32 currents'})",
+            "metric": workload_metric(wl),
             "value": value,
             "unit": "events/s",
             "n_gpus": ws,
@@ -353,12 +353,8 @@ def run_tess(args):
                              "rescale; f64 weights and accumulation"),
                       "fp64": "f64"}[wl["precision"]],
             "data": "synthetic (counter-based Philox draws, toy gluon PDF)",
-            "config": {"workload": f"{args.workload}: gg->{n - 2} gluons, {N} events per GPU, seed 1, sqrt(S)=14 TeV, "
-                                   f"pT>{wl['pt_min']:g} |eta|<2.5 dR>0.4, "
-                                   + ("random real polarisations + ordering sampled" if rp
-                                      else "helicity+ordering sampled")
-                                   + (", cut-first (amplitudes only for events passing the cuts)" if cf else ""),
-                       "events_per_gpu": N, "n_gluons": n, "l2": "flushed between timed steps (256 MB write)"},
+            "config": dict(workload_config(args.workload, wl, N, rp, cf),
+                           l2="flushed between timed steps (256 MB write)"),
             "roofline": {"bound": "alu", "kernel": "Berends-Giele amplitude kernel", "achieved": achieved,
                          "peak": FP64_PEAK_TFLOPS if wl["precision"] == "fp64" else FP32_PEAK_TFLOPS,
                          "unit": "TFLOP/s",
@@ -580,6 +576,23 @@ def cpu_baseline(wl, budget_s=12.0, events=None, random_pol=False):
             "sample": f"events 0..{events - 1} of seed 1 of the same workload ({dt:.1f} s)"}
 
 
+def workload_metric(wl):
+    n = wl["n"]
+    return f"events/s (gg->{n - 2}g, {n}-point, {'FP64' if wl['precision'] == 'fp64' else 'FP32 currents'})"
+
+
+def workload_config(name, wl, N, rp=False, cf=False):
+    """The workload description both arms print."""
+    n = wl["n"]
+    return {"workload": f"{name}: gg->{n - 2} gluons, {N} events per GPU, seed 1, sqrt(S)=14 TeV, "
+                        f"pT>{wl['pt_min']:g} |eta|<2.5 dR>0.4, "
+                        + ("random real polarisations + ordering sampled" if rp else
+                           ("helicities and orderings summed exactly" if wl["hel"] == "sum"
+                            else "helicity+ordering sampled"))
+                        + (", cut-first (amplitudes only for events passing the cuts)" if cf else ""),
+            "events_per_gpu": N, "n_gluons": n}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -594,7 +607,7 @@ def run_reference(args):
     v = statistics.mean(x["value"] for x in vals)
     line = {
         "impl": "reference",
-        "metric": f"events/s (gg->{n - 2}g, {n}-point, FP32 currents)",
+        "metric": workload_metric(wl),
         "value": v,
         "unit": "events/s",
         "n_gpus": ws,
@@ -606,7 +619,7 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic (counter-based Philox draws, toy gluon PDF)",
-        "config": {"workload": args.workload, "events_per_gpu": wl["n_events"], "n_gluons": n},
+        "config": dict(workload_config(args.workload, wl, wl["n_events"]), l2="host cores (the oracle)"),
         "cpu_baseline": {"value": v, "unit": "events/s", "cores": vals[0]["cores"], "kind": "oracle",
                          "sample": vals[0]["sample"]},
         "e2e": {"value": v, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
