@@ -215,9 +215,10 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
  * (register form compiled for more resident blocks), TESS_K2_REG_TMA (inputs
  * staged in shared memory by bulk copies), TESS_K2_REG_TMA_HI (the same for
  * more resident blocks), TESS_K2_PAIR32 / TESS_K2_PAIR64 (two threads per
- * event sharing its current table in shared memory), and for TESS_POL_RANDOM
- * only TESS_K2_REAL / TESS_K2_REAL_HI (real currents in registers) -- each
- * under every chunk schedule
+ * event sharing its current table in shared memory), TESS_K2_PAIR_W (the
+ * O(n^3) tensor rewrite of the four-vertex sum, Sec. 3), and for
+ * TESS_POL_RANDOM only TESS_K2_REAL / TESS_K2_REAL_HI / TESS_K2_ROWS_REAL
+ * (real currents) -- each under every chunk schedule
  * TESS_SCHED_* below.  acc_scratch: device, TESS_ACC_LEN doubles (not
  * written: the timed runs stop before folding their sums); workspace:
  * tess_workspace_size(proc, probe_events) bytes -- that size already covers
@@ -253,6 +254,7 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
 #define TESS_K2_REAL 9       /* real currents in registers (FP32, TESS_POL_RANDOM only, n <= 9) */
 #define TESS_K2_REAL_HI 10   /* the real form compiled for more resident blocks (FP32, TESS_POL_RANDOM, n <= 8) */
 #define TESS_K2_ROWS_REAL 11 /* row form with real currents, 64 threads (FP32, TESS_POL_RANDOM, n >= 8) */
+#define TESS_K2_PAIR_W 12    /* O(n^3) tensor rewrite of the four-vertex sum, two threads per event (FP32) */
 #define TESS_SCHED_SERIAL 0
 #define TESS_SCHED_OVERLAP 1
 #define TESS_SCHED_OVERLAP_TILES 2

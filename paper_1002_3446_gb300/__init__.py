@@ -34,7 +34,7 @@ TESS_FLAG_CUT_FIRST = 1
 TESS_OBS_PTLEAD, TESS_OBS_HT, TESS_OBS_RMIN = 0, 1, 2
 TESS_K2_REG, TESS_K2_ROWS32, TESS_K2_ROWS64, TESS_K2_LOOP, TESS_K2_REG_HI, TESS_K2_REG_TMA = 0, 1, 2, 3, 4, 5
 TESS_K2_REG_TMA_HI, TESS_K2_PAIR32, TESS_K2_PAIR64, TESS_K2_REAL, TESS_K2_REAL_HI = 6, 7, 8, 9, 10
-TESS_K2_ROWS_REAL = 11
+TESS_K2_ROWS_REAL, TESS_K2_PAIR_W = 11, 12
 TESS_SCHED_SERIAL, TESS_SCHED_OVERLAP, TESS_SCHED_OVERLAP_TILES, TESS_SCHED_SERIAL_TILES = 0, 1, 2, 3
 
 # Every symbol include/tess.h declares (checked by the ABI tests).

@@ -6,6 +6,7 @@
 #include <cudaTypedefs.h>
 
 #include "tess_pair.cuh"
+#include "tess_pair_w.cuh"
 #include "tess_pipeline.cuh"
 
 namespace tess {
@@ -110,6 +111,9 @@ inline cudaError_t encode_rows_map(CUtensorMap *map, const float *base, int rows
 //   K2_REAL_HI the real form compiled for more resident blocks   FP32, n <= 8
 //   K2_ROWS_REAL  row form with real currents, 64 threads; random real
 //              polarisations only                                 FP32, n >= 8
+//   K2_PAIR_W  tensor form: the O(n^3) rewrite of the four-vertex sum
+//              (antisymmetric tensors per set), lane-pair layout,
+//              32 events per block                               FP32, any n
 enum K2Form {
   K2_REG = 0,
   K2_ROWS32 = 1,
@@ -123,7 +127,8 @@ enum K2Form {
   K2_REAL = 9,
   K2_REAL_HI = 10,
   K2_ROWS_REAL = 11,
-  K2_NFORMS = 12
+  K2_PAIR_W = 12,
+  K2_NFORMS = 13
 };
 
 // What a call offers the amplitude kernel: CAP_REAL_EPS, its polarisation
@@ -142,6 +147,7 @@ constexpr bool k2_valid(int f, unsigned caps) {
       case K2_REAL: return real_eps && N <= 9;
       case K2_REAL_HI: return real_eps && N <= 8;
       case K2_ROWS_REAL: return real_eps && N >= 8;
+      case K2_PAIR_W: return true;
       case K2_REG_TMA: return N <= 8 && !cut_first;
       case K2_REG_TMA_HI: return N <= 7 && !cut_first;
       case K2_REG: return N <= 8;
@@ -164,16 +170,18 @@ template <int N, typename R, int F>
 struct K2V {
   static constexpr int L = N - 1;
   static constexpr int block =
-      (F == K2_ROWS32 || F == K2_PAIR32)
+      (F == K2_ROWS32 || F == K2_PAIR32 || F == K2_PAIR_W)
           ? 32
           : ((F == K2_ROWS64 || F == K2_PAIR64 || F == K2_ROWS_REAL) ? 64 : 128);
   static constexpr bool rows = F == K2_ROWS32 || F == K2_ROWS64;
-  static constexpr bool pair = F == K2_PAIR32 || F == K2_PAIR64;
+  static constexpr bool pair = F == K2_PAIR32 || F == K2_PAIR64 || F == K2_PAIR_W;
   static constexpr int threads = pair ? 2 * block : block;  // block = events per tile
   static constexpr int hi_blocks = N >= 6 ? 3 : 4;
   static constexpr int real_hi_blocks = N >= 8 ? 3 : 4;
   static void *fn() {
-    if constexpr (F == K2_ROWS_REAL)
+    if constexpr (F == K2_PAIR_W)
+      return (void *)bg_pair_w_kernel<N, block>;
+    else if constexpr (F == K2_ROWS_REAL)
       return (void *)bg_rows_real_kernel<N, block>;
     else if constexpr (F == K2_REAL)
       return (void *)bg_real_kernel<N, 128>;
@@ -195,7 +203,9 @@ struct K2V {
       return (void *)bg_loop_kernel<N, 128>;
   }
   static size_t smem(int hist_bins) {
-    if constexpr (F == K2_ROWS_REAL)
+    if constexpr (F == K2_PAIR_W)
+      return PairWSmem<L, block>::bytes + EpiSmem<threads>::bytes(hist_bins);
+    else if constexpr (F == K2_ROWS_REAL)
       return ((rows_real_smem_per_thread<L>() * block + 15) & ~(size_t)15) + EpiSmem<block>::bytes(hist_bins);
     else if constexpr (pair)
       return PairSmem<L, block>::bytes + EpiSmem<threads>::bytes(hist_bins);
@@ -210,7 +220,9 @@ struct K2V {
   // map: tensor map of B.in (staged forms only)
   static cudaError_t launch(const ChunkParams &C, const ChunkBuf<R> &B, double *partials, int grid, size_t smem,
                             cudaStream_t s, const CUtensorMap *map) {
-    if constexpr (F == K2_ROWS_REAL)
+    if constexpr (F == K2_PAIR_W)
+      bg_pair_w_kernel<N, block><<<grid, threads, smem, s>>>(C, B, partials);
+    else if constexpr (F == K2_ROWS_REAL)
       bg_rows_real_kernel<N, block><<<grid, block, smem, s>>>(C, B, partials);
     else if constexpr (F == K2_REAL)
       bg_real_kernel<N, 128><<<grid, 128, smem, s>>>(C, B, partials);
@@ -242,6 +254,7 @@ auto with_form(int f, Fn &&fn) {
   } else {
     if (f == K2_PAIR32) return fn(K2V<N, R, K2_PAIR32>{});
     if (f == K2_PAIR64) return fn(K2V<N, R, K2_PAIR64>{});
+    if (f == K2_PAIR_W) return fn(K2V<N, R, K2_PAIR_W>{});
     if constexpr (N <= 9) {
       if (f == K2_REAL) return fn(K2V<N, R, K2_REAL>{});
     }
