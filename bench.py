@@ -517,7 +517,7 @@ def plan_cap(tess, ctx, proc, n_events):
 
 
 PIPELINE_SOURCES = ("tess_async.cuh", "tess_bg.cuh", "tess_event.cuh", "tess_kernels.cuh", "tess_math.cuh",
-                    "tess_pair.cuh", "tess_pipe_launch.cuh", "tess_pipeline.cuh")
+                    "tess_pair.cuh", "tess_pair_w.cuh", "tess_pipe_launch.cuh", "tess_pipeline.cuh")
 
 
 def kernel_source_hash():
