@@ -51,17 +51,17 @@ class Process(ctypes.Structure):
         ("hist_obs", ctypes.c_int),
         ("mu_r_factor", ctypes.c_double),
         ("hist_bins", ctypes.c_int),
-        ("pad_", ctypes.c_int),
+        ("grid", ctypes.c_int),
         ("hist_lo", ctypes.c_double),
         ("hist_hi", ctypes.c_double),
     ]
 
 
 def process(n, hel_mode=1, sqrt_s=14000.0, pt_min=20.0, eta_max=2.5, dr_min=0.4, alphas_mz=0.118,
-            mz=91.19, nf=5, mu_r_factor=0.5, hist_obs=0, hist_bins=50, hist_lo=20.0, hist_hi=1020.0):
+            mz=91.19, nf=5, mu_r_factor=0.5, hist_obs=0, hist_bins=50, hist_lo=20.0, hist_hi=1020.0, grid=0):
     return Process(n=n, hel_mode=hel_mode, sqrt_s=sqrt_s, pt_min=pt_min, eta_max=eta_max, dr_min=dr_min,
                    alphas_mz=alphas_mz, mz=mz, nf=nf, hist_obs=hist_obs, mu_r_factor=mu_r_factor,
-                   hist_bins=hist_bins, pad_=0, hist_lo=hist_lo, hist_hi=hist_hi)
+                   hist_bins=hist_bins, grid=grid, hist_lo=hist_lo, hist_hi=hist_hi)
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -81,6 +81,10 @@ def lib():
             h.orc_n_uniforms.argtypes = [ctypes.c_int]
             h.orc_n_uniforms_mode.argtypes = [ctypes.c_int, ctypes.c_int]
             h.orc_polvec_real.argtypes = [_D, ctypes.c_double, _D]
+            h.orc_grid_pdf.argtypes = [ctypes.POINTER(Process), ctypes.c_float]
+            h.orc_grid_pdf.restype = ctypes.c_float
+            h.orc_grid_alphas.argtypes = [ctypes.POINTER(Process), ctypes.c_float]
+            h.orc_grid_alphas.restype = ctypes.c_float
             h.orc_xg.argtypes = [ctypes.c_double]
             h.orc_xg.restype = ctypes.c_double
             h.orc_rambo.argtypes = [ctypes.c_int, ctypes.c_double, _D, _D]
@@ -156,6 +160,16 @@ def polvec(p, h):
     e = np.zeros(8)
     lib().orc_polvec(_dp(p), int(h), _dp(e))
     return e[0::2] + 1j * e[1::2]
+
+
+def grid_pdf(proc, u):
+    """Grid-mode x g(x) at the float draw u (interpolated table)."""
+    return lib().orc_grid_pdf(ctypes.byref(proc), float(u))
+
+
+def grid_alphas(proc, v):
+    """Grid-mode alpha_s at v = ln mu^2 (float)."""
+    return lib().orc_grid_alphas(ctypes.byref(proc), float(v))
 
 
 def polvec_real(p, phi):

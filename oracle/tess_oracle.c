@@ -54,7 +54,7 @@ typedef struct {
   int hist_obs;        /* 0: leading-jet pT, 1: H_T, 2: R_min             */
   double mu_r_factor;  /* mu_R = mu_r_factor * H_T                        */
   int hist_bins;       /* number of uniform bins in [hist_lo, hist_hi)    */
-  int pad_;
+  int grid;            /* 1: PDF and alpha_s from interpolation grids     */
   double hist_lo, hist_hi;
 } orc_process;
 
@@ -129,6 +129,50 @@ int orc_n_uniforms_mode(int n, int hel_mode) { return orc_n_uniforms(n) + (hel_m
  *    choice removes no accepted event.
  * ====================================================================== */
 double orc_xg(double x) { return 1.7 * pow(x, -0.2) * pow(1.0 - x, 5.0); }
+
+/* Grid mode (the paper's mechanism, Sec. 3: PDF and alpha_s read from
+ * tables by linear interpolation).  The tables are built from the functions
+ * above and interpolated in single precision:
+ *   PDF: 1025 nodes u_i = i/1024 of the x draw (ln x = u ln x_min), value
+ *        float(xg(exp(u_i ln x_min))); at a float draw u: s = 1024 u,
+ *        i = min(floor(s), 1023), t = s - i, f = fma(t, g[i+1] - g[i], g[i]).
+ *   alpha_s: 513 nodes uniform in v = ln mu^2 over [v_lo, v_hi],
+ *        v_lo = 2 ln(mu_r_factor m pT_min) (no passing event has a smaller
+ *        H_T), v_hi = 2 ln(mu_r_factor sqrt(S)); value float(alpha_s(mu));
+ *        at v: s = (v - v_lo) * float(512 / (v_hi - v_lo)) clamped to
+ *        [0, 512], i = min(floor(s), 511), t = s - i, same blend.
+ * Every step in float arithmetic (fmaf rounds once), as the grid-mode
+ * kernels evaluate it.                                                    */
+#define ORC_PDF_NODES 1025
+#define ORC_AS_NODES 513
+static float grid_blend(const float *g, int nseg, float s) {
+  if (s < 0.0f) s = 0.0f;
+  if (s > (float)nseg) s = (float)nseg;
+  int i = (int)s;
+  if (i > nseg - 1) i = nseg - 1;
+  const float t = s - (float)i;
+  return fmaf(t, g[i + 1] - g[i], g[i]);
+}
+
+float orc_grid_pdf(const orc_process *pr, float u) {
+  float g[ORC_PDF_NODES];
+  const int m = pr->n - 2;
+  const double S = pr->sqrt_s * pr->sqrt_s;
+  const double lnxmin = log((m * pr->pt_min) * (m * pr->pt_min) / S);
+  for (int i = 0; i < ORC_PDF_NODES; ++i) g[i] = (float)orc_xg(exp((double)i / 1024.0 * lnxmin));
+  return grid_blend(g, ORC_PDF_NODES - 1, u * 1024.0f);
+}
+
+double orc_alphas(double mu, double alphas_mz, double mz, int nf);
+float orc_grid_alphas(const orc_process *pr, float v) {
+  float a[ORC_AS_NODES];
+  const int m = pr->n - 2;
+  const double vlo = 2.0 * log(pr->mu_r_factor * m * pr->pt_min), vhi = 2.0 * log(pr->mu_r_factor * pr->sqrt_s);
+  for (int i = 0; i < ORC_AS_NODES; ++i)
+    a[i] = (float)orc_alphas(exp(0.5 * (vlo + (vhi - vlo) * i / 512.0)), pr->alphas_mz, pr->mz, pr->nf);
+  const float inv = (float)(512.0 / (vhi - vlo));
+  return grid_blend(a, ORC_AS_NODES - 1, (v - (float)vlo) * inv);
+}
 
 /* ========================================================================
  * 3. Rambo (Kleiss, Stirling, Ellis 1986), cited but not restated in
@@ -460,7 +504,10 @@ static void event_kinematics(const orc_process *pr, const double *u, orc_event_o
   o->x1 = exp(u[0] * lnxmin);
   o->x2 = exp(u[1] * lnxmin);
   o->shat = o->x1 * o->x2 * S;
-  o->pdf = lnxmin * lnxmin * orc_xg(o->x1) * orc_xg(o->x2);
+  if (pr->grid) /* the grid-mode kernels read the draws as floats */
+    o->pdf = lnxmin * lnxmin * (double)orc_grid_pdf(pr, (float)u[0]) * (double)orc_grid_pdf(pr, (float)u[1]);
+  else
+    o->pdf = lnxmin * lnxmin * orc_xg(o->x1) * orc_xg(o->x2);
   o->y = 0.5 * log(o->x1 / o->x2);
   const double rs = sqrt(o->shat);
   double p[ORC_MAXN * 4];
@@ -554,7 +601,12 @@ static int event_from_uniforms(const orc_process *pr, const double *u, orc_event
   if (o->pass) {
     double mfact = 1.0;
     for (int i = 2; i <= m; ++i) mfact *= i;
-    o->alphas = orc_alphas(pr->mu_r_factor * o->ht, pr->alphas_mz, pr->mz, pr->nf);
+    if (pr->grid) {
+      const float mu = (float)pr->mu_r_factor * (float)o->ht;
+      o->alphas = (double)orc_grid_alphas(pr, logf(mu * mu));
+    } else {
+      o->alphas = orc_alphas(pr->mu_r_factor * o->ht, pr->alphas_mz, pr->mz, pr->nf);
+    }
     const double col = pow(NC, n - 2) * (NC * NC - 1.0);
     const double g2 = 4.0 * M_PI * o->alphas;
     w = o->pdf / (2.0 * o->shat) * o->phi / mfact / 256.0 * col * pow(g2, n - 2) * E * GEV2_TO_PB;
