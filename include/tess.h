@@ -75,6 +75,13 @@ extern "C" {
                                  me2 0 (not evaluated); every other output is as without the flag.
                                  Not for TESS_FP64, TESS_HEL_SUM, tess_gradients or
                                  tess_generate_noalloc. */
+#define TESS_FLAG_PDF_GRID 2 /* the paper's tabulated PDF and alpha_s (Sec. 3): x g(x) on 1025 nodes uniform
+                                in the x draw u (ln x = u ln x_min) and alpha_s on 513 nodes uniform in
+                                ln mu^2 over [2 ln(mu_r_factor m pT_min), 2 ln(mu_r_factor sqrt(S))], each
+                                node the function rounded to FP32, read by linear interpolation in FP32
+                                (s = position in node units, i = min(floor(s), last segment), t = s - i,
+                                value = fma(t, g[i+1] - g[i], g[i])).  Tables built per call in the
+                                workspace.  FP32 forms with sampled events only. */
 /* hist_observable */
 #define TESS_OBS_PTLEAD 0
 #define TESS_OBS_HT 1
@@ -97,7 +104,7 @@ typedef struct tess_process {
   double mz;               /* M_Z (> 0)                                       */
   double mu_r_factor;      /* mu_R = mu_r_factor * H_T (> 0)                  */
   double hist_lo, hist_hi; /* histogram range [lo, hi), uniform bins          */
-  int32_t flags;           /* 0 or TESS_FLAG_CUT_FIRST                        */
+  int32_t flags;           /* 0 or TESS_FLAG_CUT_FIRST | TESS_FLAG_PDF_GRID  */
   int32_t reserved;        /* 0                                               */
 } tess_process;
 

@@ -30,7 +30,7 @@ TESS_MIN_N, TESS_MAX_N, TESS_MAX_BINS, TESS_ACC_LEN = 4, 12, 1024, 8
 TESS_NOALLOC_SCRATCH_BYTES, TESS_NOALLOC_MAX_BINS = 1 << 20, 254
 TESS_FP64, TESS_FP32_CURRENTS, TESS_FP32_DS = 0, 1, 2
 TESS_HEL_SUM, TESS_HEL_SAMPLE, TESS_POL_RANDOM = 0, 1, 2
-TESS_FLAG_CUT_FIRST = 1
+TESS_FLAG_CUT_FIRST, TESS_FLAG_PDF_GRID = 1, 2
 TESS_OBS_PTLEAD, TESS_OBS_HT, TESS_OBS_RMIN = 0, 1, 2
 TESS_K2_REG, TESS_K2_ROWS32, TESS_K2_ROWS64, TESS_K2_LOOP, TESS_K2_REG_HI, TESS_K2_REG_TMA = 0, 1, 2, 3, 4, 5
 TESS_K2_REG_TMA_HI, TESS_K2_PAIR32, TESS_K2_PAIR64, TESS_K2_REAL, TESS_K2_REAL_HI = 6, 7, 8, 9, 10

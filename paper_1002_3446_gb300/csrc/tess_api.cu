@@ -221,11 +221,11 @@ int check_process(const tess_process *p) {
                 p->helicity_mode);
   if (p->helicity_mode == TESS_HEL_SUM && p->n_gluons > 5)
     return fail(TESS_E_UNSUPPORTED, "TESS_HEL_SUM is built for n <= 5 (n = %d)", p->n_gluons);
-  if ((p->flags & ~TESS_FLAG_CUT_FIRST) != 0 || p->reserved != 0)
-    return fail(TESS_E_INVALID, "flags = %d / reserved = %d: only TESS_FLAG_CUT_FIRST is defined", p->flags,
-                p->reserved);
-  if ((p->flags & TESS_FLAG_CUT_FIRST) && (p->precision == TESS_FP64 || p->helicity_mode == TESS_HEL_SUM))
-    return fail(TESS_E_UNSUPPORTED, "TESS_FLAG_CUT_FIRST is built for the FP32 forms with sampled events");
+  if ((p->flags & ~(TESS_FLAG_CUT_FIRST | TESS_FLAG_PDF_GRID)) != 0 || p->reserved != 0)
+    return fail(TESS_E_INVALID, "flags = %d / reserved = %d: only TESS_FLAG_CUT_FIRST and TESS_FLAG_PDF_GRID are defined",
+                p->flags, p->reserved);
+  if (p->flags != 0 && (p->precision == TESS_FP64 || p->helicity_mode == TESS_HEL_SUM))
+    return fail(TESS_E_UNSUPPORTED, "TESS_FLAG_* are built for the FP32 forms with sampled events");
   if (!finite_pos(p->sqrt_s)) return fail(TESS_E_INVALID, "sqrt_s must be finite and > 0");
   if (!finite_pos(p->pt_min)) return fail(TESS_E_INVALID, "pt_min must be finite and > 0");
   if (!finite_pos(p->eta_max)) return fail(TESS_E_INVALID, "eta_max must be finite and > 0");
@@ -313,7 +313,8 @@ int plan_with_form(const tess_ctx *ctx, const tess_process *p, uint64_t n_events
                    tess::PipePlan *pl) {
   const int n = p->n_gluons;
   const unsigned caps = (p->helicity_mode == TESS_POL_RANDOM ? tess::CAP_REAL_EPS : 0u) |
-                        ((p->flags & TESS_FLAG_CUT_FIRST) ? tess::CAP_CUT_FIRST : 0u);
+                        ((p->flags & TESS_FLAG_CUT_FIRST) ? tess::CAP_CUT_FIRST : 0u) |
+                        ((p->flags & TESS_FLAG_PDF_GRID) ? tess::CAP_PDF_GRID : 0u);
   int rc;
   if (p->precision == TESS_FP64)
     rc = tess::plan_pipeline_f64(n, ctx->sm_count, n_events, p->hist_bins, form, sched, caps, pl);
@@ -431,6 +432,15 @@ void fill_params(const tess_process *proc, uint64_t seed, uint64_t first_event, 
   P.kin_ds = proc->precision == TESS_FP32_DS;
   P.pol_random = proc->helicity_mode == TESS_POL_RANDOM;
   P.cut_first = (proc->flags & TESS_FLAG_CUT_FIRST) != 0;
+  P.pdf_grid = (proc->flags & TESS_FLAG_PDF_GRID) != 0;
+  {  // alpha_s table range: ln mu^2 from the smallest H_T that passes the cuts to sqrt(S)
+    const double vlo = 2.0 * std::log(proc->mu_r_factor * m * proc->pt_min);
+    const double vhi = 2.0 * std::log(proc->mu_r_factor * proc->sqrt_s);
+    P.as_vlo = vlo;
+    P.as_vhi = vhi;
+    P.f_as_vlo = (float)vlo;
+    P.f_as_inv = (float)(tess::kAsSegments / (vhi - vlo));
+  }
   P.S_hi = (float)P.S;
   P.S_lo = (float)(P.S - (double)P.S_hi);
   P.wk = P.wconst * P.lnxmin * P.lnxmin * P.phiconst * 0.5;

@@ -10,6 +10,10 @@
 namespace tess {
 
 // Per-launch constants, prepared on the host from a tess_process.
+// Node counts of the PDF and alpha_s tables of the grid mode.
+constexpr int kPdfSegments = 1024, kPdfNodes = kPdfSegments + 1;
+constexpr int kAsSegments = 512, kAsNodes = kAsSegments + 1;
+
 struct EventParams {
   uint64_t seed;
   uint64_t first_event;
@@ -34,6 +38,10 @@ struct EventParams {
   int kin_ds;          // 1: double-float kinematics kernel
   int pol_random;      // 1: random real polarisations instead of sampled helicities
   int cut_first;       // 1: amplitudes only for events passing the cuts (compacted)
+  int pdf_grid;        // 1: PDF and alpha_s from the tables below (linear interpolation)
+  const float *grid_pdf, *grid_as;  // kPdfNodes / kAsNodes values, in the workspace
+  double as_vlo, as_vhi;            // alpha_s table range in ln mu^2
+  float f_as_vlo, f_as_inv;         // the same as floats: v_lo and kAsSegments / (v_hi - v_lo)
   // outputs (device; may be null)
   double *weight, *me2, *ht, *ptlead, *rmin;
   uint8_t *pass;

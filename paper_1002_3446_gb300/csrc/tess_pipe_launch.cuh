@@ -21,6 +21,7 @@ struct PipePlan {
   int chunks = 1;
   size_t off_in = 0, off_efac = 0, off_wfac = 0, off_hval = 0, off_pass = 0;
   size_t off_col = 0, off_orig = 0, off_tcount = 0, off_toff = 0, off_dcount = 0;  // cut-first only
+  size_t off_tables = 0;  // grid mode only: PDF and alpha_s tables (before the chunk buffers)
   size_t kin_smem = 0;   // K1 dynamic shared memory (FP32 forms: the output tile)
   size_t buf_bytes = 0;  // one chunk buffer
   int sched = 0;         // Schedule
@@ -135,7 +136,7 @@ enum K2Form {
 // vectors are real (random polarisations), which the real-current forms
 // require; CAP_CUT_FIRST, its events are compacted (an index list), which the
 // staged forms do not read.
-constexpr unsigned CAP_REAL_EPS = 1u, CAP_CUT_FIRST = 2u;
+constexpr unsigned CAP_REAL_EPS = 1u, CAP_CUT_FIRST = 2u, CAP_PDF_GRID = 4u;
 
 template <int N, typename R>
 constexpr bool k2_valid(int f, unsigned caps) {
@@ -334,6 +335,11 @@ int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, in
   }
   pl->grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles, resident));
   size_t off = align256((size_t)pl->grid * partial_stride(hist_bins) * sizeof(double));
+  pl->off_tables = 0;
+  if (caps & CAP_PDF_GRID) {  // PDF and alpha_s tables of the grid mode
+    pl->off_tables = off;
+    off = align256(off + (size_t)(kPdfNodes + kAsNodes) * sizeof(float));
+  }
   pl->off_in = off;
   off = align256(off + (size_t)InRows<L>::rows * pl->cap * sizeof(R));
   pl->off_efac = off;
@@ -367,6 +373,14 @@ cudaError_t run_pipeline_t(const EventParams &P, const PipePlan &pl, char *ws, c
   double *partials = (double *)ws;
   cudaError_t e = cudaMemsetAsync(partials, 0, (size_t)pl.grid * partial_stride(P.hist_bins) * sizeof(double), s);
   if (e != cudaSuccess) return e;
+  EventParams PG = P;
+  if (P.pdf_grid) {  // tables for this call's process
+    float *g = (float *)(ws + pl.off_tables);
+    grid_fill_kernel<256><<<(kPdfNodes + kAsNodes + 255) / 256, 256, 0, s>>>(P, g);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    PG.grid_pdf = g;
+    PG.grid_as = g + kPdfNodes;
+  }
   ChunkBuf<R> BB[2];
   for (int b = 0; b < 2; ++b) {
     char *base = ws + (b ? pl.buf_bytes : 0);
@@ -385,7 +399,7 @@ cudaError_t run_pipeline_t(const EventParams &P, const PipePlan &pl, char *ws, c
     }
   }
   ChunkParams C;
-  C.P = P;
+  C.P = PG;
   CUtensorMap maps[2];
   const CUtensorMap *mp[2] = {nullptr, nullptr};
   if constexpr (sizeof(R) == 4) {

@@ -198,6 +198,43 @@ __device__ __forceinline__ float alphas_f32(const EventParams &P, float ht) {
   return __fdiv_rn(P.f_alphas_mz, __fmaf_rn(P.f_asb0, l, 1.f));
 }
 
+// Grid mode (Sec. 3's tabulated PDF and alpha_s): the tables, built once per
+// call from the functions in FP64 and rounded to FP32 ...
+template <int NT>
+__global__ void __launch_bounds__(NT) grid_fill_kernel(EventParams P, float *g) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < kPdfNodes) {
+    const double x = exp((double)i / (double)kPdfSegments * P.lnxmin);
+    g[i] = (float)(1.7 * pow(x, -0.2) * pow(1.0 - x, 5.0));
+  } else if (i < kPdfNodes + kAsNodes) {
+    const int j = i - kPdfNodes;
+    const double mu = exp(0.5 * (P.as_vlo + (P.as_vhi - P.as_vlo) * j / (double)kAsSegments));
+    g[i] = (float)(P.alphas_mz / (1.0 + P.alphas_mz * P.b0 * (log(mu * mu) - P.ln_mz2)));
+  }
+}
+
+// ... and read by linear interpolation in FP32: s in node units, clamped,
+// i = min(floor(s), nseg - 1), t = s - i, value fma(t, g[i+1] - g[i], g[i]).
+__device__ __forceinline__ float grid_blend(const float *__restrict__ g, int nseg, float s) {
+  s = fminf(fmaxf(s, 0.f), (float)nseg);
+  const int i = min((int)s, nseg - 1);
+  const float t = __fsub_rn(s, (float)i);
+  const float g0 = __ldg(g + i), g1 = __ldg(g + i + 1);
+  return __fmaf_rn(t, __fsub_rn(g1, g0), g0);
+}
+
+// x g(x) at the float x draw u (ln x = u ln x_min)
+__device__ __forceinline__ float grid_pdf(const EventParams &P, float u) {
+  return grid_blend(P.grid_pdf, kPdfSegments, __fmul_rn(u, (float)kPdfSegments));
+}
+
+// alpha_s at mu_R = mu_r_factor H_T from the table in ln mu^2
+__device__ __forceinline__ float grid_alphas(const EventParams &P, float ht) {
+  const float mu = __fmul_rn(P.f_mu_r_factor, ht);
+  const float v = logf(__fmul_rn(mu, mu));
+  return grid_blend(P.grid_as, kAsSegments, __fmul_rn(__fsub_rn(v, P.f_as_vlo), P.f_as_inv));
+}
+
 // K1, FP64 form: every step in double precision.
 template <int N, typename R, bool RP>
 __device__ __forceinline__ void kin_generic(const ChunkParams &C, const ChunkBuf<R> &B, int e) {
@@ -532,8 +569,9 @@ __device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<fl
 
   const uint4 w0 = event_block(P, ev, 0);
   const float lnxmin = P.f_lnxmin;
-  const float x1 = expf(unit_f32(w0.x, w0.y) * lnxmin);
-  const float x2 = expf(unit_f32(w0.z, w0.w) * lnxmin);
+  const float ux1 = unit_f32(w0.x, w0.y), ux2 = unit_f32(w0.z, w0.w);
+  const float x1 = expf(ux1 * lnxmin);
+  const float x2 = expf(ux2 * lnxmin);
   const double shat = (double)x1 * (double)x2 * P.S;
   const double rs = sqrt(shat);
 
@@ -600,7 +638,7 @@ __device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<fl
 
   double wf = 0.0;
   if (pass) {
-    const float as = alphas_f32(P, sum);
+    const float as = P.pdf_grid ? grid_alphas(P, sum) : alphas_f32(P, sum);
     const double g2 = 4.0 * 3.14159265358979323846 * (double)as;
     double gp = 1.0;
 #pragma unroll
@@ -608,8 +646,8 @@ __device__ __forceinline__ void kin_fp32(const ChunkParams &C, const ChunkBuf<fl
     double sp = 1.0;
 #pragma unroll
     for (int i = 0; i < M - 2; ++i) sp *= shat;
-    const float f1 = 1.7f * powf(x1, -0.2f) * powf(1.f - x1, 5.f);
-    const float f2 = 1.7f * powf(x2, -0.2f) * powf(1.f - x2, 5.f);
+    const float f1 = P.pdf_grid ? grid_pdf(P, ux1) : 1.7f * powf(x1, -0.2f) * powf(1.f - x1, 5.f);
+    const float f2 = P.pdf_grid ? grid_pdf(P, ux2) : 1.7f * powf(x2, -0.2f) * powf(1.f - x2, 5.f);
     const double lum = P.lnxmin * P.lnxmin * (double)f1 * (double)f2;
     wf = P.wconst * lum / (2.0 * shat) * (P.phiconst * sp) * gp;
   }
@@ -691,14 +729,19 @@ __device__ __forceinline__ void kin_ds_back(const ChunkParams &C, const ChunkBuf
   const float sp = __fmul_rn(__fmul_rn(shat_hi, sc), sc);
   double wf = 0.0;
   if (pass) {
-    const float as = alphas_f32(P, sum);
+    const float as = P.pdf_grid ? grid_alphas(P, sum) : alphas_f32(P, sum);
     const float g2 = __fmul_rn(4.f * 3.14159265358979323846f, as);
-    // f(x1) f(x2) with f(x) = 1.7 x^-0.2 (1 - x)^5: (x1 x2)^-0.2 from ln x1 + ln x2
-    const float t1 = __fsub_rn(1.f, x1), t2 = __fsub_rn(1.f, x2);
-    const float t1s = __fmul_rn(t1, t1), t2s = __fmul_rn(t2, t2);
-    const float p1 = __fmul_rn(__fmul_rn(t1s, t1s), t1), p2 = __fmul_rn(__fmul_rn(t2s, t2s), t2);
-    float F = __fmul_rn(__fmul_rn(__fmul_rn(2.89f, expf(__fmul_rn(__fmul_rn(-0.2f, lnxmin), __fadd_rn(ux1, ux2)))), p1),
-                        p2);
+    float F;
+    if (P.pdf_grid) {
+      F = __fmul_rn(grid_pdf(P, ux1), grid_pdf(P, ux2));
+    } else {
+      // f(x1) f(x2) with f(x) = 1.7 x^-0.2 (1 - x)^5: (x1 x2)^-0.2 from ln x1 + ln x2
+      const float t1 = __fsub_rn(1.f, x1), t2 = __fsub_rn(1.f, x2);
+      const float t1s = __fmul_rn(t1, t1), t2s = __fmul_rn(t2, t2);
+      const float p1 = __fmul_rn(__fmul_rn(t1s, t1s), t1), p2 = __fmul_rn(__fmul_rn(t2s, t2s), t2);
+      F = __fmul_rn(__fmul_rn(__fmul_rn(2.89f, expf(__fmul_rn(__fmul_rn(-0.2f, lnxmin), __fadd_rn(ux1, ux2)))), p1),
+                    p2);
+    }
 #pragma unroll
     for (int i = 0; i < N - 2; ++i) F = __fmul_rn(F, g2);
     // s_hat^(m-3) = s'^(m-3) 2^(2 ex (m-3))
