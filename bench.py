@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="time the built-in default amplitude variant")
     ap.add_argument("--no-random-pol", action="store_true", help="skip the random-polarisation measurement")
     ap.add_argument("--no-cut-first", action="store_true", help="skip the cut-first measurements")
+    ap.add_argument("--no-pdf-grid", action="store_true",
+                    help="skip the measurement with tabulated PDF and alpha_s (TESS_FLAG_PDF_GRID)")
     ap.add_argument("--cut-first", action="store_true",
                     help="the whole line with TESS_FLAG_CUT_FIRST (amplitudes only for events passing the cuts)")
     ap.add_argument("--pol", default="helicity", choices=["helicity", "random"],
@@ -298,6 +300,11 @@ def run_tess(args):
         extra["cut_first_random_polarisation"] = bench_random_pol(
             torch, tess, ctx, wl, N, seed, first, flush, max(2, args.steps // 2), not args.no_autotune,
             random_pol=True, flags=tess.TESS_FLAG_CUT_FIRST)
+    if not rp and not cf and not args.no_pdf_grid and wl["hel"] == "sample" and wl["precision"] in ("fp32", "ds") \
+            and rank == 0:
+        extra["pdf_grid"] = bench_random_pol(torch, tess, ctx, wl, N, seed, first, flush, max(2, args.steps // 2),
+                                             not args.no_autotune, random_pol=False,
+                                             flags=tess.TESS_FLAG_PDF_GRID)
     if not args.no_batched and rank == 0:
         extra["batched_mixed"] = bench_batched(torch, tess, ctx, flush, max(2, args.steps // 2))
     if not args.no_grad and rank == 0:
@@ -449,8 +456,9 @@ def bench_random_pol(torch, tess, ctx, wl, N, seed, first, flush, steps, autotun
     (TESS_POL_RANDOM) instead of sampled helicities -- real currents, so the
     real-current amplitude forms apply; FLOPs from bg_flops_real -- and/or
     with process flags (TESS_FLAG_CUT_FIRST: amplitudes only for the events
-    that pass the cuts; the amplitude kernel's FLOP rate then counts the
-    evaluated events)."""
+    that pass the cuts, the amplitude kernel's FLOP rate then counting the
+    evaluated events; TESS_FLAG_PDF_GRID: PDF and alpha_s interpolated from
+    tables, Sec. 3)."""
     p = make_proc(tess, wl, random_pol=random_pol)
     p.flags = flags
     r = tess.Run(ctx, p, N, per_event=("weight", "me2", "pass"))
