@@ -4,7 +4,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
+#include <array>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -154,6 +156,12 @@ struct tess_ctx {
   cudaEvent_t fork_ev = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<unsigned char> graph_key;
+  // pipeline plans already made on this context, keyed by what sizes them
+  // (n, precision, polarisation kind, flags, histogram bins, events, variant,
+  // schedule): planning queries the runtime (function attributes, occupancy)
+  // for every candidate kernel, and sizing a workspace plans every variant
+  mutable std::mutex plan_mu;
+  mutable std::map<std::array<int64_t, 8>, tess::PipePlan> plans;
   // opt-in stage timing: event pairs recorded around each launch
   bool timing = false;
   std::vector<cudaEvent_t> ev_free;
@@ -312,6 +320,16 @@ int variant_slot(const tess_process *p) {
 int plan_with_form(const tess_ctx *ctx, const tess_process *p, uint64_t n_events, int form, int sched,
                    tess::PipePlan *pl) {
   const int n = p->n_gluons;
+  const std::array<int64_t, 8> key = {n, p->precision, p->helicity_mode == TESS_POL_RANDOM, p->flags, p->hist_bins,
+                                      (int64_t)n_events, form, sched};
+  {
+    std::lock_guard<std::mutex> lock(ctx->plan_mu);
+    const auto it = ctx->plans.find(key);
+    if (it != ctx->plans.end()) {
+      *pl = it->second;
+      return TESS_OK;
+    }
+  }
   const unsigned caps = (p->helicity_mode == TESS_POL_RANDOM ? tess::CAP_REAL_EPS : 0u) |
                         ((p->flags & TESS_FLAG_CUT_FIRST) ? tess::CAP_CUT_FIRST : 0u) |
                         ((p->flags & TESS_FLAG_PDF_GRID) ? tess::CAP_PDF_GRID : 0u);
@@ -328,6 +346,9 @@ int plan_with_form(const tess_ctx *ctx, const tess_process *p, uint64_t n_events
     return fail(TESS_E_CUDA, "could not size the pipeline kernels (n %d, amplitude variant %d, schedule %d: %s)", n,
                 form, sched,
                 rc == tess::kPlanNoResidentBlock ? "no block fits on an SM" : cudaGetErrorString((cudaError_t)rc));
+  std::lock_guard<std::mutex> lock(ctx->plan_mu);
+  if (ctx->plans.size() >= 4096) ctx->plans.clear();
+  ctx->plans.emplace(key, *pl);
   return TESS_OK;
 }
 
