@@ -1023,9 +1023,17 @@ struct Accum {
 // |A|^2 as the epilogue's FP64 input.  FP32 amplitudes: squared in FP32 (one
 // rounding, far below the FP32 amplitude's own error) when that stays in the
 // normal range, else in FP64.
+// Exact widening of a positive normal FP32 value to FP64 on the integer pipe
+// (binary32 -> binary64 layouts: the 23 fraction bits move up by 29, the
+// exponent bias grows by 1023 - 127 = 896); FP64 conversions share the
+// 1/64-rate FP64 pipe on this GPU.
+__device__ __forceinline__ double widen_positive_normal(float s) {
+  return __longlong_as_double((long long)((((uint64_t)__float_as_uint(s)) << 29) + (896ull << 52)));
+}
+
 __device__ __forceinline__ double amp2_of(const Cx<float> &a) {
   const float s = fmaf(a.re, a.re, a.im * a.im);
-  if (s < 3.0e38f && s > 1.0e-30f) return (double)s;
+  if (s < 3.0e38f && s > 1.0e-30f) return widen_positive_normal(s);
   const double re = a.re, im = a.im;
   return re * re + im * im;
 }
@@ -1042,7 +1050,7 @@ __device__ __forceinline__ void finish_values(const ChunkParams &C, int e, doubl
   const uint64_t idx = C.chunk_first + (uint64_t)e;
   const double E = efac * amp2;
   double w = wfac * E;
-  if (!isfinite(w)) {
+  if ((__double2hiint(w) & 0x7ff00000) == 0x7ff00000) {  // not finite: exponent field all ones
     A.nbad += 1;
     w = 0.0;
   }
