@@ -142,6 +142,33 @@ def make_proc(tess, wl, precision=None, random_pol=False):
     return tess.process(wl["n"], **kw)
 
 
+def precision_error(torch, r, r64):
+    """Per-event relative difference |w - w64| / |w64| of an FP32-current run
+    against the FP64 run of the same events (the FP64 form agrees with the
+    oracle to 1e-10 per event): median, 99th percentile and maximum over the
+    events both pass; events whose FP64 |A|^2 is below 1e-16 of the median
+    (helicity configurations whose amplitude vanishes, where both forms return
+    rounding noise) are counted, not compared; cut decisions that differ are
+    counted (the FP32 forms take them on FP32 momenta).  The tail (above_1e_2)
+    is ill-conditioned events: the parity tests bound each event's FP32 error
+    by 16 times the change of its FP64 result when its inputs move by an FP32
+    rounding."""
+    p, p64 = r.t["pass"].bool(), r64.t["pass"].bool()
+    both = p & p64
+    m64 = r64.t["me2"][both].abs()
+    med = float(m64.median()) if m64.numel() else 0.0
+    live = m64 > 1e-16 * med
+    w, w64 = r.t["weight"][both][live], r64.t["weight"][both][live]
+    rel = ((w - w64).abs() / w64.abs()).double()
+    out = {"events": int(r.n_events), "compared": int(rel.numel()), "vanishing": int((~live).sum()),
+           "cut_flips": int((p != p64).sum())}
+    if rel.numel():
+        step = max(1, rel.numel() // (1 << 23))  # torch.quantile's input limit
+        out.update(median=float(rel.median()), p99=float(torch.quantile(rel[::step], 0.99)), max=float(rel.max()),
+                   above_1e_2=int((rel > 1e-2).sum()))
+    return out
+
+
 def time_steps(torch, run, seed, first, steps, warmup, flush):
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
@@ -287,7 +314,13 @@ def run_tess(args):
                          "ms_per_step": statistics.mean(ms),
                          "achieved_tflops": tess.bg_flops(n) * n64 / (statistics.mean(ms) * 1e-3) / 1e12,
                          "peak_tflops": FP64_PEAK_TFLOPS}
-        del r64
+        # the main form's per-event error against the FP64 form on the same events
+        rf = tess.Run(ctx, proc, n64, per_event=("weight", "me2", "pass"))
+        rf.reset()
+        rf.generate(seed, first)
+        torch.cuda.synchronize()
+        extra["fp64"]["error_of_" + wl["precision"]] = precision_error(torch, rf, r64)
+        del r64, rf
     if not rp and not cf and not args.no_random_pol and wl["hel"] == "sample" and wl["precision"] in ("fp32", "ds") \
             and rank == 0:
         extra["random_polarisation"] = bench_random_pol(torch, tess, ctx, wl, N, seed, first, flush,
