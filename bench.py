@@ -42,7 +42,7 @@ FP64_PEAK_TFLOPS = 1.25                                                     # GB
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tess", choices=["tess", "reference"])
     ap.add_argument("--workload", default="gg4g", choices=sorted(WORKLOADS))
@@ -77,6 +77,8 @@ def dist_env():
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
+    """nvidia-smi samples (every 20 ms, each with its host time) while the
+    block runs; summary(window) keeps those inside the timed region."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
@@ -90,10 +92,13 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                          "--format=csv,noheader,nounits", "-lms", "20"], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t_end = time.monotonic() + 5.0  # sampling live before the timed region starts
+            while not self.rows and self.proc.poll() is None and time.monotonic() < t_end:
+                time.sleep(0.01)
         except (OSError, ValueError):
             self.proc = None
         return self
@@ -102,7 +107,7 @@ class ClockSampler:
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 8:
-                self.rows.append(parts)
+                self.rows.append((time.monotonic(), parts))
 
     def __exit__(self, *a):
         if self.proc:
@@ -114,20 +119,21 @@ class ClockSampler:
         if self.thread:
             self.thread.join(timeout=5)
 
-    def summary(self):
-        if not self.rows:
+    def summary(self, window=None):
+        rows = [r for t, r in self.rows if window is None or window[0] <= t <= window[1]]
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         def num(x):
             try:
                 return float(x)
             except ValueError:
                 return None
-        sm = [num(r[0]) for r in self.rows if num(r[0]) is not None]
-        mx = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in rows if num(r[1]) is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(rows)}
 
 
 # ------------------------------------------------------------------ tess arm
@@ -169,12 +175,15 @@ def precision_error(torch, r, r64):
     return out
 
 
-def time_steps(torch, run, seed, first, steps, warmup, flush):
+def time_steps(torch, run, seed, first, steps, warmup, flush, window=None):
+    """Device times (ms) of `steps` calls after `warmup` untimed ones; window, if
+    given, receives the host times that bracket the timed calls."""
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
         run.reset()
         run.generate(seed, first)
     torch.cuda.synchronize()
+    t0 = time.monotonic()
     evs = []
     for _ in range(steps):
         flush.fill_(1.0)  # evict L2 (buffer larger than the 129 MB L2); not timed
@@ -186,6 +195,8 @@ def time_steps(torch, run, seed, first, steps, warmup, flush):
         b.record(stream)
         evs.append((a, b))
     torch.cuda.synchronize()
+    if window is not None:
+        window[:] = [t0, time.monotonic()]
     return [a.elapsed_time(b) for a, b in evs]
 
 
@@ -236,8 +247,9 @@ def run_tess(args):
     # ---- headline: device time of K steps
     barrier()
     torch.cuda.synchronize()
+    timed_window = []
     with ClockSampler(gpu_id) as clk:
-        step_ms = time_steps(torch, run, seed, first, args.steps, args.warmup, flush)
+        step_ms = time_steps(torch, run, seed, first, args.steps, args.warmup, flush, timed_window)
     torch.cuda.synchronize()
     barrier()
     total_ms = sum(step_ms)
@@ -416,7 +428,7 @@ def run_tess(args):
                            "(stored by the kernels over NVLink-C2C) + tess_result; the inputs are the seed and "
                            "event range"},
             "gpu_launches": tess.tess_kernel_launches(ctx, proc, N) * args.steps,
-            "clocks": clk.summary(),
+            "clocks": clk.summary(timed_window),
             "sigma_pb": float((acc[0] + acc[4]).item() / (ws * N)),
             "cpu_baseline": cpu,
         }
@@ -644,7 +656,7 @@ def run_reference(args):
         cpu_baseline(wl, events=1 << 12)
     vals = []
     for _ in range(args.steps):
-        vals.append(cpu_baseline(wl, budget_s=8.0))
+        vals.append(cpu_baseline(wl, budget_s=min(8.0, max(1.0, 60.0 / max(1, args.steps)))))
     v = statistics.mean(x["value"] for x in vals)
     line = {
         "impl": "reference",
