@@ -152,7 +152,12 @@ const char *tess_version(void);
 const char *tess_last_error(void);
 
 /* Create a context on CUDA device `device` (reads its properties; allocates
- * no device memory).  *ctx receives the handle; free it with tess_destroy. */
+ * no device memory).  *ctx receives the handle; free it with tess_destroy.
+ * A context holds the tuned variant table, the cached graph of
+ * tess_generate_batched, the stage timers and the streams of the overlapped
+ * schedules: calls on one context from several host threads must be
+ * serialised by the caller (contexts are independent of each other; one per
+ * thread or per device is the simple rule). */
 int tess_init(int device, tess_ctx **ctx);
 void tess_destroy(tess_ctx *ctx);
 
