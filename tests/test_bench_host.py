@@ -73,3 +73,39 @@ def test_both_arms_describe_the_same_workload(bench):
         assert cfg["workload"].startswith(name) and cfg["events_per_gpu"] == wl["n_events"]
         assert cfg["n_gluons"] == wl["n"]
         assert isinstance(bench.workload_metric(wl), str) and bench.workload_metric(wl)
+
+
+def test_traffic_record_lookup(bench, tmp_path, monkeypatch):
+    """The committed DRAM-traffic record is used only for the kernel sources it
+    was captured on and the variant it names, scaled to the launch size."""
+    import json
+    (tmp_path / "profiles").mkdir()
+    h = bench.kernel_source_hash()
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: h)
+    rec = {"source_hash": h,
+           "by_variant": {"4": {"kernel": "k", "events_per_launch": 1000, "dram_bytes_per_launch": 250_000}}}
+    (tmp_path / "profiles" / "traffic_gg4g.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.read_traffic("gg4g", 4, 500) == 125_000
+    assert bench.read_traffic("gg4g", 0, 500) is None      # no capture of this variant
+    assert bench.read_traffic("gg8g", 4, 500) is None      # no record for this workload
+    rec["source_hash"] = "0" * 64                            # kernels changed since the capture
+    (tmp_path / "profiles" / "traffic_gg4g.json").write_text(json.dumps(rec))
+    assert bench.read_traffic("gg4g", 4, 500) is None
+
+
+def test_committed_traffic_records_are_well_formed(bench):
+    """Every committed record names the source hash it was taken on and, per
+    amplitude variant, a full launch's events and DRAM bytes (a record whose
+    hash no longer matches is ignored by read_traffic, not an error)."""
+    import glob
+    import json
+    import re
+    files = glob.glob(os.path.join(ROOT, "profiles", "traffic_*.json"))
+    assert files
+    for f in files:
+        rec = json.load(open(f))
+        assert re.fullmatch(r"[0-9a-f]{64}", rec["source_hash"]), f
+        assert rec["by_variant"]
+        for v, e in rec["by_variant"].items():
+            assert int(v) >= 0 and e["events_per_launch"] > 0 and e["dram_bytes_per_launch"] > 0
