@@ -21,10 +21,12 @@
  *   k_i    all-outgoing momenta: k_1 = -p_1, k_2 = -p_2, k_i = p_i (i >= 3),
  *          so that sum_i k_i = 0.
  *
- * Parity unpinned (see the test-suite): the Philox stream layout beyond the
- * agreement of two independent implementations; the histogram range of the
- * 2 -> 2 leading-jet-pT histogram; the choice of x_min (cross-section
- * neutral by construction).
+ * Pins (see the test-suite): Philox4x32-10 against the published known-answer
+ * vectors of Salmon et al.'s Random123 library.  Conventions of this
+ * implementation with nothing external to pin them: the layout of the draws
+ * in the counter-based stream, the histogram range of the 2 -> 2
+ * leading-jet-pT histogram, and the choice of x_min (cross-section neutral
+ * by construction).
  */
 #include <complex.h>
 #include <math.h>

@@ -2,11 +2,16 @@
 
 The paper does not name its generator (Sec. 4, Fig. 2 discussion), so the
 draws are our reading: Philox4x32-10 from Salmon et al. (SC'11).  The pins are
-(a) a second, independent implementation written here in pure Python integer
-arithmetic from that paper's description, (b) the exact uniform mapping, and
-(c) statistical properties of the stream.  Beyond that the stream layout is
-"parity unpinned" (there is no published stream to compare with offline).
+(a) the published known-answer vectors of Philox4x32-10 (the Random123
+library's test file that accompanies Salmon et al.; tests/golden/
+philox4x32_10_kat.txt), (b) a second implementation written here in pure
+Python integer arithmetic from that paper's description, (c) the exact
+uniform mapping, and (d) statistical properties of the stream.  What the
+known answers do not fix is our own layout of the draws (which counter word
+carries the event index, which draw comes from which output word); that is
+a documented choice, checked on the GPU bit for bit against the oracle.
 """
+import os
 import math
 import random
 
@@ -29,6 +34,57 @@ def philox_py(ctr, key, rounds=10):
         k0 = (k0 + 0x9E3779B9) & M32
         k1 = (k1 + 0xBB67AE85) & M32
     return [c0, c1, c2, c3]
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.txt")
+
+
+def load_kat():
+    rows = []
+    with open(GOLDEN) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if not line:
+                continue
+            w = [int(x, 16) for x in line]
+            assert len(w) == 10
+            rows.append((w[0:4], w[4:6], w[6:10]))
+    return rows
+
+
+def test_philox_known_answers(orc):
+    # Salmon et al.'s published known answers pin the round function (the two
+    # multipliers and which lane each one takes), the output word permutation
+    # and the key schedule (Weyl increments, bumped after each round): a slip
+    # in any of them changes every output word.
+    kat = load_kat()
+    assert len(kat) == 3
+    for ctr, key, expect in kat:
+        assert orc.philox4x32_10(ctr, key) == expect, (ctr, key)
+        assert philox_py(ctr, key) == expect
+
+
+def test_philox_known_answers_reject_plausible_slips():
+    # the pins must fail for the mistakes a restatement could make
+    ctr, key, expect = load_kat()[2]
+
+    def swapped_multipliers(c, k):
+        c0, c1, c2, c3 = c
+        k0, k1 = k
+        for _ in range(10):
+            p0, p1 = 0xCD9E8D57 * c0, 0xD2511F53 * c2
+            c0, c1, c2, c3 = ((p1 >> 32) ^ c1 ^ k0) & M32, p1 & M32, ((p0 >> 32) ^ c3 ^ k1) & M32, p0 & M32
+            k0, k1 = (k0 + 0x9E3779B9) & M32, (k1 + 0xBB67AE85) & M32
+        return [c0, c1, c2, c3]
+
+    def key_bumped_first(c, k):
+        return philox_py(c, [(k[0] + 0x9E3779B9) & M32, (k[1] + 0xBB67AE85) & M32])
+
+    assert swapped_multipliers(ctr, key) != expect
+    assert key_bumped_first(ctr, key) != expect
+    assert philox_py(ctr, key, rounds=9) != expect
+    out = philox_py(ctr, key)
+    assert [out[1], out[0], out[3], out[2]] != expect
 
 
 def test_philox_two_implementations_agree(orc):
