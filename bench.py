@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison measurement")
     ap.add_argument("--no-per-n", action="store_true", help="skip the per-multiplicity sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the gg->2g (2^20, FP64 exact sum) and gg->8g (2^26) configuration legs")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the FMA peak probes (nominal peak instead)")
     ap.add_argument("--events", type=int, default=0, help="override events per GPU (small cases for profiling)")
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-multiplicity batched measurement")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
@@ -200,6 +203,194 @@ def time_steps(torch, run, seed, first, steps, warmup, flush, window=None):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def measure_peaks(torch, tess, ctx, gpu_id):
+    """FMA peaks of this GPU (tess_peak_flops) with the SM clock sampled while
+    they run: the roofline denominators of this run."""
+    out = {}
+    with ClockSampler(gpu_id) as clk:
+        t0 = time.monotonic()
+        for name, kind in (("fp32", tess.TESS_PEAK_FP32), ("fp32x2", tess.TESS_PEAK_FP32X2),
+                           ("fp64", tess.TESS_PEAK_FP64)):
+            out[name] = tess.tess_peak_flops(ctx, kind, reps=20)
+        t1 = time.monotonic()
+    out["clocks"] = clk.summary([t0, t1])
+    out["nominal_fp32"] = FP32_PEAK_TFLOPS
+    return out
+
+
+def peak_at(peaks, key, sm_mhz):
+    """Measured peak `key`, rescaled from the probe's median SM clock to sm_mhz."""
+    v = peaks[key]
+    c0 = peaks["clocks"].get("sm_mhz")
+    if c0 and sm_mhz:
+        v *= sm_mhz / c0
+    return v
+
+
+def sig(x, d=4):
+    """x rounded to d significant digits (compact JSON)."""
+    if x is None:
+        return None
+    if isinstance(x, (list, tuple)):
+        return [sig(v, d) for v in x]
+    if isinstance(x, dict):
+        return {k: sig(v, d) for k, v in x.items()}
+    if isinstance(x, bool) or isinstance(x, int):
+        return x
+    try:
+        return float(f"{x:.{d}g}")
+    except (TypeError, ValueError):
+        return x
+
+
+def amp_kernel_time(torch, tess, ctx, proc, run, seed, first, flush, steps):
+    """Device time per step (ms) of the amplitude kernel (or the fused kernel
+    of the exact-sum mode), from the library's CUDA events around each launch,
+    with the kernels run serially (an overlapped schedule is switched to its
+    serial counterpart with the same variant for this measurement)."""
+    N = run.n_events
+    plan = tess.tess_plan_info(ctx, proc, N)
+    serial_of = {tess.TESS_SCHED_OVERLAP: tess.TESS_SCHED_SERIAL,
+                 tess.TESS_SCHED_OVERLAP_TILES: tess.TESS_SCHED_SERIAL_TILES}
+    if plan["schedule"] in serial_of:
+        tess.tess_select_variant(ctx, proc, plan["variant"], serial_of[plan["schedule"]])
+    tess.tess_stage_timing(ctx, 1)
+    tess.tess_stage_times(ctx)
+    for _ in range(steps):
+        flush.fill_(1.0)
+        run.reset()
+        run.generate(seed, first)
+    st = tess.tess_stage_times(ctx)
+    tess.tess_stage_timing(ctx, 0)
+    if plan["schedule"] in serial_of:
+        tess.tess_select_variant(ctx, proc, plan["variant"], plan["schedule"])
+    ms, launches = st["amplitude"]
+    if launches == 0:
+        ms, launches = st["fused"]
+    return ms / steps, launches // steps, plan, st
+
+
+def bench_config(torch, tess, ctx, name, flush, steps, peaks, sm_mhz, autotune=True, with_cpu=True,
+                 forms=("ds", "fp32", "fp64"), fp64_events=None):
+    """One workload of the numerical study at its stated size: events/s of
+    each precision form, sigma +- MC error, the amplitude kernel's roofline
+    (FLOPs counted from the kernel's inner loop x events / its serial device
+    time, against the FMA peak measured in this run), the FP32 forms' per-event
+    error against the FP64 form on the same events, and the oracle on the
+    host cores."""
+    wl = dict(WORKLOADS[name])
+    N, n = wl["n_events"], wl["n"]
+    res = {"workload": workload_config(name, wl, N)["workload"]}
+    runs = {}
+    for form in forms:
+        if wl["precision"] == "fp64" and form != "fp64":
+            continue
+        ne = N if form != "fp64" or wl["precision"] == "fp64" else (fp64_events or N >> 3)
+        proc = make_proc(tess, wl, form)
+        run = tess.Run(ctx, proc, ne, per_event=("weight", "me2", "pass"))
+        if autotune and wl["hel"] == "sample":
+            tess.tess_autotune(ctx, proc, min(ne, 1 << 22), torch.zeros(tess.TESS_ACC_LEN, dtype=torch.float64,
+                                                                         device="cuda"), run.workspace)
+        ms = statistics.mean(time_steps(torch, run, 1, 0, steps, 2, flush))
+        amp_ms, amp_launches, plan, _ = amp_kernel_time(torch, tess, ctx, proc, run, 1, 0, flush, steps)
+        # the exact sum evaluates (n-1)! orderings x 2^(n-1) helicity labellings per event (flipping every
+        # label leaves |m| unchanged, so leg 0 keeps label 0 and the sum is doubled)
+        evals = ne * (math.factorial(n - 1) * 2 ** (n - 1) if wl["hel"] == "sum" else 1)
+        fl = tess.bg_flops(n)
+        achieved = fl * evals / (amp_ms * 1e-3) / 1e12
+        pk = peak_at(peaks, "fp64" if form == "fp64" else "fp32", sm_mhz)
+        sg = run.result()
+        entry = {"events": ne, "value": ne / (ms * 1e-3), "ms_per_step": ms, "sigma_pb": [sg[0], sg[1]],
+                 "n_pass": sg[2],
+                 "roofline": {"bound": "alu", "achieved": achieved, "peak": pk,
+                              "peak_kind": "measured " + ("FP64" if form == "fp64" else "FP32") + " FMA rate",
+                              "unit": "TFLOP/s", "frac": achieved / pk, "flops_per_amplitude": fl,
+                              "amplitudes_per_event": evals // ne, "kernel_ms_per_step": amp_ms,
+                              "launches_per_step": amp_launches, "variant_schedule": [plan["variant"],
+                                                                                      plan["schedule"]],
+                              "traffic": read_traffic(name if form != "fp64" else name + "_fp64", plan["variant"],
+                                                      min(ne, plan_cap(tess, ctx, proc, ne)))}}
+        if wl["hist"] and form == forms[0]:
+            hw, hw2 = run.histograms()
+            entry["hist_sumw"] = [float(x) for x in hw]
+        res[form] = entry
+        runs[form] = run
+    if "fp64" in runs and wl["precision"] != "fp64":
+        r64 = runs["fp64"]
+        ne = r64.n_events
+        for form in forms:
+            if form == "fp64":
+                continue
+            rf = tess.Run(ctx, make_proc(tess, wl, form), ne, per_event=("weight", "me2", "pass"))
+            rf.reset()
+            rf.generate(1, 0)
+            torch.cuda.synchronize()
+            res[form]["error_vs_fp64"] = precision_error(torch, rf, r64)
+            del rf
+    del runs
+    if with_cpu:
+        res["cpu_baseline"] = cpu_baseline(wl, budget_s=10.0)
+    return res
+
+
+def compact_config(res):
+    """The few numbers of a bench_config result that the summary keeps."""
+    out = {}
+    for form in ("ds", "fp32", "fp64"):
+        if form in res:
+            e = res[form]
+            r = e["roofline"]
+            out[form] = {"ev_s": sig(e["value"]), "tflops": sig(r["achieved"], 3), "frac": sig(r["frac"], 3)}
+            if "error_vs_fp64" in e:
+                er = e["error_vs_fp64"]
+                out[form]["err"] = sig({"med": er.get("median"), "p99": er.get("p99"), "max": er.get("max")}, 2)
+    first = next(f for f in ("ds", "fp32", "fp64") if f in res)
+    out["sigma"] = sig(res[first]["sigma_pb"], 5)
+    if "cpu_baseline" in res:
+        out["cpu_ev_s"] = sig(res["cpu_baseline"]["value"], 3)
+        out["cpu_cores"] = res["cpu_baseline"]["cores"]
+    return out
+
+
+def summary_of(line, configs, peaks):
+    """Compact restatement of the line's key figures, printed last so that a
+    record keeping only the end of the line still holds them: the measured
+    peaks, each configuration's events/s per precision form with its
+    amplitude-kernel TFLOP/s and fraction of the measured peak, the FP32
+    forms' error against FP64, sigma, the batched comparison and the oracle."""
+    out = {}
+    if peaks:
+        out["peak_tflops"] = sig({"fp32": peaks["fp32"], "fp32x2": peaks["fp32x2"], "fp64": peaks["fp64"],
+                                  "sm_mhz": peaks["clocks"].get("sm_mhz")}, 4)
+    r = line["roofline"]
+    c2 = {"ds": {"ev_s": sig(line["value"]), "tflops": sig(r["achieved"], 3), "frac": sig(r["frac"], 3)},
+          "e2e_ev_s": sig(line["e2e"]["value"])}
+    if "fp32_native_fp64_steps" in line:
+        c2["fp32"] = {"ev_s": sig(line["fp32_native_fp64_steps"]["value"])}
+    if "fp64" in line:
+        f = line["fp64"]
+        c2["fp64"] = {"ev_s": sig(f["value"]), "tflops": sig(f["achieved_tflops"], 3),
+                      "frac": sig(f["achieved_tflops"] / f["peak_tflops"], 3)}
+        er = next((v for k, v in f.items() if k.startswith("error_of_")), None)
+        if er:
+            c2["ds"]["err"] = sig({"med": er.get("median"), "p99": er.get("p99"), "max": er.get("max")}, 2)
+    if line.get("cpu_baseline"):
+        c2["cpu_ev_s"] = sig(line["cpu_baseline"]["value"], 3)
+    if "C1_gg2g" in configs:
+        out["C1"] = compact_config(configs["C1_gg2g"])
+    out["C2"] = c2
+    if "C3_gg8g" in configs:
+        out["C3"] = compact_config(configs["C3_gg8g"])
+    b = line.get("batched_mixed")
+    if b:
+        out["C4"] = {k: sig(b[k]["value"]) for k in ("plain_9_launches_autotuned", "graph_batched_autotuned",
+                                                      "persistent_autotuned") if k in b}
+    g = line.get("gradients_gg6g")
+    if g:
+        out["C5_grad_ev_s"] = sig(g["value"])
+    return out
+
+
 def run_tess(args):
     import torch
     import paper_1002_3446_gb300 as tess
@@ -243,6 +434,8 @@ def run_tess(args):
         gpu_id = "GPU-" + str(gpu_id) if not str(gpu_id).startswith("GPU-") else str(gpu_id)
     except Exception:
         gpu_id = str(local)
+
+    peaks = None if args.no_peaks else measure_peaks(torch, tess, ctx, gpu_id)
 
     # ---- headline: device time of K steps
     barrier()
@@ -325,7 +518,7 @@ def run_tess(args):
         extra["fp64"] = {"value": n64 / (statistics.mean(ms) * 1e-3), "events": n64,
                          "ms_per_step": statistics.mean(ms),
                          "achieved_tflops": tess.bg_flops(n) * n64 / (statistics.mean(ms) * 1e-3) / 1e12,
-                         "peak_tflops": FP64_PEAK_TFLOPS}
+                         "peak_tflops": peaks["fp64"] if peaks else FP64_PEAK_TFLOPS}
         # the main form's per-event error against the FP64 form on the same events
         rf = tess.Run(ctx, proc, n64, per_event=("weight", "me2", "pass"))
         rf.reset()
@@ -354,6 +547,14 @@ def run_tess(args):
         extra["batched_mixed"] = bench_batched(torch, tess, ctx, flush, max(2, args.steps // 2))
     if not args.no_grad and rank == 0:
         extra["gradients_gg6g"] = bench_gradients(torch, tess, ctx, max(2, args.steps // 2))
+    main_clocks = clk.summary(timed_window)
+    configs = {}
+    if not args.no_configs and rank == 0 and not args.events and not rp and not cf and peaks:
+        configs["C1_gg2g"] = bench_config(torch, tess, ctx, "gg2g", flush, max(2, args.steps // 4), peaks,
+                                          main_clocks.get("sm_mhz"), with_cpu=not args.no_cpu_baseline)
+        configs["C3_gg8g"] = bench_config(torch, tess, ctx, "gg8g", flush, max(2, args.steps // 4), peaks,
+                                          main_clocks.get("sm_mhz"), autotune=not args.no_autotune,
+                                          with_cpu=not args.no_cpu_baseline, fp64_events=1 << 23)
     if not args.no_per_n and rank == 0:
         sweep = {}
         for nn in range(4, 13):
@@ -389,6 +590,9 @@ def run_tess(args):
         tot = sum(v[0] for v in stages.values()) or 1.0
         traffic = read_traffic(args.workload + ("_rp" if rp else "") + ("_cf" if cf else ""), plan["variant"],
                                min(N, plan_cap(tess, ctx, proc, N)))
+        kind = "fp64" if wl["precision"] == "fp64" else "fp32"
+        nominal = FP64_PEAK_TFLOPS if kind == "fp64" else FP32_PEAK_TFLOPS
+        peak = peak_at(peaks, kind, main_clocks.get("sm_mhz")) if peaks else nominal
         line = {
             "metric": workload_metric(wl),
             "value": value,
@@ -408,12 +612,12 @@ def run_tess(args):
             "config": dict(workload_config(args.workload, wl, N, rp, cf),
                            l2="flushed between timed steps (256 MB write)"),
             "roofline": {"bound": "alu", "kernel": "Berends-Giele amplitude kernel", "achieved": achieved,
-                         "peak": FP64_PEAK_TFLOPS if wl["precision"] == "fp64" else FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s",
-                         "frac": achieved / (FP64_PEAK_TFLOPS if wl["precision"] == "fp64" else FP32_PEAK_TFLOPS),
-                         "traffic": traffic,
-                         "peak_source": ("152 SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts and clock); "
-                                         "an FMA probe measured 78.2 FP32 / 1.25 FP64 TFLOP/s"),
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": ((f"measured in this run: {kind.upper()} FMA probe (tess_peak_flops), "
+                                          "rescaled to the timed region's median SM clock") if peaks else
+                                         "nominal: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"),
+                         "peak_nominal": nominal,
+                         "frac_of_nominal": achieved / nominal,
                          "flops_per_event": flops_per_event, "ms_per_step": amp_ms_step,
                          "variant": variant,
                          "plan": plan,
@@ -428,11 +632,14 @@ def run_tess(args):
                            "(stored by the kernels over NVLink-C2C) + tess_result; the inputs are the seed and "
                            "event range"},
             "gpu_launches": tess.tess_kernel_launches(ctx, proc, N) * args.steps,
-            "clocks": clk.summary(timed_window),
+            "clocks": main_clocks,
             "sigma_pb": float((acc[0] + acc[4]).item() / (ws * N)),
             "cpu_baseline": cpu,
         }
         line.update(extra)
+        line["peaks"] = peaks
+        line.update(configs)
+        line["summary"] = summary_of(line, configs, peaks)
         print(json.dumps(line), flush=True)
     tess.tess_destroy(ctx)
     if dist:

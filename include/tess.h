@@ -145,14 +145,17 @@ typedef struct tess_outputs {
 
 typedef struct tess_ctx tess_ctx;
 
-/* Library version string, e.g. "tess-gb300 0.1". */
+/* Library version string, e.g. "tess-gb300 0.1".  (Library plumbing: no
+ * counterpart in the paper.) */
 const char *tess_version(void);
 
-/* Thread-local message for the last failing call on this thread ("" if none). */
+/* Thread-local message for the last failing call on this thread ("" if none).
+ * (Library plumbing: no counterpart in the paper.) */
 const char *tess_last_error(void);
 
 /* Create a context on CUDA device `device` (reads its properties; allocates
- * no device memory).  *ctx receives the handle; free it with tess_destroy.
+ * no device memory).  Paper: the initialization phase of Sec. 3 (start-up
+ * before the Fig. 1 stages), done once here instead of per sweep.  *ctx receives the handle; free it with tess_destroy.
  * A context holds the tuned variant table, the cached graph of
  * tess_generate_batched, the stage timers and the streams of the overlapped
  * schedules: calls on one context from several host threads must be
@@ -164,11 +167,16 @@ void tess_destroy(tess_ctx *ctx);
 /* Bytes of device workspace tess_generate needs for this process and event
  * count: per-block partial sums of the accumulation and, for sampled
  * helicities, one L2-sized chunk of per-event amplitude inputs.  0 is never
- * returned for a valid process. */
+ * returned for a valid process.  Paper: the events in flight of one sweep
+ * (Sec. 2, the number of events per multiprocessor and Table 2); here a
+ * chunk sized for the L2 cache plays the sweep's role.  Host-only, no
+ * errors beyond TESS_E_INVALID / TESS_E_UNSUPPORTED for a bad process. */
 int tess_workspace_size(const tess_ctx *ctx, const tess_process *proc, uint64_t n_events, size_t *bytes);
 
 /* Number of kernel launches one tess_generate call with these arguments
- * makes (for launch accounting and graph sizing). */
+ * makes (for launch accounting and graph sizing).  Paper: the kernel
+ * start-up cost of Sec. 3's initialization phase, which matters when the
+ * kernel time is small (n = 4). */
 int tess_kernel_launches(const tess_ctx *ctx, const tess_process *proc, uint64_t n_events, int *launches);
 
 /* Generate events [first_event, first_event + n_events) of the counter-based
@@ -184,7 +192,8 @@ int tess_generate(tess_ctx *ctx, const tess_process *proc, uint64_t seed, uint64
                   void *stream);
 
 /* ---- Stage timing ----------------------------------------------------------------
- * With timing enabled, tess_generate records a CUDA event pair on its stream
+ * Paper: the per-stage time split of Sec. 3 (Fig. 1: Rambo, phase-space
+ * weight, matrix-element weight, epilogue).  With timing enabled, tess_generate records a CUDA event pair on its stream
  * around every launch it makes; tess_stage_times synchronises on them and
  * returns the summed device time (ms) and launch count per stage since the
  * previous read: [0] kinematics kernel, [1] amplitude kernel, [2] finalize,
@@ -193,7 +202,9 @@ int tess_stage_timing(tess_ctx *ctx, int enable);
 int tess_stage_times(tess_ctx *ctx, double *ms /* [4] */, int *launches /* [4] */);
 
 /* ---- Batched mixed multiplicities -------------------------------------------
- * n_proc (1..16) processes -- typically gg -> 2..10 gluons with different
+ * Paper: Sec. 3's initialization phase (kernel start-up is a significant part
+ * of the time when the kernel is short, as at n = 4); one launch serves
+ * several multiplicities.  n_proc (1..16) processes -- typically gg -> 2..10 gluons with different
  * event counts -- in one call.  Process i generates events
  * [first_events[i], first_events[i] + n_events[i]) of stream seeds[i] into
  * outs[i] (accumulating into its acc/hist, as tess_generate).  The per-process
@@ -212,6 +223,9 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
                           void *workspace, size_t workspace_bytes, void *stream);
 
 /* ---- Amplitude-kernel autotuner ------------------------------------------------
+ * Paper: Sec. 2 chooses the running configuration (threads and events per
+ * multiprocessor, Table 1 / Table 2) by measurement before implementing the
+ * algorithm; this does the same per (precision, n) on the GPU at hand.
  * Times every amplitude-kernel variant built for (precision, n) of proc on
  * probe_events sampled events (one warm-up, median of three timed runs, with
  * proc's histogram settings) and makes the fastest the context's choice for
@@ -275,21 +289,24 @@ int tess_autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events
                   void *workspace, size_t workspace_bytes, void *stream, int *form_out);
 
 /* Sets the variant for (precision, polarisation kind, n) of proc without
- * timing: form one of TESS_K2_* (-1: built-in default; a form not built for
+ * timing (Sec. 2 running configuration, chosen by the caller): form one of TESS_K2_* (-1: built-in default; a form not built for
  * (precision, n) or, for the real-current forms, for helicity vectors falls
  * back to the default), schedule one of TESS_SCHED_* (-1: default, serial).
  * Takes effect for later calls; TESS_E_INVALID for values out of range.  A
  * workspace sized by tess_workspace_size covers every choice. */
 int tess_select_variant(tess_ctx *ctx, const tess_process *proc, int form, int schedule);
 
-/* What a call with (proc, n_events) would run: info[0] amplitude variant
+/* What a call with (proc, n_events) would run (Sec. 2 running configuration):
+ * info[0] amplitude variant
  * (TESS_K2_*, -1 for the exact-sum mode), info[1] the schedule in effect
  * (TESS_SCHED_*), info[2] number of chunks, info[3] amplitude-kernel grid
  * (blocks).  info: host, 4 ints.  Launches nothing. */
 int tess_plan_info(const tess_ctx *ctx, const tess_process *proc, uint64_t n_events, int *info);
 
 /* ---- Draws and gradients (no counterpart in the paper's method) --------------
- * tess_draws writes the generator's own random inputs of events
+ * tess_draws writes the generator's own random inputs of events (the
+ * per-event random numbers whose generator Sec. 4 discusses with Fig. 2;
+ * here Philox4x32-10, layout as in tess_generate)
  * [first_event, first_event + n_events) of stream `seed`:
  *   u      device [n_events][2 + 4(n-2)] doubles: u_x1, u_x2, then four Rambo
  *          uniforms per final-state gluon (layout of the counter-based draws)
@@ -350,29 +367,65 @@ int tess_gauge_ratio(tess_ctx *ctx, int n, int precision, uint64_t n_events, con
 
 /* Cross section from a device acc (synchronises the stream):
  * host out[4] = {sigma_pb, mc_error_pb, n_pass, n_generated}.
+ * Paper: the Monte Carlo estimate of the cross-section formula at the end of
+ * Sec. 3 (mean weight over all generated events) and its mean standard
+ * deviation, from the compensated (Kahan-style) sums of Sec. 4 (Fig. 2
+ * discussion): sigma = S1/N, error = sqrt((S2/N - sigma^2)/(N - 1)).
  * Returns TESS_E_CUDA (after filling out) if acc counts stalled blocks,
  * else TESS_E_NUMERICAL (after filling out) if non-finite weights were seen. */
 int tess_result(tess_ctx *ctx, const double *acc, double *out, void *stream);
 
 /* Copy per-event outputs to host buffers (synchronises the stream).  Any of
- * the host pointers may be NULL. */
+ * the host pointers may be NULL.  Paper: the last step of Sec. 3 returns the
+ * results to the CPU for processing; events are flagged rather than dropped,
+ * so the CPU can re-apply other cuts when histogramming (Sec. 3).
+ * dev: device pointers as filled by tess_generate; errors TESS_E_INVALID
+ * (NULL dev), TESS_E_CUDA (copy failed). */
 int tess_weights(tess_ctx *ctx, const tess_outputs *dev, uint64_t n_events, double *host_weight,
                  uint8_t *host_pass, double *host_me2, void *stream);
 
 /* Histogram from a device hist (synchronises): host sumw[hist_bins + 2] and
- * sumw2[hist_bins + 2], compensation folded in. */
+ * sumw2[hist_bins + 2], compensation folded in.  Paper: the differential
+ * distributions of Sec. 4 (Fig. 3: H_T and Delta R_min), whose histogramming
+ * the paper leaves to the CPU; here the bins are filled on the device and
+ * only read back.  Errors TESS_E_INVALID (no histogram in proc), TESS_E_CUDA. */
 int tess_histograms(tess_ctx *ctx, const tess_process *proc, const double *hist, double *host_sumw,
                     double *host_sumw2, void *stream);
+
+/* ---- Arithmetic peaks (measurement; no counterpart in the paper) -------------
+ * The paper reports times per event only; the rooflines of this library's
+ * amplitude kernels divide by the GPU's own fused-multiply-add rate, measured
+ * here: every thread of 4 x SMs blocks of 512 runs independent FMA chains
+ * (inline PTX, so nothing is folded away) of kind
+ *   TESS_PEAK_FP32    scalar fma.rn.f32
+ *   TESS_PEAK_FP32X2  packed fma.rn.f32x2 (two FP32 lanes per instruction)
+ *   TESS_PEAK_FP64    fma.rn.f64
+ * *tflops = best of `reps` (>= 1) launches after one warm-up, FLOPs counted
+ * as 2 per lane per FMA, timed with CUDA events on `stream` (synchronised).
+ * Allocates no device memory.  The rate follows the SM clock of the moment:
+ * sample the clock beside it.  Errors: TESS_E_INVALID (kind, reps),
+ * TESS_E_CUDA. */
+#define TESS_PEAK_FP32 0
+#define TESS_PEAK_FP32X2 1
+#define TESS_PEAK_FP64 2
+int tess_peak_flops(tess_ctx *ctx, int kind, int reps, double *tflops, void *stream);
 
 /* ---- Allocation-free generation (no counterpart in the paper) ----------------
  * Some callers cannot call cudaMalloc or give the library a workspace: for
  * example a host program whose memory manager reserves the whole device at
  * start-up and forbids other allocations, or a latency-critical loop that
  * cannot afford an allocation's implicit device synchronisation.  For them,
- * tess_generate_noalloc does exactly what tess_generate does (same outputs,
- * same accumulation into acc / hist, which the caller still provides) but
- * keeps its scratch -- the per-block partial sums -- in a fixed device array
- * of TESS_NOALLOC_SCRATCH_BYTES that is part of the library.  Every GPU that
+ * tess_generate_noalloc generates the same events as tess_generate (the
+ * same per-event outputs, device memory or mapped pinned host memory, and
+ * the same accumulation into acc / hist, which the caller still provides)
+ * but keeps its scratch -- the per-block partial sums -- in a fixed device
+ * array of TESS_NOALLOC_SCRATCH_BYTES that is part of the library.  It runs
+ * the fused one-kernel-per-event form: for the exact sum (TESS_HEL_SUM) that
+ * is tess_generate's own kernel; for sampled helicities it is offered at
+ * TESS_FP64 only (FP64 in every step, equal to tess_generate to 1e-10
+ * relative, but thread-per-event with no chunk pipeline, so several times
+ * slower than tess_generate at large n), and the FP32 precisions with
+ * sampled helicities return TESS_E_UNSUPPORTED.  Every GPU that
  * loads the library holds that array until the process exits.
  *   - It calls no cudaMalloc, cudaFree or allocating library routine.
  *   - The first call on each device looks up the array's device address (a

@@ -36,13 +36,14 @@ TESS_K2_REG, TESS_K2_ROWS32, TESS_K2_ROWS64, TESS_K2_LOOP, TESS_K2_REG_HI, TESS_
 TESS_K2_REG_TMA_HI, TESS_K2_PAIR32, TESS_K2_PAIR64, TESS_K2_REAL, TESS_K2_REAL_HI = 6, 7, 8, 9, 10
 TESS_K2_ROWS_REAL, TESS_K2_PAIR_W = 11, 12
 TESS_SCHED_SERIAL, TESS_SCHED_OVERLAP, TESS_SCHED_OVERLAP_TILES, TESS_SCHED_SERIAL_TILES = 0, 1, 2, 3
+TESS_PEAK_FP32, TESS_PEAK_FP32X2, TESS_PEAK_FP64 = 0, 1, 2
 
 # Every symbol include/tess.h declares (checked by the ABI tests).
 EXPORTED = ["tess_version", "tess_last_error", "tess_init", "tess_destroy", "tess_workspace_size", "tess_generate",
             "tess_me2", "tess_result", "tess_weights", "tess_histograms", "tess_generate_noalloc",
             "tess_kernel_launches", "tess_workspace_size_batched", "tess_generate_batched", "tess_autotune",
             "tess_stage_timing", "tess_stage_times", "tess_draws", "tess_gradients", "tess_select_variant",
-            "tess_plan_info", "tess_gradients_workspace_size", "tess_gauge_ratio"]
+            "tess_plan_info", "tess_gradients_workspace_size", "tess_gauge_ratio", "tess_peak_flops"]
 
 
 class TessError(RuntimeError):
@@ -118,6 +119,7 @@ def _load():
         lib.tess_result.argtypes = [vp, vp, P(ctypes.c_double), vp]
         lib.tess_weights.argtypes = [vp, P(tess_outputs), u64, vp, vp, vp, vp]
         lib.tess_histograms.argtypes = [vp, P(tess_process), vp, vp, vp, vp]
+        lib.tess_peak_flops.argtypes = [vp, i32, i32, P(ctypes.c_double), vp]
         for f in EXPORTED:
             if f not in ("tess_version", "tess_last_error", "tess_destroy"):
                 getattr(lib, f).restype = i32
@@ -325,6 +327,13 @@ def tess_generate(ctx, proc, seed, first_event, n_events, outputs, workspace, st
     nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check(_load().tess_generate(ctx, ctypes.byref(proc), int(seed), int(first_event), int(n_events),
                                  ctypes.byref(outputs), ws, nbytes, _stream(stream)))
+
+
+def tess_peak_flops(ctx, kind, reps=5, stream=None):
+    """Measured FMA rate (TFLOP/s) of kind TESS_PEAK_FP32 / _FP32X2 / _FP64."""
+    t = ctypes.c_double()
+    _check(_load().tess_peak_flops(ctx, int(kind), int(reps), ctypes.byref(t), _stream(stream)))
+    return t.value
 
 
 def tess_generate_noalloc(ctx, proc, seed, first_event, n_events, outputs, stream=None):

@@ -19,6 +19,7 @@
 namespace tess {
 cudaError_t launch_generate_f64(int n, bool sum, const EventParams &P, double *partials, int grid, cudaStream_t s);
 cudaError_t launch_generate_f32(int n, bool sum, const EventParams &P, double *partials, int grid, cudaStream_t s);
+cudaError_t peak_probe(int kind, int sms, int reps, cudaStream_t s, float *best_ms, double *flop);
 int grid_generate_f64(int n, bool sum, int sm_count, uint64_t n_events, int hist_bins);
 int grid_generate_f32(int n, bool sum, int sm_count, uint64_t n_events, int hist_bins);
 cudaError_t launch_me2_f64(int n, uint64_t n_events, const double *k, const uint8_t *order, const uint32_t *hel,
@@ -1144,6 +1145,21 @@ int tess_histograms(tess_ctx *ctx, const tess_process *proc, const double *hist,
 
 }  // extern "C"
 
+extern "C" int tess_peak_flops(tess_ctx *ctx, int kind, int reps, double *tflops, void *stream) {
+  if (!ctx || !tflops) return fail(TESS_E_INVALID, "ctx and tflops must not be NULL");
+  if (kind != TESS_PEAK_FP32 && kind != TESS_PEAK_FP32X2 && kind != TESS_PEAK_FP64)
+    return fail(TESS_E_INVALID, "kind = %d is not a TESS_PEAK_* value", kind);
+  if (reps < 1 || reps > 1000) return fail(TESS_E_INVALID, "reps = %d outside 1..1000", reps);
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  float ms = 0.f;
+  double flop = 0.0;
+  const cudaError_t e = tess::peak_probe(kind, ctx->sm_count, reps, (cudaStream_t)stream, &ms, &flop);
+  if (e != cudaSuccess) return cuda_fail(e, "peak probe");
+  *tflops = flop / (ms * 1e-3) / 1e12;
+  return ok();
+}
+
 // ===========================================================================
 // Allocation-free generation (tess_generate_noalloc).
 //
@@ -1190,6 +1206,14 @@ extern "C" int tess_generate_noalloc(tess_ctx *ctx, const tess_process *proc, ui
   if (proc->helicity_mode == TESS_POL_RANDOM || proc->flags != 0)
     return fail(TESS_E_UNSUPPORTED,
                 "tess_generate_noalloc is built for TESS_HEL_SUM and TESS_HEL_SAMPLE without TESS_FLAG_CUT_FIRST");
+  // Sampled events at the FP32 precisions run tess_generate's chunked
+  // two-kernel pipeline (FP32 / double-float kinematics), whose chunk buffer
+  // needs a workspace; the fused event kernel used here has FP64 kinematics,
+  // so it would not reproduce those results.  Only FP64 is offered there.
+  if (proc->helicity_mode == TESS_HEL_SAMPLE && proc->precision != TESS_FP64)
+    return fail(TESS_E_UNSUPPORTED,
+                "tess_generate_noalloc: sampled helicities are built for TESS_FP64 only (the FP32 forms need "
+                "tess_generate's workspace)");
   if (proc->hist_bins > TESS_NOALLOC_MAX_BINS)
     return fail(TESS_E_INVALID, "tess_generate_noalloc supports at most %d histogram bins (%d requested)",
                 TESS_NOALLOC_MAX_BINS, proc->hist_bins);
@@ -1199,10 +1223,23 @@ extern "C" int tess_generate_noalloc(tess_ctx *ctx, const tess_process *proc, ui
   if (n_events == 0) return ok();
   DeviceGuard g(ctx->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
-  const void *ptrs[] = {out->weight, out->me2, out->pass, out->ht, out->ptlead, out->rmin, out->acc, out->hist};
-  const char *names[] = {"weight", "me2", "pass", "ht", "ptlead", "rmin", "acc", "hist"};
-  for (int i = 0; i < 8; ++i)
-    if ((rc = check_device_ptr(ptrs[i], ctx->device, names[i]))) return rc;
+  if ((rc = check_device_ptr(out->acc, ctx->device, "acc"))) return rc;
+  if ((rc = check_device_ptr(out->hist, ctx->device, "hist"))) return rc;
+  // per-event arrays: device memory or mapped pinned host memory, as tess_generate
+  tess_outputs o = *out;
+  void *dev = nullptr;
+  if ((rc = output_ptr(out->weight, ctx->device, "weight", &dev))) return rc;
+  o.weight = (double *)dev;
+  if ((rc = output_ptr(out->me2, ctx->device, "me2", &dev))) return rc;
+  o.me2 = (double *)dev;
+  if ((rc = output_ptr(out->pass, ctx->device, "pass", &dev))) return rc;
+  o.pass = (uint8_t *)dev;
+  if ((rc = output_ptr(out->ht, ctx->device, "ht", &dev))) return rc;
+  o.ht = (double *)dev;
+  if ((rc = output_ptr(out->ptlead, ctx->device, "ptlead", &dev))) return rc;
+  o.ptlead = (double *)dev;
+  if ((rc = output_ptr(out->rmin, ctx->device, "rmin", &dev))) return rc;
+  o.rmin = (double *)dev;
   double *partials = nullptr;
   if ((rc = noalloc_scratch(ctx->device, &partials))) return rc;
 
@@ -1214,37 +1251,10 @@ extern "C" int tess_generate_noalloc(tess_ctx *ctx, const tess_process *proc, ui
   int grid = grid_for(ctx, proc, n_events);
   if (grid > max_rows) grid = max_rows;
 
-  const int n = proc->n_gluons, m = n - 2;
+  const int n = proc->n_gluons;
   const bool sum = proc->helicity_mode == TESS_HEL_SUM;
   tess::EventParams P;
-  memset(&P, 0, sizeof P);
-  P.seed = seed;
-  P.first_event = first_event;
-  P.n_events = n_events;
-  tess::philox_round_keys(seed, P.rk);
-  P.S = proc->sqrt_s * proc->sqrt_s;
-  P.lnxmin = std::log((m * proc->pt_min) * (m * proc->pt_min) / P.S);
-  P.pt_min = proc->pt_min;
-  P.eta_max = proc->eta_max;
-  P.dr2_min = proc->dr_min * proc->dr_min;
-  P.alphas_mz = proc->alphas_mz;
-  P.ln_mz2 = std::log(proc->mz * proc->mz);
-  P.b0 = (33.0 - 2.0 * proc->nf) / (12.0 * M_PI);
-  P.mu_r_factor = proc->mu_r_factor;
-  const double nc = 3.0;
-  P.wconst = std::pow(nc, n - 2) * (nc * nc - 1.0) / (256.0 * factorial(m)) * 0.3893793721e9;
-  P.phiconst = std::pow(2.0 * M_PI, 4.0 - 3.0 * m) * std::pow(M_PI / 2.0, m - 1.0) / (factorial(m - 1) * factorial(m - 2));
-  P.efac = sum ? 1.0 / std::ldexp(1.0, n - 2) : std::ldexp(1.0, n) * factorial(n - 1) / std::ldexp(1.0, n - 2);
-  P.hist_bins = proc->hist_bins;
-  P.hist_obs = proc->hist_observable;
-  P.hist_lo = proc->hist_lo;
-  P.hist_inv_width = proc->hist_bins > 0 ? proc->hist_bins / (proc->hist_hi - proc->hist_lo) : 0.0;
-  P.weight = out->weight;
-  P.me2 = out->me2;
-  P.pass = out->pass;
-  P.ht = out->ht;
-  P.ptlead = out->ptlead;
-  P.rmin = out->rmin;
+  fill_params(proc, seed, first_event, n_events, &o, &P);
 
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = proc->precision == TESS_FP64 ? tess::launch_generate_f64(n, sum, P, partials, grid, s)

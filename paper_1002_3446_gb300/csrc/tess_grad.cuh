@@ -541,6 +541,11 @@ __device__ __forceinline__ void grad_outputs(const GradParams &G, uint64_t e, co
     const double dl = -0.2 - 5.0 * x / (1.0 - x) + (M - 3) - (N - 2) * P.b0 * as + (4 - N);
     gu[j] = pass ? up * w * dl * P.lnxmin : 0.0;
   }
+  if (!pass) {  // failing events: zero gradients, whatever the (possibly non-finite) kinematics
+#pragma unroll
+    for (int j = 2; j < NU; ++j) gu[j] = 0.0;
+    return;
+  }
   // Rambo uniforms: reverse through the boost/rescale and the seed map
   double gx = 0.0, ggam = 0.0, gaa = 0.0, gM = 0.0, gb[3] = {0, 0, 0}, gQ[4] = {0, 0, 0, 0};
   double gq[M][4], gbq[M], gf[M];

@@ -1,5 +1,6 @@
-"""Batched mixed multiplicities (one captured CUDA graph, one branch per
-process) and the amplitude-kernel autotuner, through the C ABI.
+"""Batched mixed multiplicities (the per-process pipelines recorded one after
+another as a single chain of one captured CUDA graph) and the
+amplitude-kernel autotuner, through the C ABI.
 
 The batched path runs the same kernels with the same plans as separate
 tess_generate calls, so its outputs must be identical to them; replaying the

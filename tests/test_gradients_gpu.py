@@ -9,7 +9,8 @@ Tolerances: with the Berends-Giele pass in FP64 each gradient component
 agrees with the oracle to 1e-8 of the event's largest component (rounding
 in an adjoint sweep is amplified like the amplitude's own conditioning,
 with the same rare ill-conditioned exceptions, which are counted); with FP32
-currents the median of that relative difference is below 1e-4.
+currents the median and the 99th percentile of that relative difference are
+bounded at about three times their measured values (on 2^12 events).
 """
 import math
 
@@ -62,7 +63,7 @@ def test_draws_match_oracle(ctx, orc):
                                          (8, tess.TESS_FP32_CURRENTS), (10, tess.TESS_FP32_CURRENTS)])
 def test_gradients_match_oracle(ctx, orc, n, precision):
     pt_min = 30.0 if n >= 10 else 20.0
-    E = 1 << 10 if n <= 8 else 1 << 12  # acceptance at n = 10 is a few per cent
+    E = 1 << 12
     u, hel, order = tess.tess_draws(ctx, n, 11, 0, E)
     proc = tess.process(n, precision=precision, pt_min=pt_min)
     g = tess.tess_gradients(ctx, proc, u, hel, order)
@@ -72,7 +73,10 @@ def test_gradients_match_oracle(ctx, orc, n, precision):
     gu = g["dw_du"].cpu().numpy()
     gk = g["dw_dk"].cpu().numpy()
     ok = (w > 0) & (w_o > 0)
-    assert ((w > 0) != (w_o > 0)).sum() <= 1  # a cut flag at its threshold
+    # a cut flag at its threshold; vanishing-helicity weights are rounding
+    # noise that either side may round to exactly zero
+    live = np.maximum(w, w_o) > 1e-6 * w_o.max()
+    assert (((w > 0) != (w_o > 0)) & live).sum() <= 1
     big = ok & (w_o > 1e-6 * w_o.max())  # skip vanishing-helicity noise
     assert big.sum() > 20
     def rel(a, b):
@@ -81,12 +85,15 @@ def test_gradients_match_oracle(ctx, orc, n, precision):
     ru, rk = rel(gu[big], gu_o[big]), rel(gk[big], gk_o[big])
     rw = np.abs(w[big] - w_o[big]) / w_o[big]
     print(f"gradients n={n} precision={precision}: weight rel median {np.median(rw):.1e}, "
-          f"dw/du median {np.median(ru):.1e} max {ru.max():.1e}, dw/dk median {np.median(rk):.1e} max {rk.max():.1e}")
+          f"dw/du median {np.median(ru):.1e} p99 {np.quantile(ru, 0.99):.1e} max {ru.max():.1e}, "
+          f"dw/dk median {np.median(rk):.1e} p99 {np.quantile(rk, 0.99):.1e} max {rk.max():.1e}, {big.sum()} events")
     if precision == tess.TESS_FP64:
         assert np.median(ru) < 1e-11 and np.median(rk) < 1e-11
         assert (ru > 1e-8).sum() <= max(1, big.sum() // 100) and (rk > 1e-8).sum() <= max(1, big.sum() // 100)
     else:
-        assert np.median(ru) < 1e-4 and np.median(rk) < 1e-4
+        # measured at n = 8 / 10: medians 3.4e-6 .. 5.8e-6, 99th percentiles 4.9e-5 .. 9.1e-5
+        assert np.median(ru) < 2e-5 and np.median(rk) < 2e-5
+        assert np.quantile(ru, 0.99) < 3e-4 and np.quantile(rk, 0.99) < 3e-4
     # failing events: zero weight and zero gradients
     assert np.all(gu[w == 0] == 0) and np.all(gk[w == 0] == 0)
 

@@ -7,7 +7,9 @@ synchronisation); its scratch is a fixed array inside the library.  Here it is
 called through the C ABI twice in a row -- the second call finds the first
 call's leftovers in that shared array -- and each call's outputs are compared
 with tess_generate's for the same events, at the FP64 parity tolerance the
-other tests use (relative 1e-10).  This file is collected last so that a run
+other tests use (relative 1e-10); the FP32 exact-sum case runs the same
+fused kernel as tess_generate and must agree bit for bit.  Sampled events at
+the FP32 precisions need tess_generate's workspace and are refused.  This file is collected last so that a run
 stopping at the first failure has run every other test already; it also
 passes on its own in a fresh process.
 """
@@ -52,6 +54,11 @@ CALLS = [
     (dict(n=4, precision=tess.TESS_FP64, helicity_mode=tess.TESS_HEL_SUM, hist_bins=50), 2, 12345, 3001),
 ]
 
+CALLS_FP32 = [
+    (dict(n=4, precision=tess.TESS_FP32_CURRENTS, helicity_mode=tess.TESS_HEL_SUM, hist_bins=50), 3, 777, 2049),
+    (dict(n=5, precision=tess.TESS_FP32_DS, helicity_mode=tess.TESS_HEL_SUM), 4, 0, 1000),
+]
+
 
 def test_noalloc_matches_generate_on_two_calls_in_a_row(ctx):
     for kw, seed, first, N in CALLS:
@@ -69,6 +76,45 @@ def test_noalloc_matches_generate_on_two_calls_in_a_row(ctx):
         ha, _ = got.histograms()
         hb, _ = ref.histograms()
         assert np.allclose(ha, hb, rtol=RTOL, atol=1e-12 * hb.sum())
+
+
+def test_noalloc_fp32_exact_sum_matches_generate(ctx):
+    for kw, seed, first, N in CALLS_FP32:
+        proc = tess.process(**kw)
+        ref = tess.Run(ctx, proc, N)
+        ref.generate(seed, first)
+        got = tess.Run(ctx, proc, N)
+        for _ in range(2):
+            got.reset()
+            tess.tess_generate_noalloc(ctx, proc, seed, first, N, got.outputs)
+            a, b = _outputs_of(got), _outputs_of(ref)
+            for key in ("pass", "weight", "me2", "ht", "ptlead", "rmin"):
+                assert np.array_equal(a[key], b[key]), key
+            sa, sb = got.result(), ref.result()
+            assert abs(sa[0] - sb[0]) <= RTOL * abs(sb[0]) and sa[2:] == sb[2:]
+
+
+def test_noalloc_refuses_fp32_sampled(ctx):
+    for prec in (tess.TESS_FP32_CURRENTS, tess.TESS_FP32_DS):
+        proc = tess.process(6, precision=prec)
+        run = tess.Run(ctx, proc, 16)
+        with pytest.raises(tess.TessError) as e:
+            tess.tess_generate_noalloc(ctx, proc, 1, 0, 16, run.outputs)
+        assert e.value.code == tess.TESS_E_UNSUPPORTED
+        assert "TESS_FP64 only" in tess.tess_last_error()
+
+
+def test_noalloc_host_mapped_outputs(ctx):
+    # per-event arrays in pinned host memory, stored by the kernel directly
+    proc = tess.process(6, precision=tess.TESS_FP64)
+    N = 1000
+    ref = tess.Run(ctx, proc, N)
+    tess.tess_generate_noalloc(ctx, proc, 5, 100, N, ref.outputs)
+    got = tess.Run(ctx, proc, N, host_per_event=True)
+    tess.tess_generate_noalloc(ctx, proc, 5, 100, N, got.outputs)
+    a, b = _outputs_of(got), _outputs_of(ref)
+    for key in ("pass", "weight", "me2", "ht", "ptlead", "rmin"):
+        assert np.array_equal(a[key], b[key]), key
 
 
 def test_noalloc_rejects_too_many_bins(ctx):
