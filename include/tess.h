@@ -281,6 +281,11 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
 #define TESS_K2_REAL_HI 10   /* the real form compiled for more resident blocks (FP32, TESS_POL_RANDOM, n <= 8) */
 #define TESS_K2_ROWS_REAL 11 /* row form with real currents, 64 threads (FP32, TESS_POL_RANDOM, n >= 8) */
 #define TESS_K2_PAIR_W 12    /* O(n^3) tensor rewrite of the four-vertex sum, two threads per event (FP32) */
+#define TESS_K2_WAVE 13      /* row form with a runtime step loop, 64 events per block (FP32, n >= 6) */
+#define TESS_K2_WAVE2 14     /* wavefront row form: two lanes of a warp per event build two rows of the
+                                current table in step (Sec. 3's one thread per current of a length), 32 events
+                                per block (FP32, n >= 6) */
+#define TESS_K2_WAVE2U 15    /* TESS_K2_WAVE2 with the code of every step unrolled (FP32, n >= 6) */
 #define TESS_SCHED_SERIAL 0
 #define TESS_SCHED_OVERLAP 1
 #define TESS_SCHED_OVERLAP_TILES 2

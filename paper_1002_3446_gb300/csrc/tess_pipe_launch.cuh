@@ -8,6 +8,7 @@
 #include "tess_pair.cuh"
 #include "tess_pair_w.cuh"
 #include "tess_pipeline.cuh"
+#include "tess_wave.cuh"
 
 namespace tess {
 
@@ -115,6 +116,12 @@ inline cudaError_t encode_rows_map(CUtensorMap *map, const float *base, int rows
 //   K2_PAIR_W  tensor form: the O(n^3) rewrite of the four-vertex sum
 //              (antisymmetric tensors per set), lane-pair layout,
 //              32 events per block                               FP32, any n
+//   K2_WAVE    row form with a runtime step loop (one copy of the split
+//              code serves every step), 64 events per block     FP32, n >= 6
+//   K2_WAVE2   the same with two lanes of a warp per event building two
+//              rows in step (tess_wave.cuh), 32 events per block (64
+//              threads)                                          FP32, n >= 6
+//   K2_WAVE2U  K2_WAVE2 with every step's code unrolled           FP32, n >= 6
 enum K2Form {
   K2_REG = 0,
   K2_ROWS32 = 1,
@@ -129,7 +136,10 @@ enum K2Form {
   K2_REAL_HI = 10,
   K2_ROWS_REAL = 11,
   K2_PAIR_W = 12,
-  K2_NFORMS = 13
+  K2_WAVE = 13,
+  K2_WAVE2 = 14,
+  K2_WAVE2U = 15,
+  K2_NFORMS = 16
 };
 
 // What a call offers the amplitude kernel: CAP_REAL_EPS, its polarisation
@@ -154,7 +164,10 @@ constexpr bool k2_valid(int f, unsigned caps) {
       case K2_REG: return N <= 8;
       case K2_REG_HI: return N <= 7;
       case K2_ROWS32:
-      case K2_ROWS64: return N >= 6;
+      case K2_ROWS64:
+      case K2_WAVE:
+      case K2_WAVE2:
+      case K2_WAVE2U: return N >= 6;
       case K2_PAIR32:
       case K2_PAIR64: return true;
       default: return false;
@@ -171,16 +184,21 @@ template <int N, typename R, int F>
 struct K2V {
   static constexpr int L = N - 1;
   static constexpr int block =
-      (F == K2_ROWS32 || F == K2_PAIR32 || F == K2_PAIR_W)
+      (F == K2_ROWS32 || F == K2_PAIR32 || F == K2_PAIR_W || F == K2_WAVE2 || F == K2_WAVE2U)
           ? 32
-          : ((F == K2_ROWS64 || F == K2_PAIR64 || F == K2_ROWS_REAL) ? 64 : 128);
+          : ((F == K2_ROWS64 || F == K2_PAIR64 || F == K2_ROWS_REAL || F == K2_WAVE) ? 64 : 128);
   static constexpr bool rows = F == K2_ROWS32 || F == K2_ROWS64;
   static constexpr bool pair = F == K2_PAIR32 || F == K2_PAIR64 || F == K2_PAIR_W;
-  static constexpr int threads = pair ? 2 * block : block;  // block = events per tile
+  static constexpr int wave_g = (F == K2_WAVE2 || F == K2_WAVE2U) ? 2 : 1;  // lanes per event (wavefront forms)
+  static constexpr bool wave = F == K2_WAVE || F == K2_WAVE2 || F == K2_WAVE2U;
+  static constexpr bool wave_unr = F == K2_WAVE2U;
+  static constexpr int threads = pair ? 2 * block : (wave ? wave_g * block : block);  // block = events per tile
   static constexpr int hi_blocks = N >= 6 ? 3 : 4;
   static constexpr int real_hi_blocks = N >= 8 ? 3 : 4;
   static void *fn() {
-    if constexpr (F == K2_PAIR_W)
+    if constexpr (wave)
+      return (void *)bg_wave_kernel<N, block, wave_g, wave_unr>;
+    else if constexpr (F == K2_PAIR_W)
       return (void *)bg_pair_w_kernel<N, block>;
     else if constexpr (F == K2_ROWS_REAL)
       return (void *)bg_rows_real_kernel<N, block>;
@@ -204,7 +222,9 @@ struct K2V {
       return (void *)bg_loop_kernel<N, 128>;
   }
   static size_t smem(int hist_bins) {
-    if constexpr (F == K2_PAIR_W)
+    if constexpr (wave)
+      return wave_smem_per_event<L>() * block + EpiSmem<threads>::bytes(hist_bins);
+    else if constexpr (F == K2_PAIR_W)
       return PairWSmem<L, block>::bytes + EpiSmem<threads>::bytes(hist_bins);
     else if constexpr (F == K2_ROWS_REAL)
       return ((rows_real_smem_per_thread<L>() * block + 15) & ~(size_t)15) + EpiSmem<block>::bytes(hist_bins);
@@ -221,7 +241,9 @@ struct K2V {
   // map: tensor map of B.in (staged forms only)
   static cudaError_t launch(const ChunkParams &C, const ChunkBuf<R> &B, double *partials, int grid, size_t smem,
                             cudaStream_t s, const CUtensorMap *map) {
-    if constexpr (F == K2_PAIR_W)
+    if constexpr (wave)
+      bg_wave_kernel<N, block, wave_g, wave_unr><<<grid, threads, smem, s>>>(C, B, partials);
+    else if constexpr (F == K2_PAIR_W)
       bg_pair_w_kernel<N, block><<<grid, threads, smem, s>>>(C, B, partials);
     else if constexpr (F == K2_ROWS_REAL)
       bg_rows_real_kernel<N, block><<<grid, block, smem, s>>>(C, B, partials);
@@ -274,6 +296,9 @@ auto with_form(int f, Fn &&fn) {
       if (f == K2_ROWS_REAL) return fn(K2V<N, R, K2_ROWS_REAL>{});
     }
     if constexpr (N >= 6) {
+      if (f == K2_WAVE) return fn(K2V<N, R, K2_WAVE>{});
+      if (f == K2_WAVE2) return fn(K2V<N, R, K2_WAVE2>{});
+      if (f == K2_WAVE2U) return fn(K2V<N, R, K2_WAVE2U>{});
       if (f == K2_ROWS64) return fn(K2V<N, R, K2_ROWS64>{});
       return fn(K2V<N, R, K2_ROWS32>{});
     } else {
