@@ -384,7 +384,7 @@ def summary_of(line, configs, peaks):
     b = line.get("batched_mixed")
     if b:
         out["C4"] = {k: sig(b[k]["value"]) for k in ("plain_9_launches_autotuned", "graph_batched_autotuned",
-                                                      "persistent_autotuned") if k in b}
+                                                      "persistent_graph") if k in b}
     g = line.get("gradients_gg6g")
     if g:
         out["C5_grad_ev_s"] = sig(g["value"])
@@ -699,6 +699,22 @@ def bench_batched(torch, tess, ctx, flush, steps):
     res["graph_batched_autotuned"] = {"value": total / (ms * 1e-3), "ms": ms, "variant_schedule": chosen}
     ms = timed(plain)
     res["plain_9_launches_autotuned"] = {"value": total / (ms * 1e-3), "ms": ms}
+    # one persistent launch over every multiplicity (atomic work counter), captured in a graph
+    pws_bytes = tess.tess_workspace_size_persistent(ctx, procs, counts)
+    pws = torch.empty((pws_bytes + 7) // 8, dtype=torch.float64, device="cuda")
+
+    def persistent():
+        tess.tess_generate_persistent(ctx, procs, seeds, firsts, counts, outs, pws)
+
+    ms = timed(persistent)
+    res["persistent"] = {"value": total / (ms * 1e-3), "ms": ms}
+    g = torch.cuda.CUDAGraph()
+    cs = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=cs, capture_error_mode="thread_local"):
+        tess.tess_generate_persistent(ctx, procs, seeds, firsts, counts, outs, pws, stream=cs)
+    ms = timed(g.replay)
+    res["persistent_graph"] = {"value": total / (ms * 1e-3), "ms": ms}
     res["unit"] = "events/s"
     return res
 

@@ -222,6 +222,32 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
                           const uint64_t *first_events, const uint64_t *n_events, const tess_outputs *outs,
                           void *workspace, size_t workspace_bytes, void *stream);
 
+/* ---- Batched mixed multiplicities, one persistent launch ----------------------
+ * Paper: Sec. 3's initialization phase (kernel start-up matters when the
+ * kernel is short, n = 4); here every multiplicity of a batch runs in one
+ * kernel launch.  Same arguments and outputs as tess_generate_batched (n_proc
+ * 1..16); each process must be TESS_FP32_DS with TESS_HEL_SAMPLE and no flags
+ * (else TESS_E_UNSUPPORTED).  Work items are (process, tile of 128 events),
+ * handed out by one atomic counter in the workspace to resident blocks (none
+ * waits on another), from the process with the most gluons down; each block
+ * runs the whole event path of its tile (double-float kinematics into a
+ * shared-memory tile, the register-form amplitude up to n = 8, the loop form
+ * above, the epilogue) and writes the tile's partial sums to the tile's own
+ * row, which a second kernel folds per process in tile order, so the sums do
+ * not depend on which block took which tile.  Three stream operations (a
+ * 4-byte memset of the counter, the persistent kernel, the fold); no host
+ * synchronisation, no allocation, so the call can be captured in a CUDA
+ * graph by the caller.  Per-event values equal tess_generate's with the same
+ * precision up to the FP32 summation order of the amplitude form.
+ * workspace: tess_workspace_size_persistent() bytes, device, 256-byte aligned
+ * (the counter and every tile's row of partial sums); calls that overlap on
+ * the GPU must not share it.  Errors as tess_generate_batched. */
+int tess_workspace_size_persistent(const tess_ctx *ctx, int n_proc, const tess_process *procs,
+                                   const uint64_t *n_events, size_t *bytes);
+int tess_generate_persistent(tess_ctx *ctx, int n_proc, const tess_process *procs, const uint64_t *seeds,
+                             const uint64_t *first_events, const uint64_t *n_events, const tess_outputs *outs,
+                             void *workspace, size_t workspace_bytes, void *stream);
+
 /* ---- Amplitude-kernel autotuner ------------------------------------------------
  * Paper: Sec. 2 chooses the running configuration (threads and events per
  * multiprocessor, Table 1 / Table 2) by measurement before implementing the

@@ -43,7 +43,8 @@ EXPORTED = ["tess_version", "tess_last_error", "tess_init", "tess_destroy", "tes
             "tess_me2", "tess_result", "tess_weights", "tess_histograms", "tess_generate_noalloc",
             "tess_kernel_launches", "tess_workspace_size_batched", "tess_generate_batched", "tess_autotune",
             "tess_stage_timing", "tess_stage_times", "tess_draws", "tess_gradients", "tess_select_variant",
-            "tess_plan_info", "tess_gradients_workspace_size", "tess_gauge_ratio", "tess_peak_flops"]
+            "tess_plan_info", "tess_gradients_workspace_size", "tess_gauge_ratio", "tess_peak_flops",
+            "tess_workspace_size_persistent", "tess_generate_persistent"]
 
 
 class TessError(RuntimeError):
@@ -103,6 +104,9 @@ def _load():
         lib.tess_workspace_size_batched.argtypes = [vp, i32, P(tess_process), P(u64), P(ctypes.c_size_t)]
         lib.tess_generate_batched.argtypes = [vp, i32, P(tess_process), P(u64), P(u64), P(u64), P(tess_outputs), vp,
                                               ctypes.c_size_t, vp]
+        lib.tess_workspace_size_persistent.argtypes = [vp, i32, P(tess_process), P(u64), P(ctypes.c_size_t)]
+        lib.tess_generate_persistent.argtypes = [vp, i32, P(tess_process), P(u64), P(u64), P(u64), P(tess_outputs),
+                                                 vp, ctypes.c_size_t, vp]
         lib.tess_autotune.argtypes = [vp, P(tess_process), u64, vp, vp, ctypes.c_size_t, vp, P(ctypes.c_int)]
         lib.tess_stage_timing.argtypes = [vp, i32]
         lib.tess_select_variant.argtypes = [vp, P(tess_process), i32, i32]
@@ -201,6 +205,22 @@ def tess_generate_batched(ctx, procs, seeds, first_events, n_events, outputs, wo
     nbytes = workspace.numel() * workspace.element_size()
     _check(_load().tess_generate_batched(ctx, k, arr, _u64s(seeds), _u64s(first_events), _u64s(n_events), outs,
                                          _ptr(workspace), nbytes, _stream(stream)))
+
+
+def tess_workspace_size_persistent(ctx, procs, n_events):
+    arr = (tess_process * len(procs))(*procs)
+    b = ctypes.c_size_t()
+    _check(_load().tess_workspace_size_persistent(ctx, len(procs), arr, _u64s(n_events), ctypes.byref(b)))
+    return b.value
+
+
+def tess_generate_persistent(ctx, procs, seeds, first_events, n_events, outputs, workspace, stream=None):
+    k = len(procs)
+    arr = (tess_process * k)(*procs)
+    outs = (tess_outputs * k)(*outputs)
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(_load().tess_generate_persistent(ctx, k, arr, _u64s(seeds), _u64s(first_events), _u64s(n_events), outs,
+                                            _ptr(workspace), nbytes, _stream(stream)))
 
 
 def tess_autotune(ctx, proc, probe_events, acc_scratch, workspace, stream=None):

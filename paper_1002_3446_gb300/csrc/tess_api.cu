@@ -14,12 +14,15 @@
 #include "tess.h"
 #include "tess_grad.cuh"
 #include "tess_kernels.cuh"
+#include "tess_persist.cuh"
 #include "tess_pipe_launch.cuh"
 
 namespace tess {
 cudaError_t launch_generate_f64(int n, bool sum, const EventParams &P, double *partials, int grid, cudaStream_t s);
 cudaError_t launch_generate_f32(int n, bool sum, const EventParams &P, double *partials, int grid, cudaStream_t s);
 cudaError_t peak_probe(int kind, int sms, int reps, cudaStream_t s, float *best_ms, double *flop);
+cudaError_t persist_launch(const PersistParams &Q, const PersistFold &F, int nmax, int max_hist_bins, int sm_count,
+                           cudaStream_t s, int *grid_out);
 int grid_generate_f64(int n, bool sum, int sm_count, uint64_t n_events, int hist_bins);
 int grid_generate_f32(int n, bool sum, int sm_count, uint64_t n_events, int hist_bins);
 cudaError_t launch_me2_f64(int n, uint64_t n_events, const double *k, const uint8_t *order, const uint32_t *hel,
@@ -1144,6 +1147,116 @@ int tess_histograms(tess_ctx *ctx, const tess_process *proc, const double *hist,
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Batched mixed multiplicities in one persistent launch (tess_persist.cuh).
+// ===========================================================================
+namespace {
+
+// Workspace: the work counter, then each process's tile rows of partial sums.
+int persistent_layout(int n_proc, const tess_process *procs, const uint64_t *n_events, size_t *offsets,
+                      size_t *total) {
+  if (n_proc < 1 || n_proc > tess::kPersistMaxProc)
+    return fail(TESS_E_INVALID, "n_proc must be 1..%d", tess::kPersistMaxProc);
+  size_t off = 256;  // the counter
+  uint64_t items = 0;
+  for (int i = 0; i < n_proc; ++i) {
+    int rc = check_process(&procs[i]);
+    if (rc) return rc;
+    const tess_process &p = procs[i];
+    if (p.precision != TESS_FP32_DS || p.helicity_mode != TESS_HEL_SAMPLE || p.flags != 0)
+      return fail(TESS_E_UNSUPPORTED,
+                  "persistent batched form: process %d must be TESS_FP32_DS, TESS_HEL_SAMPLE, no flags", i);
+    const uint64_t tiles = (n_events[i] + tess::kBlock - 1) / tess::kBlock;
+    items += tiles;
+    if (items > (uint64_t)INT32_MAX) return fail(TESS_E_INVALID, "too many events for one persistent launch");
+    offsets[i] = off;
+    off = align256(off + (size_t)tiles * tess::partial_stride(p.hist_bins) * sizeof(double));
+  }
+  *total = off;
+  return TESS_OK;
+}
+
+}  // namespace
+
+extern "C" int tess_workspace_size_persistent(const tess_ctx *ctx, int n_proc, const tess_process *procs,
+                                              const uint64_t *n_events, size_t *bytes) {
+  if (!ctx || !procs || !n_events || !bytes) return fail(TESS_E_INVALID, "NULL argument");
+  size_t offs[tess::kPersistMaxProc];
+  const int rc = persistent_layout(n_proc, procs, n_events, offs, bytes);
+  return rc ? rc : ok();
+}
+
+extern "C" int tess_generate_persistent(tess_ctx *ctx, int n_proc, const tess_process *procs, const uint64_t *seeds,
+                                        const uint64_t *first_events, const uint64_t *n_events,
+                                        const tess_outputs *outs, void *workspace, size_t workspace_bytes,
+                                        void *stream) {
+  if (!ctx || !procs || !seeds || !first_events || !n_events || !outs) return fail(TESS_E_INVALID, "NULL argument");
+  size_t offs[tess::kPersistMaxProc], need = 0;
+  int rc = persistent_layout(n_proc, procs, n_events, offs, &need);
+  if (rc) return rc;
+  DeviceGuard g(ctx->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  if ((rc = check_device_ptr(workspace, ctx->device, "workspace"))) return rc;
+  if (!workspace || workspace_bytes < need)
+    return fail(TESS_E_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, workspace ? workspace_bytes : 0);
+  if (((uintptr_t)workspace) % 256 != 0) return fail(TESS_E_WORKSPACE, "workspace must be 256-byte aligned");
+  // processes from the most gluons down: the longest tiles are handed out first
+  int order[tess::kPersistMaxProc];
+  for (int i = 0; i < n_proc; ++i) order[i] = i;
+  std::stable_sort(order, order + n_proc, [&](int a, int b) { return procs[a].n_gluons > procs[b].n_gluons; });
+  tess::PersistParams Q;
+  memset(&Q, 0, sizeof Q);
+  tess::PersistFold F;
+  memset(&F, 0, sizeof F);
+  Q.counter = (int *)workspace;
+  int items = 0, nmax = 4, max_bins = 0;
+  for (int j = 0; j < n_proc; ++j) {
+    const int i = order[j];
+    const tess_outputs *out = &outs[i];
+    if (!out->acc) return fail(TESS_E_INVALID, "outputs[%d].acc must not be NULL", i);
+    if (procs[i].hist_bins > 0 && !out->hist) return fail(TESS_E_INVALID, "process %d: hist_bins > 0 needs hist", i);
+    if (n_events[i] > (UINT64_MAX - first_events[i])) return fail(TESS_E_INVALID, "event range overflows 64 bits");
+    if ((rc = check_device_ptr(out->acc, ctx->device, "acc"))) return rc;
+    if ((rc = check_device_ptr(out->hist, ctx->device, "hist"))) return rc;
+    tess_outputs o = *out;
+    void *dev = nullptr;
+    if ((rc = output_ptr(out->weight, ctx->device, "weight", &dev))) return rc;
+    o.weight = (double *)dev;
+    if ((rc = output_ptr(out->me2, ctx->device, "me2", &dev))) return rc;
+    o.me2 = (double *)dev;
+    if ((rc = output_ptr(out->pass, ctx->device, "pass", &dev))) return rc;
+    o.pass = (uint8_t *)dev;
+    if ((rc = output_ptr(out->ht, ctx->device, "ht", &dev))) return rc;
+    o.ht = (double *)dev;
+    if ((rc = output_ptr(out->ptlead, ctx->device, "ptlead", &dev))) return rc;
+    o.ptlead = (double *)dev;
+    if ((rc = output_ptr(out->rmin, ctx->device, "rmin", &dev))) return rc;
+    o.rmin = (double *)dev;
+    tess::PersistProc &pp = Q.proc[j];
+    fill_params(&procs[i], seeds[i], first_events[i], n_events[i], &o, &pp.P);
+    pp.n = procs[i].n_gluons;
+    pp.tiles = (int)((n_events[i] + tess::kBlock - 1) / tess::kBlock);
+    pp.first_item = items;
+    pp.tile_sums = (double *)((char *)workspace + offs[i]);
+    items += pp.tiles;
+    nmax = std::max(nmax, pp.n);
+    max_bins = std::max(max_bins, procs[i].hist_bins);
+    F.tile_sums[j] = pp.tile_sums;
+    F.acc[j] = out->acc;
+    F.hist[j] = out->hist;
+    F.tiles[j] = pp.tiles;
+    F.hist_bins[j] = procs[i].hist_bins;
+    F.n_events[j] = n_events[i];
+  }
+  Q.nproc = n_proc;
+  Q.items = items;
+  if (items == 0) return ok();
+  const cudaError_t e =
+      tess::persist_launch(Q, F, nmax, max_bins, ctx->sm_count, (cudaStream_t)stream, nullptr);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent launch");
+  return ok();
+}
 
 extern "C" int tess_peak_flops(tess_ctx *ctx, int kind, int reps, double *tflops, void *stream) {
   if (!ctx || !tflops) return fail(TESS_E_INVALID, "ctx and tflops must not be NULL");
