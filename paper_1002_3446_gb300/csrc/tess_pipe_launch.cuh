@@ -9,6 +9,7 @@
 #include "tess_pair_w.cuh"
 #include "tess_pipeline.cuh"
 #include "tess_wave.cuh"
+#include "tess_wavep.cuh"
 
 namespace tess {
 
@@ -122,6 +123,9 @@ inline cudaError_t encode_rows_map(CUtensorMap *map, const float *base, int rows
 //              rows in step (tess_wave.cuh), 32 events per block (64
 //              threads)                                          FP32, n >= 6
 //   K2_WAVE2U  K2_WAVE2 with every step's code unrolled           FP32, n >= 6
+//   K2_WAVE2P  K2_WAVE2 with the vertex algebra in packed FP32 pairs
+//              (tess_wavep.cuh)                                  FP32, n >= 6
+//   K2_WAVE2PU K2_WAVE2P with every step's code unrolled          FP32, n >= 6
 enum K2Form {
   K2_REG = 0,
   K2_ROWS32 = 1,
@@ -139,7 +143,9 @@ enum K2Form {
   K2_WAVE = 13,
   K2_WAVE2 = 14,
   K2_WAVE2U = 15,
-  K2_NFORMS = 16
+  K2_WAVE2P = 16,
+  K2_WAVE2PU = 17,
+  K2_NFORMS = 18
 };
 
 // What a call offers the amplitude kernel: CAP_REAL_EPS, its polarisation
@@ -167,7 +173,9 @@ constexpr bool k2_valid(int f, unsigned caps) {
       case K2_ROWS64:
       case K2_WAVE:
       case K2_WAVE2:
-      case K2_WAVE2U: return N >= 6;
+      case K2_WAVE2U:
+      case K2_WAVE2P:
+      case K2_WAVE2PU: return N >= 6;
       case K2_PAIR32:
       case K2_PAIR64: return true;
       default: return false;
@@ -184,19 +192,24 @@ template <int N, typename R, int F>
 struct K2V {
   static constexpr int L = N - 1;
   static constexpr int block =
-      (F == K2_ROWS32 || F == K2_PAIR32 || F == K2_PAIR_W || F == K2_WAVE2 || F == K2_WAVE2U)
+      (F == K2_ROWS32 || F == K2_PAIR32 || F == K2_PAIR_W || F == K2_WAVE2 || F == K2_WAVE2U || F == K2_WAVE2P ||
+           F == K2_WAVE2PU)
           ? 32
           : ((F == K2_ROWS64 || F == K2_PAIR64 || F == K2_ROWS_REAL || F == K2_WAVE) ? 64 : 128);
   static constexpr bool rows = F == K2_ROWS32 || F == K2_ROWS64;
   static constexpr bool pair = F == K2_PAIR32 || F == K2_PAIR64 || F == K2_PAIR_W;
-  static constexpr int wave_g = (F == K2_WAVE2 || F == K2_WAVE2U) ? 2 : 1;  // lanes per event (wavefront forms)
-  static constexpr bool wave = F == K2_WAVE || F == K2_WAVE2 || F == K2_WAVE2U;
-  static constexpr bool wave_unr = F == K2_WAVE2U;
+  static constexpr int wave_g =
+      (F == K2_WAVE2 || F == K2_WAVE2U || F == K2_WAVE2P || F == K2_WAVE2PU) ? 2 : 1;  // lanes per event
+  static constexpr bool wavep = F == K2_WAVE2P || F == K2_WAVE2PU;  // packed-pair arithmetic
+  static constexpr bool wave = F == K2_WAVE || F == K2_WAVE2 || F == K2_WAVE2U || wavep;
+  static constexpr bool wave_unr = F == K2_WAVE2U || F == K2_WAVE2PU;
   static constexpr int threads = pair ? 2 * block : (wave ? wave_g * block : block);  // block = events per tile
   static constexpr int hi_blocks = N >= 6 ? 3 : 4;
   static constexpr int real_hi_blocks = N >= 8 ? 3 : 4;
   static void *fn() {
-    if constexpr (wave)
+    if constexpr (wavep)
+      return (void *)bg_wavep_kernel<N, block, wave_g, wave_unr>;
+    else if constexpr (wave)
       return (void *)bg_wave_kernel<N, block, wave_g, wave_unr>;
     else if constexpr (F == K2_PAIR_W)
       return (void *)bg_pair_w_kernel<N, block>;
@@ -241,7 +254,9 @@ struct K2V {
   // map: tensor map of B.in (staged forms only)
   static cudaError_t launch(const ChunkParams &C, const ChunkBuf<R> &B, double *partials, int grid, size_t smem,
                             cudaStream_t s, const CUtensorMap *map) {
-    if constexpr (wave)
+    if constexpr (wavep)
+      bg_wavep_kernel<N, block, wave_g, wave_unr><<<grid, threads, smem, s>>>(C, B, partials);
+    else if constexpr (wave)
       bg_wave_kernel<N, block, wave_g, wave_unr><<<grid, threads, smem, s>>>(C, B, partials);
     else if constexpr (F == K2_PAIR_W)
       bg_pair_w_kernel<N, block><<<grid, threads, smem, s>>>(C, B, partials);
@@ -299,6 +314,8 @@ auto with_form(int f, Fn &&fn) {
       if (f == K2_WAVE) return fn(K2V<N, R, K2_WAVE>{});
       if (f == K2_WAVE2) return fn(K2V<N, R, K2_WAVE2>{});
       if (f == K2_WAVE2U) return fn(K2V<N, R, K2_WAVE2U>{});
+      if (f == K2_WAVE2P) return fn(K2V<N, R, K2_WAVE2P>{});
+      if (f == K2_WAVE2PU) return fn(K2V<N, R, K2_WAVE2PU>{});
       if (f == K2_ROWS64) return fn(K2V<N, R, K2_ROWS64>{});
       return fn(K2V<N, R, K2_ROWS32>{});
     } else {
