@@ -315,6 +315,9 @@ int tess_generate_persistent(tess_ctx *ctx, int n_proc, const tess_process *proc
 #define TESS_K2_WAVE2P 16    /* TESS_K2_WAVE2 with the vertex algebra in packed FP32 pairs (f32x2: two lanes of
                                 FP32 work per instruction; FP32, n >= 6) */
 #define TESS_K2_WAVE2PU 17   /* TESS_K2_WAVE2P with the code of every step unrolled (FP32, n >= 6) */
+#define TESS_K2_WAVE2L 18    /* TESS_K2_WAVE2 with only the row's currents in registers (momentum sums by
+                                subtraction, split sums read back from the table), compiled for 12 resident
+                                warps per SM where the tables leave room (FP32, n >= 6) */
 #define TESS_SCHED_SERIAL 0
 #define TESS_SCHED_OVERLAP 1
 #define TESS_SCHED_OVERLAP_TILES 2

@@ -126,6 +126,8 @@ inline cudaError_t encode_rows_map(CUtensorMap *map, const float *base, int rows
 //   K2_WAVE2P  K2_WAVE2 with the vertex algebra in packed FP32 pairs
 //              (tess_wavep.cuh)                                  FP32, n >= 6
 //   K2_WAVE2PU K2_WAVE2P with every step's code unrolled          FP32, n >= 6
+//   K2_WAVE2L  K2_WAVE2 with only the row's currents in registers,
+//              compiled for 12 resident warps per SM             FP32, n >= 6
 enum K2Form {
   K2_REG = 0,
   K2_ROWS32 = 1,
@@ -145,7 +147,8 @@ enum K2Form {
   K2_WAVE2U = 15,
   K2_WAVE2P = 16,
   K2_WAVE2PU = 17,
-  K2_NFORMS = 18
+  K2_WAVE2L = 18,
+  K2_NFORMS = 19
 };
 
 // What a call offers the amplitude kernel: CAP_REAL_EPS, its polarisation
@@ -175,7 +178,8 @@ constexpr bool k2_valid(int f, unsigned caps) {
       case K2_WAVE2:
       case K2_WAVE2U:
       case K2_WAVE2P:
-      case K2_WAVE2PU: return N >= 6;
+      case K2_WAVE2PU:
+      case K2_WAVE2L: return N >= 6;
       case K2_PAIR32:
       case K2_PAIR64: return true;
       default: return false;
@@ -193,15 +197,17 @@ struct K2V {
   static constexpr int L = N - 1;
   static constexpr int block =
       (F == K2_ROWS32 || F == K2_PAIR32 || F == K2_PAIR_W || F == K2_WAVE2 || F == K2_WAVE2U || F == K2_WAVE2P ||
-           F == K2_WAVE2PU)
+           F == K2_WAVE2PU || F == K2_WAVE2L)
           ? 32
           : ((F == K2_ROWS64 || F == K2_PAIR64 || F == K2_ROWS_REAL || F == K2_WAVE) ? 64 : 128);
   static constexpr bool rows = F == K2_ROWS32 || F == K2_ROWS64;
   static constexpr bool pair = F == K2_PAIR32 || F == K2_PAIR64 || F == K2_PAIR_W;
   static constexpr int wave_g =
-      (F == K2_WAVE2 || F == K2_WAVE2U || F == K2_WAVE2P || F == K2_WAVE2PU) ? 2 : 1;  // lanes per event
+      (F == K2_WAVE2 || F == K2_WAVE2U || F == K2_WAVE2P || F == K2_WAVE2PU || F == K2_WAVE2L) ? 2 : 1;
   static constexpr bool wavep = F == K2_WAVE2P || F == K2_WAVE2PU;  // packed-pair arithmetic
-  static constexpr bool wave = F == K2_WAVE || F == K2_WAVE2 || F == K2_WAVE2U || wavep;
+  static constexpr bool wave_lean = F == K2_WAVE2L;
+  static constexpr int wave_minb = wave_lean ? 6 : 1;
+  static constexpr bool wave = F == K2_WAVE || F == K2_WAVE2 || F == K2_WAVE2U || wavep || wave_lean;
   static constexpr bool wave_unr = F == K2_WAVE2U || F == K2_WAVE2PU;
   static constexpr int threads = pair ? 2 * block : (wave ? wave_g * block : block);  // block = events per tile
   static constexpr int hi_blocks = N >= 6 ? 3 : 4;
@@ -210,7 +216,7 @@ struct K2V {
     if constexpr (wavep)
       return (void *)bg_wavep_kernel<N, block, wave_g, wave_unr>;
     else if constexpr (wave)
-      return (void *)bg_wave_kernel<N, block, wave_g, wave_unr>;
+      return (void *)bg_wave_kernel<N, block, wave_g, wave_unr, wave_lean, wave_minb>;
     else if constexpr (F == K2_PAIR_W)
       return (void *)bg_pair_w_kernel<N, block>;
     else if constexpr (F == K2_ROWS_REAL)
@@ -235,7 +241,9 @@ struct K2V {
       return (void *)bg_loop_kernel<N, 128>;
   }
   static size_t smem(int hist_bins) {
-    if constexpr (wave)
+    if constexpr (wave_lean)
+      return wave_lean_smem_per_event<L>() * block + EpiSmem<threads>::bytes(hist_bins);
+    else if constexpr (wave)
       return wave_smem_per_event<L>() * block + EpiSmem<threads>::bytes(hist_bins);
     else if constexpr (F == K2_PAIR_W)
       return PairWSmem<L, block>::bytes + EpiSmem<threads>::bytes(hist_bins);
@@ -257,7 +265,7 @@ struct K2V {
     if constexpr (wavep)
       bg_wavep_kernel<N, block, wave_g, wave_unr><<<grid, threads, smem, s>>>(C, B, partials);
     else if constexpr (wave)
-      bg_wave_kernel<N, block, wave_g, wave_unr><<<grid, threads, smem, s>>>(C, B, partials);
+      bg_wave_kernel<N, block, wave_g, wave_unr, wave_lean, wave_minb><<<grid, threads, smem, s>>>(C, B, partials);
     else if constexpr (F == K2_PAIR_W)
       bg_pair_w_kernel<N, block><<<grid, threads, smem, s>>>(C, B, partials);
     else if constexpr (F == K2_ROWS_REAL)
@@ -316,6 +324,7 @@ auto with_form(int f, Fn &&fn) {
       if (f == K2_WAVE2U) return fn(K2V<N, R, K2_WAVE2U>{});
       if (f == K2_WAVE2P) return fn(K2V<N, R, K2_WAVE2P>{});
       if (f == K2_WAVE2PU) return fn(K2V<N, R, K2_WAVE2PU>{});
+      if (f == K2_WAVE2L) return fn(K2V<N, R, K2_WAVE2L>{});
       if (f == K2_ROWS64) return fn(K2V<N, R, K2_ROWS64>{});
       return fn(K2V<N, R, K2_ROWS32>{});
     } else {

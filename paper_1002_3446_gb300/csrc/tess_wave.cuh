@@ -212,6 +212,126 @@ __device__ __forceinline__ Cx<float> bg_wave(const float4 *K4, float4 *J4, float
   return amp;
 }
 
+// Lean form of bg_wave: only the row's currents stay in registers.  The left
+// part's momentum sum is K[a..b] - K[r0..b] (both at hand in the split
+// loop), and its split sum S is read back from the table (row 0's split
+// sums, not otherwise stored, in their own slots S0[d]).  About 50 registers
+// fewer per lane, so that 12 warps fit on an SM beside the tables (6 blocks
+// of 32 events).  Subtracting momentum sums instead of adding legs changes
+// only the rounding: its absolute error, eps |K[r0..b]|, is of the order of
+// the rounding already present in the K[r0..b] terms of the same bracket.
+template <int L, int NE, int G>
+__device__ __forceinline__ Cx<float> bg_wave_lean(const float4 *K4, float4 *J4, float2 *S2, float2 *S0, int e, int g,
+                                                  const float *in_eps0, const float *in_e0, size_t cap) {
+  Cx<float> amp = cx<float>(0.f, 0.f);
+#pragma unroll 1
+  for (int a0 = wave_top_group<L, G>(); a0 >= 0; a0 -= G) {
+    const int a = a0 - g;
+    const int len = L - a;
+    const int steps = L - (a0 - G + 1) - 1;
+    CV4<float> row[L - 1];
+    RV4<float> kcur;
+    if (a == 0) {
+      load_eps(in_eps0, cap, row[0]);
+    } else {
+      row[0] = wld_cv<NE>(J4, t1<L>(a, a), e);
+    }
+    kcur = wld_k<NE>(K4, a, e);
+#pragma unroll 1
+    for (int d = 1; d <= steps; ++d) {
+      if (d < len) {
+        const int b = a + d;
+        kcur = radd(kcur, wld_k<NE>(K4, b, e));
+        CV4<float> acc = cv_zero<float>(), tri = cv_zero<float>();
+        Cx<float> s = cx<float>(0.f, 0.f);
+        RV4<float> kr = {{0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+        for (int dp = L - 2; dp >= 0; --dp) {
+          if (dp < d) {  // split: left [a..a+dp] (row register dp), right [a+dp+1..b]
+            const int r0 = a + dp + 1;
+            kr = radd(kr, wld_k<NE>(K4, r0, e));
+            const RV4<float> kl = rsub(kcur, kr);
+            const int tr = t1<L>(r0, b);
+            const CV4<float> Jr = wld_cv<NE>(J4, tr, e);
+            const CV4<float> &Jl = row[dp];
+            const Cx<float> d0 = mdot(Jl, Jr);
+            const Cx<float> jlkr = mdot(Jl, kr);
+            const Cx<float> krjl = mdot(Jr, kl);
+            Cx<float> cr = cx<float>(2.f * jlkr.re, 2.f * jlkr.im);
+            if (dp > 0) {  // left part has more than one leg
+              const float2 sl = a > 0 ? S2[t1<L>(a, a + dp) * NE + e] : S0[dp * NE + e];
+              cr.re -= sl.x;
+              cr.im -= sl.y;
+            }
+            Cx<float> cl = cx<float>(-2.f * krjl.re, -2.f * krjl.im);
+            if (dp + 1 < d) {  // right part has more than one leg
+              const float2 sr = S2[tr * NE + e];
+              cl.re -= sr.x;
+              cl.im -= sr.y;
+            }
+            axpy(acc, cr, Jr);
+            axpy(acc, cl, Jl);
+            axpy(acc, d0, rsub(kl, kr));
+            s.re += d0.re;
+            s.im += d0.im;
+#pragma unroll
+            for (int dpp = 0; dpp < dp; ++dpp) {
+              const CV4<float> JB = wld_cv<NE>(J4, t1<L>(a + dpp + 1, a + dp), e);
+              axpy(tri, mdot(row[dpp], Jr), JB);
+            }
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          acc.c[m].re = fmaf(2.f, tri.c[m].re, acc.c[m].re);
+          acc.c[m].im = fmaf(2.f, tri.c[m].im, acc.c[m].im);
+        }
+        if (a == 0 && d == L - 1) {
+          CV4<float> e0;
+          load_eps(in_e0, cap, e0);
+          amp = mdot(e0, acc);
+        } else {
+          const float inv = 1.f / mdot(kcur, kcur);
+          CV4<float> cur;
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            cur.c[m].re = acc.c[m].re * inv;
+            cur.c[m].im = acc.c[m].im * inv;
+          }
+          switch (d) {
+#define TESS_WAVE_LEAN_KEEP(D) \
+  case D:                      \
+    if constexpr (D < L - 1) row[D] = cur; \
+    break;
+            TESS_WAVE_LEAN_KEEP(1)
+            TESS_WAVE_LEAN_KEEP(2)
+            TESS_WAVE_LEAN_KEEP(3)
+            TESS_WAVE_LEAN_KEEP(4)
+            TESS_WAVE_LEAN_KEEP(5)
+            TESS_WAVE_LEAN_KEEP(6)
+            TESS_WAVE_LEAN_KEEP(7)
+            TESS_WAVE_LEAN_KEEP(8)
+            TESS_WAVE_LEAN_KEEP(9)
+            TESS_WAVE_LEAN_KEEP(10)
+#undef TESS_WAVE_LEAN_KEEP
+            default:
+              break;
+          }
+          if (a > 0) {
+            wst_cv<NE>(J4, t1<L>(a, b), e, cur);
+            S2[t1<L>(a, b) * NE + e] = make_float2(s.re, s.im);
+          } else {
+            S0[d * NE + e] = make_float2(s.re, s.im);
+          }
+        }
+      }
+      if (G > 1) __syncwarp();
+    }
+    if (G > 1) __syncwarp();
+  }
+  return amp;
+}
+
 // Event slot and group lane of this thread: G = 1, one thread per event; G =
 // 2, lanes l and l + 16 of a warp share event slot 16 w + (l & 15), so that
 // the eight lanes of a shared-memory phase read eight consecutive slots.
@@ -227,8 +347,13 @@ __device__ __forceinline__ void wave_slot(int &slot, int &g) {
   }
 }
 
-template <int N, int NE, int G, bool UNR = false>
-__global__ void __launch_bounds__(NE * G) bg_wave_kernel(ChunkParams C, ChunkBuf<float> B, double *partials) {
+template <int L>
+__host__ __device__ constexpr size_t wave_lean_smem_per_event() {
+  return wave_smem_per_event<L>() + (size_t)(L - 1) * sizeof(float2);
+}
+
+template <int N, int NE, int G, bool UNR = false, bool LEAN = false, int MINB = 1>
+__global__ void __launch_bounds__(NE * G, MINB) bg_wave_kernel(ChunkParams C, ChunkBuf<float> B, double *partials) {
   static_assert(G == 1 || G == 2, "one or two lanes per event");
   static_assert(G == 1 || NE % 16 == 0, "two-lane groups fill half warps");
   constexpr int L = N - 1, T1 = L * (L - 1) / 2, NT = NE * G;
@@ -236,8 +361,9 @@ __global__ void __launch_bounds__(NE * G) bg_wave_kernel(ChunkParams C, ChunkBuf
   float4 *J4 = (float4 *)smem_raw;
   float4 *K4 = J4 + 2 * T1 * NE;
   float2 *S2 = (float2 *)(K4 + L * NE);
+  float2 *S0 = S2 + T1 * NE;  // lean form only: row 0's split sums
   const int nb2 = C.P.hist_bins > 0 ? C.P.hist_bins + 2 : 0;
-  EpiSmem<NT> S((char *)(S2 + T1 * NE), nb2);
+  EpiSmem<NT> S((char *)(LEAN ? S0 + (L - 1) * NE : S0), nb2);
   for (int i = threadIdx.x; i < 2 * nb2; i += NT) S.hw[i] = 0.0;
   Accum<NT> A;
   int slot, g;
@@ -262,8 +388,13 @@ __global__ void __launch_bounds__(NE * G) bg_wave_kernel(ChunkParams C, ChunkBuf
       }
     }
     if (G > 1) __syncwarp();
-    const Cx<float> amp = bg_wave<L, NE, G, UNR>(K4, J4, S2, slot, g, B.in + (size_t)InRows<L>::eps(0) * cap + e,
-                                            B.in + (size_t)InRows<L>::eps0 * cap + e, cap);
+    Cx<float> amp;
+    if constexpr (LEAN)
+      amp = bg_wave_lean<L, NE, G>(K4, J4, S2, S0, slot, g, B.in + (size_t)InRows<L>::eps(0) * cap + e,
+                                   B.in + (size_t)InRows<L>::eps0 * cap + e, cap);
+    else
+      amp = bg_wave<L, NE, G, UNR>(K4, J4, S2, slot, g, B.in + (size_t)InRows<L>::eps(0) * cap + e,
+                                   B.in + (size_t)InRows<L>::eps0 * cap + e, cap);
     double w = 0.0;
     int bin = -1;
     if (has && g == G - 1) finish_event<NT, float>(C, B, e, amp2_of(amp), A, w, bin);

@@ -106,7 +106,8 @@ def test_autotune_choice_is_valid_and_consistent(ctx, n, prec):
         ({tess.TESS_K2_REG, tess.TESS_K2_REG_TMA} if n <= 8 else set()) | ({tess.TESS_K2_REG_HI, tess.TESS_K2_REG_TMA_HI} if n <= 7 else set())
         | ({tess.TESS_K2_ROWS32, tess.TESS_K2_ROWS64, tess.TESS_K2_WAVE, tess.TESS_K2_WAVE2,
                                                                     tess.TESS_K2_WAVE2U, tess.TESS_K2_WAVE2P,
-                                                                    tess.TESS_K2_WAVE2PU} if n >= 6 else set())
+                                                                    tess.TESS_K2_WAVE2PU, tess.TESS_K2_WAVE2L}
+           if n >= 6 else set())
         | {tess.TESS_K2_PAIR32, tess.TESS_K2_PAIR64, tess.TESS_K2_PAIR_W})
     assert form in valid
     run.reset()
