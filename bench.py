@@ -289,7 +289,7 @@ def bench_config(torch, tess, ctx, name, flush, steps, peaks, sm_mhz, autotune=T
         proc = make_proc(tess, wl, form)
         run = tess.Run(ctx, proc, ne, per_event=("weight", "me2", "pass"))
         if autotune and wl["hel"] == "sample":
-            tess.tess_autotune(ctx, proc, min(ne, 1 << 22), torch.zeros(tess.TESS_ACC_LEN, dtype=torch.float64,
+            tess.tess_autotune(ctx, proc, min(ne, 1 << 24), torch.zeros(tess.TESS_ACC_LEN, dtype=torch.float64,
                                                                          device="cuda"), run.workspace)
         ms = statistics.mean(time_steps(torch, run, 1, 0, steps, 2, flush))
         amp_ms, amp_launches, plan, _ = amp_kernel_time(torch, tess, ctx, proc, run, 1, 0, flush, steps)
@@ -419,7 +419,9 @@ def run_tess(args):
         tess.tess_select_variant(ctx, proc, form, sched)
     elif not args.no_autotune and wl["hel"] == "sample":
         probe_acc = torch.zeros(tess.TESS_ACC_LEN, dtype=torch.float64, device="cuda")
-        variant = tess.tess_autotune(ctx, proc, min(N, 1 << 22), probe_acc, run.workspace)
+        # tuned on the workload itself (candidates within a few per cent of each
+        # other change order between a 2^22-event probe and the full size)
+        variant = tess.tess_autotune(ctx, proc, min(N, 1 << 25), probe_acc, run.workspace)
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB > L2
     from paper_1002_3446_gb300 import dist as tdist
     first, _ = tdist.event_range(rank, ws, N)

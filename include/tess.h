@@ -318,6 +318,8 @@ int tess_generate_persistent(tess_ctx *ctx, int n_proc, const tess_process *proc
 #define TESS_K2_WAVE2L 18    /* TESS_K2_WAVE2 with only the row's currents in registers (momentum sums by
                                 subtraction, split sums read back from the table), compiled for 12 resident
                                 warps per SM where the tables leave room (FP32, n >= 6) */
+#define TESS_K2_REG_HI4 19   /* register form compiled for 4 resident blocks of 128 per SM (128 registers, the
+                                rest spilled; FP32, n <= 6) */
 #define TESS_SCHED_SERIAL 0
 #define TESS_SCHED_OVERLAP 1
 #define TESS_SCHED_OVERLAP_TILES 2

@@ -128,6 +128,8 @@ inline cudaError_t encode_rows_map(CUtensorMap *map, const float *base, int rows
 //   K2_WAVE2PU K2_WAVE2P with every step's code unrolled          FP32, n >= 6
 //   K2_WAVE2L  K2_WAVE2 with only the row's currents in registers,
 //              compiled for 12 resident warps per SM             FP32, n >= 6
+//   K2_REG_HI4 register form compiled for 4 resident blocks (16 warps)
+//              per SM: 128 registers, the rest spilled           FP32, n <= 6
 enum K2Form {
   K2_REG = 0,
   K2_ROWS32 = 1,
@@ -148,7 +150,8 @@ enum K2Form {
   K2_WAVE2P = 16,
   K2_WAVE2PU = 17,
   K2_WAVE2L = 18,
-  K2_NFORMS = 19
+  K2_REG_HI4 = 19,
+  K2_NFORMS = 20
 };
 
 // What a call offers the amplitude kernel: CAP_REAL_EPS, its polarisation
@@ -172,6 +175,7 @@ constexpr bool k2_valid(int f, unsigned caps) {
       case K2_REG_TMA_HI: return N <= 7 && !cut_first;
       case K2_REG: return N <= 8;
       case K2_REG_HI: return N <= 7;
+      case K2_REG_HI4: return N <= 6;
       case K2_ROWS32:
       case K2_ROWS64:
       case K2_WAVE:
@@ -237,6 +241,8 @@ struct K2V {
       return (void *)bg_reg_kernel<N, float, 128>;
     else if constexpr (F == K2_REG_HI)
       return (void *)bg_reg_kernel<N, float, 128, hi_blocks>;
+    else if constexpr (F == K2_REG_HI4)
+      return (void *)bg_reg_kernel<N, float, 128, 4>;
     else
       return (void *)bg_loop_kernel<N, 128>;
   }
@@ -286,6 +292,8 @@ struct K2V {
       bg_reg_kernel<N, float, 128><<<grid, 128, smem, s>>>(C, B, partials);
     else if constexpr (F == K2_REG_HI)
       bg_reg_kernel<N, float, 128, hi_blocks><<<grid, 128, smem, s>>>(C, B, partials);
+    else if constexpr (F == K2_REG_HI4)
+      bg_reg_kernel<N, float, 128, 4><<<grid, 128, smem, s>>>(C, B, partials);
     else
       bg_loop_kernel<N, 128><<<grid, 128, smem, s>>>(C, B, partials);
     return cudaGetLastError();
@@ -306,6 +314,9 @@ auto with_form(int f, Fn &&fn) {
     }
     if constexpr (N <= 8) {
       if (f == K2_REAL_HI) return fn(K2V<N, R, K2_REAL_HI>{});
+    }
+    if constexpr (N <= 6) {
+      if (f == K2_REG_HI4) return fn(K2V<N, R, K2_REG_HI4>{});
     }
     if constexpr (N <= 7) {
       if (f == K2_REG_HI) return fn(K2V<N, R, K2_REG_HI>{});

@@ -171,17 +171,23 @@ __device__ __forceinline__ void cuts_observables(const EventParams &P, const flo
 }
 
 // Delta R of every pair (the Delta R cut); returns the smallest Delta R^2.
+// Azimuths once per gluon (m arctangents instead of m(m-1)/2), the pair's
+// Delta phi = |phi_i - phi_j| folded into [0, pi]; each azimuth is within an
+// ulp or two of the exact one, so Delta phi is within ~1e-6 absolute, far
+// inside the FP32 forms' tolerance on cut decisions and R_min.
 template <int M>
 __device__ __forceinline__ float pair_cuts(const EventParams &P, const float (&px)[M], const float (&py)[M],
                                            const float (&eta)[M], int &pass) {
   float dr2min = 1e30f;
+  float phi[M];
+#pragma unroll
+  for (int i = 0; i < M; ++i) phi[i] = atan2f(py[i], px[i]);
 #pragma unroll
   for (int i = 0; i < M; ++i) {
 #pragma unroll
     for (int j = i + 1; j < M; ++j) {
-      const float cross = __fmaf_rn(px[i], py[j], -__fmul_rn(py[i], px[j]));
-      const float dot = __fmaf_rn(px[i], px[j], __fmul_rn(py[i], py[j]));
-      const float dphi = atan2f(fabsf(cross), dot);
+      float dphi = fabsf(__fsub_rn(phi[i], phi[j]));
+      dphi = dphi > 3.14159265358979f ? __fsub_rn(6.28318530717959f, dphi) : dphi;
       const float de = __fsub_rn(eta[i], eta[j]);
       const float dr2 = __fmaf_rn(de, de, __fmul_rn(dphi, dphi));
       dr2min = fminf(dr2min, dr2);
