@@ -320,6 +320,8 @@ int tess_generate_persistent(tess_ctx *ctx, int n_proc, const tess_process *proc
                                 warps per SM where the tables leave room (FP32, n >= 6) */
 #define TESS_K2_REG_HI4 19   /* register form compiled for 4 resident blocks of 128 per SM (128 registers, the
                                 rest spilled; FP32, n <= 6) */
+#define TESS_K2_REG_HI_PF 20 /* TESS_K2_REG_HI with the block's next tile of inputs prefetched into L1 before
+                                each tile (FP32, n <= 7) */
 #define TESS_SCHED_SERIAL 0
 #define TESS_SCHED_OVERLAP 1
 #define TESS_SCHED_OVERLAP_TILES 2

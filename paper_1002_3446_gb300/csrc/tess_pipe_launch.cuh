@@ -130,6 +130,8 @@ inline cudaError_t encode_rows_map(CUtensorMap *map, const float *base, int rows
 //              compiled for 12 resident warps per SM             FP32, n >= 6
 //   K2_REG_HI4 register form compiled for 4 resident blocks (16 warps)
 //              per SM: 128 registers, the rest spilled           FP32, n <= 6
+//   K2_REG_HI_PF  K2_REG_HI with the next tile's inputs prefetched into
+//              L1 before each tile                               FP32, n <= 7
 enum K2Form {
   K2_REG = 0,
   K2_ROWS32 = 1,
@@ -151,7 +153,8 @@ enum K2Form {
   K2_WAVE2PU = 17,
   K2_WAVE2L = 18,
   K2_REG_HI4 = 19,
-  K2_NFORMS = 20
+  K2_REG_HI_PF = 20,
+  K2_NFORMS = 21
 };
 
 // What a call offers the amplitude kernel: CAP_REAL_EPS, its polarisation
@@ -174,7 +177,8 @@ constexpr bool k2_valid(int f, unsigned caps) {
       case K2_REG_TMA: return N <= 8 && !cut_first;
       case K2_REG_TMA_HI: return N <= 7 && !cut_first;
       case K2_REG: return N <= 8;
-      case K2_REG_HI: return N <= 7;
+      case K2_REG_HI:
+      case K2_REG_HI_PF: return N <= 7;
       case K2_REG_HI4: return N <= 6;
       case K2_ROWS32:
       case K2_ROWS64:
@@ -243,6 +247,8 @@ struct K2V {
       return (void *)bg_reg_kernel<N, float, 128, hi_blocks>;
     else if constexpr (F == K2_REG_HI4)
       return (void *)bg_reg_kernel<N, float, 128, 4>;
+    else if constexpr (F == K2_REG_HI_PF)
+      return (void *)bg_reg_kernel<N, float, 128, hi_blocks, true>;
     else
       return (void *)bg_loop_kernel<N, 128>;
   }
@@ -294,6 +300,8 @@ struct K2V {
       bg_reg_kernel<N, float, 128, hi_blocks><<<grid, 128, smem, s>>>(C, B, partials);
     else if constexpr (F == K2_REG_HI4)
       bg_reg_kernel<N, float, 128, 4><<<grid, 128, smem, s>>>(C, B, partials);
+    else if constexpr (F == K2_REG_HI_PF)
+      bg_reg_kernel<N, float, 128, hi_blocks, true><<<grid, 128, smem, s>>>(C, B, partials);
     else
       bg_loop_kernel<N, 128><<<grid, 128, smem, s>>>(C, B, partials);
     return cudaGetLastError();
@@ -319,6 +327,7 @@ auto with_form(int f, Fn &&fn) {
       if (f == K2_REG_HI4) return fn(K2V<N, R, K2_REG_HI4>{});
     }
     if constexpr (N <= 7) {
+      if (f == K2_REG_HI_PF) return fn(K2V<N, R, K2_REG_HI_PF>{});
       if (f == K2_REG_HI) return fn(K2V<N, R, K2_REG_HI>{});
       if (f == K2_REG_TMA_HI) return fn(K2V<N, R, K2_REG_TMA_HI>{});
     }

@@ -1153,9 +1153,26 @@ __device__ __forceinline__ void epi_flush(const EpiSmem<NB> &S, int nb2, Accum<N
   for (int i = threadIdx.x; i < 2 * nb2; i += NB) row[kPartialHead + i] += S.hw[i];
 }
 
+// L1 prefetch of the amplitude inputs and event factors of the event in chunk
+// column jn (one line per row for a warp's 32 consecutive columns), so that
+// the tile after the current one starts from L1 instead of L2.
+template <int L, typename R>
+__device__ __forceinline__ void prefetch_inputs(const ChunkBuf<R> &B, int jn, bool hist) {
+  const R *p = B.in + jn;
+  const size_t cap = (size_t)B.cap;
+#pragma unroll
+  for (int r = 0; r < InRows<L>::rows; ++r) asm volatile("prefetch.global.L1 [%0];" ::"l"(p + r * cap));
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(B.efac + jn));
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(B.wfac + jn));
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(B.pass + jn));
+  if (hist) asm volatile("prefetch.global.L1 [%0];" ::"l"(B.hval + jn));
+}
+
 // K2, register form (FP32, n <= 7): thread per event, the whole current table
-// in registers.
-template <int N, typename R, int NB, int MINB = 1>
+// in registers.  PF: before each tile, the block's next tile is prefetched
+// into L1 (the inputs are read once per event from the L2-resident chunk
+// buffer, and L2 latency was the kernel's long-scoreboard stall).
+template <int N, typename R, int NB, int MINB = 1, bool PF = false>
 __global__ void __launch_bounds__(NB, MINB) bg_reg_kernel(ChunkParams C, ChunkBuf<R> B, double *partials) {
   constexpr int L = N - 1;
   extern __shared__ __align__(16) char smem_raw[];
@@ -1167,6 +1184,10 @@ __global__ void __launch_bounds__(NB, MINB) bg_reg_kernel(ChunkParams C, ChunkBu
   const int ntiles = (count + NB - 1) / NB;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int j = tile * NB + threadIdx.x;
+    if constexpr (PF) {
+      const int jn = j + (int)gridDim.x * NB;  // this thread's column of the block's next tile
+      if (!C.P.cut_first && jn < count) prefetch_inputs<L, R>(B, jn, nb2 > 0);
+    }
     double w = 0.0;
     int bin = -1;
     if (j < count) {

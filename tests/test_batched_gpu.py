@@ -103,7 +103,7 @@ def test_autotune_choice_is_valid_and_consistent(ctx, n, prec):
     acc = torch.zeros(tess.TESS_ACC_LEN, dtype=torch.float64, device="cuda")
     form = tess.tess_autotune(ctx, proc, N, acc, run.workspace)
     valid = {tess.TESS_K2_LOOP} if prec == tess.TESS_FP64 else (
-        ({tess.TESS_K2_REG, tess.TESS_K2_REG_TMA} if n <= 8 else set()) | ({tess.TESS_K2_REG_HI, tess.TESS_K2_REG_TMA_HI} if n <= 7 else set())
+        ({tess.TESS_K2_REG, tess.TESS_K2_REG_TMA} if n <= 8 else set()) | ({tess.TESS_K2_REG_HI, tess.TESS_K2_REG_TMA_HI, tess.TESS_K2_REG_HI_PF} if n <= 7 else set())
         | ({tess.TESS_K2_REG_HI4} if n <= 6 else set())
         | ({tess.TESS_K2_ROWS32, tess.TESS_K2_ROWS64, tess.TESS_K2_WAVE, tess.TESS_K2_WAVE2,
                                                                     tess.TESS_K2_WAVE2U, tess.TESS_K2_WAVE2P,

@@ -351,8 +351,8 @@ def test_random_polarisation_sigma_matches_helicity_sampling(ctx):
 
 
 FORMS_BY_N = {
-    4: ["REG", "REG_HI", "REG_HI4", "REG_TMA", "REG_TMA_HI", "PAIR32", "PAIR64", "PAIR_W"],
-    6: ["REG", "REG_HI", "REG_HI4", "REG_TMA", "REG_TMA_HI", "ROWS32", "ROWS64", "PAIR32", "PAIR64", "PAIR_W", "WAVE",
+    4: ["REG", "REG_HI", "REG_HI4", "REG_HI_PF", "REG_TMA", "REG_TMA_HI", "PAIR32", "PAIR64", "PAIR_W"],
+    6: ["REG", "REG_HI", "REG_HI4", "REG_HI_PF", "REG_TMA", "REG_TMA_HI", "ROWS32", "ROWS64", "PAIR32", "PAIR64", "PAIR_W", "WAVE",
         "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"],
     7: ["WAVE", "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"],
     8: ["REG", "REG_TMA", "ROWS32", "ROWS64", "PAIR32", "PAIR64", "PAIR_W", "WAVE", "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"],
