@@ -289,8 +289,7 @@ def bench_config(torch, tess, ctx, name, flush, steps, peaks, sm_mhz, autotune=T
         proc = make_proc(tess, wl, form)
         run = tess.Run(ctx, proc, ne, per_event=("weight", "me2", "pass"))
         if autotune and wl["hel"] == "sample":
-            tess.tess_autotune(ctx, proc, min(ne, 1 << 24), torch.zeros(tess.TESS_ACC_LEN, dtype=torch.float64,
-                                                                         device="cuda"), run.workspace)
+            tess.tess_autotune(ctx, proc, min(ne, 1 << 25), None, run.workspace, outputs=run.outputs)
         ms = statistics.mean(time_steps(torch, run, 1, 0, steps, 2, flush))
         amp_ms, amp_launches, plan, _ = amp_kernel_time(torch, tess, ctx, proc, run, 1, 0, flush, steps)
         # the exact sum evaluates (n-1)! orderings x 2^(n-1) helicity labellings per event (flipping every
@@ -421,7 +420,7 @@ def run_tess(args):
         probe_acc = torch.zeros(tess.TESS_ACC_LEN, dtype=torch.float64, device="cuda")
         # tuned on the workload itself (candidates within a few per cent of each
         # other change order between a 2^22-event probe and the full size)
-        variant = tess.tess_autotune(ctx, proc, min(N, 1 << 25), probe_acc, run.workspace)
+        variant = tess.tess_autotune(ctx, proc, min(N, 1 << 25), probe_acc, run.workspace, outputs=run.outputs)
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB > L2
     from paper_1002_3446_gb300 import dist as tdist
     first, _ = tdist.event_range(rank, ws, N)
@@ -567,8 +566,7 @@ def run_tess(args):
                 ne = (1 << 16) if prec == "fp64" else (1 << 20)
                 rr = tess.Run(ctx, pp, ne, per_event=("weight",))
                 if not args.no_autotune:
-                    tess.tess_autotune(ctx, pp, ne, torch.zeros(tess.TESS_ACC_LEN, dtype=torch.float64,
-                                                                device="cuda"), rr.workspace)
+                    tess.tess_autotune(ctx, pp, ne, None, rr.workspace, outputs=rr.outputs)
                 ms = time_steps(torch, rr, seed, 0, 2, 1, flush)
                 ev = ne / (min(ms) * 1e-3)
                 info = tess.tess_plan_info(ctx, pp, ne)
@@ -694,7 +692,7 @@ def bench_batched(torch, tess, ctx, flush, steps):
     chosen = {}
     for p, r in zip(procs, runs):
         probe = min(r.n_events, 1 << 21)
-        tess.tess_autotune(ctx, p, probe, acc, r.workspace)
+        tess.tess_autotune(ctx, p, probe, acc, r.workspace, outputs=r.outputs)
         info = tess.tess_plan_info(ctx, p, r.n_events)
         chosen[p.n_gluons] = [info["variant"], info["schedule"]]
     ms = timed(batched)
@@ -733,8 +731,7 @@ def bench_random_pol(torch, tess, ctx, wl, N, seed, first, flush, steps, autotun
     p.flags = flags
     r = tess.Run(ctx, p, N, per_event=("weight", "me2", "pass"))
     if autotune:
-        tess.tess_autotune(ctx, p, min(N, 1 << 22), torch.zeros(tess.TESS_ACC_LEN, dtype=torch.float64,
-                                                                 device="cuda"), r.workspace)
+        tess.tess_autotune(ctx, p, min(N, 1 << 22), None, r.workspace, outputs=r.outputs)
     ms = time_steps(torch, r, seed, first, steps, 2, flush)
     info = tess.tess_plan_info(ctx, p, N)
     serial_of = {tess.TESS_SCHED_OVERLAP: tess.TESS_SCHED_SERIAL,

@@ -166,10 +166,11 @@ void tess_destroy(tess_ctx *ctx);
 
 /* Bytes of device workspace tess_generate needs for this process and event
  * count: per-block partial sums of the accumulation and, for sampled
- * helicities, one L2-sized chunk of per-event amplitude inputs.  0 is never
+ * helicities, one chunk of per-event amplitude inputs (tess_set_chunk_bytes;
+ * two under the overlapped schedules).  0 is never
  * returned for a valid process.  Paper: the events in flight of one sweep
  * (Sec. 2, the number of events per multiprocessor and Table 2); here a
- * chunk sized for the L2 cache plays the sweep's role.  Host-only, no
+ * chunk plays the sweep's role.  Host-only, no
  * errors beyond TESS_E_INVALID / TESS_E_UNSUPPORTED for a bad process. */
 int tess_workspace_size(const tess_ctx *ctx, const tess_process *proc, uint64_t n_events, size_t *bytes);
 
@@ -209,8 +210,8 @@ int tess_stage_times(tess_ctx *ctx, double *ms /* [4] */, int *launches /* [4] *
  * [first_events[i], first_events[i] + n_events[i]) of stream seeds[i] into
  * outs[i] (accumulating into its acc/hist, as tess_generate).  The per-process
  * pipelines are recorded one after another as a single chain of one CUDA
- * graph (each pipeline's chunks are sized to stay resident in L2, so
- * concurrent branches would evict each other's chunk buffers), captured on an
+ * graph (nine concurrent branches measured slower than nine plain launches,
+ * 3.6e9 against 4.2e9 events/s for gg -> 2..10 gluons), captured on an
  * internal stream the first time an argument set is seen and replayed on
  * `stream` after that, so a batch is a single graph launch with no launch
  * gaps.  Capture happens inside this call; do not call it while `stream`
@@ -253,7 +254,7 @@ int tess_generate_persistent(tess_ctx *ctx, int n_proc, const tess_process *proc
  * multiprocessor, Table 1 / Table 2) by measurement before implementing the
  * algorithm; this does the same per (precision, n) on the GPU at hand.
  * Times every amplitude-kernel variant built for (precision, n) of proc on
- * probe_events sampled events (one warm-up, median of three timed runs, with
+ * probe_events sampled events (one warm-up, median of five timed runs, with
  * proc's histogram settings) and makes the fastest the context's choice for
  * later calls with that (precision, polarisation kind, n) -- the kinds being
  * helicity vectors (TESS_HEL_SAMPLE) and random real vectors
@@ -281,8 +282,8 @@ int tess_generate_persistent(tess_ctx *ctx, int n_proc, const tess_process *proc
  * sums can differ in the last bits, since the amplitude grid sets their
  * summation order.
  *
- * Chunk schedules (events are processed in chunks sized to stay in L2, each
- * by a kinematics kernel and an amplitude kernel):
+ * Chunk schedules (events are processed in chunks of tess_set_chunk_bytes,
+ * each by a kinematics kernel and an amplitude kernel):
  *   TESS_SCHED_SERIAL         both kernels of a chunk back to back on
  *                             `stream`; amplitude grid = resident blocks
  *   TESS_SCHED_OVERLAP        kinematics of chunk c+1 on `stream` while the
@@ -329,6 +330,19 @@ int tess_generate_persistent(tess_ctx *ctx, int n_proc, const tess_process *proc
 int tess_autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events, double *acc_scratch,
                   void *workspace, size_t workspace_bytes, void *stream, int *form_out);
 
+/* tess_autotune timed with the per-event outputs the later calls will write:
+ * out is the tess_outputs of those calls (the per-event arrays it names, each
+ * holding at least probe_events entries, device or mapped host memory, are
+ * written with the probe's events; out->acc must be non-NULL and, like
+ * out->hist, is not written, since the timed runs stop before the fold).
+ * Variants differ in how their stores of the per-event arrays overlap the
+ * arithmetic, so a choice tuned without them can lose a few per cent to the
+ * runner-up when they are written.  Errors as tess_autotune, and
+ * TESS_E_INVALID for a NULL out or out->acc. */
+int tess_autotune_outputs(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events,
+                          const tess_outputs *out, void *workspace, size_t workspace_bytes, void *stream,
+                          int *form_out);
+
 /* Sets the variant for (precision, polarisation kind, n) of proc without
  * timing (Sec. 2 running configuration, chosen by the caller): form one of TESS_K2_* (-1: built-in default; a form not built for
  * (precision, n) or, for the real-current forms, for helicity vectors falls
@@ -336,6 +350,21 @@ int tess_autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events
  * Takes effect for later calls; TESS_E_INVALID for values out of range.  A
  * workspace sized by tess_workspace_size covers every choice. */
 int tess_select_variant(tess_ctx *ctx, const tess_process *proc, int form, int schedule);
+
+/* Bytes of per-event intermediate data (amplitude inputs and event factors)
+ * per chunk of the sampled-event pipeline on this context, and per chunk
+ * buffer of the FP32 gradient pipeline (tess_gradients); 0 restores the
+ * defaults (4 GiB and 1 GiB).  Paper: the events in flight of one sweep (Sec. 2); here
+ * the chunk is a trade between workspace and per-launch cost: every chunk
+ * costs a kinematics and an amplitude launch, each with a ramp-up and a tail
+ * of about one block's run time, so on GB300 fewer, larger chunks are faster
+ * (measured at n = 6: 64 MB chunks 3.6e9 events/s, 1 GB 4.7e9, one 3.8 GB
+ * chunk 4.9e9).  Takes effect for later calls (workspace sizes included:
+ * tess_workspace_size and tess_gradients_workspace_size reflect it), and the
+ * next tess_generate_batched call
+ * recaptures its graph.  TESS_E_INVALID for a NULL ctx or a nonzero size
+ * below 1 MiB.  Host-only. */
+int tess_set_chunk_bytes(tess_ctx *ctx, size_t bytes);
 
 /* What a call with (proc, n_events) would run (Sec. 2 running configuration):
  * info[0] amplitude variant

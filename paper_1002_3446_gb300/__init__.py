@@ -45,7 +45,8 @@ EXPORTED = ["tess_version", "tess_last_error", "tess_init", "tess_destroy", "tes
             "tess_kernel_launches", "tess_workspace_size_batched", "tess_generate_batched", "tess_autotune",
             "tess_stage_timing", "tess_stage_times", "tess_draws", "tess_gradients", "tess_select_variant",
             "tess_plan_info", "tess_gradients_workspace_size", "tess_gauge_ratio", "tess_peak_flops",
-            "tess_workspace_size_persistent", "tess_generate_persistent"]
+            "tess_workspace_size_persistent", "tess_generate_persistent", "tess_autotune_outputs",
+            "tess_set_chunk_bytes"]
 
 
 class TessError(RuntimeError):
@@ -109,8 +110,11 @@ def _load():
         lib.tess_generate_persistent.argtypes = [vp, i32, P(tess_process), P(u64), P(u64), P(u64), P(tess_outputs),
                                                  vp, ctypes.c_size_t, vp]
         lib.tess_autotune.argtypes = [vp, P(tess_process), u64, vp, vp, ctypes.c_size_t, vp, P(ctypes.c_int)]
+        lib.tess_autotune_outputs.argtypes = [vp, P(tess_process), u64, P(tess_outputs), vp, ctypes.c_size_t, vp,
+                                              P(ctypes.c_int)]
         lib.tess_stage_timing.argtypes = [vp, i32]
         lib.tess_select_variant.argtypes = [vp, P(tess_process), i32, i32]
+        lib.tess_set_chunk_bytes.argtypes = [vp, ctypes.c_size_t]
         lib.tess_plan_info.argtypes = [vp, P(tess_process), u64, P(ctypes.c_int)]
         lib.tess_draws.argtypes = [vp, i32, u64, u64, u64, vp, vp, vp, vp]
         lib.tess_gradients.argtypes = [vp, P(tess_process), u64, vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t,
@@ -224,16 +228,29 @@ def tess_generate_persistent(ctx, procs, seeds, first_events, n_events, outputs,
                                             _ptr(workspace), nbytes, _stream(stream)))
 
 
-def tess_autotune(ctx, proc, probe_events, acc_scratch, workspace, stream=None):
+def tess_autotune(ctx, proc, probe_events, acc_scratch, workspace, stream=None, outputs=None):
+    """Times every amplitude variant and schedule on probe_events events and keeps the fastest.
+    With `outputs` (a tess_outputs, e.g. Run.outputs, per-event arrays of at least probe_events
+    entries) the timed runs write those per-event arrays as the later calls will
+    (tess_autotune_outputs); acc_scratch is then unused."""
     f = ctypes.c_int()
     nbytes = workspace.numel() * workspace.element_size()
-    _check(_load().tess_autotune(ctx, ctypes.byref(proc), int(probe_events), _ptr(acc_scratch), _ptr(workspace),
-                                 nbytes, _stream(stream), ctypes.byref(f)))
+    if outputs is not None:
+        _check(_load().tess_autotune_outputs(ctx, ctypes.byref(proc), int(probe_events), ctypes.byref(outputs),
+                                             _ptr(workspace), nbytes, _stream(stream), ctypes.byref(f)))
+    else:
+        _check(_load().tess_autotune(ctx, ctypes.byref(proc), int(probe_events), _ptr(acc_scratch),
+                                     _ptr(workspace), nbytes, _stream(stream), ctypes.byref(f)))
     return f.value
 
 
 def tess_select_variant(ctx, proc, form=-1, schedule=-1):
     _check(_load().tess_select_variant(ctx, ctypes.byref(proc), int(form), int(schedule)))
+
+
+def tess_set_chunk_bytes(ctx, nbytes):
+    """Bytes of per-event intermediate data per chunk of the sampled-event pipeline (0: default, 4 GiB)."""
+    _check(_load().tess_set_chunk_bytes(ctx, int(nbytes)))
 
 
 def tess_plan_info(ctx, proc, n_events):

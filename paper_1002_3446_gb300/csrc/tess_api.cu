@@ -35,9 +35,9 @@ cudaError_t launch_grad_b(int n, bool fp64, const GradParams &G, void *ws, cudaS
                            const GradStreams &gs);
 cudaError_t launch_grad_c(int n, bool fp64, const GradParams &G, void *ws, cudaStream_t s,
                            const GradStreams &gs);
-size_t grad_workspace_a(int n, uint64_t n_events);
-size_t grad_workspace_b(int n, uint64_t n_events);
-size_t grad_workspace_c(int n, uint64_t n_events);
+size_t grad_workspace_a(int n, uint64_t n_events, size_t chunk_bytes);
+size_t grad_workspace_b(int n, uint64_t n_events, size_t chunk_bytes);
+size_t grad_workspace_c(int n, uint64_t n_events, size_t chunk_bytes);
 cudaError_t launch_draws_a(int n, const EventParams &P, double *u, uint32_t *hel, uint8_t *order, cudaStream_t s);
 cudaError_t launch_draws_b(int n, const EventParams &P, double *u, uint32_t *hel, uint8_t *order, cudaStream_t s);
 cudaError_t launch_draws_c(int n, const EventParams &P, double *u, uint32_t *hel, uint8_t *order, cudaStream_t s);
@@ -165,7 +165,9 @@ struct tess_ctx {
   // schedule): planning queries the runtime (function attributes, occupancy)
   // for every candidate kernel, and sizing a workspace plans every variant
   mutable std::mutex plan_mu;
-  mutable std::map<std::array<int64_t, 8>, tess::PipePlan> plans;
+  mutable std::map<std::array<int64_t, 9>, tess::PipePlan> plans;
+  // bytes of per-event intermediate data per generation chunk (0 = default)
+  size_t chunk_bytes = 0;
   // opt-in stage timing: event pairs recorded around each launch
   bool timing = false;
   std::vector<cudaEvent_t> ev_free;
@@ -324,8 +326,8 @@ int variant_slot(const tess_process *p) {
 int plan_with_form(const tess_ctx *ctx, const tess_process *p, uint64_t n_events, int form, int sched,
                    tess::PipePlan *pl) {
   const int n = p->n_gluons;
-  const std::array<int64_t, 8> key = {n, p->precision, p->helicity_mode == TESS_POL_RANDOM, p->flags, p->hist_bins,
-                                      (int64_t)n_events, form, sched};
+  const std::array<int64_t, 9> key = {n,    p->precision, p->helicity_mode == TESS_POL_RANDOM, p->flags,
+                                      p->hist_bins, (int64_t)n_events, form, sched, (int64_t)ctx->chunk_bytes};
   {
     std::lock_guard<std::mutex> lock(ctx->plan_mu);
     const auto it = ctx->plans.find(key);
@@ -338,6 +340,8 @@ int plan_with_form(const tess_ctx *ctx, const tess_process *p, uint64_t n_events
                         ((p->flags & TESS_FLAG_CUT_FIRST) ? tess::CAP_CUT_FIRST : 0u) |
                         ((p->flags & TESS_FLAG_PDF_GRID) ? tess::CAP_PDF_GRID : 0u);
   int rc;
+  *pl = tess::PipePlan();
+  pl->chunk_target = ctx->chunk_bytes;
   if (p->precision == TESS_FP64)
     rc = tess::plan_pipeline_f64(n, ctx->sm_count, n_events, p->hist_bins, form, sched, caps, pl);
   else if (n <= 7)
@@ -773,11 +777,10 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
       tess::OverlapRes *ov = nullptr;
       if (prs[i].pipeline && prs[i].pl.overlap && (rc = overlap_res(ctx, 1 + i, &ov))) return rc;
     }
-    // the processes one after another in a single chain: each pipeline's
-    // chunks are sized to stay resident in L2, so concurrent branches would
-    // evict each other's chunk buffers (measured slower than sequential
-    // launches); the graph removes the launch gaps, and a process with an
-    // overlapped schedule keeps its own second stream inside the chain
+    // the processes one after another in a single chain (concurrent branches
+    // measured slower than sequential launches); the graph removes the launch
+    // gaps, and a process with an overlapped schedule keeps its own second
+    // stream inside the chain
     cudaGraph_t graph = nullptr;
     if ((e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
       return cuda_fail(e, "cudaStreamBeginCapture");
@@ -810,6 +813,16 @@ int tess_generate_batched(tess_ctx *ctx, int n_proc, const tess_process *procs, 
   }
   if ((e = cudaGraphLaunch(ctx->graph_exec, (cudaStream_t)stream)) != cudaSuccess)
     return cuda_fail(e, "cudaGraphLaunch");
+  return ok();
+}
+
+int tess_set_chunk_bytes(tess_ctx *ctx, size_t bytes) {
+  if (!ctx) return fail(TESS_E_INVALID, "ctx is NULL");
+  if (bytes != 0 && bytes < ((size_t)1 << 20))
+    return fail(TESS_E_INVALID, "chunk size %zu bytes is below 1 MiB", bytes);
+  std::lock_guard<std::mutex> lock(ctx->plan_mu);
+  ctx->chunk_bytes = bytes;
+  ctx->graph_key.clear();  // the batched graph's pipelines were planned with the old size
   return ok();
 }
 
@@ -850,11 +863,32 @@ int tess_plan_info(const tess_ctx *ctx, const tess_process *proc, uint64_t n_eve
   return ok();
 }
 
-constexpr int kTuneReps = 3;  // timed runs per candidate (median)
+constexpr int kTuneReps = 5;  // timed runs per candidate (median)
+
+static int autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events, const tess_outputs &out,
+                    void *workspace, size_t workspace_bytes, void *stream, int *form_out);
 
 int tess_autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events, double *acc_scratch,
                   void *workspace, size_t workspace_bytes, void *stream, int *form_out) {
   if (!ctx || !proc || !acc_scratch || !form_out) return fail(TESS_E_INVALID, "NULL argument");
+  tess_outputs out;
+  memset(&out, 0, sizeof out);
+  out.acc = acc_scratch;
+  out.hist = acc_scratch;  // never written: no fold
+  return autotune(ctx, proc, probe_events, out, workspace, workspace_bytes, stream, form_out);
+}
+
+int tess_autotune_outputs(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events,
+                          const tess_outputs *out, void *workspace, size_t workspace_bytes, void *stream,
+                          int *form_out) {
+  if (!ctx || !proc || !out || !out->acc || !form_out) return fail(TESS_E_INVALID, "NULL argument");
+  tess_outputs o = *out;
+  if (!o.hist) o.hist = o.acc;  // never written: no fold
+  return autotune(ctx, proc, probe_events, o, workspace, workspace_bytes, stream, form_out);
+}
+
+static int autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events, const tess_outputs &out,
+                    void *workspace, size_t workspace_bytes, void *stream, int *form_out) {
   int rc = check_process(proc);
   if (rc) return rc;
   if (probe_events == 0) return fail(TESS_E_INVALID, "probe_events must be > 0");
@@ -868,12 +902,7 @@ int tess_autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
   // timed with the process's own histogram settings (the epilogue cost
   // differs between variants); the runs stop before the final fold, so
-  // nothing is written through `out` beyond the per-event outputs, which are
-  // not requested
-  tess_outputs out;
-  memset(&out, 0, sizeof out);
-  out.acc = acc_scratch;
-  out.hist = acc_scratch;  // never written: no fold
+  // nothing is written through `out` beyond the per-event outputs it names
   const tess_process pp = *proc;
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t a = nullptr, b = nullptr;
@@ -970,8 +999,9 @@ int tess_gradients_workspace_size(const tess_ctx *ctx, const tess_process *proc,
   if (proc->precision == TESS_FP64) {
     *bytes = 0;
   } else {
-    *bytes = n <= 8 ? tess::grad_workspace_a(n, n_events)
-                    : (n <= 10 ? tess::grad_workspace_b(n, n_events) : tess::grad_workspace_c(n, n_events));
+    const size_t cb = ctx->chunk_bytes;
+    *bytes = n <= 8 ? tess::grad_workspace_a(n, n_events, cb)
+                    : (n <= 10 ? tess::grad_workspace_b(n, n_events, cb) : tess::grad_workspace_c(n, n_events, cb));
   }
   return ok();
 }
@@ -1008,6 +1038,7 @@ int tess_gradients(tess_ctx *ctx, const tess_process *proc, uint64_t n_events, c
   G.dw_dk = dw_dk;
   G.dw_dlnmu = dw_dlnmu;
   G.n_events = n_events;
+  G.chunk_bytes = ctx->chunk_bytes;
   const int n = proc->n_gluons;
   const bool fp64 = proc->precision == TESS_FP64;
   size_t need = 0;

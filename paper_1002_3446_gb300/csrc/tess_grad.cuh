@@ -25,6 +25,7 @@ struct GradParams {
   double *w, *dw_du, *dw_dk, *dw_dlnmu;
   const double *dL_dw;  // optional upstream gradient
   uint64_t n_events;
+  size_t chunk_bytes;  // bytes per chunk buffer of the FP32 split pipeline (0 = default)
 };
 
 // Streams and events of the overlapped split pipeline of the FP32 forms

@@ -15,13 +15,13 @@ cudaError_t launch_grad_a(int n, bool fp64, const GradParams &G, void *ws, cudaS
   }
 }
 
-size_t grad_workspace_a(int n, uint64_t n_events) {
+size_t grad_workspace_a(int n, uint64_t n_events, size_t chunk_bytes) {
   switch (n) {
-    case 4: return grad_workspace_bytes<4>(n_events);
-    case 5: return grad_workspace_bytes<5>(n_events);
-    case 6: return grad_workspace_bytes<6>(n_events);
-    case 7: return grad_workspace_bytes<7>(n_events);
-    case 8: return grad_workspace_bytes<8>(n_events);
+    case 4: return grad_workspace_bytes<4>(n_events, chunk_bytes);
+    case 5: return grad_workspace_bytes<5>(n_events, chunk_bytes);
+    case 6: return grad_workspace_bytes<6>(n_events, chunk_bytes);
+    case 7: return grad_workspace_bytes<7>(n_events, chunk_bytes);
+    case 8: return grad_workspace_bytes<8>(n_events, chunk_bytes);
     default: return 0;
   }
 }

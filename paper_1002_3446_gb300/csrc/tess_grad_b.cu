@@ -12,10 +12,10 @@ cudaError_t launch_grad_b(int n, bool fp64, const GradParams &G, void *ws, cudaS
   }
 }
 
-size_t grad_workspace_b(int n, uint64_t n_events) {
+size_t grad_workspace_b(int n, uint64_t n_events, size_t chunk_bytes) {
   switch (n) {
-    case 9: return grad_workspace_bytes<9>(n_events);
-    case 10: return grad_workspace_bytes<10>(n_events);
+    case 9: return grad_workspace_bytes<9>(n_events, chunk_bytes);
+    case 10: return grad_workspace_bytes<10>(n_events, chunk_bytes);
     default: return 0;
   }
 }

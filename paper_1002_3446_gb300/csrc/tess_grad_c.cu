@@ -12,10 +12,10 @@ cudaError_t launch_grad_c(int n, bool fp64, const GradParams &G, void *ws, cudaS
   }
 }
 
-size_t grad_workspace_c(int n, uint64_t n_events) {
+size_t grad_workspace_c(int n, uint64_t n_events, size_t chunk_bytes) {
   switch (n) {
-    case 11: return grad_workspace_bytes<11>(n_events);
-    case 12: return grad_workspace_bytes<12>(n_events);
+    case 11: return grad_workspace_bytes<11>(n_events, chunk_bytes);
+    case 12: return grad_workspace_bytes<12>(n_events, chunk_bytes);
     default: return 0;
   }
 }

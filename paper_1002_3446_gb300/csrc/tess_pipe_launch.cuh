@@ -20,6 +20,7 @@ struct PipePlan {
   int block = 128;   // events per K2 tile (= threads per block except the lane-pair forms)
   size_t smem = 0;   // K2 dynamic shared memory
   int cap = 128;     // events per chunk
+  size_t chunk_target = 0;  // input to planning: bytes per chunk (0 = kChunkTargetBytes)
   int chunks = 1;
   size_t off_in = 0, off_efac = 0, off_wfac = 0, off_hval = 0, off_pass = 0;
   size_t off_col = 0, off_orig = 0, off_tcount = 0, off_toff = 0, off_dcount = 0;  // cut-first only
@@ -51,7 +52,20 @@ struct OverlapRes {
   cudaEvent_t k1done[2] = {nullptr, nullptr}, k2done[2] = {nullptr, nullptr};
 };
 
-constexpr size_t kChunkTargetBytes = 64ull << 20;  // stays resident in the 129 MB L2
+// Default bytes of per-event intermediate data (amplitude inputs and event
+// factors) per chunk.  Measured on GB300 at n = 6 (2^24 events, serial
+// schedule): 64 MB chunks 3.57e9 events/s, 256 MB 4.28e9, 1 GB 4.69e9, one
+// 3.8 GB chunk 4.86e9.  Each launch pays a ramp-up and a tail of about one
+// block's run time (~30 us for the kinematics kernel), which small chunks
+// multiply; an L2-sized chunk does not stay in L2 between the two kernels
+// anyway (live L2 hit rate of the amplitude kernel's reads 26-35 % even at
+// 16 MB), and streaming it through HBM costs the ALU-bound kernels nothing
+// measurable.  4 GB bounds the workspace (two such buffers under an
+// overlapped schedule) and keeps the per-chunk cost near 1 %.
+#ifndef TESS_CHUNK_TARGET_MB
+#define TESS_CHUNK_TARGET_MB 4096
+#endif
+constexpr size_t kChunkTargetBytes = (size_t)TESS_CHUNK_TARGET_MB << 20;
 
 // plan_pipeline_t result: 0, a cudaError_t of a failed attribute / occupancy
 // call, or this code when no block of the variant fits on an SM
@@ -391,7 +405,17 @@ int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, in
   const bool cut_first = (caps & CAP_CUT_FIRST) != 0;
   const uint64_t per_event =
       (uint64_t)InRows<L>::rows * sizeof(R) + 3 * sizeof(double) + 1 + (cut_first ? 2 * sizeof(int) : 0);
-  const uint64_t target = std::max<uint64_t>(128, (kChunkTargetBytes / per_event) / 128 * 128);
+  const uint64_t chunk_bytes = pl->chunk_target ? pl->chunk_target : kChunkTargetBytes;
+  // events per chunk: a multiple of 128 below 2^31 (chunk columns are ints)
+  uint64_t target = std::min<uint64_t>(std::max<uint64_t>(128, (chunk_bytes / per_event) / 128 * 128),
+                                       (uint64_t)INT32_MAX / 256 * 128);
+  // A whole number of amplitude-grid waves per chunk: the chunk's tiles are
+  // spread over the resident blocks, and a last wave with few tiles leaves
+  // most SMs idle for one tile's time (measured at n = 6: 2330 tiles on 456
+  // resident blocks ran as six waves, the sixth 2 % full, about 15 % of the
+  // amplitude kernel's time).  Cut-first chunks have a data-dependent count.
+  const uint64_t wave = (uint64_t)sm_count * (uint64_t)per_sm * (uint64_t)pl->block;
+  if (!cut_first && target >= wave) target = std::max<uint64_t>(128, target / wave * wave / 128 * 128);
   const uint64_t want = (std::max<uint64_t>(n_events, 1) + 127) / 128 * 128;
   pl->cap = (int)std::min(target, want);
   pl->chunks = (int)((std::max<uint64_t>(n_events, 1) + pl->cap - 1) / pl->cap);

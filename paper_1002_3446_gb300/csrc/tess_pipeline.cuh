@@ -4,7 +4,8 @@
 //       Berends-Giele inputs of a chunk of events to workspace (SoA).
 //   K2 (bg_*_kernel): Berends-Giele amplitude of every event of the chunk ->
 //       |A|^2 estimator, weight -> per-block partial sums (deterministic).
-// The chunk is sized to stay resident in L2 between the two launches.
+// The chunk buffer is streamed through HBM between the two launches (its
+// size is the caller's trade between workspace and per-launch cost).
 //
 // Precision: with R = double every step is FP64 (the plain FP64 form).  With
 // R = float (FP32 currents) the Rambo seeds, cuts, observables, alpha_s and
@@ -1170,8 +1171,8 @@ __device__ __forceinline__ void prefetch_inputs(const ChunkBuf<R> &B, int jn, bo
 
 // K2, register form (FP32, n <= 7): thread per event, the whole current table
 // in registers.  PF: before each tile, the block's next tile is prefetched
-// into L1 (the inputs are read once per event from the L2-resident chunk
-// buffer, and L2 latency was the kernel's long-scoreboard stall).
+// into L1 (the inputs are read once per event from the chunk buffer, and
+// memory latency was the kernel's long-scoreboard stall).
 template <int N, typename R, int NB, int MINB = 1, bool PF = false>
 __global__ void __launch_bounds__(NB, MINB) bg_reg_kernel(ChunkParams C, ChunkBuf<R> B, double *partials) {
   constexpr int L = N - 1;

@@ -352,6 +352,36 @@ __host__ __device__ constexpr size_t wave_lean_smem_per_event() {
   return wave_smem_per_event<L>() + (size_t)(L - 1) * sizeof(float2);
 }
 
+// The block's next tile of amplitude inputs (NE consecutive chunk columns, one
+// 128-byte line per input row when NE = 32) and event factors into L2 while
+// the current tile is computed: the chunk buffer is read once, mostly from
+// DRAM, so every tile otherwise starts with a DRAM-latency wait.  Columns
+// past the chunk's count are inside the buffer (its capacity is a multiple of
+// 128 columns), so no prefetch leaves it.  Not for cut-first chunks, whose
+// tiles are gathered through a column list.  Used by the packed-pair forms
+// (measured at n = 10 / 12: +4 / +5 %); the scalar wavefront forms measured
+// 2-4 % slower with it (n = 10, 11) and do without.
+template <int L, int NE, int NT>
+__device__ __forceinline__ void wave_prefetch_next(const ChunkParams &C, const ChunkBuf<float> &B, int tile,
+                                                   int ntiles) {
+  const int nt = tile + (int)gridDim.x;
+  if (C.P.cut_first || nt >= ntiles) return;
+  static_assert(NE % 32 == 0, "whole 128-byte lines per input row");
+  const size_t col = (size_t)nt * NE;
+  const size_t cap = (size_t)B.cap;
+  constexpr int R = InRows<L>::rows, LF = NE / 32, LD = NE / 16;  // lines per float row, per double row
+  for (int i = threadIdx.x; i < R * LF + 2 * LD; i += NT) {
+    const char *p;
+    if (i < R * LF)
+      p = (const char *)(B.in + (size_t)(i / LF) * cap + col) + (i % LF) * 128;
+    else {
+      const int k = i - R * LF;
+      p = (const char *)((k < LD ? B.efac : B.wfac) + col) + (k % LD) * 128;
+    }
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+  }
+}
+
 template <int N, int NE, int G, bool UNR = false, bool LEAN = false, int MINB = 1>
 __global__ void __launch_bounds__(NE * G, MINB) bg_wave_kernel(ChunkParams C, ChunkBuf<float> B, double *partials) {
   static_assert(G == 1 || G == 2, "one or two lanes per event");

@@ -235,6 +235,7 @@ __global__ void __launch_bounds__(NE * G) bg_wavep_kernel(ChunkParams C, ChunkBu
       }
     }
     if (G > 1) __syncwarp();
+    wave_prefetch_next<L, NE, NT>(C, B, tile, ntiles);
     const Cx<float> amp = bg_wavep<L, NE, G, UNR>(K4, J4, S2, slot, g, B.in + (size_t)InRows<L>::eps(0) * cap + e,
                                                   B.in + (size_t)InRows<L>::eps0 * cap + e, cap);
     double w = 0.0;

@@ -127,3 +127,43 @@ def test_autotune_choice_is_valid_and_consistent(ctx, n, prec):
 def _host_generate(run):
     run.generate(7, 0)
     return _host(run)
+
+
+def test_autotune_with_outputs_writes_only_the_per_event_arrays(ctx):
+    """tess_autotune_outputs times the variants with the caller's per-event arrays
+    written: they hold the probe's events afterwards (the event values do not depend
+    on the variant beyond FP32 summation order), acc and hist stay untouched, and the
+    choice is a form built for (precision, n)."""
+    proc = tess.process(6, precision=tess.TESS_FP32_DS, hist_bins=10, hist_observable=tess.TESS_OBS_HT,
+                        hist_lo=100.0, hist_hi=1100.0)
+    N = 1 << 17
+    run = tess.Run(ctx, proc, N)
+    ref = _host_generate(run)
+    run.reset()
+    for k in ("weight", "me2"):
+        run.t[k].fill_(-1.0)
+    run.t["pass"].fill_(7)
+    form = tess.tess_autotune(ctx, proc, N // 2, None, run.workspace, outputs=run.outputs)
+    torch.cuda.synchronize()
+    assert form in {tess.TESS_K2_REG, tess.TESS_K2_REG_TMA, tess.TESS_K2_REG_HI, tess.TESS_K2_REG_TMA_HI,
+                    tess.TESS_K2_REG_HI_PF, tess.TESS_K2_REG_HI4, tess.TESS_K2_ROWS32, tess.TESS_K2_ROWS64,
+                    tess.TESS_K2_WAVE, tess.TESS_K2_WAVE2, tess.TESS_K2_WAVE2U, tess.TESS_K2_WAVE2P,
+                    tess.TESS_K2_WAVE2PU, tess.TESS_K2_WAVE2L, tess.TESS_K2_PAIR32, tess.TESS_K2_PAIR64,
+                    tess.TESS_K2_PAIR_W}
+    assert float(run.acc.abs().sum()) == 0.0 and float(run.hist.abs().sum()) == 0.0
+    got = _host(run)
+    # the probe draws events [0, N/2) of seed 1
+    probe = tess.Run(ctx, proc, N // 2)
+    probe.generate(1, 0)
+    want = _host(probe)
+    h = N // 2
+    assert np.array_equal(got["pass"][:h], want["pass"])
+    assert np.all(got["pass"][h:] == 7) and np.all(got["weight"][h:] == -1.0)
+    ok = want["me2"] > 1e-6 * np.median(want["me2"][want["me2"] > 0])
+    rel = np.abs(got["me2"][:h][ok] - want["me2"][ok]) / want["me2"][ok]
+    assert np.median(rel) < 1e-5
+    assert ref["weight"].shape == got["weight"].shape
+    bad = tess.make_outputs(run.t["weight"], None, None, None, None, None, None, None)
+    with pytest.raises(tess.TessError) as e:
+        tess.tess_autotune(ctx, proc, 1024, None, run.workspace, outputs=bad)
+    assert e.value.code == tess.TESS_E_INVALID

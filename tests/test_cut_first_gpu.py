@@ -20,6 +20,8 @@ import paper_1002_3446_gb300 as tess  # noqa: E402
 def ctx():
     assert torch.cuda.is_available()
     c = tess.tess_init(0)
+    # 16 MB chunks: the cases span several chunks with a ragged last one
+    tess.tess_set_chunk_bytes(c, 16 << 20)
     yield c
     tess.tess_destroy(c)
 

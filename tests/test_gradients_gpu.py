@@ -166,9 +166,17 @@ def test_chunk_boundaries_do_not_change_results(ctx, n):
     E = 300_017
     u, hel, order = tess.tess_draws(ctx, n, 13, 0, E)
     proc = tess.process(n, precision=tess.TESS_FP32_CURRENTS)
-    full = tess.tess_gradients(ctx, proc, u, hel, order)
-    need = tess.tess_gradients_workspace_size(ctx, proc, E)
-    assert need > 0 and need < 80 << 20  # chunked, not sized for every event
+    one = tess.tess_gradients(ctx, proc, u, hel, order)  # default chunk: every event in one
+    tess.tess_set_chunk_bytes(ctx, 16 << 20)
+    try:
+        full = tess.tess_gradients(ctx, proc, u, hel, order)
+        need = tess.tess_gradients_workspace_size(ctx, proc, E)
+    finally:
+        tess.tess_set_chunk_bytes(ctx, 0)
+    assert need > 0 and need < 40 << 20  # two 16 MB chunk buffers, not sized for every event
+    assert tess.tess_gradients_workspace_size(ctx, proc, E) > need
+    for key in ("w", "dw_du", "dw_dk", "dw_dlnmu"):
+        assert torch.equal(full[key], one[key]), key
     for lo in (0, 65_000, 121_000, 190_000, E - 700):
         hi = min(lo + 2_000, E)
         part = tess.tess_gradients(ctx, proc, u[lo:hi].contiguous(), hel[lo:hi].contiguous(),

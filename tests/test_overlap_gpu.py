@@ -22,6 +22,8 @@ import paper_1002_3446_gb300 as tess  # noqa: E402
 def ctx():
     assert torch.cuda.is_available()
     c = tess.tess_init(0)
+    # 16 MB chunks: the cases span several chunks with a ragged last one
+    tess.tess_set_chunk_bytes(c, 16 << 20)
     yield c
     tess.tess_destroy(c)
 
@@ -155,3 +157,49 @@ def test_select_variant_rejects_out_of_range(ctx):
         with pytest.raises(tess.TessError) as e:
             tess.tess_select_variant(ctx, proc, form, ov)
         assert e.value.code == tess.TESS_E_INVALID
+
+
+def test_chunk_size_changes_no_event_and_resizes_the_workspace(ctx):
+    """tess_set_chunk_bytes: every event's arithmetic is independent of the chunk
+    it lands in, so per-event outputs are bit-identical across chunk sizes and
+    the sums agree to rounding (the block partial sums regroup); the workspace
+    follows the setting; the batched graph is recaptured after a change; sizes
+    below 1 MiB are refused."""
+    proc = tess.process(7, precision=tess.TESS_FP32_DS, hist_bins=16, hist_observable=tess.TESS_OBS_HT,
+                        hist_lo=100.0, hist_hi=1700.0)
+    N = 300_007
+    res, ws = {}, {}
+    try:
+        for mb in (1, 16, 0):
+            tess.tess_set_chunk_bytes(ctx, mb << 20)
+            info = tess.tess_plan_info(ctx, proc, N)
+            ws[mb] = tess.tess_workspace_size(ctx, proc, N)
+            run = tess.Run(ctx, proc, N)
+            run.generate(9, 77)
+            res[mb] = (_host(run), run.result(), info["chunks"])
+        assert res[1][2] > res[16][2] > res[0][2] == 1
+        assert ws[1] < ws[16] < ws[0]
+        for mb in (16, 0):
+            for k in ("weight", "me2", "pass", "ht"):
+                assert np.array_equal(res[mb][0][k], res[1][0][k]), (mb, k)
+            assert res[mb][1][2:] == res[1][1][2:]
+            assert np.isclose(res[mb][1][0], res[1][1][0], rtol=1e-12)
+            assert np.allclose(res[mb][0]["hist"], res[1][0]["hist"], rtol=1e-12, atol=0)
+        # the batched graph follows the setting (recaptured, same events)
+        procs, counts = [proc], [N]
+        outs = []
+        for mb in (1, 0):
+            tess.tess_set_chunk_bytes(ctx, mb << 20)
+            r = tess.Run(ctx, proc, N)
+            nb = tess.tess_workspace_size_batched(ctx, procs, counts)
+            w = torch.empty((nb + 7) // 8, dtype=torch.float64, device="cuda")
+            tess.tess_generate_batched(ctx, procs, [9], [77], counts, [r.outputs], w)
+            outs.append(_host(r))
+        assert np.array_equal(outs[0]["weight"], res[1][0]["weight"])
+        assert np.array_equal(outs[1]["weight"], res[0][0]["weight"])
+        for bad in (1, 4096, (1 << 20) - 1):
+            with pytest.raises(tess.TessError) as e:
+                tess.tess_set_chunk_bytes(ctx, bad)
+            assert e.value.code == tess.TESS_E_INVALID
+    finally:
+        tess.tess_set_chunk_bytes(ctx, 16 << 20)

@@ -515,10 +515,14 @@ def test_fp64_multichunk_parity(ctx, orc, n, N, pt):
     import draws_np
     p = tess.process(n, precision=tess.TESS_FP64, pt_min=pt, hist_bins=40, hist_observable=tess.TESS_OBS_HT,
                      hist_lo=200.0, hist_hi=3000.0)
-    info = tess.tess_plan_info(ctx, p, N)
-    assert info["chunks"] >= 8, info
-    seed = 21
-    g = gpu_generate(ctx, p, seed, 0, N)
+    tess.tess_set_chunk_bytes(ctx, 64 << 20)  # many chunks at a size the oracle covers in seconds
+    try:
+        info = tess.tess_plan_info(ctx, p, N)
+        assert info["chunks"] >= 8, info
+        seed = 21
+        g = gpu_generate(ctx, p, seed, 0, N)
+    finally:
+        tess.tess_set_chunk_bytes(ctx, 0)
     op = orc_proc(orc, p)
     r = orc.generate(op, seed, 0, N)
     # sigma and histogram against the oracle over all events
