@@ -53,6 +53,8 @@ def parse():
                     help="skip the gg->2g (2^20, FP64 exact sum) and gg->8g (2^26) configuration legs")
     ap.add_argument("--no-peaks", action="store_true", help="skip the FMA peak probes (nominal peak instead)")
     ap.add_argument("--events", type=int, default=0, help="override events per GPU (small cases for profiling)")
+    ap.add_argument("--chunk-mb", type=int, default=0,
+                    help="chunk size of the generation pipeline in MiB (tess_set_chunk_bytes; 0: the library default)")
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-multiplicity batched measurement")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
     ap.add_argument("--grad-only", action="store_true",
@@ -407,6 +409,8 @@ def run_tess(args):
     rp = args.pol == "random" and wl["hel"] == "sample"
     flops_per_event = tess.bg_flops_real(n) if rp else tess.bg_flops(n)
     ctx = tess.tess_init(local)
+    if args.chunk_mb:
+        tess.tess_set_chunk_bytes(ctx, args.chunk_mb << 20)
     proc = make_proc(tess, wl, random_pol=rp)
     cf = args.cut_first and wl["hel"] == "sample" and wl["precision"] in ("fp32", "ds")
     if cf:
@@ -610,7 +614,8 @@ def run_tess(args):
                       "fp64": "f64"}[wl["precision"]],
             "data": "synthetic (counter-based Philox draws, toy gluon PDF)",
             "config": dict(workload_config(args.workload, wl, N, rp, cf),
-                           l2="flushed between timed steps (256 MB write)"),
+                           l2="flushed between timed steps (256 MB write)",
+                           chunk_mb=args.chunk_mb or "library default (4096)"),
             "roofline": {"bound": "alu", "kernel": "Berends-Giele amplitude kernel", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_source": ((f"measured in this run: {kind.upper()} FMA probe (tess_peak_flops), "
