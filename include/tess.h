@@ -261,8 +261,8 @@ int tess_generate_persistent(tess_ctx *ctx, int n_proc, const tess_process *proc
  * (TESS_POL_RANDOM); the choice ignores the histogram settings, so tune with
  * the ones the calls will use.  Choose
  * probe_events to span several chunks (a few million events) so that the
- * overlapped schedules can show their gain.  Variants (all one thread per
- * event): TESS_K2_REG (current table in registers), TESS_K2_ROWS32 /
+ * overlapped schedules can show their gain.  Variants (one thread per event
+ * unless noted): TESS_K2_REG (current table in registers), TESS_K2_ROWS32 /
  * TESS_K2_ROWS64 (current row in registers, older rows in shared memory, 32 /
  * 64 threads per block), TESS_K2_LOOP (FP64 loop form), TESS_K2_REG_HI
  * (register form compiled for more resident blocks), TESS_K2_REG_TMA (inputs
@@ -271,7 +271,9 @@ int tess_generate_persistent(tess_ctx *ctx, int n_proc, const tess_process *proc
  * event sharing its current table in shared memory), TESS_K2_PAIR_W (the
  * O(n^3) tensor rewrite of the four-vertex sum, Sec. 3), and for
  * TESS_POL_RANDOM only TESS_K2_REAL / TESS_K2_REAL_HI / TESS_K2_ROWS_REAL
- * (real currents) -- each under every chunk schedule
+ * (real currents), the wavefront forms TESS_K2_WAVE* (two lanes of a warp
+ * per event) and the warp-lanes forms TESS_K2_LANES8/16/32 -- each under
+ * every chunk schedule
  * TESS_SCHED_* below.  acc_scratch: device, TESS_ACC_LEN doubles (not
  * written: the timed runs stop before folding their sums); workspace:
  * tess_workspace_size(proc, probe_events) bytes -- that size already covers
@@ -323,6 +325,11 @@ int tess_generate_persistent(tess_ctx *ctx, int n_proc, const tess_process *proc
                                 rest spilled; FP32, n <= 6) */
 #define TESS_K2_REG_HI_PF 20 /* TESS_K2_REG_HI with the block's next tile of inputs prefetched into L1 before
                                 each tile (FP32, n <= 7) */
+#define TESS_K2_LANES8 21    /* 8 lanes of one warp per event sharing the currents of one length (Sec. 3's
+                                one thread per current of a length), long sets split over lanes and their
+                                partial sums added by warp shuffles; table in shared memory (FP32, n >= 6) */
+#define TESS_K2_LANES16 22   /* the same with 16 lanes per event (FP32, n >= 6) */
+#define TESS_K2_LANES32 23   /* the same with a whole warp per event (FP32, n >= 6) */
 #define TESS_SCHED_SERIAL 0
 #define TESS_SCHED_OVERLAP 1
 #define TESS_SCHED_OVERLAP_TILES 2

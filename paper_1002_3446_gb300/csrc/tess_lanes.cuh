@@ -105,9 +105,8 @@ __device__ __forceinline__ void lanes_sums(const LanesView<L> &V, int a, int b, 
       xm += 1;
     }
     // next split of this lane: [a..i+di] is di entries on; [i+di+1..b] is
-    // sum_{t=1..di} (L - i - t - 1) on
-#pragma unroll 1
-    for (int t = 1; t <= di; ++t) xr += L - i - t - 1;
+    // sum_{t=1..di} (L - i - t - 1) = di (L - i - 1) - di (di + 1) / 2 on
+    xr += di * (L - i - 1) - (di * (di + 1)) / 2;
     xl += di;
   }
 #pragma unroll

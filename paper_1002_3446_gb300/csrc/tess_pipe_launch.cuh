@@ -10,6 +10,7 @@
 #include "tess_pipeline.cuh"
 #include "tess_wave.cuh"
 #include "tess_wavep.cuh"
+#include "tess_lanes.cuh"
 
 namespace tess {
 
@@ -146,6 +147,10 @@ inline cudaError_t encode_rows_map(CUtensorMap *map, const float *base, int rows
 //              per SM: 128 registers, the rest spilled           FP32, n <= 6
 //   K2_REG_HI_PF  K2_REG_HI with the next tile's inputs prefetched into
 //              L1 before each tile                               FP32, n <= 7
+//   K2_LANES8 / K2_LANES16 / K2_LANES32  8, 16 or 32 lanes of one warp per
+//              event sharing the sets of one length, long sets split over
+//              lanes and reduced by shuffles (tess_lanes.cuh), 128 threads
+//                                                                FP32, n >= 6
 enum K2Form {
   K2_REG = 0,
   K2_ROWS32 = 1,
@@ -168,7 +173,10 @@ enum K2Form {
   K2_WAVE2L = 18,
   K2_REG_HI4 = 19,
   K2_REG_HI_PF = 20,
-  K2_NFORMS = 21
+  K2_LANES8 = 21,
+  K2_LANES16 = 22,
+  K2_LANES32 = 23,
+  K2_NFORMS = 24
 };
 
 // What a call offers the amplitude kernel: CAP_REAL_EPS, its polarisation
@@ -201,7 +209,10 @@ constexpr bool k2_valid(int f, unsigned caps) {
       case K2_WAVE2U:
       case K2_WAVE2P:
       case K2_WAVE2PU:
-      case K2_WAVE2L: return N >= 6;
+      case K2_WAVE2L:
+      case K2_LANES8:
+      case K2_LANES16:
+      case K2_LANES32: return N >= 6;
       case K2_PAIR32:
       case K2_PAIR64: return true;
       default: return false;
@@ -217,11 +228,14 @@ constexpr int k2_default() {
 template <int N, typename R, int F>
 struct K2V {
   static constexpr int L = N - 1;
+  static constexpr bool lanes = F == K2_LANES8 || F == K2_LANES16 || F == K2_LANES32;
+  static constexpr int lanes_ln = F == K2_LANES8 ? 8 : (F == K2_LANES16 ? 16 : 32);
   static constexpr int block =
-      (F == K2_ROWS32 || F == K2_PAIR32 || F == K2_PAIR_W || F == K2_WAVE2 || F == K2_WAVE2U || F == K2_WAVE2P ||
-           F == K2_WAVE2PU || F == K2_WAVE2L)
-          ? 32
-          : ((F == K2_ROWS64 || F == K2_PAIR64 || F == K2_ROWS_REAL || F == K2_WAVE) ? 64 : 128);
+      lanes ? 128 / lanes_ln
+            : ((F == K2_ROWS32 || F == K2_PAIR32 || F == K2_PAIR_W || F == K2_WAVE2 || F == K2_WAVE2U ||
+                F == K2_WAVE2P || F == K2_WAVE2PU || F == K2_WAVE2L)
+                   ? 32
+                   : ((F == K2_ROWS64 || F == K2_PAIR64 || F == K2_ROWS_REAL || F == K2_WAVE) ? 64 : 128));
   static constexpr bool rows = F == K2_ROWS32 || F == K2_ROWS64;
   static constexpr bool pair = F == K2_PAIR32 || F == K2_PAIR64 || F == K2_PAIR_W;
   static constexpr int wave_g =
@@ -231,11 +245,14 @@ struct K2V {
   static constexpr int wave_minb = wave_lean ? 6 : 1;
   static constexpr bool wave = F == K2_WAVE || F == K2_WAVE2 || F == K2_WAVE2U || wavep || wave_lean;
   static constexpr bool wave_unr = F == K2_WAVE2U || F == K2_WAVE2PU;
-  static constexpr int threads = pair ? 2 * block : (wave ? wave_g * block : block);  // block = events per tile
+  static constexpr int threads =
+      lanes ? 128 : (pair ? 2 * block : (wave ? wave_g * block : block));  // block = events per tile
   static constexpr int hi_blocks = N >= 6 ? 3 : 4;
   static constexpr int real_hi_blocks = N >= 8 ? 3 : 4;
   static void *fn() {
-    if constexpr (wavep)
+    if constexpr (lanes)
+      return (void *)bg_lanes_kernel<N, lanes_ln, 4>;
+    else if constexpr (wavep)
       return (void *)bg_wavep_kernel<N, block, wave_g, wave_unr>;
     else if constexpr (wave)
       return (void *)bg_wave_kernel<N, block, wave_g, wave_unr, wave_lean, wave_minb>;
@@ -267,7 +284,9 @@ struct K2V {
       return (void *)bg_loop_kernel<N, 128>;
   }
   static size_t smem(int hist_bins) {
-    if constexpr (wave_lean)
+    if constexpr (lanes)
+      return lanes_smem_bytes<L, 4, lanes_ln>() + EpiSmem<threads>::bytes(hist_bins);
+    else if constexpr (wave_lean)
       return wave_lean_smem_per_event<L>() * block + EpiSmem<threads>::bytes(hist_bins);
     else if constexpr (wave)
       return wave_smem_per_event<L>() * block + EpiSmem<threads>::bytes(hist_bins);
@@ -288,7 +307,9 @@ struct K2V {
   // map: tensor map of B.in (staged forms only)
   static cudaError_t launch(const ChunkParams &C, const ChunkBuf<R> &B, double *partials, int grid, size_t smem,
                             cudaStream_t s, const CUtensorMap *map) {
-    if constexpr (wavep)
+    if constexpr (lanes)
+      bg_lanes_kernel<N, lanes_ln, 4><<<grid, threads, smem, s>>>(C, B, partials);
+    else if constexpr (wavep)
       bg_wavep_kernel<N, block, wave_g, wave_unr><<<grid, threads, smem, s>>>(C, B, partials);
     else if constexpr (wave)
       bg_wave_kernel<N, block, wave_g, wave_unr, wave_lean, wave_minb><<<grid, threads, smem, s>>>(C, B, partials);
@@ -359,6 +380,9 @@ auto with_form(int f, Fn &&fn) {
       if (f == K2_WAVE2P) return fn(K2V<N, R, K2_WAVE2P>{});
       if (f == K2_WAVE2PU) return fn(K2V<N, R, K2_WAVE2PU>{});
       if (f == K2_WAVE2L) return fn(K2V<N, R, K2_WAVE2L>{});
+      if (f == K2_LANES8) return fn(K2V<N, R, K2_LANES8>{});
+      if (f == K2_LANES16) return fn(K2V<N, R, K2_LANES16>{});
+      if (f == K2_LANES32) return fn(K2V<N, R, K2_LANES32>{});
       if (f == K2_ROWS64) return fn(K2V<N, R, K2_ROWS64>{});
       return fn(K2V<N, R, K2_ROWS32>{});
     } else {

@@ -350,16 +350,18 @@ def test_random_polarisation_sigma_matches_helicity_sampling(ctx):
     assert res[0][2] == res[1][2]  # the same kinematics pass the same cuts
 
 
+_LANES = ["LANES8", "LANES16", "LANES32"]
 FORMS_BY_N = {
     4: ["REG", "REG_HI", "REG_HI4", "REG_HI_PF", "REG_TMA", "REG_TMA_HI", "PAIR32", "PAIR64", "PAIR_W"],
     6: ["REG", "REG_HI", "REG_HI4", "REG_HI_PF", "REG_TMA", "REG_TMA_HI", "ROWS32", "ROWS64", "PAIR32", "PAIR64", "PAIR_W", "WAVE",
-        "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"],
-    7: ["WAVE", "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"],
-    8: ["REG", "REG_TMA", "ROWS32", "ROWS64", "PAIR32", "PAIR64", "PAIR_W", "WAVE", "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"],
-    9: ["WAVE", "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"],
-    10: ["ROWS32", "ROWS64", "PAIR32", "PAIR64", "PAIR_W", "WAVE", "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"],
-    11: ["WAVE", "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"],
-    12: ["ROWS32", "ROWS64", "PAIR32", "PAIR64", "PAIR_W", "WAVE", "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"],
+        "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"] + _LANES,
+    7: ["WAVE", "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"] + _LANES,
+    8: ["REG", "REG_TMA", "ROWS32", "ROWS64", "PAIR32", "PAIR64", "PAIR_W", "WAVE", "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"]
+    + _LANES,
+    9: ["WAVE", "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"] + _LANES,
+    10: ["ROWS32", "ROWS64", "PAIR32", "PAIR64", "PAIR_W", "WAVE", "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"] + _LANES,
+    11: ["WAVE", "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"] + _LANES,
+    12: ["ROWS32", "ROWS64", "PAIR32", "PAIR64", "PAIR_W", "WAVE", "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"] + _LANES,
 }
 
 
