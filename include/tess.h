@@ -323,7 +323,7 @@ int tess_generate_persistent(tess_ctx *ctx, int n_proc, const tess_process *proc
                                 warps per SM where the tables leave room (FP32, n >= 6) */
 #define TESS_K2_REG_HI4 19   /* register form compiled for 4 resident blocks of 128 per SM (128 registers, the
                                 rest spilled; FP32, n <= 6) */
-#define TESS_K2_REG_HI_PF 20 /* TESS_K2_REG_HI with the block's next tile of inputs prefetched into L1 before
+#define TESS_K2_REG_HI_PF 20 /* TESS_K2_REG_HI with the block's next tile of inputs prefetched into L2 before
                                 each tile (FP32, n <= 7) */
 #define TESS_K2_LANES8 21    /* 8 lanes of one warp per event sharing the currents of one length (Sec. 3's
                                 one thread per current of a length), long sets split over lanes and their

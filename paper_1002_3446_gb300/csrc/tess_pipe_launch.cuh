@@ -145,8 +145,8 @@ inline cudaError_t encode_rows_map(CUtensorMap *map, const float *base, int rows
 //              compiled for 12 resident warps per SM             FP32, n >= 6
 //   K2_REG_HI4 register form compiled for 4 resident blocks (16 warps)
 //              per SM: 128 registers, the rest spilled           FP32, n <= 6
-//   K2_REG_HI_PF  K2_REG_HI with the next tile's inputs prefetched into
-//              L1 before each tile                               FP32, n <= 7
+//   K2_REG_HI_PF  K2_REG_HI with the block's next tile of inputs prefetched
+//              into L2 before each tile                          FP32, n <= 7
 //   K2_LANES8 / K2_LANES16 / K2_LANES32  8, 16 or 32 lanes of one warp per
 //              event sharing the sets of one length, long sets split over
 //              lanes and reduced by shuffles (tess_lanes.cuh), 128 threads

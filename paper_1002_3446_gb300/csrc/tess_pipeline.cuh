@@ -1154,25 +1154,37 @@ __device__ __forceinline__ void epi_flush(const EpiSmem<NB> &S, int nb2, Accum<N
   for (int i = threadIdx.x; i < 2 * nb2; i += NB) row[kPartialHead + i] += S.hw[i];
 }
 
-// L1 prefetch of the amplitude inputs and event factors of the event in chunk
-// column jn (one line per row for a warp's 32 consecutive columns), so that
-// the tile after the current one starts from L1 instead of L2.
-template <int L, typename R>
-__device__ __forceinline__ void prefetch_inputs(const ChunkBuf<R> &B, int jn, bool hist) {
-  const R *p = B.in + jn;
+// L2 prefetch, by the whole block, of the amplitude inputs and event factors
+// of the NB chunk columns starting at c0 (NB a multiple of 32: whole
+// 128-byte lines of every float row, NB / 16 lines of every double row), so
+// that the block's next tile starts from L2 instead of DRAM: the chunk buffer
+// is streamed through HBM once.  Columns past the chunk's count stay inside
+// the buffer (its capacity is a multiple of 128 columns).
+template <int L, int NB, typename R>
+__device__ __forceinline__ void prefetch_tile_l2(const ChunkBuf<R> &B, int c0, bool hist) {
+  static_assert(NB % 32 == 0 && sizeof(R) == 4, "whole lines of FP32 rows");
+  constexpr int LF = NB / 32, LD = NB / 16, RF = InRows<L>::rows * LF;
   const size_t cap = (size_t)B.cap;
-#pragma unroll
-  for (int r = 0; r < InRows<L>::rows; ++r) asm volatile("prefetch.global.L1 [%0];" ::"l"(p + r * cap));
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(B.efac + jn));
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(B.wfac + jn));
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(B.pass + jn));
-  if (hist) asm volatile("prefetch.global.L1 [%0];" ::"l"(B.hval + jn));
+  const int nd = hist ? 3 : 2;  // efac, wfac (and hval)
+  for (int i = threadIdx.x; i < RF + nd * LD + 1; i += NB) {
+    const char *p;
+    if (i < RF) {
+      p = (const char *)(B.in + (size_t)(i / LF) * cap + c0) + (i % LF) * 128;
+    } else if (i < RF + nd * LD) {
+      const int k = i - RF;
+      const double *row = k < LD ? B.efac : (k < 2 * LD ? B.wfac : B.hval);
+      p = (const char *)(row + c0) + (k % LD) * 128;
+    } else {
+      p = (const char *)(B.pass + c0);
+    }
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+  }
 }
 
 // K2, register form (FP32, n <= 7): thread per event, the whole current table
 // in registers.  PF: before each tile, the block's next tile is prefetched
-// into L1 (the inputs are read once per event from the chunk buffer, and
-// memory latency was the kernel's long-scoreboard stall).
+// into L2 (the inputs are read once per event from the chunk buffer in HBM,
+// and the tile's input loads are the kernel's long-scoreboard stall).
 template <int N, typename R, int NB, int MINB = 1, bool PF = false>
 __global__ void __launch_bounds__(NB, MINB) bg_reg_kernel(ChunkParams C, ChunkBuf<R> B, double *partials) {
   constexpr int L = N - 1;
@@ -1186,8 +1198,8 @@ __global__ void __launch_bounds__(NB, MINB) bg_reg_kernel(ChunkParams C, ChunkBu
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int j = tile * NB + threadIdx.x;
     if constexpr (PF) {
-      const int jn = j + (int)gridDim.x * NB;  // this thread's column of the block's next tile
-      if (!C.P.cut_first && jn < count) prefetch_inputs<L, R>(B, jn, nb2 > 0);
+      const int next = tile + (int)gridDim.x;  // the block's next tile
+      if (!C.P.cut_first && next < ntiles) prefetch_tile_l2<L, NB, R>(B, next * NB, nb2 > 0);
     }
     double w = 0.0;
     int bin = -1;
