@@ -252,6 +252,7 @@ def amp_kernel_time(torch, tess, ctx, proc, run, seed, first, flush, steps):
     serial counterpart with the same variant for this measurement)."""
     N = run.n_events
     plan = tess.tess_plan_info(ctx, proc, N)
+    flops_per_event = tess.flops_per_event(n, plan["variant"], rp)  # as the chosen variant evaluates it
     serial_of = {tess.TESS_SCHED_OVERLAP: tess.TESS_SCHED_SERIAL,
                  tess.TESS_SCHED_OVERLAP_TILES: tess.TESS_SCHED_SERIAL_TILES}
     if plan["schedule"] in serial_of:
@@ -297,7 +298,7 @@ def bench_config(torch, tess, ctx, name, flush, steps, peaks, sm_mhz, autotune=T
         # the exact sum evaluates (n-1)! orderings x 2^(n-1) helicity labellings per event (flipping every
         # label leaves |m| unchanged, so leg 0 keeps label 0 and the sum is doubled)
         evals = ne * (math.factorial(n - 1) * 2 ** (n - 1) if wl["hel"] == "sum" else 1)
-        fl = tess.bg_flops(n)
+        fl = tess.flops_per_event(n, plan["variant"])  # as the timed variant evaluates it
         achieved = fl * evals / (amp_ms * 1e-3) / 1e12
         pk = peak_at(peaks, "fp64" if form == "fp64" else "fp32", sm_mhz)
         sg = run.result()
@@ -465,6 +466,7 @@ def run_tess(args):
     # Under an overlapped schedule the two kernels share the SMs, so the stages
     # are timed with the same kernel variants run serially (each kernel alone).
     plan = tess.tess_plan_info(ctx, proc, N)
+    flops_per_event = tess.flops_per_event(n, plan["variant"], rp)  # as the chosen variant evaluates it
     serial_of = {tess.TESS_SCHED_OVERLAP: tess.TESS_SCHED_SERIAL,
                  tess.TESS_SCHED_OVERLAP_TILES: tess.TESS_SCHED_SERIAL_TILES}
     if plan["schedule"] in serial_of:
@@ -574,7 +576,7 @@ def run_tess(args):
                 ms = time_steps(torch, rr, seed, 0, 2, 1, flush)
                 ev = ne / (min(ms) * 1e-3)
                 info = tess.tess_plan_info(ctx, pp, ne)
-                row[prec] = {"events_per_s": ev, "tflops": tess.bg_flops(nn) * ev / 1e12,
+                row[prec] = {"events_per_s": ev, "tflops": tess.flops_per_event(nn, info["variant"]) * ev / 1e12,
                              "variant_schedule": [info["variant"], info["schedule"]]}
                 del rr
             sweep[str(nn)] = row
@@ -754,7 +756,7 @@ def bench_random_pol(torch, tess, ctx, wl, N, seed, first, flush, steps, autotun
     tess.tess_select_variant(ctx, p, info["variant"], info["schedule"])
     amp_ms, amp_n = st["amplitude"]
     res_ = r.result()
-    fl = tess.bg_flops_real(wl["n"]) if random_pol else tess.bg_flops(wl["n"])
+    fl = tess.flops_per_event(wl["n"], info["variant"], random_pol)
     evaluated = res_[2] if flags & tess.TESS_FLAG_CUT_FIRST else N  # amplitudes computed per step
     res = {"value": N / (statistics.mean(ms) * 1e-3), "unit": "events/s", "ms_per_step": statistics.mean(ms),
            "sigma_pb": res_[:2], "variant_schedule": [info["variant"], info["schedule"]],

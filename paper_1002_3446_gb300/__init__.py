@@ -498,6 +498,59 @@ def bg_flops(n):
     return total + 30
 
 
+def _bg_flops_sparse(n, right_leaves, final_leaf):
+    L = n - 1
+    total = 0
+    for ln in range(2, L + 1):
+        for a in range(0, L - ln + 1):
+            b = a + ln - 1
+            for i in range(a, b):
+                ll, lr = i == a, right_leaves and i + 1 == b
+                d = 16 if (ll and lr) else (18 if (ll or lr) else 30)
+                jlkr = 8 if ll else 14
+                krjl = 8 if lr else 14
+                ax_r = 20 if lr else 32
+                ax_l = 20 if ll else 32
+                total += d + jlkr + krjl + 4 + ax_r + ax_l + 4 + 16 + 2
+                total += (2 if i > a else 0) + (2 if b > i + 1 else 0)
+                for j in range(i + 1, b):  # triples ([a..i], [i+1..j], [j+1..b])
+                    la, lc = i == a, right_leaves and j + 1 == b
+                    total += (16 if (la and lc) else (18 if (la or lc) else 30)) + (20 if j == i + 1 else 32)
+            total += 20 + (16 if ln < L else 0)
+    return total + (18 if final_leaf else 30)
+
+
+def bg_flops_leaf(n):
+    """bg_flops for the register forms (TESS_K2_REG, _REG_HI, _REG_HI4, _REG_HI_PF,
+    _REG_TMA, _REG_TMA_HI; tess_bg.cuh bg_amplitude), which leave out the products
+    with the exact zeros of a single leg's polarisation vector (eps^0 and
+    Im eps^3): complex dot with one leaf 18 (two leaves 16) instead of 30, a
+    leaf's dot with a momentum 8 instead of 14, a multiply-add of a leaf 20
+    instead of 32, the final contraction 18."""
+    return _bg_flops_sparse(n, True, True)
+
+
+def bg_flops_wave(n):
+    """bg_flops for the scalar wavefront forms (TESS_K2_WAVE, _WAVE2, _WAVE2U;
+    tess_wave.cuh bg_wave), which leave out the zero products where the left
+    part of a split, or the first or middle part of a triple, is a single leg
+    (the compile-time cases of their step code)."""
+    return _bg_flops_sparse(n, False, False)
+
+
+REGISTER_FORMS = (0, 4, 5, 6, 19, 20)  # TESS_K2_REG, _REG_HI, _REG_TMA, _REG_TMA_HI, _REG_HI4, _REG_HI_PF
+WAVE_FORMS = (13, 14, 15)  # TESS_K2_WAVE, _WAVE2, _WAVE2U
+
+
+def flops_per_event(n, variant, random_pol=False):
+    """FLOPs of one amplitude as the given amplitude variant evaluates it."""
+    if random_pol:
+        return bg_flops_real(n)
+    if variant in REGISTER_FORMS:
+        return bg_flops_leaf(n)
+    return bg_flops_wave(n) if variant in WAVE_FORMS else bg_flops(n)
+
+
 def bg_flops_real(n):
     """The same count for the real-current recursion (random real
     polarisations, tess_bg.cuh bg_amplitude_real): per split 52 (+1 for each

@@ -15,9 +15,74 @@
 // All loops have compile-time trip counts, so after full unrolling every
 // table index is a constant and the tables live in registers.
 #pragma once
+#include <type_traits>
+
 #include "tess_math.cuh"
 
 namespace tess {
+
+// Single-leg currents are polarisation vectors of the helicity basis, whose
+// components eps^0 and Im eps^3 are exact zeros (e1 and e2 have no time
+// component, e2 no z component).  Where a part of a split or a triple is a
+// single leg (a "leaf"), the products with those components are left out:
+// each would add an exact +-0 to a finite partial sum, so the results are the
+// full products' (up to the sign of an exactly zero sum).  LA / LB: a / b is
+// a leaf.  The order of the remaining operations is that of mdot / axpy.
+template <bool LA, bool LB, typename R>
+__device__ __forceinline__ Cx<R> mdot_l(const CV4<R> &a, const CV4<R> &b) {
+  R re, im;
+  if constexpr (!LA && !LB) {
+    re = a.c[0].re * b.c[0].re;
+    im = a.c[0].re * b.c[0].im;
+    re = fma(-a.c[0].im, b.c[0].im, re);
+    im = fma(a.c[0].im, b.c[0].re, im);
+  } else {
+    re = -a.c[1].re * b.c[1].re;
+    im = -a.c[1].re * b.c[1].im;
+  }
+#pragma unroll
+  for (int m = 1; m < 4; ++m) {
+    const bool first = (LA || LB) && m == 1;  // its leading products are already in re, im
+    if (!first) re = fma(-a.c[m].re, b.c[m].re, re);
+    if (m < 3 || (!LA && !LB)) re = fma(a.c[m].im, b.c[m].im, re);
+    if (!first && (m < 3 || !LB)) im = fma(-a.c[m].re, b.c[m].im, im);
+    if (m < 3 || !LA) im = fma(-a.c[m].im, b.c[m].re, im);
+  }
+  return cx<R>(re, im);
+}
+
+// leaf a (complex) . k (real)
+template <typename R>
+__device__ __forceinline__ Cx<R> mdot_leaf(const CV4<R> &a, const RV4<R> &k) {
+  R re = -a.c[1].re * k.v[1];
+  R im = -a.c[1].im * k.v[1];
+  re = fma(-a.c[2].re, k.v[2], re);
+  im = fma(-a.c[2].im, k.v[2], im);
+  re = fma(-a.c[3].re, k.v[3], re);
+  return cx<R>(re, im);
+}
+
+// acc += s * v for a leaf v
+template <typename R>
+__device__ __forceinline__ void axpy_leaf(CV4<R> &acc, const Cx<R> &s, const CV4<R> &v) {
+#pragma unroll
+  for (int m = 1; m < 4; ++m) {
+    acc.c[m].re = fma(s.re, v.c[m].re, acc.c[m].re);
+    if (m < 3) acc.c[m].re = fma(-s.im, v.c[m].im, acc.c[m].re);
+    if (m < 3) acc.c[m].im = fma(s.re, v.c[m].im, acc.c[m].im);
+    acc.c[m].im = fma(s.im, v.c[m].re, acc.c[m].im);
+  }
+}
+
+// f(integral_constant<la>, integral_constant<lb>) for runtime flags that are
+// constants after unrolling (so only one branch survives)
+template <typename F>
+__device__ __forceinline__ auto leaf_sel(bool la, bool lb, F &&f) {
+  if (la && lb) return f(std::true_type{}, std::true_type{});
+  if (la) return f(std::true_type{}, std::false_type{});
+  if (lb) return f(std::false_type{}, std::true_type{});
+  return f(std::false_type{}, std::false_type{});
+}
 
 template <typename R, int L>
 struct BGTables {
@@ -49,12 +114,13 @@ __device__ __forceinline__ Cx<R> bg_amplitude(const RV4<R> (&k)[L], const CV4<R>
       Cx<R> s = cx<R>(R(0), R(0));
 #pragma unroll
       for (int i = a; i < b; ++i) {
-        // split l = [a..i], r = [i+1..b]
+        // split l = [a..i], r = [i+1..b] (leaves: i == a, i + 1 == b)
         const CV4<R> &Jl = t.J[a][i];
         const CV4<R> &Jr = t.J[i + 1][b];
-        const Cx<R> d = mdot(Jl, Jr);
-        const Cx<R> jlkr = mdot(Jl, t.K[i + 1][b]);
-        const Cx<R> krjl = mdot(Jr, t.K[a][i]);
+        const bool ll = i == a, lr = i + 1 == b;
+        const Cx<R> d = leaf_sel(ll, lr, [&](auto la, auto lb) { return mdot_l<decltype(la)::value, decltype(lb)::value>(Jl, Jr); });
+        const Cx<R> jlkr = ll ? mdot_leaf(Jl, t.K[i + 1][b]) : mdot(Jl, t.K[i + 1][b]);
+        const Cx<R> krjl = lr ? mdot_leaf(Jr, t.K[a][i]) : mdot(Jr, t.K[a][i]);
         Cx<R> cr = cx<R>(R(2) * jlkr.re, R(2) * jlkr.im);
         Cx<R> cl = cx<R>(R(-2) * krjl.re, R(-2) * krjl.im);
         if (i > a) {
@@ -65,8 +131,14 @@ __device__ __forceinline__ Cx<R> bg_amplitude(const RV4<R> (&k)[L], const CV4<R>
           cl.re -= t.S[i + 1][b].re;
           cl.im -= t.S[i + 1][b].im;
         }
-        axpy(acc, cr, Jr);
-        axpy(acc, cl, Jl);
+        if (lr)
+          axpy_leaf(acc, cr, Jr);
+        else
+          axpy(acc, cr, Jr);
+        if (ll)
+          axpy_leaf(acc, cl, Jl);
+        else
+          axpy(acc, cl, Jl);
         axpy(acc, d, rsub(t.K[a][i], t.K[i + 1][b]));
         s.re += d.re;
         s.im += d.im;
@@ -75,7 +147,14 @@ __device__ __forceinline__ Cx<R> bg_amplitude(const RV4<R> (&k)[L], const CV4<R>
       for (int i = a; i + 1 < b; ++i) {
 #pragma unroll
         for (int j = i + 1; j < b; ++j) {
-          axpy(tri, mdot(t.J[a][i], t.J[j + 1][b]), t.J[i + 1][j]);
+          // triple ([a..i], [i+1..j], [j+1..b]): leaves i == a, j == i + 1, j + 1 == b
+          const Cx<R> x = leaf_sel(i == a, j + 1 == b, [&](auto la, auto lb) {
+            return mdot_l<decltype(la)::value, decltype(lb)::value>(t.J[a][i], t.J[j + 1][b]);
+          });
+          if (j == i + 1)
+            axpy_leaf(tri, x, t.J[i + 1][j]);
+          else
+            axpy(tri, x, t.J[i + 1][j]);
         }
       }
 #pragma unroll
@@ -96,7 +175,7 @@ __device__ __forceinline__ Cx<R> bg_amplitude(const RV4<R> (&k)[L], const CV4<R>
       }
     }
   }
-  return mdot(e0, num);
+  return mdot_l<true, false>(e0, num);  // e0: leg 0's polarisation vector
 }
 
 // The same recursion with real polarisation vectors (Sec. 3's random real

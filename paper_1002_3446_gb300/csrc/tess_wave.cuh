@@ -148,8 +148,10 @@ __device__ __forceinline__ Cx<float> bg_wave(const float4 *K4, float4 *J4, float
             const int tr = t1<L>(r0, b);
             const CV4<float> Jr = wld_cv<NE>(J4, tr, e);
             const CV4<float> &Jl = row[dp];
-            const Cx<float> d0 = mdot(Jl, Jr);
-            const Cx<float> jlkr = mdot(Jl, kr);
+            // the left part [a..a] (dp = 0) is a single leg: its polarisation
+            // vector's exact zeros are left out (tess_bg.cuh, mdot_l)
+            const Cx<float> d0 = dp == 0 ? mdot_l<true, false>(Jl, Jr) : mdot(Jl, Jr);
+            const Cx<float> jlkr = dp == 0 ? mdot_leaf(Jl, kr) : mdot(Jl, kr);
             const Cx<float> krjl = mdot(Jr, krow[dp]);
             Cx<float> cr = cx<float>(2.f * jlkr.re - srow[dp].re, 2.f * jlkr.im - srow[dp].im);
             Cx<float> cl = cx<float>(-2.f * krjl.re, -2.f * krjl.im);
@@ -159,15 +161,23 @@ __device__ __forceinline__ Cx<float> bg_wave(const float4 *K4, float4 *J4, float
               cl.im -= sr.y;
             }
             axpy(acc, cr, Jr);
-            axpy(acc, cl, Jl);
+            if (dp == 0)
+              axpy_leaf(acc, cl, Jl);
+            else
+              axpy(acc, cl, Jl);
             axpy(acc, d0, rsub(krow[dp], kr));
             s.re += d0.re;
             s.im += d0.im;
-            // four-vertex triples whose last part is [r0..b]
+            // four-vertex triples whose last part is [r0..b] (first part
+            // [a..a+dpp] a single leg for dpp = 0, middle part one for dpp = dp - 1)
 #pragma unroll
             for (int dpp = 0; dpp < dp; ++dpp) {
               const CV4<float> JB = wld_cv<NE>(J4, t1<L>(a + dpp + 1, a + dp), e);
-              axpy(tri, mdot(row[dpp], Jr), JB);
+              const Cx<float> x = dpp == 0 ? mdot_l<true, false>(row[dpp], Jr) : mdot(row[dpp], Jr);
+              if (dpp + 1 == dp)
+                axpy_leaf(tri, x, JB);
+              else
+                axpy(tri, x, JB);
             }
           }
         }

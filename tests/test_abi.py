@@ -99,3 +99,64 @@ def test_null_arguments_rejected_without_device():
     assert lib.tess_generate(None, None, 0, 0, 0, None, None, 0, None) == tess.TESS_E_INVALID
     assert lib.tess_result(None, None, None, None) == tess.TESS_E_INVALID
     assert lib.tess_workspace_size(None, None, 0, None) == tess.TESS_E_INVALID
+
+
+def _counted_flops(n, leaf_zeros, right_leaves=True):
+    """FLOPs of the recursion by replaying the operation sequence of the
+    complex-vector helpers (mdot, axpy, radd, ...) with a mask of structural
+    zeros per operand: a product with a structurally zero factor is dropped
+    when leaf_zeros is set (the first kept product of a sum is a multiply, 1
+    FLOP; every further one an FMA, 2).  right_leaves: the right part of a
+    split, the last part of a triple and the final contraction vector are
+    treated as leaves where they are single legs (the register forms), or as
+    general vectors (the wavefront forms, whose step code knows only the left
+    and middle parts' lengths at compile time)."""
+    L = n - 1
+    full = [(True, True)] * 4
+    leaf = [(False, False), (True, True), (True, True), (True, False)] if leaf_zeros else full
+    rleaf = leaf if right_leaves else full
+    realk = [True] * 4
+
+    def sum_cost(products):  # products: list of bools (kept)
+        k = sum(products)
+        return 0 if k == 0 else 1 + 2 * (k - 1)
+
+    def mdot_cc(a, b):  # re: a_r b_r, a_i b_i per m; im: a_r b_i, a_i b_r per m
+        re = [a[m][0] and b[m][0] for m in range(4)] + [a[m][1] and b[m][1] for m in range(4)]
+        im = [a[m][0] and b[m][1] for m in range(4)] + [a[m][1] and b[m][0] for m in range(4)]
+        return sum_cost(re) + sum_cost(im)
+
+    def mdot_ck(a):
+        return sum_cost([a[m][0] for m in range(4)]) + sum_cost([a[m][1] for m in range(4)])
+
+    def axpy_c(v):  # acc += s v: per component two FMAs on v's real part, two on its imaginary part
+        return sum(2 * 2 * (int(v[m][0]) + int(v[m][1])) for m in range(4))
+
+    total = 0
+    for ln in range(2, L + 1):
+        for a in range(0, L - ln + 1):
+            b = a + ln - 1
+            for i in range(a, b):
+                jl = leaf if i == a else full
+                jr = rleaf if i + 1 == b else full
+                total += mdot_cc(jl, jr) + mdot_ck(jl) + mdot_ck(jr)
+                total += 2 + 2 + axpy_c(jr) + axpy_c(jl) + 4 + 16 + 2
+                total += (2 if i > a else 0) + (2 if b > i + 1 else 0)
+                for j in range(i + 1, b):
+                    ja = leaf if i == a else full
+                    jc = rleaf if j + 1 == b else full
+                    jb = leaf if j == i + 1 else full
+                    total += mdot_cc(ja, jc) + axpy_c(jb)
+            total += 20 + (16 if ln < L else 0)
+    return total + mdot_cc(rleaf, full)
+
+
+def test_cost_model_matches_a_replay_of_the_operations():
+    for n in range(4, 13):
+        assert _counted_flops(n, False) == tess.bg_flops(n), n
+        assert _counted_flops(n, True) == tess.bg_flops_leaf(n), n
+        assert _counted_flops(n, True, right_leaves=False) == tess.bg_flops_wave(n), n
+    assert tess.flops_per_event(6, tess.TESS_K2_REG_HI) == tess.bg_flops_leaf(6) == 3432
+    assert tess.flops_per_event(10, tess.TESS_K2_WAVE2) == tess.bg_flops_wave(10) == 29330
+    assert tess.flops_per_event(10, tess.TESS_K2_WAVE2P) == tess.bg_flops(10) == 32426
+    assert tess.flops_per_event(6, tess.TESS_K2_REAL, random_pol=True) == tess.bg_flops_real(6)
