@@ -531,15 +531,15 @@ def bg_flops_leaf(n):
 
 
 def bg_flops_wave(n):
-    """bg_flops for the scalar wavefront forms (TESS_K2_WAVE, _WAVE2, _WAVE2U;
-    tess_wave.cuh bg_wave), which leave out the zero products where the left
+    """bg_flops for the scalar wavefront forms (TESS_K2_WAVE, _WAVE2, _WAVE2U,
+    _WAVE2L; tess_wave.cuh bg_wave, bg_wave_lean), which leave out the zero products where the left
     part of a split, or the first or middle part of a triple, is a single leg
     (the compile-time cases of their step code)."""
     return _bg_flops_sparse(n, False, False)
 
 
 REGISTER_FORMS = (0, 4, 5, 6, 19, 20)  # TESS_K2_REG, _REG_HI, _REG_TMA, _REG_TMA_HI, _REG_HI4, _REG_HI_PF
-WAVE_FORMS = (13, 14, 15)  # TESS_K2_WAVE, _WAVE2, _WAVE2U
+WAVE_FORMS = (13, 14, 15, 18)  # TESS_K2_WAVE, _WAVE2, _WAVE2U, _WAVE2L
 
 
 def flops_per_event(n, variant, random_pol=False):

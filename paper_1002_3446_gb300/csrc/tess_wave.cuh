@@ -264,8 +264,8 @@ __device__ __forceinline__ Cx<float> bg_wave_lean(const float4 *K4, float4 *J4, 
             const int tr = t1<L>(r0, b);
             const CV4<float> Jr = wld_cv<NE>(J4, tr, e);
             const CV4<float> &Jl = row[dp];
-            const Cx<float> d0 = mdot(Jl, Jr);
-            const Cx<float> jlkr = mdot(Jl, kr);
+            const Cx<float> d0 = dp == 0 ? mdot_l<true, false>(Jl, Jr) : mdot(Jl, Jr);  // leaf left part
+            const Cx<float> jlkr = dp == 0 ? mdot_leaf(Jl, kr) : mdot(Jl, kr);
             const Cx<float> krjl = mdot(Jr, kl);
             Cx<float> cr = cx<float>(2.f * jlkr.re, 2.f * jlkr.im);
             if (dp > 0) {  // left part has more than one leg
@@ -280,14 +280,21 @@ __device__ __forceinline__ Cx<float> bg_wave_lean(const float4 *K4, float4 *J4, 
               cl.im -= sr.y;
             }
             axpy(acc, cr, Jr);
-            axpy(acc, cl, Jl);
+            if (dp == 0)
+              axpy_leaf(acc, cl, Jl);
+            else
+              axpy(acc, cl, Jl);
             axpy(acc, d0, rsub(kl, kr));
             s.re += d0.re;
             s.im += d0.im;
 #pragma unroll
             for (int dpp = 0; dpp < dp; ++dpp) {
               const CV4<float> JB = wld_cv<NE>(J4, t1<L>(a + dpp + 1, a + dp), e);
-              axpy(tri, mdot(row[dpp], Jr), JB);
+              const Cx<float> x = dpp == 0 ? mdot_l<true, false>(row[dpp], Jr) : mdot(row[dpp], Jr);
+              if (dpp + 1 == dp)
+                axpy_leaf(tri, x, JB);
+              else
+                axpy(tri, x, JB);
             }
           }
         }
