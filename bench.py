@@ -252,7 +252,6 @@ def amp_kernel_time(torch, tess, ctx, proc, run, seed, first, flush, steps):
     serial counterpart with the same variant for this measurement)."""
     N = run.n_events
     plan = tess.tess_plan_info(ctx, proc, N)
-    flops_per_event = tess.flops_per_event(n, plan["variant"], rp)  # as the chosen variant evaluates it
     serial_of = {tess.TESS_SCHED_OVERLAP: tess.TESS_SCHED_SERIAL,
                  tess.TESS_SCHED_OVERLAP_TILES: tess.TESS_SCHED_SERIAL_TILES}
     if plan["schedule"] in serial_of:
