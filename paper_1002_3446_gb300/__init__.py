@@ -530,8 +530,14 @@ def bg_flops_leaf(n):
     return _bg_flops_sparse(n, True, True)
 
 
+def bg_flops_wave_unrolled(n):
+    """bg_flops for TESS_K2_WAVE2U (every step's code unrolled), which also
+    leaves out the zeros of single-leg right and last parts."""
+    return _bg_flops_sparse(n, True, False)
+
+
 def bg_flops_wave(n):
-    """bg_flops for the scalar wavefront forms (TESS_K2_WAVE, _WAVE2, _WAVE2U,
+    """bg_flops for the rolled scalar wavefront forms (TESS_K2_WAVE, _WAVE2,
     _WAVE2L; tess_wave.cuh bg_wave, bg_wave_lean), which leave out the zero products where the left
     part of a split, or the first or middle part of a triple, is a single leg
     (the compile-time cases of their step code)."""
@@ -539,7 +545,7 @@ def bg_flops_wave(n):
 
 
 REGISTER_FORMS = (0, 4, 5, 6, 19, 20)  # TESS_K2_REG, _REG_HI, _REG_TMA, _REG_TMA_HI, _REG_HI4, _REG_HI_PF
-WAVE_FORMS = (13, 14, 15, 18)  # TESS_K2_WAVE, _WAVE2, _WAVE2U, _WAVE2L
+WAVE_FORMS = (13, 14, 18)  # TESS_K2_WAVE, _WAVE2, _WAVE2L
 
 
 def flops_per_event(n, variant, random_pol=False):
@@ -548,6 +554,8 @@ def flops_per_event(n, variant, random_pol=False):
         return bg_flops_real(n)
     if variant in REGISTER_FORMS:
         return bg_flops_leaf(n)
+    if variant == 15:  # TESS_K2_WAVE2U
+        return bg_flops_wave_unrolled(n)
     return bg_flops_wave(n) if variant in WAVE_FORMS else bg_flops(n)
 
 

@@ -149,10 +149,15 @@ __device__ __forceinline__ Cx<float> bg_wave(const float4 *K4, float4 *J4, float
             const CV4<float> Jr = wld_cv<NE>(J4, tr, e);
             const CV4<float> &Jl = row[dp];
             // the left part [a..a] (dp = 0) is a single leg: its polarisation
-            // vector's exact zeros are left out (tess_bg.cuh, mdot_l)
-            const Cx<float> d0 = dp == 0 ? mdot_l<true, false>(Jl, Jr) : mdot(Jl, Jr);
+            // vector's exact zeros are left out (tess_bg.cuh, mdot_l); so are
+            // the right part's when it is one ([b..b], dp = d - 1), where the
+            // step is known at compile time (UNR)
+            const bool rl = UNR && dp + 1 == d;
+            const Cx<float> d0 = leaf_sel(dp == 0, rl, [&](auto la, auto lb) {
+              return mdot_l<decltype(la)::value, decltype(lb)::value>(Jl, Jr);
+            });
             const Cx<float> jlkr = dp == 0 ? mdot_leaf(Jl, kr) : mdot(Jl, kr);
-            const Cx<float> krjl = mdot(Jr, krow[dp]);
+            const Cx<float> krjl = rl ? mdot_leaf(Jr, krow[dp]) : mdot(Jr, krow[dp]);
             Cx<float> cr = cx<float>(2.f * jlkr.re - srow[dp].re, 2.f * jlkr.im - srow[dp].im);
             Cx<float> cl = cx<float>(-2.f * krjl.re, -2.f * krjl.im);
             if (dp + 1 < d) {  // right part has more than one leg
@@ -160,7 +165,10 @@ __device__ __forceinline__ Cx<float> bg_wave(const float4 *K4, float4 *J4, float
               cl.re -= sr.x;
               cl.im -= sr.y;
             }
-            axpy(acc, cr, Jr);
+            if (rl)
+              axpy_leaf(acc, cr, Jr);
+            else
+              axpy(acc, cr, Jr);
             if (dp == 0)
               axpy_leaf(acc, cl, Jl);
             else
@@ -173,7 +181,9 @@ __device__ __forceinline__ Cx<float> bg_wave(const float4 *K4, float4 *J4, float
 #pragma unroll
             for (int dpp = 0; dpp < dp; ++dpp) {
               const CV4<float> JB = wld_cv<NE>(J4, t1<L>(a + dpp + 1, a + dp), e);
-              const Cx<float> x = dpp == 0 ? mdot_l<true, false>(row[dpp], Jr) : mdot(row[dpp], Jr);
+              const Cx<float> x = leaf_sel(dpp == 0, rl, [&](auto la, auto lb) {
+                return mdot_l<decltype(la)::value, decltype(lb)::value>(row[dpp], Jr);
+              });
               if (dpp + 1 == dp)
                 axpy_leaf(tri, x, JB);
               else

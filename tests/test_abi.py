@@ -156,6 +156,8 @@ def test_cost_model_matches_a_replay_of_the_operations():
         assert _counted_flops(n, False) == tess.bg_flops(n), n
         assert _counted_flops(n, True) == tess.bg_flops_leaf(n), n
         assert _counted_flops(n, True, right_leaves=False) == tess.bg_flops_wave(n), n
+        # unrolled wavefront form: right leaves too, final contraction general
+        assert _counted_flops(n, True) - 18 + 30 == tess.bg_flops_wave_unrolled(n), n
     assert tess.flops_per_event(6, tess.TESS_K2_REG_HI) == tess.bg_flops_leaf(6) == 3432
     assert tess.flops_per_event(10, tess.TESS_K2_WAVE2) == tess.bg_flops_wave(10) == 29330
     assert tess.flops_per_event(10, tess.TESS_K2_WAVE2P) == tess.bg_flops(10) == 32426
