@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(32 * NW) bg_lanes_kernel(ChunkParams C, ChunkB
   const LanesView<L> V(smem_lanes, g);
   const int nb2 = C.P.hist_bins > 0 ? C.P.hist_bins + 2 : 0;
   EpiSmem<NB> ES(smem_lanes + lanes_smem_bytes<L, NW, LN>(), nb2);
-  for (int i = threadIdx.x; i < 2 * nb2; i += NB) ES.hw[i] = 0.0;
+  epi_init(ES, nb2);
   Accum<NB> A;
   const int count = k2_count(C, B);
   const int ntiles = (count + NE - 1) / NE;

@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(2 * NEV) bg_pair_w_kernel(ChunkParams C, Chunk
   V.g = threadIdx.x % NEV;
   const int nb2 = C.P.hist_bins > 0 ? C.P.hist_bins + 2 : 0;
   EpiSmem<NB> ES(smem_pw + PS::bytes, nb2);
-  for (int i = threadIdx.x; i < 2 * nb2; i += NB) ES.hw[i] = 0.0;
+  epi_init(ES, nb2);
   Accum<NB> A;
   const int count = k2_count(C, B);
   const int ntiles = (count + NEV - 1) / NEV;

@@ -116,7 +116,7 @@ __device__ __forceinline__ void persist_tile(const PersistProc &pp, int t, const
   __syncthreads();
   const int nb2 = C.P.hist_bins > 0 ? C.P.hist_bins + 2 : 0;
   EpiSmem<kBlock> ES(S.epi, nb2);
-  for (int i = threadIdx.x; i < 2 * nb2; i += kBlock) ES.hw[i] = 0.0;
+  epi_init(ES, nb2);
   Accum<kBlock> A;
   double w = 0.0;
   int bin = -1;
@@ -144,7 +144,7 @@ __device__ __forceinline__ void persist_tile(const PersistProc &pp, int t, const
   double *row = pp.tile_sums + (size_t)t * partial_stride(C.P.hist_bins);
   if (threadIdx.x < 4) row[threadIdx.x] = red[threadIdx.x * kBlock];
   if (threadIdx.x == 4) row[4] = 0.0;
-  for (int i = threadIdx.x; i < 2 * nb2; i += kBlock) row[kPartialHead + i] = ES.hw[i];
+  for (int i = threadIdx.x; i < 2 * nb2; i += kBlock) row[kPartialHead + i] = epi_hist_sum(ES, nb2, i);
   __syncthreads();  // the tile and factors are reused by the next item
 }
 

@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(NE * G, MINB) bg_wave_kernel(ChunkParams C, Ch
   float2 *S0 = S2 + T1 * NE;  // lean form only: row 0's split sums
   const int nb2 = C.P.hist_bins > 0 ? C.P.hist_bins + 2 : 0;
   EpiSmem<NT> S((char *)(LEAN ? S0 + (L - 1) * NE : S0), nb2);
-  for (int i = threadIdx.x; i < 2 * nb2; i += NT) S.hw[i] = 0.0;
+  epi_init(S, nb2);
   Accum<NT> A;
   int slot, g;
   wave_slot<G>(slot, g);

@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(NE * G) bg_wavep_kernel(ChunkParams C, ChunkBu
   float2 *S2 = (float2 *)(K4 + L * NE);
   const int nb2 = C.P.hist_bins > 0 ? C.P.hist_bins + 2 : 0;
   EpiSmem<NT> S((char *)(S2 + T1 * NE), nb2);
-  for (int i = threadIdx.x; i < 2 * nb2; i += NT) S.hw[i] = 0.0;
+  epi_init(S, nb2);
   Accum<NT> A;
   int slot, g;
   wave_slot<G>(slot, g);
