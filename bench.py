@@ -297,7 +297,7 @@ def bench_config(torch, tess, ctx, name, flush, steps, peaks, sm_mhz, autotune=T
         # the exact sum evaluates (n-1)! orderings x 2^(n-1) helicity labellings per event (flipping every
         # label leaves |m| unchanged, so leg 0 keeps label 0 and the sum is doubled)
         evals = ne * (math.factorial(n - 1) * 2 ** (n - 1) if wl["hel"] == "sum" else 1)
-        fl = tess.flops_per_event(n, plan["variant"])  # as the timed variant evaluates it
+        fl = tess.flops_per_event(n, plan["variant"], precision=proc.precision)  # as the timed variant evaluates it
         achieved = fl * evals / (amp_ms * 1e-3) / 1e12
         pk = peak_at(peaks, "fp64" if form == "fp64" else "fp32", sm_mhz)
         sg = run.result()
@@ -465,7 +465,7 @@ def run_tess(args):
     # Under an overlapped schedule the two kernels share the SMs, so the stages
     # are timed with the same kernel variants run serially (each kernel alone).
     plan = tess.tess_plan_info(ctx, proc, N)
-    flops_per_event = tess.flops_per_event(n, plan["variant"], rp)  # as the chosen variant evaluates it
+    flops_per_event = tess.flops_per_event(n, plan["variant"], rp, precision=proc.precision)  # as the chosen variant evaluates it
     serial_of = {tess.TESS_SCHED_OVERLAP: tess.TESS_SCHED_SERIAL,
                  tess.TESS_SCHED_OVERLAP_TILES: tess.TESS_SCHED_SERIAL_TILES}
     if plan["schedule"] in serial_of:
@@ -591,6 +591,8 @@ def run_tess(args):
             amp_ms, amp_launches = stages["fused"]
         amp_ms_step = amp_ms / args.steps
         evaluated = n_pass_local if cf else N  # amplitudes computed per step (cut-first: passing events)
+        if wl["hel"] == "sum":  # every colour ordering and helicity labelling of each event (leg 0's label fixed)
+            evaluated = N * math.factorial(n - 1) * 2 ** (n - 1)
         achieved = flops_per_event * evaluated / (amp_ms_step * 1e-3) / 1e12
         tot = sum(v[0] for v in stages.values()) or 1.0
         traffic = read_traffic(args.workload + ("_rp" if rp else "") + ("_cf" if cf else ""), plan["variant"],

@@ -548,8 +548,14 @@ REGISTER_FORMS = (0, 4, 5, 6, 19, 20)  # TESS_K2_REG, _REG_HI, _REG_TMA, _REG_TM
 WAVE_FORMS = (13, 14, 18)  # TESS_K2_WAVE, _WAVE2, _WAVE2L
 
 
-def flops_per_event(n, variant, random_pol=False):
-    """FLOPs of one amplitude as the given amplitude variant evaluates it."""
+def flops_per_event(n, variant, random_pol=False, precision=None):
+    """FLOPs of one amplitude as the given amplitude variant evaluates it
+    (variant -1: the exact-sum mode's fused kernel, whose recursion is the
+    register form for FP32 up to n = 7 and FP64 up to n = 5, else the loop
+    form; pass the process's precision)."""
+    if variant == -1 and not random_pol:
+        reg = n <= 7 if precision in (TESS_FP32_CURRENTS, TESS_FP32_DS) else n <= 5
+        return bg_flops_leaf(n) if reg else bg_flops(n)
     if random_pol:
         return bg_flops_real(n)
     if variant in REGISTER_FORMS:

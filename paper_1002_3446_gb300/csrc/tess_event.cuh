@@ -251,10 +251,13 @@ __device__ __forceinline__ uint32_t sample_positions(const EventParams &P, uint6
 }
 
 // Which Berends-Giele form a (precision, n) uses: the unrolled register
-// form while its table fits in registers, else the loop form.
+// form while its table fits in registers (FP32 up to n = 7, FP64 up to
+// n = 5), else the loop form.  The register form also leaves out the exact
+// zeros of single-leg polarisation vectors, which the loop form's runtime
+// indices cannot know.
 template <typename R, int N>
 struct UseRegisterBG {
-  static constexpr bool value = sizeof(R) == 4 && N <= 7;
+  static constexpr bool value = sizeof(R) == 4 ? N <= 7 : N <= 5;
 };
 
 // Momentum of leg `leg` gathered into colour position order without dynamic

@@ -162,3 +162,7 @@ def test_cost_model_matches_a_replay_of_the_operations():
     assert tess.flops_per_event(10, tess.TESS_K2_WAVE2) == tess.bg_flops_wave(10) == 29330
     assert tess.flops_per_event(10, tess.TESS_K2_WAVE2P) == tess.bg_flops(10) == 32426
     assert tess.flops_per_event(6, tess.TESS_K2_REAL, random_pol=True) == tess.bg_flops_real(6)
+    # exact-sum mode: register form for FP64 up to n = 5, FP32 up to n = 7
+    assert tess.flops_per_event(4, -1, precision=tess.TESS_FP64) == tess.bg_flops_leaf(4)
+    assert tess.flops_per_event(6, -1, precision=tess.TESS_FP64) == tess.bg_flops(6)
+    assert tess.flops_per_event(7, -1, precision=tess.TESS_FP32_DS) == tess.bg_flops_leaf(7)
