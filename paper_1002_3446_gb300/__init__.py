@@ -548,6 +548,30 @@ REGISTER_FORMS = (0, 4, 5, 6, 19, 20)  # TESS_K2_REG, _REG_HI, _REG_TMA, _REG_TM
 WAVE_FORMS = (13, 14, 18)  # TESS_K2_WAVE, _WAVE2, _WAVE2L
 
 
+def bg_flops_real_leaf(n):
+    """bg_flops_real for the real-current register forms (TESS_K2_REAL,
+    _REAL_HI; tess_bg.cuh bg_amplitude_real), which leave out the time
+    component (exactly zero) of single-leg polarisation vectors: a dot with a
+    leaf 5 instead of 7, a multiply-add of a leaf 6 instead of 8, the final
+    contraction 5."""
+    L = n - 1
+    total = 0
+    for ln in range(2, L + 1):
+        for a in range(0, L - ln + 1):
+            b = a + ln - 1
+            for i in range(a, b):
+                ll, lr = i == a, i + 1 == b
+                d = 5 if (ll or lr) else 7
+                cr = (5 if ll else 7) + 1
+                cl = (5 if lr else 7) + 1
+                total += d + cr + cl + (6 if lr else 8) + (6 if ll else 8) + 8 + 4 + 1
+                total += (1 if i > a else 0) + (1 if b > i + 1 else 0)
+                for j in range(i + 1, b):
+                    total += (5 if (i == a or j + 1 == b) else 7) + (6 if j == i + 1 else 8)
+            total += 12 + (12 if ln < L else 0)
+    return total + 5
+
+
 def flops_per_event(n, variant, random_pol=False, precision=None):
     """FLOPs of one amplitude as the given amplitude variant evaluates it
     (variant -1: the exact-sum mode's fused kernel, whose recursion is the
@@ -556,8 +580,11 @@ def flops_per_event(n, variant, random_pol=False, precision=None):
     if variant == -1 and not random_pol:
         reg = n <= 7 if precision in (TESS_FP32_CURRENTS, TESS_FP32_DS) else n <= 5
         return bg_flops_leaf(n) if reg else bg_flops(n)
-    if random_pol:
+    if random_pol and variant in (9, 10):  # TESS_K2_REAL, _REAL_HI
+        return bg_flops_real_leaf(n)
+    if random_pol and variant == 11:  # TESS_K2_ROWS_REAL
         return bg_flops_real(n)
+    # the complex-current forms run on real vectors as on helicity vectors
     if variant in REGISTER_FORMS:
         return bg_flops_leaf(n)
     if variant == 15:  # TESS_K2_WAVE2U

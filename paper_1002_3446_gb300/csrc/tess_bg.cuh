@@ -188,6 +188,29 @@ __device__ __forceinline__ void raxpy(RV4<R> &acc, R s, const RV4<R> &v) {
   for (int m = 0; m < 4; ++m) acc.v[m] = fma(s, v.v[m], acc.v[m]);
 }
 
+// Real polarisation vectors cos(phi) e1 + sin(phi) e2 have eps^0 = 0
+// exactly: where a part is a single leg its time component is left out
+// (products with an exact zero; the same argument as mdot_l).
+template <bool LA, bool LB, typename R>
+__device__ __forceinline__ R rdot_l(const RV4<R> &a, const RV4<R> &b) {
+  R s;
+  if constexpr (!LA && !LB) {
+    s = a.v[0] * b.v[0];
+    s = fma(-a.v[1], b.v[1], s);
+  } else {
+    s = -a.v[1] * b.v[1];
+  }
+  s = fma(-a.v[2], b.v[2], s);
+  s = fma(-a.v[3], b.v[3], s);
+  return s;
+}
+
+template <typename R>
+__device__ __forceinline__ void raxpy_leaf(RV4<R> &acc, R s, const RV4<R> &v) {
+#pragma unroll
+  for (int m = 1; m < 4; ++m) acc.v[m] = fma(s, v.v[m], acc.v[m]);
+}
+
 template <typename R, int L>
 __device__ __forceinline__ R bg_amplitude_real(const RV4<R> (&k)[L], const RV4<R> (&e)[L], const RV4<R> &e0) {
   RV4<R> J[L][L], K[L][L];
@@ -211,20 +234,37 @@ __device__ __forceinline__ R bg_amplitude_real(const RV4<R> (&k)[L], const RV4<R
         // split l = [a..i], r = [i+1..b]
         const RV4<R> &Jl = J[a][i];
         const RV4<R> &Jr = J[i + 1][b];
-        const R d = mdot(Jl, Jr);
-        R cr = R(2) * mdot(Jl, K[i + 1][b]);
-        R cl = R(-2) * mdot(Jr, K[a][i]);
+        const bool ll = i == a, lr = i + 1 == b;  // single-leg parts
+        const R d = leaf_sel(ll, lr, [&](auto la, auto lb) {
+          return rdot_l<decltype(la)::value, decltype(lb)::value>(Jl, Jr);
+        });
+        R cr = R(2) * (ll ? rdot_l<true, false>(Jl, K[i + 1][b]) : mdot(Jl, K[i + 1][b]));
+        R cl = R(-2) * (lr ? rdot_l<true, false>(Jr, K[a][i]) : mdot(Jr, K[a][i]));
         if (i > a) cr -= S[a][i];
         if (b > i + 1) cl -= S[i + 1][b];
-        raxpy(acc, cr, Jr);
-        raxpy(acc, cl, Jl);
+        if (lr)
+          raxpy_leaf(acc, cr, Jr);
+        else
+          raxpy(acc, cr, Jr);
+        if (ll)
+          raxpy_leaf(acc, cl, Jl);
+        else
+          raxpy(acc, cl, Jl);
         raxpy(acc, d, rsub(K[a][i], K[i + 1][b]));
         sum += d;
       }
 #pragma unroll
       for (int i = a; i + 1 < b; ++i) {
 #pragma unroll
-        for (int j = i + 1; j < b; ++j) raxpy(tri, mdot(J[a][i], J[j + 1][b]), J[i + 1][j]);
+        for (int j = i + 1; j < b; ++j) {
+          const R x = leaf_sel(i == a, j + 1 == b, [&](auto la, auto lb) {
+            return rdot_l<decltype(la)::value, decltype(lb)::value>(J[a][i], J[j + 1][b]);
+          });
+          if (j == i + 1)
+            raxpy_leaf(tri, x, J[i + 1][j]);
+          else
+            raxpy(tri, x, J[i + 1][j]);
+        }
       }
 #pragma unroll
       for (int m = 0; m < 4; ++m) acc.v[m] = fma(R(2), tri.v[m], acc.v[m]);
@@ -238,7 +278,7 @@ __device__ __forceinline__ R bg_amplitude_real(const RV4<R> (&k)[L], const RV4<R
       }
     }
   }
-  return mdot(e0, num);
+  return rdot_l<true, false>(e0, num);  // e0: leg 0's polarisation vector
 }
 
 // ---------------------------------------------------------------------------

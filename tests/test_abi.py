@@ -161,8 +161,50 @@ def test_cost_model_matches_a_replay_of_the_operations():
     assert tess.flops_per_event(6, tess.TESS_K2_REG_HI) == tess.bg_flops_leaf(6) == 3432
     assert tess.flops_per_event(10, tess.TESS_K2_WAVE2) == tess.bg_flops_wave(10) == 29330
     assert tess.flops_per_event(10, tess.TESS_K2_WAVE2P) == tess.bg_flops(10) == 32426
-    assert tess.flops_per_event(6, tess.TESS_K2_REAL, random_pol=True) == tess.bg_flops_real(6)
+    assert tess.flops_per_event(6, tess.TESS_K2_REAL, random_pol=True) == tess.bg_flops_real_leaf(6)
     # exact-sum mode: register form for FP64 up to n = 5, FP32 up to n = 7
     assert tess.flops_per_event(4, -1, precision=tess.TESS_FP64) == tess.bg_flops_leaf(4)
     assert tess.flops_per_event(6, -1, precision=tess.TESS_FP64) == tess.bg_flops(6)
     assert tess.flops_per_event(7, -1, precision=tess.TESS_FP32_DS) == tess.bg_flops_leaf(7)
+
+
+def _counted_flops_real(n, leaf_zeros):
+    """The same replay for the real-current recursion (bg_amplitude_real):
+    real four-vectors, a single leg's polarisation vector with an exact zero
+    time component."""
+    L = n - 1
+    full = [True] * 4
+    leaf = [False, True, True, True] if leaf_zeros else full
+
+    def dot(a, b):
+        k = sum(x and y for x, y in zip(a, b))
+        return 0 if k == 0 else 1 + 2 * (k - 1)
+
+    def axpy(v):
+        return 2 * sum(v)
+
+    total = 0
+    for ln in range(2, L + 1):
+        for a in range(0, L - ln + 1):
+            b = a + ln - 1
+            for i in range(a, b):
+                jl = leaf if i == a else full
+                jr = leaf if i + 1 == b else full
+                total += dot(jl, jr) + dot(jl, full) + 1 + dot(jr, full) + 1
+                total += axpy(jr) + axpy(jl) + axpy(full) + 4 + 1
+                total += (1 if i > a else 0) + (1 if b > i + 1 else 0)
+                for j in range(i + 1, b):
+                    total += dot(leaf if i == a else full, leaf if j + 1 == b else full)
+                    total += axpy(leaf if j == i + 1 else full)
+            total += 12 + (12 if ln < L else 0)
+    return total + dot(leaf, full)
+
+
+def test_real_cost_model_matches_a_replay_of_the_operations():
+    for n in range(4, 13):
+        assert _counted_flops_real(n, False) == tess.bg_flops_real(n), n
+        assert _counted_flops_real(n, True) == tess.bg_flops_real_leaf(n), n
+    assert tess.flops_per_event(6, tess.TESS_K2_REAL_HI, random_pol=True) == tess.bg_flops_real_leaf(6)
+    assert tess.flops_per_event(10, tess.TESS_K2_ROWS_REAL, random_pol=True) == tess.bg_flops_real(10)
+    # complex-current forms on real vectors: their own count
+    assert tess.flops_per_event(6, tess.TESS_K2_REG_HI, random_pol=True) == tess.bg_flops_leaf(6)
