@@ -15,7 +15,10 @@ oracle's inputs; nothing is derived from the CUDA path):
     by O(1)); the median, 99th percentile and the weight-weighted mean (the
     quantity that enters sigma) of the per-event relative error against the
     FP64 oracle are asserted at about three times their measured values
-    (FP32_MEDIAN, FP32_P99, FP32_WEIGHTED below) and printed.
+    (FP32_MEDIAN, FP32_P99, FP32_WEIGHTED below) and printed.  An event
+    whose Rambo boost amplifies the FP32 seeds' rounding beyond BOOST_ALONE
+    (8 ulp(FP32) x gamma^2, as for the observables) is held to that bound
+    alone and left out of the weight-weighted mean.
   FP64 events that pass only through the ill-conditioning fallback are
     bounded in number (at most ILL_RATE of the compared events) and listed
     with the oracle's Sec. 4 gauge ratio |k^.Num|^2/|eps.Num|^2.
@@ -52,6 +55,10 @@ RTOL32 = 1e-4
 # events it happens to hold, so it is bounded per n as measured.
 FP32_P99 = {4: 4e-4, 5: 1.5e-3, 6: 3e-3, 7: 5e-3, 8: 3.5e-2, 9: 5e-3, 10: 5e-3, 11: 3e-3, 12: 3.5e-3}
 FP32_WEIGHTED = {4: 5e-6, 5: 1.5e-5, 6: 2.5e-5, 7: 4e-5, 8: 5e-5, 9: 3e-5, 10: 4e-5, 11: 4e-5, 12: 4e-5}
+# FP32 forms: an event whose seed-rounding bound through the Rambo boost,
+# 8 u gamma^2 (u = 2^-24), exceeds this is compared alone against that bound
+# and left out of the weight-weighted statistic (gamma above about 11)
+BOOST_ALONE = 1e-5
 # FP64: share of compared events allowed to need the ill-conditioning fallback
 # (measured: 0.19 % at n = 6 over 2^21 events, 0.14 % at n = 10 over 2^22)
 ILL_RATE = 5e-3
@@ -168,15 +175,17 @@ def compare_events(orc, p, g, seed, first, idx, stats=None, events=None):
     floor = RTOL32 if fp32 else RTOL64  # FP32: events above it are only counted
     vtol = 1e-6 if fp32 else 1e-20
     otol = 1e-4 if fp32 else 1e-10  # FP32 form: FP32 Rambo seeds, cuts and observables
-    flips = fallback = 0
+    flips = fallback = boosted = 0
     rel = []
     wdiff = wsum = 0.0
     for i in idx:
         ev = first + int(i) if events is None else int(events[i])
         r = orc.event(op, seed, ev)
         etol = otol
+        gtol = 0.0
         if fp32:  # FP32 seeds through the boost: a few ulp times gamma^2
-            etol = max(otol, 8 * 2.0**-24 * rambo_gamma(orc, op, seed, ev) ** 2)
+            gtol = 8 * 2.0**-24 * rambo_gamma(orc, op, seed, ev) ** 2
+            etol = max(otol, gtol)
         for key in ("ht", "ptlead", "rmin"):
             assert np.isclose(g[key][i], r[key], rtol=etol, atol=0), (key, i, g[key][i], r[key], etol)
         if bool(g["pass"][i]) != r["pass"]:
@@ -191,8 +200,17 @@ def compare_events(orc, p, g, seed, first, idx, stats=None, events=None):
         e = abs(g["me2"][i] - r["me2"]) / abs(r["me2"])
         if r["pass"]:
             e = max(e, abs(g["weight"][i] - r["weight"]) / abs(r["weight"]))
-            wdiff += abs(g["weight"][i] - r["weight"])
-            wsum += r["weight"]
+            if gtol > BOOST_ALONE:
+                # the FP32 seeds' rounding through a large boost bounds this
+                # event's accuracy, as it bounds its observables: held to that
+                # bound (plus the currents' own FP32 bound) alone, not weighted
+                # into the sample's statistic (one such event can carry a fifth
+                # of a small sample's weight)
+                assert e <= gtol + FP32_P99[n], (i, e, gtol)
+                boosted += 1
+            else:
+                wdiff += abs(g["weight"][i] - r["weight"])
+                wsum += r["weight"]
         else:
             assert g["weight"][i] == 0.0
         if e > floor:
@@ -208,7 +226,7 @@ def compare_events(orc, p, g, seed, first, idx, stats=None, events=None):
         assert fallback <= max(1, ILL_RATE * len(rel)), f"{fallback} of {len(rel)} events needed the fallback"
     if stats is not None:
         stats.update(median=float(np.median(rel)), max=float(rel.max()), p99=float(np.quantile(rel, 0.99)),
-                     flips=flips, compared=len(rel), ill_conditioned=fallback,
+                     flips=flips, compared=len(rel), ill_conditioned=fallback, boosted=boosted,
                      weighted=wdiff / wsum if wsum > 0 else 0.0)
     return rel
 
@@ -352,8 +370,9 @@ def test_random_polarisation_sigma_matches_helicity_sampling(ctx):
 
 _LANES = ["LANES8", "LANES16", "LANES32"]
 FORMS_BY_N = {
-    4: ["REG", "REG_HI", "REG_HI4", "REG_HI_PF", "REG_TMA", "REG_TMA_HI", "PAIR32", "PAIR64", "PAIR_W"],
-    6: ["REG", "REG_HI", "REG_HI4", "REG_HI_PF", "REG_TMA", "REG_TMA_HI", "ROWS32", "ROWS64", "PAIR32", "PAIR64", "PAIR_W", "WAVE",
+    4: ["REG", "REG_HI", "REG_HI4", "REG_HI_PF", "REG_TMA", "REG_TMA_HI", "PAIR32", "PAIR64", "PAIR_W", "FUSED"],
+    6: ["REG", "REG_HI", "REG_HI4", "REG_HI_PF", "REG_TMA", "REG_TMA_HI", "FUSED", "ROWS32", "ROWS64", "PAIR32", "PAIR64",
+        "PAIR_W", "WAVE",
         "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"] + _LANES,
     7: ["WAVE", "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"] + _LANES,
     8: ["REG", "REG_TMA", "ROWS32", "ROWS64", "PAIR32", "PAIR64", "PAIR_W", "WAVE", "WAVE2", "WAVE2U", "WAVE2P", "WAVE2PU", "WAVE2L"]
