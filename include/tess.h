@@ -272,8 +272,9 @@ int tess_generate_persistent(tess_ctx *ctx, int n_proc, const tess_process *proc
  * O(n^3) tensor rewrite of the four-vertex sum, Sec. 3), and for
  * TESS_POL_RANDOM only TESS_K2_REAL / TESS_K2_REAL_HI / TESS_K2_ROWS_REAL
  * (real currents), the wavefront forms TESS_K2_WAVE* (two lanes of a warp
- * per event) and the warp-lanes forms TESS_K2_LANES8/16/32 -- each under
- * every chunk schedule
+ * per event), the warp-lanes forms TESS_K2_LANES8/16/32 and the
+ * warp-specialised one-kernel form TESS_K2_FUSED (TESS_FP32_DS, n <= 6) --
+ * each under every chunk schedule
  * TESS_SCHED_* below.  acc_scratch: device, TESS_ACC_LEN doubles (not
  * written: the timed runs stop before folding their sums); workspace:
  * tess_workspace_size(proc, probe_events) bytes -- that size already covers
@@ -285,7 +286,8 @@ int tess_generate_persistent(tess_ctx *ctx, int n_proc, const tess_process *proc
  * summation order.
  *
  * Chunk schedules (events are processed in chunks of tess_set_chunk_bytes,
- * each by a kinematics kernel and an amplitude kernel):
+ * each by a kinematics kernel and an amplitude kernel; TESS_K2_FUSED runs
+ * one kernel per chunk and takes the serial ones):
  *   TESS_SCHED_SERIAL         both kernels of a chunk back to back on
  *                             `stream`; amplitude grid = resident blocks
  *   TESS_SCHED_OVERLAP        kinematics of chunk c+1 on `stream` while the
@@ -330,6 +332,10 @@ int tess_generate_persistent(tess_ctx *ctx, int n_proc, const tess_process *proc
                                 partial sums added by warp shuffles; table in shared memory (FP32, n >= 6) */
 #define TESS_K2_LANES16 22   /* the same with 16 lanes per event (FP32, n >= 6) */
 #define TESS_K2_LANES32 23   /* the same with a whole warp per event (FP32, n >= 6) */
+#define TESS_K2_FUSED 24     /* no separate kinematics kernel: one warp-specialised kernel per chunk, a
+                                kinematics warpgroup handing tiles of 128 events to a register-form
+                                amplitude warpgroup through shared memory; no chunk buffer in the
+                                workspace (TESS_FP32_DS with TESS_HEL_SAMPLE, no cut-first, n = 4..6) */
 #define TESS_SCHED_SERIAL 0
 #define TESS_SCHED_OVERLAP 1
 #define TESS_SCHED_OVERLAP_TILES 2

@@ -37,6 +37,7 @@ TESS_K2_REG_TMA_HI, TESS_K2_PAIR32, TESS_K2_PAIR64, TESS_K2_REAL, TESS_K2_REAL_H
 TESS_K2_ROWS_REAL, TESS_K2_PAIR_W, TESS_K2_WAVE, TESS_K2_WAVE2, TESS_K2_WAVE2U = 11, 12, 13, 14, 15
 TESS_K2_WAVE2P, TESS_K2_WAVE2PU, TESS_K2_WAVE2L, TESS_K2_REG_HI4, TESS_K2_REG_HI_PF = 16, 17, 18, 19, 20
 TESS_K2_LANES8, TESS_K2_LANES16, TESS_K2_LANES32 = 21, 22, 23
+TESS_K2_FUSED = 24
 TESS_SCHED_SERIAL, TESS_SCHED_OVERLAP, TESS_SCHED_OVERLAP_TILES, TESS_SCHED_SERIAL_TILES = 0, 1, 2, 3
 TESS_PEAK_FP32, TESS_PEAK_FP32X2, TESS_PEAK_FP64 = 0, 1, 2
 
@@ -544,7 +545,7 @@ def bg_flops_wave(n):
     return _bg_flops_sparse(n, False, False)
 
 
-REGISTER_FORMS = (0, 4, 5, 6, 19, 20)  # TESS_K2_REG, _REG_HI, _REG_TMA, _REG_TMA_HI, _REG_HI4, _REG_HI_PF
+REGISTER_FORMS = (0, 4, 5, 6, 19, 20, 24)  # TESS_K2_REG, _REG_HI, _REG_TMA, _REG_TMA_HI, _REG_HI4, _REG_HI_PF, _FUSED
 WAVE_FORMS = (13, 14, 18)  # TESS_K2_WAVE, _WAVE2, _WAVE2L
 
 

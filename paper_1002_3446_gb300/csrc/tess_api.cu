@@ -338,7 +338,8 @@ int plan_with_form(const tess_ctx *ctx, const tess_process *p, uint64_t n_events
   }
   const unsigned caps = (p->helicity_mode == TESS_POL_RANDOM ? tess::CAP_REAL_EPS : 0u) |
                         ((p->flags & TESS_FLAG_CUT_FIRST) ? tess::CAP_CUT_FIRST : 0u) |
-                        ((p->flags & TESS_FLAG_PDF_GRID) ? tess::CAP_PDF_GRID : 0u);
+                        ((p->flags & TESS_FLAG_PDF_GRID) ? tess::CAP_PDF_GRID : 0u) |
+                        (p->precision == TESS_FP32_DS ? tess::CAP_KIN_DS : 0u);
   int rc;
   *pl = tess::PipePlan();
   pl->chunk_target = ctx->chunk_bytes;

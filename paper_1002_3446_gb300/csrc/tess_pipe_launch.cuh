@@ -11,6 +11,7 @@
 #include "tess_wave.cuh"
 #include "tess_wavep.cuh"
 #include "tess_lanes.cuh"
+#include "tess_fused.cuh"
 
 namespace tess {
 
@@ -151,6 +152,10 @@ inline cudaError_t encode_rows_map(CUtensorMap *map, const float *base, int rows
 //              event sharing the sets of one length, long sets split over
 //              lanes and reduced by shuffles (tess_lanes.cuh), 128 threads
 //                                                                FP32, n >= 6
+//   K2_FUSED   no separate kinematics launch: one warp-specialised kernel
+//              (tess_fused.cuh), a kinematics warpgroup feeding the
+//              register form through shared memory, 256 threads, no
+//              chunk buffer                  FP32 double-float, n = 4..6
 enum K2Form {
   K2_REG = 0,
   K2_ROWS32 = 1,
@@ -176,14 +181,16 @@ enum K2Form {
   K2_LANES8 = 21,
   K2_LANES16 = 22,
   K2_LANES32 = 23,
-  K2_NFORMS = 24
+  K2_FUSED = 24,
+  K2_NFORMS = 25
 };
 
 // What a call offers the amplitude kernel: CAP_REAL_EPS, its polarisation
 // vectors are real (random polarisations), which the real-current forms
 // require; CAP_CUT_FIRST, its events are compacted (an index list), which the
-// staged forms do not read.
-constexpr unsigned CAP_REAL_EPS = 1u, CAP_CUT_FIRST = 2u, CAP_PDF_GRID = 4u;
+// staged forms do not read; CAP_KIN_DS, its kinematics are the double-float
+// form, the only one the fused kernel carries.
+constexpr unsigned CAP_REAL_EPS = 1u, CAP_CUT_FIRST = 2u, CAP_PDF_GRID = 4u, CAP_KIN_DS = 8u;
 
 template <int N, typename R>
 constexpr bool k2_valid(int f, unsigned caps) {
@@ -192,6 +199,7 @@ constexpr bool k2_valid(int f, unsigned caps) {
     return f == K2_LOOP && !cut_first;
   } else {
     switch (f) {
+      case K2_FUSED: return N >= 4 && N <= 6 && !real_eps && !cut_first && (caps & CAP_KIN_DS) != 0;
       case K2_REAL: return real_eps && N <= 9;
       case K2_REAL_HI: return real_eps && N <= 8;
       case K2_ROWS_REAL: return real_eps && N >= 8;
@@ -229,6 +237,7 @@ template <int N, typename R, int F>
 struct K2V {
   static constexpr int L = N - 1;
   static constexpr bool lanes = F == K2_LANES8 || F == K2_LANES16 || F == K2_LANES32;
+  static constexpr bool fused = F == K2_FUSED;
   static constexpr int lanes_ln = F == K2_LANES8 ? 8 : (F == K2_LANES16 ? 16 : 32);
   static constexpr int block =
       lanes ? 128 / lanes_ln
@@ -246,11 +255,14 @@ struct K2V {
   static constexpr bool wave = F == K2_WAVE || F == K2_WAVE2 || F == K2_WAVE2U || wavep || wave_lean;
   static constexpr bool wave_unr = F == K2_WAVE2U || F == K2_WAVE2PU;
   static constexpr int threads =
-      lanes ? 128 : (pair ? 2 * block : (wave ? wave_g * block : block));  // block = events per tile
+      fused ? kFusedThreads
+            : (lanes ? 128 : (pair ? 2 * block : (wave ? wave_g * block : block)));  // block = events per tile
   static constexpr int hi_blocks = N >= 6 ? 3 : 4;
   static constexpr int real_hi_blocks = N >= 8 ? 3 : 4;
   static void *fn() {
-    if constexpr (lanes)
+    if constexpr (fused)
+      return (void *)fused_kernel<N>;
+    else if constexpr (lanes)
       return (void *)bg_lanes_kernel<N, lanes_ln, 4>;
     else if constexpr (wavep)
       return (void *)bg_wavep_kernel<N, block, wave_g, wave_unr>;
@@ -284,7 +296,9 @@ struct K2V {
       return (void *)bg_loop_kernel<N, 128>;
   }
   static size_t smem(int hist_bins) {
-    if constexpr (lanes)
+    if constexpr (fused)
+      return FusedSmem<N>::bytes(hist_bins);
+    else if constexpr (lanes)
       return lanes_smem_bytes<L, 4, lanes_ln>() + EpiSmem<threads>::bytes(hist_bins);
     else if constexpr (wave_lean)
       return wave_lean_smem_per_event<L>() * block + EpiSmem<threads>::bytes(hist_bins);
@@ -307,7 +321,9 @@ struct K2V {
   // map: tensor map of B.in (staged forms only)
   static cudaError_t launch(const ChunkParams &C, const ChunkBuf<R> &B, double *partials, int grid, size_t smem,
                             cudaStream_t s, const CUtensorMap *map) {
-    if constexpr (lanes)
+    if constexpr (fused)
+      fused_kernel<N><<<grid, threads, smem, s>>>(C, partials);
+    else if constexpr (lanes)
       bg_lanes_kernel<N, lanes_ln, 4><<<grid, threads, smem, s>>>(C, B, partials);
     else if constexpr (wavep)
       bg_wavep_kernel<N, block, wave_g, wave_unr><<<grid, threads, smem, s>>>(C, B, partials);
@@ -361,6 +377,9 @@ auto with_form(int f, Fn &&fn) {
     if constexpr (N <= 6) {
       if (f == K2_REG_HI4) return fn(K2V<N, R, K2_REG_HI4>{});
     }
+    if constexpr (N >= 4 && N <= 6) {
+      if (f == K2_FUSED) return fn(K2V<N, R, K2_FUSED>{});
+    }
     if constexpr (N <= 7) {
       if (f == K2_REG_HI_PF) return fn(K2V<N, R, K2_REG_HI_PF>{});
       if (f == K2_REG_HI) return fn(K2V<N, R, K2_REG_HI>{});
@@ -396,7 +415,16 @@ int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, in
                     PipePlan *pl) {
   constexpr int L = N - 1;
   if (!k2_valid<N, R>(form, caps)) form = k2_default<N, R>();
+  if (form == K2_FUSED) {
+    // its register split (setmaxnreg) assumes the launch's 128 registers a
+    // thread; any other compiled count and the form is not offered
+    cudaFuncAttributes fa;
+    const cudaError_t e = with_form<N, R>(form, [&](auto K) { return cudaFuncGetAttributes(&fa, decltype(K)::fn()); });
+    if (e != cudaSuccess) return (int)e;
+    if (fa.numRegs != kFusedLaunchRegs) form = k2_default<N, R>();
+  }
   pl->form = form;
+  const bool fused = form == K2_FUSED;
   const int rc = with_form<N, R>(form, [&](auto K) {
     using KV = decltype(K);
     pl->block = KV::block;  // events per tile
@@ -430,7 +458,9 @@ int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, in
   const uint64_t per_event =
       (uint64_t)InRows<L>::rows * sizeof(R) + 3 * sizeof(double) + 1 + (cut_first ? 2 * sizeof(int) : 0);
   const uint64_t chunk_bytes = pl->chunk_target ? pl->chunk_target : kChunkTargetBytes;
-  // events per chunk: a multiple of 128 below 2^31 (chunk columns are ints)
+  // events per chunk: a multiple of 128 below 2^31 (chunk columns are ints);
+  // the fused kernel keeps its events on chip but takes the same chunks (one
+  // launch per chunk)
   uint64_t target = std::min<uint64_t>(std::max<uint64_t>(128, (chunk_bytes / per_event) / 128 * 128),
                                        (uint64_t)INT32_MAX / 256 * 128);
   // A whole number of amplitude-grid waves per chunk: the chunk's tiles are
@@ -446,7 +476,7 @@ int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, in
   const uint64_t tiles = ((uint64_t)pl->cap + pl->block - 1) / pl->block;
   if (sched < 0 || sched >= SCHED_N) sched = SCHED_SERIAL;
   pl->sched = sched;
-  pl->overlap = (sched == SCHED_OVERLAP || sched == SCHED_OVERLAP_TILES) && pl->chunks > 1;
+  pl->overlap = (sched == SCHED_OVERLAP || sched == SCHED_OVERLAP_TILES) && pl->chunks > 1 && !fused;
   uint64_t resident = (uint64_t)sm_count * per_sm;
   if (sched == SCHED_OVERLAP_TILES || sched == SCHED_SERIAL_TILES) {
     const uint64_t flush_budget = (uint64_t)pl->cap * per_event / 50 / (partial_stride(hist_bins) * sizeof(double));
@@ -460,6 +490,11 @@ int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, in
     off = align256(off + (size_t)(kPdfNodes + kAsNodes) * sizeof(float));
   }
   pl->off_in = off;
+  if (fused) {  // partial rows (and grid tables) only
+    pl->buf_bytes = 0;
+    pl->bytes = off;
+    return 0;
+  }
   off = align256(off + (size_t)InRows<L>::rows * pl->cap * sizeof(R));
   pl->off_efac = off;
   off = align256(off + (size_t)pl->cap * sizeof(double));
@@ -556,6 +591,18 @@ cudaError_t run_pipeline_t(const EventParams &P, const PipePlan &pl, char *ws, c
     }
     if ((e = cudaEventRecord(ov->join, a)) != cudaSuccess) return e;
     return cudaStreamWaitEvent(s, ov->join, 0);
+  }
+  if (pl.form == K2_FUSED) {  // one warp-specialised launch per chunk, no kinematics launch
+    for (uint64_t off = 0; off < P.n_events; off += (uint64_t)pl.cap) {
+      C.chunk_first = off;
+      C.count = (int)std::min<uint64_t>((uint64_t)pl.cap, P.n_events - off);
+      if (hook) (*hook)(STAGE_AMP, true, s);
+      e = with_form<N, R>(pl.form,
+                          [&](auto K) { return decltype(K)::launch(C, BB[0], partials, pl.grid, pl.smem, s, nullptr); });
+      if (e != cudaSuccess) return e;
+      if (hook) (*hook)(STAGE_AMP, false, s);
+    }
+    return cudaSuccess;
   }
   const ChunkBuf<R> &B = BB[0];
   for (uint64_t off = 0; off < P.n_events; off += (uint64_t)pl.cap) {

@@ -151,7 +151,8 @@ def test_autotune_with_outputs_writes_only_the_per_event_arrays(ctx):
                     tess.TESS_K2_REG_HI_PF, tess.TESS_K2_REG_HI4, tess.TESS_K2_ROWS32, tess.TESS_K2_ROWS64,
                     tess.TESS_K2_WAVE, tess.TESS_K2_WAVE2, tess.TESS_K2_WAVE2U, tess.TESS_K2_WAVE2P,
                     tess.TESS_K2_WAVE2PU, tess.TESS_K2_WAVE2L, tess.TESS_K2_PAIR32, tess.TESS_K2_PAIR64,
-                    tess.TESS_K2_PAIR_W, tess.TESS_K2_LANES8, tess.TESS_K2_LANES16, tess.TESS_K2_LANES32}
+                    tess.TESS_K2_PAIR_W, tess.TESS_K2_LANES8, tess.TESS_K2_LANES16, tess.TESS_K2_LANES32,
+                    tess.TESS_K2_FUSED}
     assert float(run.acc.abs().sum()) == 0.0 and float(run.hist.abs().sum()) == 0.0
     got = _host(run)
     # the probe draws events [0, N/2) of seed 1
