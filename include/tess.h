@@ -297,7 +297,15 @@ int tess_generate_persistent(tess_ctx *ctx, int n_proc, const tess_process *proc
  *   TESS_SCHED_OVERLAP_TILES  overlapped, one amplitude block per tile of
  *                             events (bounded so that the blocks' partial-sum
  *                             flushes stay small next to the chunk's traffic)
- *   TESS_SCHED_SERIAL_TILES   serial, one amplitude block per tile */
+ *   TESS_SCHED_SERIAL_TILES   serial, one amplitude block per tile
+ *   TESS_SCHED_SERIAL_HIST    serial; with a histogram, the amplitude kernel
+ *                             keeps only the sums and a third kernel per
+ *                             chunk fills the histogram from the events'
+ *                             weights (8 more workspace bytes per chunk
+ *                             event), so that the amplitude kernel's code
+ *                             keeps the instruction cache to itself (not
+ *                             with cut-first or TESS_K2_FUSED, and without
+ *                             a histogram: TESS_SCHED_SERIAL) */
 #define TESS_K2_REG 0
 #define TESS_K2_ROWS32 1
 #define TESS_K2_ROWS64 2
@@ -340,6 +348,7 @@ int tess_generate_persistent(tess_ctx *ctx, int n_proc, const tess_process *proc
 #define TESS_SCHED_OVERLAP 1
 #define TESS_SCHED_OVERLAP_TILES 2
 #define TESS_SCHED_SERIAL_TILES 3
+#define TESS_SCHED_SERIAL_HIST 4
 int tess_autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_events, double *acc_scratch,
                   void *workspace, size_t workspace_bytes, void *stream, int *form_out);
 

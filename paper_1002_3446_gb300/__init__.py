@@ -39,6 +39,7 @@ TESS_K2_WAVE2P, TESS_K2_WAVE2PU, TESS_K2_WAVE2L, TESS_K2_REG_HI4, TESS_K2_REG_HI
 TESS_K2_LANES8, TESS_K2_LANES16, TESS_K2_LANES32 = 21, 22, 23
 TESS_K2_FUSED = 24
 TESS_SCHED_SERIAL, TESS_SCHED_OVERLAP, TESS_SCHED_OVERLAP_TILES, TESS_SCHED_SERIAL_TILES = 0, 1, 2, 3
+TESS_SCHED_SERIAL_HIST = 4
 TESS_PEAK_FP32, TESS_PEAK_FP32X2, TESS_PEAK_FP64 = 0, 1, 2
 
 # Every symbol include/tess.h declares (checked by the ABI tests).

@@ -855,10 +855,14 @@ int tess_plan_info(const tess_ctx *ctx, const tess_process *proc, uint64_t n_eve
   tess::PipePlan pl;
   if ((rc = pipeline_plan(ctx, proc, n_events, &pl))) return rc;
   info[0] = pl.form;
-  // the schedule in effect: an overlapped one runs serially on a single chunk
-  info[1] = pl.overlap || pl.sched == tess::SCHED_SERIAL || pl.sched == tess::SCHED_SERIAL_TILES
-                ? pl.sched
-                : (pl.sched == tess::SCHED_OVERLAP ? tess::SCHED_SERIAL : tess::SCHED_SERIAL_TILES);
+  // the schedule in effect: an overlapped one runs serially on a single chunk,
+  // the deferred-histogram one serially where it does not apply
+  if (pl.sched == tess::SCHED_SERIAL_HIST)
+    info[1] = pl.defer_hist ? tess::SCHED_SERIAL_HIST : tess::SCHED_SERIAL;
+  else
+    info[1] = pl.overlap || pl.sched == tess::SCHED_SERIAL || pl.sched == tess::SCHED_SERIAL_TILES
+                  ? pl.sched
+                  : (pl.sched == tess::SCHED_OVERLAP ? tess::SCHED_SERIAL : tess::SCHED_SERIAL_TILES);
   info[2] = pl.chunks;
   info[3] = pl.grid;
   return ok();
@@ -922,6 +926,7 @@ static int autotune(tess_ctx *ctx, const tess_process *proc, uint64_t probe_even
       if (pl.form != f) continue;  // not built for (precision, n)
       const bool wants_overlap = o == tess::SCHED_OVERLAP || o == tess::SCHED_OVERLAP_TILES;
       if (wants_overlap && !pl.overlap) continue;  // a single chunk: nothing to overlap
+      if (o == tess::SCHED_SERIAL_HIST && !pl.defer_hist) continue;  // the serial schedule again
       ctx->form[pi][n] = f;
       ctx->sched[pi][n] = o;
       Prepared pr;

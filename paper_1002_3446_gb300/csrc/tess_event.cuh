@@ -26,7 +26,8 @@ struct EventParams {
   double phiconst;     // Phi_m(s) = phiconst * s^(m-2)
   double efac;         // sampled estimator factor 2^n (n-1)! / 2^(n-2)
   double hist_lo, hist_inv_width;
-  int hist_bins;       // 0: no histogram
+  int hist_bins;       // 0: no histogram; < 0 (amplitude kernel of a deferred
+                       // histogram): -hist_bins bins filled by another kernel
   int hist_obs;
   // double-float kinematics: S split into two floats, and the weight
   // constant wconst (ln x_min)^2 phiconst / 2

@@ -13,8 +13,11 @@ constexpr int kPartialHead = 5;   // sum w, sum w^2, n_pass, n_nonfinite, n_stal
 // Workspace layout: one row of partials per block,
 //   [sum w, sum w^2, n_pass, n_nonfinite, n_stalled, hist w (nb2), hist w^2 (nb2)].
 // n_stalled counts blocks that gave up waiting for a staged input copy.
+// hist_bins < 0: an amplitude kernel whose histogram (-hist_bins bins) a
+// separate kernel fills; its rows keep the histogram's columns.
 __host__ __device__ inline int partial_stride(int hist_bins) {
-  return kPartialHead + (hist_bins > 0 ? 2 * (hist_bins + 2) : 0);
+  const int h = hist_bins < 0 ? -hist_bins : hist_bins;
+  return kPartialHead + (h > 0 ? 2 * (h + 2) : 0);
 }
 
 __device__ __forceinline__ int hist_bin(double v, double lo, double inv_w, int nb) {

@@ -27,6 +27,8 @@ struct PipePlan {
   size_t off_in = 0, off_efac = 0, off_wfac = 0, off_hval = 0, off_pass = 0;
   size_t off_col = 0, off_orig = 0, off_tcount = 0, off_toff = 0, off_dcount = 0;  // cut-first only
   size_t off_tables = 0;  // grid mode only: PDF and alpha_s tables (before the chunk buffers)
+  size_t off_wev = 0;     // deferred histogram only: event weights of the chunk
+  bool defer_hist = false;  // SCHED_SERIAL_HIST with a histogram: filled by its own kernel
   size_t kin_smem = 0;   // K1 dynamic shared memory (FP32 forms: the output tile)
   size_t buf_bytes = 0;  // one chunk buffer
   int sched = 0;         // Schedule
@@ -42,10 +44,22 @@ struct PipePlan {
 //   SCHED_OVERLAP_TILES  as SCHED_OVERLAP with one K2 block per tile, so that
 //                        K1 blocks are scheduled as K2 blocks retire
 //   SCHED_SERIAL_TILES   serial with one K2 block per tile
+//   SCHED_SERIAL_HIST    serial; with a histogram, K2 keeps only the sums
+//                        and leaves each event's weight in the chunk buffer,
+//                        and a third kernel per chunk (hist_chunk_kernel)
+//                        fills the histogram (no cut-first, not the fused
+//                        form; without a histogram it is SCHED_SERIAL)
 // The per-tile grid is bounded so that the blocks' partial-row flushes stay
 // under 1/50 of the chunk's own traffic (large histograms keep the
 // persistent grid).
-enum Schedule { SCHED_SERIAL = 0, SCHED_OVERLAP = 1, SCHED_OVERLAP_TILES = 2, SCHED_SERIAL_TILES = 3, SCHED_N = 4 };
+enum Schedule {
+  SCHED_SERIAL = 0,
+  SCHED_OVERLAP = 1,
+  SCHED_OVERLAP_TILES = 2,
+  SCHED_SERIAL_TILES = 3,
+  SCHED_SERIAL_HIST = 4,
+  SCHED_N = 5
+};
 
 // Streams and events of the overlapped pipeline (owned by the context).
 struct OverlapRes {
@@ -455,8 +469,10 @@ int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, in
   }
   const int per_sm = pl->per_sm;
   const bool cut_first = (caps & CAP_CUT_FIRST) != 0;
-  const uint64_t per_event =
-      (uint64_t)InRows<L>::rows * sizeof(R) + 3 * sizeof(double) + 1 + (cut_first ? 2 * sizeof(int) : 0);
+  if (sched < 0 || sched >= SCHED_N) sched = SCHED_SERIAL;
+  pl->defer_hist = sched == SCHED_SERIAL_HIST && hist_bins > 0 && !cut_first && !fused;
+  const uint64_t per_event = (uint64_t)InRows<L>::rows * sizeof(R) + 3 * sizeof(double) + 1 +
+                             (cut_first ? 2 * sizeof(int) : 0) + (pl->defer_hist ? sizeof(double) : 0);
   const uint64_t chunk_bytes = pl->chunk_target ? pl->chunk_target : kChunkTargetBytes;
   // events per chunk: a multiple of 128 below 2^31 (chunk columns are ints);
   // the fused kernel keeps its events on chip but takes the same chunks (one
@@ -474,7 +490,6 @@ int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, in
   pl->cap = (int)std::min(target, want);
   pl->chunks = (int)((std::max<uint64_t>(n_events, 1) + pl->cap - 1) / pl->cap);
   const uint64_t tiles = ((uint64_t)pl->cap + pl->block - 1) / pl->block;
-  if (sched < 0 || sched >= SCHED_N) sched = SCHED_SERIAL;
   pl->sched = sched;
   pl->overlap = (sched == SCHED_OVERLAP || sched == SCHED_OVERLAP_TILES) && pl->chunks > 1 && !fused;
   uint64_t resident = (uint64_t)sm_count * per_sm;
@@ -504,6 +519,12 @@ int plan_pipeline_t(int sm_count, uint64_t n_events, int hist_bins, int form, in
   off = align256(off + (size_t)pl->cap * sizeof(double));
   pl->off_pass = off;
   off = align256(off + (size_t)pl->cap);
+  if (pl->defer_hist) {
+    const cudaError_t e = allow_max_smem((const void *)hist_chunk_kernel<kBlock>);  // up to 1024 bins: 68 KB
+    if (e != cudaSuccess) return (int)e;
+    pl->off_wev = off;
+    off = align256(off + (size_t)pl->cap * sizeof(double));
+  }
   if (cut_first) {  // compaction: column and source index per event, count per K1 tile, total
     pl->off_col = off;
     off = align256(off + (size_t)pl->cap * sizeof(int));
@@ -551,6 +572,7 @@ cudaError_t run_pipeline_t(const EventParams &P, const PipePlan &pl, char *ws, c
       BB[b].toff = (int *)(base + pl.off_toff);
       BB[b].dcount = (int *)(base + pl.off_dcount);
     }
+    if (pl.defer_hist) BB[b].wev = (double *)(base + pl.off_wev);
   }
   ChunkParams C;
   C.P = PG;
@@ -605,16 +627,25 @@ cudaError_t run_pipeline_t(const EventParams &P, const PipePlan &pl, char *ws, c
     return cudaSuccess;
   }
   const ChunkBuf<R> &B = BB[0];
+  // deferred histogram: the amplitude kernel adds only the sums to rows that
+  // keep the histogram's columns (hist_bins < 0)
+  ChunkParams CK = C;
+  if (pl.defer_hist) CK.P.hist_bins = -P.hist_bins;
   for (uint64_t off = 0; off < P.n_events; off += (uint64_t)pl.cap) {
-    C.chunk_first = off;
-    C.count = (int)std::min<uint64_t>((uint64_t)pl.cap, P.n_events - off);
+    C.chunk_first = CK.chunk_first = off;
+    C.count = CK.count = (int)std::min<uint64_t>((uint64_t)pl.cap, P.n_events - off);
     if (hook) (*hook)(STAGE_KIN, true, s);
     if ((e = launch_kin<N, R>(C, B, pl.kin_smem, s)) != cudaSuccess) return e;
     if (hook) (*hook)(STAGE_KIN, false, s);
-    if (hook) (*hook)(STAGE_AMP, true, s);
+    if (hook) (*hook)(STAGE_AMP, true, s);  // the amplitude stage includes the deferred histogram
     e = with_form<N, R>(pl.form,
-                        [&](auto K) { return decltype(K)::launch(C, B, partials, pl.grid, pl.smem, s, mp[0]); });
+                        [&](auto K) { return decltype(K)::launch(CK, B, partials, pl.grid, pl.smem, s, mp[0]); });
     if (e != cudaSuccess) return e;
+    if (pl.defer_hist) {
+      hist_chunk_kernel<kBlock><<<pl.grid, kBlock, EpiSmem<kBlock>::bytes(P.hist_bins), s>>>(C, B.wev, B.hval, B.pass,
+                                                                                            partials);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     if (hook) (*hook)(STAGE_AMP, false, s);
   }
   return cudaSuccess;

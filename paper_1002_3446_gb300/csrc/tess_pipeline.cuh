@@ -38,6 +38,9 @@ struct ChunkBuf {
   int *tcount = nullptr;  // [cap / kBlock] kept events per kinematics tile
   int *toff = nullptr;    // [cap / kBlock] kept events before the tile
   int *dcount = nullptr;  // [1] kept events of the chunk
+  // deferred histogram only (else null): the amplitude kernel's event
+  // weights, which the histogram kernel bins after it
+  double *wev = nullptr;  // [cap]
 };
 
 struct ChunkParams {
@@ -1090,6 +1093,7 @@ __device__ __forceinline__ void finish_event(const ChunkParams &C, const ChunkBu
                                              Accum<NB> &A, double &w_out, int &bin_out) {
   const int o = C.P.cut_first ? B.orig[e] : e;
   finish_values<NB>(C, o, B.efac[e], B.wfac[e], B.pass[e], B.hval + e, amp2, A, w_out, bin_out);
+  if (B.wev) B.wev[e] = w_out;
 }
 
 // Shared-memory scratch of the epilogue: one histogram per warp (w bins then
@@ -1183,6 +1187,39 @@ __device__ __forceinline__ void epi_flush(const EpiSmem<NB> &S, int nb2, Accum<N
   double *row = partials + (size_t)blockIdx.x * partial_stride(hist_bins);
   if (threadIdx.x < 4) row[threadIdx.x] += red[threadIdx.x][0];
   if (threadIdx.x == 4 && stalled) row[4] += 1.0;
+  for (int i = threadIdx.x; i < 2 * nb2; i += NB) row[kPartialHead + i] += epi_hist_sum(S, nb2, i);
+}
+
+// Deferred histogram (schedule SCHED_SERIAL_HIST): after the amplitude kernel
+// of a chunk, block b bins the events of tiles b, b + gridDim.x, ... (NB
+// events each) from the weights the amplitude kernel left in B.wev and the
+// flags and observables the kinematics kernel left, and adds its histogram to
+// the histogram columns of partial row b (the amplitude kernel, launched with
+// hist_bins < 0, adds only the sums).  The histogram epilogue then runs as
+// its own small kernel instead of inside the amplitude kernel, whose code
+// (the unrolled wavefront forms reach ~100 KB) then keeps the instruction
+// cache to itself.  Fills as epi_tile does: per-warp copies, fixed order.
+template <int NB>
+__global__ void __launch_bounds__(NB) hist_chunk_kernel(ChunkParams C, const double *__restrict__ wev,
+                                                        const double *__restrict__ hval,
+                                                        const uint8_t *__restrict__ pass, double *partials) {
+  extern __shared__ __align__(16) char smem_raw[];
+  const int nb2 = C.P.hist_bins + 2;
+  EpiSmem<NB> S(smem_raw, nb2);
+  epi_init(S, nb2);
+  const int ntiles = (C.count + NB - 1) / NB;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int e = tile * NB + (int)threadIdx.x;
+    double w = 0.0;
+    int bin = -1;
+    if (e < C.count && pass[e]) {
+      w = wev[e];
+      bin = hist_bin(hval[e], C.P.hist_lo, C.P.hist_inv_width, C.P.hist_bins);
+    }
+    epi_tile<NB>(S, nb2, w, bin);
+  }
+  __syncthreads();
+  double *row = partials + (size_t)blockIdx.x * partial_stride(C.P.hist_bins);
   for (int i = threadIdx.x; i < 2 * nb2; i += NB) row[kPartialHead + i] += epi_hist_sum(S, nb2, i);
 }
 
@@ -1428,6 +1465,7 @@ __global__ void __launch_bounds__(NB, MINB)
           const double *hval = (const double *)(st + W::off_hval);
           const uint8_t *pass = (const uint8_t *)(st + W::off_pass);
           finish_values<NB>(C, e, efac[lane], wfac[lane], pass[lane], hval + lane, amp2_of(amp), A, w, bin);
+          if (B.wev) B.wev[e] = w;
         }
       }
     }

@@ -1,7 +1,8 @@
 """Chunk schedules: serial or overlapped (kinematics of chunk c+1 on the
 caller's stream while the amplitude kernel of chunk c runs on the context's
 second stream, two chunk buffers), each with a persistent or a per-tile
-amplitude grid.
+amplitude grid, and serial with the histogram deferred to its own kernel per
+chunk (the amplitude kernel keeping only the sums).
 
 Every schedule runs the same kernels on the same chunks, so every per-event
 output is bit-identical; the accumulated sums differ only in summation order
@@ -48,11 +49,15 @@ CASES = [
     (10, tess.TESS_FP32_DS, tess.TESS_K2_PAIR32, 300_007),
     (9, tess.TESS_FP32_CURRENTS, tess.TESS_K2_ROWS64, 600_003),
     (6, tess.TESS_FP32_CURRENTS, tess.TESS_K2_PAIR64, 600_011),
+    (10, tess.TESS_FP32_DS, tess.TESS_K2_WAVE2U, 300_013),
+    (10, tess.TESS_FP32_DS, tess.TESS_K2_WAVE2, 300_019),
+    (11, tess.TESS_FP32_DS, tess.TESS_K2_WAVE2P, 200_003),
+    (12, tess.TESS_FP32_DS, tess.TESS_K2_LANES8, 200_009),
 ]
 
 
 SCHEDS = (tess.TESS_SCHED_SERIAL, tess.TESS_SCHED_OVERLAP, tess.TESS_SCHED_OVERLAP_TILES,
-          tess.TESS_SCHED_SERIAL_TILES)
+          tess.TESS_SCHED_SERIAL_TILES, tess.TESS_SCHED_SERIAL_HIST)
 
 
 @pytest.mark.parametrize("n,prec,form,N", CASES)
@@ -153,7 +158,7 @@ def test_overlap_stage_timing_and_batched(ctx):
 
 def test_select_variant_rejects_out_of_range(ctx):
     proc = tess.process(6)
-    for form, ov in ((99, 0), (-2, 0), (0, 4), (0, -2)):
+    for form, ov in ((99, 0), (-2, 0), (0, 5), (0, -2)):
         with pytest.raises(tess.TessError) as e:
             tess.tess_select_variant(ctx, proc, form, ov)
         assert e.value.code == tess.TESS_E_INVALID
@@ -203,3 +208,37 @@ def test_chunk_size_changes_no_event_and_resizes_the_workspace(ctx):
             assert e.value.code == tess.TESS_E_INVALID
     finally:
         tess.tess_set_chunk_bytes(ctx, 16 << 20)
+
+
+def test_deferred_histogram_where_it_applies(ctx):
+    """The deferred-histogram schedule against the serial one: with cut-first
+    (compacted events) it runs as serial, as it does without a histogram;
+    with a histogram and random real polarisations it defers, and the bins
+    match a re-binning of the per-event weights."""
+    N = 250_007
+    for flags, mode, hb in ((tess.TESS_FLAG_CUT_FIRST, tess.TESS_HEL_SAMPLE, 20), (0, tess.TESS_HEL_SAMPLE, 0),
+                            (0, tess.TESS_POL_RANDOM, 20)):
+        proc = tess.process(8, precision=tess.TESS_FP32_DS, flags=flags, helicity_mode=mode, hist_bins=hb,
+                            hist_observable=tess.TESS_OBS_RMIN, hist_lo=0.4, hist_hi=3.4)
+        res = {}
+        try:
+            for sc in (tess.TESS_SCHED_SERIAL, tess.TESS_SCHED_SERIAL_HIST):
+                tess.tess_select_variant(ctx, proc, -1, sc)
+                run = tess.Run(ctx, proc, N)
+                run.generate(3, 11)
+                res[sc] = (_host(run), run.result())
+        finally:
+            tess.tess_select_variant(ctx, proc)
+        a, b = res[tess.TESS_SCHED_SERIAL_HIST], res[tess.TESS_SCHED_SERIAL]
+        for key in ("weight", "me2", "pass"):
+            assert np.array_equal(a[0][key], b[0][key]), key
+        assert a[1][2:] == b[1][2:] and np.isclose(a[1][0], b[1][0], rtol=1e-12)
+        if hb:
+            assert np.allclose(a[0]["hist"], b[0]["hist"], rtol=1e-12, atol=1e-14 * np.abs(b[0]["hist"]).sum())
+            ok = a[0]["pass"].astype(bool)
+            v, w = a[0]["rmin"][ok], a[0]["weight"][ok]
+            t = (v - 0.4) * (hb / 3.0)
+            idx = np.where(v < 0.4, 0, np.where(t >= hb, hb + 1, 1 + np.floor(t).astype(int)))
+            expect = np.bincount(idx, weights=w, minlength=hb + 2)
+            hw, _ = tess.tess_histograms(ctx, proc, torch.from_numpy(a[0]["hist"]).cuda())
+            assert np.allclose(hw, expect, rtol=1e-12, atol=1e-12 * w.sum())
