@@ -799,9 +799,9 @@ def plan_cap(tess, ctx, proc, n_events):
     return -(-n_events // max(info["chunks"], 1))
 
 
-PIPELINE_SOURCES = ("tess_async.cuh", "tess_bg.cuh", "tess_event.cuh", "tess_f2.cuh", "tess_kernels.cuh",
-                    "tess_lanes.cuh", "tess_math.cuh", "tess_pair.cuh", "tess_pair_w.cuh", "tess_pipe_launch.cuh",
-                    "tess_pipeline.cuh", "tess_wave.cuh", "tess_wavep.cuh")
+PIPELINE_SOURCES = ("tess_async.cuh", "tess_bg.cuh", "tess_event.cuh", "tess_f2.cuh", "tess_fused.cuh",
+                    "tess_kernels.cuh", "tess_lanes.cuh", "tess_math.cuh", "tess_pair.cuh", "tess_pair_w.cuh",
+                    "tess_pipe_launch.cuh", "tess_pipeline.cuh", "tess_wave.cuh", "tess_wavep.cuh")
 
 
 def kernel_source_hash():
