@@ -386,8 +386,9 @@ __host__ __device__ constexpr size_t wave_lean_smem_per_event() {
 // past the chunk's count are inside the buffer (its capacity is a multiple of
 // 128 columns), so no prefetch leaves it.  Not for cut-first chunks, whose
 // tiles are gathered through a column list.  Used by the packed-pair forms
-// (measured at n = 10 / 12: +4 / +5 %); the scalar wavefront forms measured
-// 2-4 % slower with it (n = 10, 11) and do without.
+// (measured at n = 10 / 12: +4 / +5 %) and the unrolled scalar form (+6 % at
+// n = 10 with the histogram deferred); the rolled scalar forms measured 2-4 %
+// slower with it (n = 10, 11) and do without.
 template <int L, int NE, int NT>
 __device__ __forceinline__ void wave_prefetch_next(const ChunkParams &C, const ChunkBuf<float> &B, int tile,
                                                    int ntiles) {
@@ -445,6 +446,7 @@ __global__ void __launch_bounds__(NE * G, MINB) bg_wave_kernel(ChunkParams C, Ch
       }
     }
     if (G > 1) __syncwarp();
+    if constexpr (UNR) wave_prefetch_next<L, NE, NT>(C, B, tile, ntiles);
     Cx<float> amp;
     if constexpr (LEAN)
       amp = bg_wave_lean<L, NE, G>(K4, J4, S2, S0, slot, g, B.in + (size_t)InRows<L>::eps(0) * cap + e,
