@@ -31,8 +31,26 @@
 namespace tess {
 
 // Per-event shared-memory column: J of the sets [a..b], 1 <= a <= b <= L-1
-// (two float4 each, index t1<L>), the leg momenta (float4), the split sums S
-// (float2).  Event slot e of NE, element (plane p, slot e) at p * NE + e.
+// (two float4 each, index wix<L, UNR>), the leg momenta (float4), the split
+// sums S (float2).  Event slot e of NE, element (plane p, slot e) at
+// p * NE + e.
+//
+// Index of the set [s..s+len-1] (1 <= s, s + len - 1 <= L-1) in the
+// length-major layout: the sets of length 1, then of length 2, ...  A set of
+// row a with a given length sits at a + (a constant of the length), so in
+// the unrolled step code, where every length is known at compile time,
+// every table address is one register per row plus an immediate offset
+// (measured at n = 10: 2.7 % faster than the row-major t1 layout).  The
+// rolled step code, whose lengths are runtime values, keeps the row-major
+// layout (7 % slower with this one).
+template <int L>
+__host__ __device__ constexpr int dsx(int s, int len) {
+  return (len - 1) * L - ((len - 1) * len) / 2 + (s - 1);
+}
+template <int L, bool LENGTH_MAJOR>
+__host__ __device__ constexpr int wix(int s, int len) {
+  return LENGTH_MAJOR ? dsx<L>(s, len) : t1<L>(s, s + len - 1);
+}
 template <int L>
 __host__ __device__ constexpr size_t wave_smem_per_event() {
   return (size_t)(L * (L - 1) / 2) * (2 * sizeof(float4) + sizeof(float2)) + (size_t)L * sizeof(float4);
@@ -125,7 +143,7 @@ __device__ __forceinline__ Cx<float> bg_wave(const float4 *K4, float4 *J4, float
       if (a == 0) {
         load_eps(in_eps0, cap, row[0]);
       } else {
-        row[0] = wld_cv<NE>(J4, t1<L>(a, a), e);
+        row[0] = wld_cv<NE>(J4, wix<L, UNR>(a, 1), e);
       }
       kcur = wld_k<NE>(K4, a, e);
     } else {
@@ -145,7 +163,7 @@ __device__ __forceinline__ Cx<float> bg_wave(const float4 *K4, float4 *J4, float
           if (dp < d) {  // split: left [a..a+dp] (row register dp), right [a+dp+1..b]
             const int r0 = a + dp + 1;
             kr = radd(kr, wld_k<NE>(K4, r0, e));
-            const int tr = t1<L>(r0, b);
+            const int tr = wix<L, UNR>(r0, d - dp);  // [r0..b]
             const CV4<float> Jr = wld_cv<NE>(J4, tr, e);
             const CV4<float> &Jl = row[dp];
             // the left part [a..a] (dp = 0) is a single leg: its polarisation
@@ -180,7 +198,7 @@ __device__ __forceinline__ Cx<float> bg_wave(const float4 *K4, float4 *J4, float
             // [a..a+dpp] a single leg for dpp = 0, middle part one for dpp = dp - 1)
 #pragma unroll
             for (int dpp = 0; dpp < dp; ++dpp) {
-              const CV4<float> JB = wld_cv<NE>(J4, t1<L>(a + dpp + 1, a + dp), e);
+              const CV4<float> JB = wld_cv<NE>(J4, wix<L, UNR>(a + dpp + 1, dp - dpp), e);  // [a+dpp+1..a+dp]
               const Cx<float> x = leaf_sel(dpp == 0, rl, [&](auto la, auto lb) {
                 return mdot_l<decltype(la)::value, decltype(lb)::value>(row[dpp], Jr);
               });
@@ -210,8 +228,9 @@ __device__ __forceinline__ Cx<float> bg_wave(const float4 *K4, float4 *J4, float
           }
           wave_keep<L>(d, cur, s, kcur, row, srow, krow);
           if (a > 0) {
-            wst_cv<NE>(J4, t1<L>(a, b), e, cur);
-            S2[t1<L>(a, b) * NE + e] = make_float2(s.re, s.im);
+            const int t = wix<L, UNR>(a, d + 1);  // [a..b]
+            wst_cv<NE>(J4, t, e, cur);
+            S2[t * NE + e] = make_float2(s.re, s.im);
           }
         }
       }
@@ -345,8 +364,9 @@ __device__ __forceinline__ Cx<float> bg_wave_lean(const float4 *K4, float4 *J4, 
               break;
           }
           if (a > 0) {
-            wst_cv<NE>(J4, t1<L>(a, b), e, cur);
-            S2[t1<L>(a, b) * NE + e] = make_float2(s.re, s.im);
+            const int t = t1<L>(a, b);
+            wst_cv<NE>(J4, t, e, cur);
+            S2[t * NE + e] = make_float2(s.re, s.im);
           } else {
             S0[d * NE + e] = make_float2(s.re, s.im);
           }
@@ -442,7 +462,7 @@ __global__ void __launch_bounds__(NE * G, MINB) bg_wave_kernel(ChunkParams C, Ch
       if (a > 0) {
         CV4<float> ea;
         load_eps(B.in + (size_t)InRows<L>::eps(a) * cap + e, cap, ea);
-        wst_cv<NE>(J4, t1<L>(a, a), slot, ea);
+        wst_cv<NE>(J4, wix<L, UNR && !LEAN>(a, 1), slot, ea);
       }
     }
     if (G > 1) __syncwarp();

@@ -21,13 +21,6 @@
 
 namespace tess {
 
-// Index of the set [s..s+len-1] (1 <= s, s + len - 1 <= L-1) in the
-// length-major layout: the sets of length 1, then of length 2, ...
-template <int L>
-__host__ __device__ constexpr int dsx(int s, int len) {
-  return (len - 1) * L - ((len - 1) * len) / 2 + (s - 1);
-}
-
 // Current of set index t: raised real parts (x0..x3) in plane 2t, imaginary
 // parts in plane 2t + 1 (event slot e of NE).
 template <int NE>
