@@ -82,6 +82,47 @@ def test_batched_equals_separate_calls_and_replays(ctx):
         assert np.array_equal(_host(a)["weight"], _host(b)["weight"])
 
 
+def test_batched_with_fused_form_and_deferred_histogram(ctx):
+    """The graph chain with the warp-specialised one-kernel form (n = 6) and the
+    deferred-histogram schedule (n = 10 with a histogram, n = 4 FP64 with one)
+    selected: bit-identical to separate calls with the same selections, and a
+    replay accumulates the same sums again."""
+    procs = [tess.process(6, precision=tess.TESS_FP32_DS),
+             tess.process(10, precision=tess.TESS_FP32_DS, pt_min=30.0, hist_bins=40,
+                          hist_observable=tess.TESS_OBS_HT, hist_lo=200.0, hist_hi=2200.0),
+             tess.process(4, precision=tess.TESS_FP64, hist_bins=12, hist_observable=tess.TESS_OBS_PTLEAD)]
+    sel = [(tess.TESS_K2_FUSED, tess.TESS_SCHED_SERIAL), (tess.TESS_K2_WAVE2U, tess.TESS_SCHED_SERIAL_HIST),
+           (-1, tess.TESS_SCHED_SERIAL_HIST)]
+    counts = [200_003, 50_001, 30_007]
+    seeds, firsts = [21, 22, 23], [0, 1 << 20, 77]
+    try:
+        for p, (f, sc) in zip(procs, sel):
+            tess.tess_select_variant(ctx, p, f, sc)
+            info = tess.tess_plan_info(ctx, p, 1000)
+            assert (f < 0 or info["variant"] == f) and info["schedule"] == sc
+        sep = _runs(ctx, procs, counts)
+        for r, sd, f in zip(sep, seeds, firsts):
+            r.generate(sd, f)
+        bat = _runs(ctx, procs, counts)
+        ws_bytes = tess.tess_workspace_size_batched(ctx, procs, counts)
+        ws = torch.empty((ws_bytes + 7) // 8, dtype=torch.float64, device="cuda")
+        outs = [r.outputs for r in bat]
+        tess.tess_generate_batched(ctx, procs, seeds, firsts, counts, outs, ws)
+        for a, b in zip(bat, sep):
+            ha, hb = _host(a), _host(b)
+            for key in ("weight", "me2", "pass", "ht", "ptlead", "rmin", "acc"):
+                assert np.array_equal(ha[key], hb[key]), key
+            if ha["hist"] is not None:
+                assert np.array_equal(ha["hist"], hb["hist"])
+        tess.tess_generate_batched(ctx, procs, seeds, firsts, counts, outs, ws)
+        for a, b, n in zip(bat, sep, counts):
+            sa, sb = a.result(), b.result()
+            assert sa[3] == 2 * n and np.isclose(sa[0], sb[0], rtol=1e-12)
+    finally:
+        for p in procs:
+            tess.tess_select_variant(ctx, p)
+
+
 def test_batched_rejects_small_workspace(ctx):
     procs = _procs()[:2]
     counts = [1000, 1000]
