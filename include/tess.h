@@ -342,8 +342,9 @@ int tess_generate_persistent(tess_ctx *ctx, int n_proc, const tess_process *proc
 #define TESS_K2_LANES32 23   /* the same with a whole warp per event (FP32, n >= 6) */
 #define TESS_K2_FUSED 24     /* no separate kinematics kernel: one warp-specialised kernel per chunk, a
                                 kinematics warpgroup handing tiles of 128 events to a register-form
-                                amplitude warpgroup through shared memory; no chunk buffer in the
-                                workspace (TESS_FP32_DS with TESS_HEL_SAMPLE, no cut-first, n = 4..6) */
+                                amplitude warpgroup through shared memory; the events never leave the
+                                chip (its plan needs no chunk buffer; tess_workspace_size still covers
+                                every form) (TESS_FP32_DS with TESS_HEL_SAMPLE, no cut-first, n = 4..6) */
 #define TESS_SCHED_SERIAL 0
 #define TESS_SCHED_OVERLAP 1
 #define TESS_SCHED_OVERLAP_TILES 2
