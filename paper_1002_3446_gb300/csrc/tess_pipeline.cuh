@@ -766,7 +766,7 @@ __device__ __forceinline__ void kin_ds_back(const ChunkParams &C, const ChunkBuf
   B.efac[ec] = scale_pow2(P.efac, -2 * ex * (N - 4));
   B.wfac[ec] = wf;
   B.pass[ec] = (uint8_t)pass;
-  if (B.hval) B.hval[ec] = (double)(P.hist_obs == 0 ? lead : (P.hist_obs == 1 ? sum : rmin));
+  if (B.hval && P.hist_bins > 0) B.hval[ec] = (double)(P.hist_obs == 0 ? lead : (P.hist_obs == 1 ? sum : rmin));
 
   float lk[N][4], le1[N][3], le2[N][2];
   const float hs = 0.5f * rs_hi * sc;
