@@ -161,6 +161,9 @@ def test_cost_model_matches_a_replay_of_the_operations():
     assert tess.flops_per_event(6, tess.TESS_K2_REG_HI) == tess.bg_flops_leaf(6) == 3432
     assert tess.flops_per_event(10, tess.TESS_K2_WAVE2) == tess.bg_flops_wave(10) == 29330
     assert tess.flops_per_event(10, tess.TESS_K2_WAVE2P) == tess.bg_flops(10) == 32426
+    assert tess.flops_per_event(10, tess.TESS_K2_WAVE2U) == tess.bg_flops_wave_unrolled(10) == 27602
+    # the one-kernel form runs the register form's amplitude code
+    assert tess.flops_per_event(6, tess.TESS_K2_FUSED) == tess.bg_flops_leaf(6)
     assert tess.flops_per_event(6, tess.TESS_K2_REAL, random_pol=True) == tess.bg_flops_real_leaf(6)
     # exact-sum mode: register form for FP64 up to n = 5, FP32 up to n = 7
     assert tess.flops_per_event(4, -1, precision=tess.TESS_FP64) == tess.bg_flops_leaf(4)
